@@ -1,0 +1,342 @@
+"""Benchmark of the superquadric renderer's training step on GB300.
+
+One step = one pass of the whole hot path over one synthetic six-camera frame
+(4096 superquadrics, 6 x 225 x 400 rays, 100 samples per ray, 200x200x16 grid):
+index build (ranges, count, scan, scatter, sort) -> forward render -> loss
+gradient (CE + MSE of Supp. A.5) -> backward render.  Metric: ray-samples per
+second through forward + backward (R * L / step time); ms_per_step is the
+"ms per 6-camera frame".
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+For N > 1 run under torchrun; every rank renders its own frame (seed 1 + rank),
+no collective on the data path, and the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2511_17361_gb300 import synth  # noqa: E402
+
+WORKLOAD = 1
+MUFU_PER_PAIR = {"fwd": 9, "bwd": 22}  # SFU ops per (sample, primitive) pair in each kernel
+LAUNCHES_PER_STEP = 14                  # index 9, forward 2, loss 1, backward 2
+# DRAM traffic per launch from the committed ncu summaries, valid only while the
+# kernel source is unchanged (sha256 of the file holding it).
+NCU_TRAFFIC = {}
+
+
+def _sha(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ----------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------- reference arm (FP64 oracle)
+def _oracle_sample(cfg, n_rays, seed=0):
+    R = synth.n_rays(cfg["rig"])
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(R, size=min(n_rays, R), replace=False))
+
+
+def oracle_step_time(cfg, index_np, ray_ids, targets):
+    """One oracle fwd + loss-gradient + bwd pass over ray_ids (seconds, threads used)."""
+    import oracle
+    t0 = time.perf_counter()
+    D, S, _, _ = oracle.render_fwd(cfg["prims"], cfg["grid"], index_np, cfg["rig"], cfg["t"], ray_ids=ray_ids)
+    td, tl = targets
+    R = len(ray_ids)
+    e = np.exp(S - S.max(1, keepdims=True))
+    gs = 2.0 / R * (e / e.sum(1, keepdims=True) - np.eye(S.shape[1])[tl[ray_ids]])
+    gd = 0.05 / R * 2 * (D - td[ray_ids])
+    oracle.render_bwd(cfg["prims"], cfg["grid"], index_np, cfg["rig"], cfg["t"], gd, gs, ray_ids=ray_ids)
+    return time.perf_counter() - t0, oracle.max_threads()
+
+
+def cpu_baseline(cfg, index_np, targets, budget_s=12.0):
+    """The FP64 oracle on a bounded random ray sample of the same frame."""
+    probe = _oracle_sample(cfg, 600, seed=1)
+    t_probe, threads = oracle_step_time(cfg, index_np, probe, targets)
+    n = int(min(synth.n_rays(cfg["rig"]), max(600, 600 * budget_s / max(t_probe, 1e-3))))
+    ids = _oracle_sample(cfg, n, seed=2)
+    t, threads = oracle_step_time(cfg, index_np, ids, targets)
+    L = len(cfg["t"])
+    return {"value": n * L / t, "unit": "ray-samples/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} random rays of the {cfg['name']} frame (index built by the oracle), "
+                      f"forward + loss gradient + backward, FP64, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cfg = synth.make_config(WORKLOAD, seed=1)
+    idx = oracle.build_index(cfg["prims"], cfg["grid"])
+    targets = synth.loss_targets(synth.n_rays(cfg["rig"]), 1)
+    # each step: a bounded sample sized so that warmup + steps finish in minutes
+    probe = _oracle_sample(cfg, 300, seed=1)
+    t_probe, threads = oracle_step_time(cfg, idx, probe, targets)
+    per_step_budget = max(1.0, 120.0 / max(1, args.steps + args.warmup))
+    n = int(max(100, min(synth.n_rays(cfg["rig"]), 300 * per_step_budget / max(t_probe, 1e-3))))
+    times = []
+    for s in range(args.warmup + args.steps):
+        ids = _oracle_sample(cfg, n, seed=100 + s)
+        t, threads = oracle_step_time(cfg, idx, ids, targets)
+        if s >= args.warmup:
+            times.append(t)
+    L = len(cfg["t"])
+    tot = sum(times)
+    value = n * L * len(times) / tot
+    line = {"metric": "ray-samples/s (forward + backward), six-camera frame", "value": value,
+            "unit": "ray-samples/s", "impl": "reference", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "rays_per_step": n, "samples_per_ray": L, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "ray-samples/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{n} random rays of the frame per step, FP64 forward + backward"},
+            "e2e": {"value": value, "unit": "ray-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------- GPU arm
+def run_mine(args):
+    import torch
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2511_17361_gb300 import _build
+    _build.build()
+    from paper_2511_17361_gb300 import sqr
+
+    dev = torch.device("cuda", local)
+    cfg = synth.make_config(WORKLOAD, seed=1 + rank)
+    grid = {"n": cfg["grid"]["n"], "lo": [float(v) for v in cfg["grid"]["lo"]],
+            "vs": [float(v) for v in cfg["grid"]["vs"]]}
+    prims = sqr.to_device(cfg["prims"], dev)
+    rays = sqr.Rays.from_rig(cfg["rig"], cfg["t"], device=dev)
+    R, L, C = rays.R, len(cfg["t"]), cfg["prims"]["logits"].shape[1]
+    td_np, tl_np = synth.loss_targets(R, 1 + rank)
+    td = torch.from_numpy(td_np).to(dev)
+    tl = torch.from_numpy(tl_np).to(dev)
+
+    ix = sqr.build_index(prims, grid)  # sizes V_sq (host sync once, before timing)
+    P = ix.P()
+    Q, in_grid = sqr.count_pairs(ix, grid, rays)
+    depth = torch.empty(R, device=dev)
+    sem = torch.empty((R, C), device=dev)
+    tf = torch.empty(R, device=dev)
+    loss_out = (torch.empty(1, device=dev), torch.empty(R, device=dev), torch.empty((R, C), device=dev))
+    grads = {k: torch.empty_like(prims[k]) for k in sqr.PRIM_KEYS}
+
+    def step(ev=None):
+        if ev: ev[0].record()
+        sqr.build_index(prims, grid, index=ix, sync=False)
+        if ev: ev[1].record()
+        sqr.render_fwd(prims, ix, grid, rays, out=(depth, sem, tf))
+        if ev: ev[2].record()
+        _, gd, gs = sqr.loss_ce_mse(depth, sem, td, tl, out=loss_out)
+        if ev: ev[3].record()
+        sqr.render_bwd(prims, ix, grid, rays, gd, gs, out=grads)
+        if ev: ev[4].record()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ix.check()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        step(evs[s])
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    phase = np.array([[evs[s][i].elapsed_time(evs[s][i + 1]) for i in range(4)] for s in range(args.steps)])
+    step_ms = phase.sum(1)
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    value = world * R * L * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the public API: pinned host inputs in, gradients + loss out
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(cfg["prims"][k])).pin_memory() for k in sqr.PRIM_KEYS}
+    host_in["td"], host_in["tl"] = torch.from_numpy(td_np).pin_memory(), torch.from_numpy(tl_np).pin_memory()
+    host_in["K"] = torch.from_numpy(np.ascontiguousarray(cfg["rig"]["K"])).pin_memory()
+    host_in["c2w"] = torch.from_numpy(np.ascontiguousarray(cfg["rig"]["cam2world"])).pin_memory()
+    host_in["t"] = torch.from_numpy(np.ascontiguousarray(cfg["t"])).pin_memory()
+    host_out = {k: torch.empty_like(host_in[k]).pin_memory() for k in sqr.PRIM_KEYS}
+    host_loss = torch.empty(1).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + 4
+
+    def e2e_step():
+        for k in sqr.PRIM_KEYS:
+            prims[k].copy_(host_in[k], non_blocking=True)
+        td.copy_(host_in["td"], non_blocking=True)
+        tl.copy_(host_in["tl"], non_blocking=True)
+        rays.K.copy_(host_in["K"], non_blocking=True)
+        rays.cam2world.copy_(host_in["c2w"], non_blocking=True)
+        rays.t.copy_(host_in["t"], non_blocking=True)
+        step()
+        for k in sqr.PRIM_KEYS:
+            host_out[k].copy_(grads[k], non_blocking=True)
+        host_loss.copy_(loss_out[0], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        e0.record()
+        e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * R * L * args.steps / (e2e_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (SFU-bound: MUFU ops per pair)
+    mean_phase = phase.mean(0)
+    names = ["index", "fwd", "loss", "bwd"]
+    dom = int(np.argmax(mean_phase))
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    peak_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sm_count * 16 * peak_mhz * 1e6 / 1e9  # G MUFU ops / s
+    roof = None
+    if names[dom] in MUFU_PER_PAIR:
+        achieved = Q * MUFU_PER_PAIR[names[dom]] / (mean_phase[dom] / 1e3) / 1e9
+        src = os.path.join(ROOT, "paper_2511_17361_gb300", "csrc", "sqr_render.cu")
+        kname = "k_" + ("forward" if names[dom] == "fwd" else "backward")
+        tr = NCU_TRAFFIC.get(kname)
+        traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _sha(src) else None
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GMUFUop/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{sm_count} SMs x 16 SFU ops/clk x {peak_mhz:.0f} MHz (max SM clock seen)"}
+    # algorithmic HBM bytes of the backward: cotangents in, parameters + index lists read, gradients out
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bwd_bytes = R * (1 + C) * 4 + prims["means"].shape[0] * (13 + C) * 4 * 2 + in_grid * 8 + Q * 4
+    hbm = {"bwd_algorithmic_GBps": bwd_bytes / (mean_phase[3] / 1e3) / 1e9,
+           "frac_of_measured_peak": bwd_bytes / (mean_phase[3] / 1e3) / 1e9 / hbm_peak, "peak_gbs": hbm_peak}
+
+    line = {"metric": "ray-samples/s (forward + backward), six-camera frame", "value": value,
+            "unit": "ray-samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg["name"], "rays": R, "samples_per_ray": L, "superquadrics": int(
+                prims["means"].shape[0]), "grid": list(grid["n"]), "index_entries_P": P, "pairs_Q": Q,
+                "in_grid_samples": in_grid, "l2": "flushed (256 MB write) between timed steps",
+                "parallelism": f"replicas x{world} (one frame per GPU)"},
+            "phases_ms": {n: float(v) for n, v in zip(names, mean_phase)},
+            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "e2e": {"value": e2e_value, "unit": "ray-samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": roof, "hbm": hbm, "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        idx_np = {"v_n": ix.v_n.cpu().numpy(), "v_f": ix.v_f.cpu().numpy(), "v_sq": ix.v_sq[:P].cpu().numpy()}
+        line["cpu_baseline"] = cpu_baseline(cfg, idx_np, (td_np, tl_np), budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

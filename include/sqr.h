@@ -1,0 +1,197 @@
+/*
+ * sqr.h -- C ABI of the GB300 superquadric volume renderer (SuperQuadricOcc-Render).
+ *
+ * The renderer of the SuperQuadricOcc paper (Sec. 3.3): a scene of N
+ * superquadrics S_i = {m_i, s_i, r_i, eps_i, sigma_i, c_i} (Sec. 3.1) is
+ * rendered by marching L samples along every pixel ray; each sample only
+ * queries the superquadrics listed in its voxel (Sec. 3.3.1), sums their
+ * occupancy p_o = exp(-f(x_S)) (Eq. 1-2) into an alpha and a semantic vector
+ * (Eq. 4), and is alpha-composited front to back into a depth and a semantic
+ * map (Eq. 5-6).  The backward pass (Sec. 3.3.3) returns the gradient of a
+ * loss with respect to every superquadric parameter.  The voxelisation query
+ * (Supp. A.4) evaluates density and semantics at voxel centres.
+ *
+ * Conventions for every entry point:
+ *  - All array pointers are DEVICE pointers to contiguous, row-major FP32 (or
+ *    int32 / int64 where stated) memory owned by the caller.  The library
+ *    never allocates device memory; scratch comes from the caller's workspace
+ *    (size from sq_workspace_size, 256-byte aligned pointer).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous on that stream and never synchronise the host.
+ *  - Argument errors are detected on the host before any launch and return
+ *    SQ_ERR_INVALID_ARG; launch failures return SQ_ERR_CUDA.  Data-dependent
+ *    errors (index capacity overflow) are written to the device status word
+ *    sq_index_t.status, read by the caller after the stream completes.
+ *  - Quaternions are (w, x, y, z), a Hamilton local-to-world rotation; the
+ *    canonical-frame point is x_S = R(q/|q|)^T (x - m) (Eq. 2).
+ *  - Cameras are OpenCV pinholes: K[cam] = (fx, fy, cx, cy); cam2world[cam] is
+ *    3x4 row-major [R | centre].  Ray r = (cam*H + v)*W + u goes through the
+ *    centre of pixel (u, v).  Sample j sits at x = o + t[j] d.
+ *  - The voxel of a point is floor((x - lo) * (1/vs)) per axis (FP32, fixed
+ *    op order); voxel id = (ix*ny + iy)*nz + iz.  Samples outside the grid
+ *    contribute alpha = 0 and s = 0 (they are skipped, Sec. 3.3.2).
+ */
+#ifndef SQR_H
+#define SQR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SQ_OK = 0,
+    SQ_ERR_INVALID_ARG = 1, /* bad size, null pointer, out-of-domain option */
+    SQ_ERR_CAPACITY = 2,    /* index entries exceed sq_index_t.capacity (device status only) */
+    SQ_ERR_CUDA = 3,        /* a CUDA launch or runtime call failed */
+    SQ_ERR_TIMEOUT = 4,     /* reserved: a bounded device wait gave up */
+    SQ_ERR_NUMERIC = 5      /* reserved: non-finite parameters detected */
+} sq_status_t;
+
+enum { SQ_INDEX_OBB = 0, SQ_INDEX_CUBE = 1 };
+enum { SQ_OP_INDEX = 0, SQ_OP_FWD = 1, SQ_OP_BWD = 2, SQ_OP_QUERY = 3 };
+
+/* Limits of this build. */
+#define SQ_MAX_CLASSES 32 /* n_classes in [1, 32] */
+#define SQ_MAX_SAMPLES 1024 /* L in [1, 1024] */
+
+/* Axis-aligned voxel grid: cells [lo + i*vs, lo + (i+1)*vs), n* >= 1, vs > 0,
+ * nx*ny*nz < 2^31.  The paper's grid is [-40,40]^2 x [-1,5.4] m at 0.4 m
+ * (Sec. 4.1): 200 x 200 x 16. */
+typedef struct {
+    int nx, ny, nz;
+    float lo[3];
+    float vs[3];
+} sq_grid_t;
+
+/* Superquadric set S (Sec. 3.1).  Device FP32 arrays:
+ *   means [n,3], quats [n,4] (any non-zero length), scales [n,3] (> 0),
+ *   eps [n,2] = (eps1, eps2) in (0, 2] (the paper constrains [0.1, 2.0], Supp. A.9),
+ *   opacity [n] (sigma), logits [n, n_classes] (c). */
+typedef struct {
+    const float* means;
+    const float* quats;
+    const float* scales;
+    const float* eps;
+    const float* opacity;
+    const float* logits;
+    int n;         /* >= 0 */
+    int n_classes; /* 1 .. SQ_MAX_CLASSES */
+} sq_prims_t;
+
+/* How a primitive's voxel neighbourhood is chosen (Sec. 3.3.1).
+ *  SQ_INDEX_OBB:  the world AABB of the oriented box that holds the level set
+ *                 p_o >= tau_cut (local half-extents s_i * ln(1/tau_cut)^(eps1/2)),
+ *                 mapped to an inclusive voxel range.  tau_cut in (0, 1).
+ *  SQ_INDEX_CUBE: the voxel holding the centre +- nv voxels per axis (the
+ *                 paper's cubic neighbourhood N_v = 5, Sec. 4.2).  nv >= 0. */
+typedef struct {
+    int mode;
+    float tau_cut;
+    int nv;
+} sq_index_opts_t;
+
+/* The voxel -> superquadric index (V_n, V_f, V_sq of Sec. 3.3.1), caller-owned
+ * device buffers:
+ *   v_n    [nvox] int32  number of primitives listed for each voxel
+ *   v_f    [nvox] int32  offset of each voxel's list in v_sq (exclusive prefix sum of v_n)
+ *   v_sq   [capacity] int32  primitive ids, each voxel's list ascending, no duplicates
+ *   ranges [n,6] int32  per primitive (i0,i1,j0,j1,k0,k1) inclusive; empty = (0,-1,0,-1,0,-1)
+ *   p_total  device int64 scalar: total entries P (written even on overflow)
+ *   status   device int32 scalar: SQ_OK or SQ_ERR_CAPACITY after sq_build_index;
+ *            render and query kernels do no work while it is non-zero.
+ * P must stay below 2^31. */
+typedef struct {
+    int* v_n;
+    int* v_f;
+    int* v_sq;
+    int* ranges;
+    long long capacity;
+    long long* p_total;
+    int* status;
+} sq_index_t;
+
+/* Rays and samples (Sec. 3.3.1): n_cam cameras of H x W pixels, L sample depths
+ * t[L] (device FP32, the caller's spacing; the paper samples uniformly in
+ * [t_near, t_far]), kappa = early-termination threshold on T (0 = none, the
+ * paper's default, Sec. 4.2), alpha_max = upper bound of alpha (1 in the paper,
+ * Sec. 3.3.2). */
+typedef struct {
+    int n_cam, H, W;
+    const float* K;         /* [n_cam, 4] device */
+    const float* cam2world; /* [n_cam, 3, 4] device */
+    const float* t;         /* [L] device */
+    int L;
+    float kappa;
+    float alpha_max;
+} sq_rays_t;
+
+/* Bytes of workspace an entry point needs (op = SQ_OP_*); rays may be NULL for
+ * SQ_OP_INDEX and SQ_OP_QUERY.  Returns 0 on invalid arguments. */
+size_t sq_workspace_size(int op, const sq_prims_t* prims, const sq_grid_t* grid, const sq_rays_t* rays);
+
+/* Sec. 3.3.1 "Preliminary Construction": per-primitive voxel ranges, V_n by a
+ * count pass, V_f by an exclusive scan, V_sq by a scatter and a per-voxel sort
+ * by id.  Writes ranges, v_n, v_f, p_total, status and (when P <= capacity)
+ * v_sq.  On P > capacity, status = SQ_ERR_CAPACITY, v_sq is left partial and
+ * p_total holds the needed capacity. */
+sq_status_t sq_build_index(const sq_prims_t* prims, const sq_grid_t* grid, const sq_index_opts_t* opts,
+                           sq_index_t* index, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Sec. 3.3.2 forward pass (Eq. 2, 4-6).  Per ray r:
+ *   depth[r]   = sum_j w_j t_j,                  w_j = T_j alpha_j, T_j = prod_{l<j} (1 - alpha_l)
+ *   sem[r, :]  = sum_j w_j s_j,                  alpha_j = min(sum_k p_o sigma_k, alpha_max),
+ *                                                 s_j = sum_k p_o c_k over k in Q(voxel of sample j)
+ *   t_final[r] = transmittance after the last composited sample (nullable).
+ * With kappa > 0 a ray stops after the first sample whose following T < kappa.
+ * Outputs: depth [R], sem [R, n_classes], t_final [R]; R = n_cam*H*W. */
+sq_status_t sq_render_fwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
+                          const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* Sec. 3.3.3 backward pass: given dL/d depth [R] and dL/d sem [R, n_classes],
+ * overwrites g_means [n,3], g_quats [n,4] (w.r.t. the raw, unnormalised
+ * quaternion), g_scales [n,3], g_eps [n,2], g_opacity [n], g_logits [n, C]
+ * with dL/d(parameter).  The forward quantities are recomputed (the sample
+ * alphas replayed front to back, then swept back to front), so no forward
+ * state is needed.  The index is treated as constant.  Where the alpha clamp
+ * is active (sum > alpha_max) no gradient flows through that sample's alpha. */
+sq_status_t sq_render_bwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
+                          const sq_rays_t* rays, const float* grad_depth, const float* grad_sem, float* g_means,
+                          float* g_quats, float* g_scales, float* g_eps, float* g_opacity, float* g_logits,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/* Supp. A.4 voxelisation at every voxel centre p = lo + (i + 0.5) vs (FP32):
+ *   density[v] = sum_{k in Q(v)} p_o(p, S_k) sigma_k, sem[v, :] = sum p_o c_k,
+ *   label[v] = argmax_c sem[v, c] (lowest c on ties) if density >= tau, else
+ *   n_classes ("free").  label is nullable (uint8, so n_classes <= 255). */
+sq_status_t sq_query_grid(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid, float tau,
+                          float* density, float* sem, unsigned char* label, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/* Training loss of Supp. A.5 (Eq. 8) and its gradient w.r.t. the rendered maps:
+ *   L = lambda_s * mean_r CE(softmax(sem[r]), label[r]) + lambda_d * mean_r (depth[r] - target[r])^2.
+ * Writes loss (device scalar, overwritten), grad_depth [R], grad_sem [R, C].
+ * labels are int32 in [0, C). */
+sq_status_t sq_loss_ce_mse(const float* depth, const float* sem, const float* target_depth, const int* target_label,
+                           long long n_rays, int n_classes, float lambda_s, float lambda_d, float* loss,
+                           float* grad_depth, float* grad_sem, void* stream);
+
+/* Work counter for throughput and roofline reports: out[0] = Q, the number of
+ * (sample, primitive) pairs the forward pass evaluates (sum over in-grid
+ * samples of V_n of the sample's voxel, all L samples, no early termination),
+ * out[1] = number of in-grid samples.  out: device int64[2], overwritten. */
+sq_status_t sq_count_pairs(const sq_index_t* index, const sq_grid_t* grid, const sq_rays_t* rays, long long* out,
+                           void* stream);
+
+const char* sq_status_string(sq_status_t status);
+
+/* Human-readable text of the last SQ_ERR_* raised on the calling host thread. */
+const char* sq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQR_H */

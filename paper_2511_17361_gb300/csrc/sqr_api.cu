@@ -1,0 +1,288 @@
+// sqr_api.cu -- the extern "C" entry points declared in include/sqr.h: host-side
+// argument validation, workspace sizing, status strings, and the training-loss
+// kernel (Supp. A.5, Eq. 8) used to drive the backward pass.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "sqr_common.cuh"
+
+namespace sqr {
+
+static thread_local char g_last_error[512] = "";
+
+void set_last_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+}
+
+sq_status_t cuda_status(cudaError_t e, const char* where) {
+    set_last_error("%s: %s", where, cudaGetErrorString(e));
+    return SQ_ERR_CUDA;
+}
+
+GridC make_grid(const sq_grid_t* g) {
+    GridC c;
+    c.n[0] = g->nx; c.n[1] = g->ny; c.n[2] = g->nz;
+    for (int i = 0; i < 3; ++i) {
+        c.lo[i] = g->lo[i];
+        c.vs[i] = g->vs[i];
+        c.inv_vs[i] = 1.0f / g->vs[i];
+        c.nf[i] = (float)c.n[i];
+    }
+    return c;
+}
+
+sq_status_t check_prims(const sq_prims_t* p) {
+    if (!p) { set_last_error("prims is NULL"); return SQ_ERR_INVALID_ARG; }
+    if (p->n < 0) { set_last_error("prims.n = %d < 0", p->n); return SQ_ERR_INVALID_ARG; }
+    if (p->n_classes < 1 || p->n_classes > SQ_MAX_CLASSES) {
+        set_last_error("prims.n_classes = %d outside [1, %d]", p->n_classes, SQ_MAX_CLASSES);
+        return SQ_ERR_INVALID_ARG;
+    }
+    if (p->n > 0 && (!p->means || !p->quats || !p->scales || !p->eps || !p->opacity || !p->logits)) {
+        set_last_error("a primitive parameter pointer is NULL");
+        return SQ_ERR_INVALID_ARG;
+    }
+    return SQ_OK;
+}
+
+sq_status_t check_grid(const sq_grid_t* g) {
+    if (!g) { set_last_error("grid is NULL"); return SQ_ERR_INVALID_ARG; }
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nx > (1 << 24) || g->ny > (1 << 24) || g->nz > (1 << 24)) {
+        set_last_error("grid dims (%d, %d, %d) invalid", g->nx, g->ny, g->nz);
+        return SQ_ERR_INVALID_ARG;
+    }
+    long long nvox = (long long)g->nx * g->ny * g->nz;
+    long long ndiff = (long long)(g->nx + 1) * (g->ny + 1) * (g->nz + 1);
+    if (nvox >= 2147483647LL || ndiff >= 2147483647LL) {
+        set_last_error("grid has %lld voxels, at most 2^31 - 1 supported", nvox);
+        return SQ_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < 3; ++i) {
+        if (!(g->vs[i] > 0.f) || !isfinite(g->vs[i]) || !isfinite(g->lo[i])) {
+            set_last_error("grid lo/vs invalid on axis %d", i);
+            return SQ_ERR_INVALID_ARG;
+        }
+    }
+    return SQ_OK;
+}
+
+sq_status_t check_index(const sq_index_t* idx, const sq_grid_t* g, int n) {
+    (void)g;
+    if (!idx) { set_last_error("index is NULL"); return SQ_ERR_INVALID_ARG; }
+    if (!idx->v_n || !idx->v_f || !idx->status || !idx->p_total || (n > 0 && !idx->ranges)) {
+        set_last_error("an index buffer pointer is NULL");
+        return SQ_ERR_INVALID_ARG;
+    }
+    if (idx->capacity < 0) { set_last_error("index capacity < 0"); return SQ_ERR_INVALID_ARG; }
+    if (idx->capacity > 0 && !idx->v_sq) { set_last_error("index v_sq is NULL"); return SQ_ERR_INVALID_ARG; }
+    return SQ_OK;
+}
+
+sq_status_t check_rays(const sq_rays_t* r) {
+    if (!r) { set_last_error("rays is NULL"); return SQ_ERR_INVALID_ARG; }
+    if (r->n_cam < 0 || r->H < 0 || r->W < 0) {
+        set_last_error("rays dims (%d, %d, %d) invalid", r->n_cam, r->H, r->W);
+        return SQ_ERR_INVALID_ARG;
+    }
+    if (r->L < 1 || r->L > SQ_MAX_SAMPLES) {
+        set_last_error("rays.L = %d outside [1, %d]", r->L, SQ_MAX_SAMPLES);
+        return SQ_ERR_INVALID_ARG;
+    }
+    if ((long long)r->n_cam * r->H * r->W > 0 && (!r->K || !r->cam2world || !r->t)) {
+        set_last_error("a camera pointer is NULL");
+        return SQ_ERR_INVALID_ARG;
+    }
+    if (!(r->kappa >= 0.f && r->kappa < 1.f) || !(r->alpha_max > 0.f) || !isfinite(r->alpha_max)) {
+        set_last_error("kappa must be in [0, 1) and alpha_max > 0");
+        return SQ_ERR_INVALID_ARG;
+    }
+    return SQ_OK;
+}
+
+size_t index_workspace_size(const sq_grid_t* g);
+size_t render_workspace_size(const sq_prims_t* p);
+sq_status_t build_index_impl(const sq_prims_t*, const sq_grid_t*, const sq_index_opts_t*, sq_index_t*, void*, size_t,
+                             cudaStream_t);
+sq_status_t render_fwd_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, const sq_rays_t*, float*, float*,
+                            float*, void*, size_t, cudaStream_t);
+sq_status_t render_bwd_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, const sq_rays_t*, const float*,
+                            const float*, float*, float*, float*, float*, float*, float*, void*, size_t, cudaStream_t);
+sq_status_t query_grid_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, float, float*, float*,
+                            unsigned char*, void*, size_t, cudaStream_t);
+sq_status_t count_pairs_impl(const sq_index_t*, const sq_grid_t*, const sq_rays_t*, long long*, cudaStream_t);
+
+// ------------------------------------------------------------------ loss
+namespace {
+constexpr int LOSS_THREADS = 256;
+
+__global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float* __restrict__ depth, const float* __restrict__ sem,
+                                                       const float* __restrict__ td, const int* __restrict__ lab,
+                                                       long long R, int C, float ws, float wd, float* __restrict__ loss,
+                                                       float* __restrict__ gd, float* __restrict__ gs) {
+    __shared__ float red[LOSS_THREADS / 32];
+    float part = 0.f;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (long long)gridDim.x * blockDim.x) {
+        const float* s = sem + r * C;
+        float mx = s[0];
+        for (int c = 1; c < C; ++c) mx = fmaxf(mx, s[c]);
+        float z = 0.f;
+        for (int c = 0; c < C; ++c) z += expf(s[c] - mx);
+        const int y = lab[r];
+        const float ce = mx + logf(z) - s[y];
+        const float iz = 1.f / z;
+        for (int c = 0; c < C; ++c) gs[r * C + c] = ws * (expf(s[c] - mx) * iz - (c == y ? 1.f : 0.f));
+        const float diff = depth[r] - td[r];
+        gd[r] = wd * 2.f * diff;
+        part += ws * ce + wd * diff * diff;
+    }
+    part = warp_sum(part);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (LOSS_THREADS / 32) ? red[threadIdx.x] : 0.f;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) atomicAdd(loss, v);
+    }
+}
+}  // namespace
+
+}  // namespace sqr
+
+using namespace sqr;
+
+extern "C" {
+
+const char* sq_status_string(sq_status_t s) {
+    switch (s) {
+        case SQ_OK: return "SQ_OK";
+        case SQ_ERR_INVALID_ARG: return "SQ_ERR_INVALID_ARG: invalid argument";
+        case SQ_ERR_CAPACITY: return "SQ_ERR_CAPACITY: index entries exceed the v_sq capacity";
+        case SQ_ERR_CUDA: return "SQ_ERR_CUDA: CUDA error";
+        case SQ_ERR_TIMEOUT: return "SQ_ERR_TIMEOUT: bounded device wait expired";
+        case SQ_ERR_NUMERIC: return "SQ_ERR_NUMERIC: non-finite input";
+    }
+    return "unknown status";
+}
+
+const char* sq_last_error(void) { return g_last_error; }
+
+size_t sq_workspace_size(int op, const sq_prims_t* prims, const sq_grid_t* grid, const sq_rays_t* rays) {
+    (void)rays;
+    switch (op) {
+        case SQ_OP_INDEX:
+            if (check_grid(grid) != SQ_OK) return 0;
+            return index_workspace_size(grid);
+        case SQ_OP_FWD:
+        case SQ_OP_BWD:
+        case SQ_OP_QUERY:
+            if (check_prims(prims) != SQ_OK) return 0;
+            return render_workspace_size(prims);
+    }
+    set_last_error("sq_workspace_size: unknown op %d", op);
+    return 0;
+}
+
+sq_status_t sq_build_index(const sq_prims_t* prims, const sq_grid_t* grid, const sq_index_opts_t* opts,
+                           sq_index_t* index, void* ws, size_t ws_bytes, void* stream) {
+    sq_status_t s;
+    if ((s = check_prims(prims)) != SQ_OK) return s;
+    if ((s = check_grid(grid)) != SQ_OK) return s;
+    if ((s = check_index(index, grid, prims->n)) != SQ_OK) return s;
+    if (!opts) { set_last_error("opts is NULL"); return SQ_ERR_INVALID_ARG; }
+    if (opts->mode == SQ_INDEX_OBB) {
+        if (!(opts->tau_cut > 0.f && opts->tau_cut < 1.f)) {
+            set_last_error("tau_cut = %g outside (0, 1)", (double)opts->tau_cut);
+            return SQ_ERR_INVALID_ARG;
+        }
+    } else if (opts->mode == SQ_INDEX_CUBE) {
+        if (opts->nv < 0 || opts->nv > (1 << 20)) { set_last_error("nv = %d invalid", opts->nv); return SQ_ERR_INVALID_ARG; }
+    } else {
+        set_last_error("index mode %d unknown", opts->mode);
+        return SQ_ERR_INVALID_ARG;
+    }
+    return build_index_impl(prims, grid, opts, index, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+sq_status_t sq_render_fwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
+                          const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* ws, size_t ws_bytes,
+                          void* stream) {
+    sq_status_t s;
+    if ((s = check_prims(prims)) != SQ_OK) return s;
+    if ((s = check_grid(grid)) != SQ_OK) return s;
+    if ((s = check_index(index, grid, prims->n)) != SQ_OK) return s;
+    if ((s = check_rays(rays)) != SQ_OK) return s;
+    if ((long long)rays->n_cam * rays->H * rays->W > 0 && (!depth || !sem)) {
+        set_last_error("sq_render_fwd: depth/sem output is NULL");
+        return SQ_ERR_INVALID_ARG;
+    }
+    return render_fwd_impl(prims, index, grid, rays, depth, sem, t_final, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+sq_status_t sq_render_bwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
+                          const sq_rays_t* rays, const float* grad_depth, const float* grad_sem, float* g_means,
+                          float* g_quats, float* g_scales, float* g_eps, float* g_opacity, float* g_logits, void* ws,
+                          size_t ws_bytes, void* stream) {
+    sq_status_t s;
+    if ((s = check_prims(prims)) != SQ_OK) return s;
+    if ((s = check_grid(grid)) != SQ_OK) return s;
+    if ((s = check_index(index, grid, prims->n)) != SQ_OK) return s;
+    if ((s = check_rays(rays)) != SQ_OK) return s;
+    if ((long long)rays->n_cam * rays->H * rays->W > 0 && (!grad_depth || !grad_sem)) {
+        set_last_error("sq_render_bwd: grad_depth/grad_sem is NULL");
+        return SQ_ERR_INVALID_ARG;
+    }
+    if (prims->n > 0 && (!g_means || !g_quats || !g_scales || !g_eps || !g_opacity || !g_logits)) {
+        set_last_error("sq_render_bwd: a gradient output is NULL");
+        return SQ_ERR_INVALID_ARG;
+    }
+    return render_bwd_impl(prims, index, grid, rays, grad_depth, grad_sem, g_means, g_quats, g_scales, g_eps,
+                           g_opacity, g_logits, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+sq_status_t sq_query_grid(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid, float tau,
+                          float* density, float* sem, unsigned char* label, void* ws, size_t ws_bytes, void* stream) {
+    sq_status_t s;
+    if ((s = check_prims(prims)) != SQ_OK) return s;
+    if ((s = check_grid(grid)) != SQ_OK) return s;
+    if ((s = check_index(index, grid, prims->n)) != SQ_OK) return s;
+    if (!density || !sem) { set_last_error("sq_query_grid: output is NULL"); return SQ_ERR_INVALID_ARG; }
+    if (label && prims->n_classes > 255) { set_last_error("labels need n_classes <= 255"); return SQ_ERR_INVALID_ARG; }
+    return query_grid_impl(prims, index, grid, tau, density, sem, label, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+sq_status_t sq_loss_ce_mse(const float* depth, const float* sem, const float* target_depth, const int* target_label,
+                           long long n_rays, int n_classes, float lambda_s, float lambda_d, float* loss,
+                           float* grad_depth, float* grad_sem, void* stream) {
+    if (n_rays < 0 || n_classes < 1) { set_last_error("sq_loss_ce_mse: bad sizes"); return SQ_ERR_INVALID_ARG; }
+    if (!loss || (n_rays > 0 && (!depth || !sem || !target_depth || !target_label || !grad_depth || !grad_sem))) {
+        set_last_error("sq_loss_ce_mse: NULL pointer");
+        return SQ_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+    if (e != cudaSuccess) return cuda_status(e, "memset loss");
+    if (n_rays == 0) return SQ_OK;
+    const float ws = lambda_s / (float)n_rays, wd = lambda_d / (float)n_rays;
+    long long want = (n_rays + LOSS_THREADS - 1) / LOSS_THREADS;
+    int blocks = (int)(want < 152LL * 16 ? want : 152LL * 16);
+    k_loss<<<blocks, LOSS_THREADS, 0, st>>>(depth, sem, target_depth, target_label, n_rays, n_classes, ws, wd, loss,
+                                            grad_depth, grad_sem);
+    SQ_CHECK_LAUNCH("k_loss");
+    return SQ_OK;
+}
+
+sq_status_t sq_count_pairs(const sq_index_t* index, const sq_grid_t* grid, const sq_rays_t* rays, long long* out,
+                           void* stream) {
+    sq_status_t s;
+    if ((s = check_grid(grid)) != SQ_OK) return s;
+    if ((s = check_index(index, grid, 0)) != SQ_OK) return s;
+    if ((s = check_rays(rays)) != SQ_OK) return s;
+    if (!out) { set_last_error("sq_count_pairs: out is NULL"); return SQ_ERR_INVALID_ARG; }
+    return count_pairs_impl(index, grid, rays, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

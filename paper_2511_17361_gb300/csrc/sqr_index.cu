@@ -1,0 +1,419 @@
+// sqr_index.cu -- the voxel -> superquadric index of Sec. 3.3.1 ("Preliminary
+// Construction"): V_n (count per voxel), V_f (offset per voxel) and V_sq
+// (primitive ids per voxel, ascending), built on the GPU without any host sync.
+//
+//   1. k_ranges     one thread per primitive: its inclusive voxel box, in FP64 with
+//                   explicitly rounded operations (bit-reproducible), and the 8
+//                   signed corner updates of a 3-D difference array;
+//   2. k_prefix_*   three axis-wise prefix sums turn the difference array into V_n;
+//   3. k_scan_*     exclusive scan of V_n -> V_f and the total P (+ capacity check);
+//   4. k_scatter    one CTA per primitive writes its id into every voxel of its box
+//                   at V_f[v] + (atomic cursor);
+//   5. k_sort       one warp per voxel sorts its list ascending (bitonic network in
+//                   registers, shared memory, or global memory by list length).
+#include <math.h>
+#include <stdio.h>
+
+#include "sqr_common.cuh"
+
+namespace sqr {
+
+namespace {
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr int SORT_WARPS = 8;
+constexpr int SORT_SMEM = 1024;  // per-warp list capacity staged in shared memory
+
+struct RangeArgs {
+    const float* means;
+    const float* quats;
+    const float* scales;
+    const float* eps;
+    int n;
+    int mode;
+    int nv;
+    double log_kc;  // ln(ln(1/tau_cut)), computed on the host
+    int gn[3];
+    double glo[3];
+    double gvs[3];
+};
+
+// Voxel box of one primitive.  OBB mode: the level set p_o >= tau_cut lies in the
+// local box |x_i| <= s_i Kc^(eps1/2) (Kc = ln(1/tau_cut)); its world AABB has
+// half-width sum_i |R_ji| h_i.  Cube mode: centre voxel +- nv.  Clipped to the grid.
+__device__ void prim_box(const RangeArgs& a, int k, int lo_i[3], int hi_i[3], bool& empty) {
+    double w = a.quats[4 * k + 0], x = a.quats[4 * k + 1], y = a.quats[4 * k + 2], z = a.quats[4 * k + 3];
+    double nq = __dsqrt_rn(__dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(w, w), __dmul_rn(x, x)), __dmul_rn(y, y)),
+                                     __dmul_rn(z, z)));
+    w = __ddiv_rn(w, nq);
+    x = __ddiv_rn(x, nq);
+    y = __ddiv_rn(y, nq);
+    z = __ddiv_rn(z, nq);
+    double R[9];
+    R[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, y), __dmul_rn(z, z))));
+    R[1] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
+    R[2] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
+    R[3] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
+    R[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(z, z))));
+    R[5] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
+    R[6] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
+    R[7] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
+    R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
+    double e1 = a.eps[2 * k + 0];
+    double ext = exp(__dmul_rn(__dmul_rn(0.5, e1), a.log_kc));
+    double h[3];
+    for (int i = 0; i < 3; ++i) h[i] = __dmul_rn((double)a.scales[3 * k + i], ext);
+    empty = false;
+    for (int j = 0; j < 3; ++j) {
+        double m = a.means[3 * k + j];
+        double ulo, uhi;
+        if (a.mode == SQ_INDEX_OBB) {
+            double hw = __dadd_rn(__dmul_rn(fabs(R[3 * j + 0]), h[0]), __dmul_rn(fabs(R[3 * j + 1]), h[1]));
+            hw = __dadd_rn(hw, __dmul_rn(fabs(R[3 * j + 2]), h[2]));
+            ulo = __ddiv_rn(__dsub_rn(__dsub_rn(m, hw), a.glo[j]), a.gvs[j]);
+            uhi = __ddiv_rn(__dsub_rn(__dadd_rn(m, hw), a.glo[j]), a.gvs[j]);
+        } else {
+            double uc = __ddiv_rn(__dsub_rn(m, a.glo[j]), a.gvs[j]);
+            double cf = floor(fmin(fmax(uc, -1.0 - a.nv), (double)a.gn[j] + a.nv));
+            ulo = cf - a.nv;
+            uhi = cf + a.nv;
+        }
+        if (isnan(ulo) || isnan(uhi)) {
+            empty = true;
+            lo_i[j] = 0;
+            hi_i[j] = -1;
+            continue;
+        }
+        int i0 = (int)floor(fmin(fmax(ulo, -1.0), (double)a.gn[j]));
+        int i1 = (int)floor(fmin(fmax(uhi, -1.0), (double)a.gn[j]));
+        i0 = max(i0, 0);
+        i1 = min(i1, a.gn[j] - 1);
+        if (i0 > i1) empty = true;
+        lo_i[j] = i0;
+        hi_i[j] = i1;
+    }
+}
+
+__global__ void k_ranges(RangeArgs a, int* __restrict__ ranges, int* __restrict__ diff) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.n) return;
+    int lo[3], hi[3];
+    bool empty;
+    prim_box(a, k, lo, hi, empty);
+    int* r = ranges + 6 * k;
+    if (empty) {
+        r[0] = 0; r[1] = -1; r[2] = 0; r[3] = -1; r[4] = 0; r[5] = -1;
+        return;
+    }
+    r[0] = lo[0]; r[1] = hi[0]; r[2] = lo[1]; r[3] = hi[1]; r[4] = lo[2]; r[5] = hi[2];
+    const int sy = a.gn[2] + 1, sx = (a.gn[1] + 1) * sy;
+    for (int c = 0; c < 8; ++c) {
+        int ix = (c & 4) ? hi[0] + 1 : lo[0];
+        int iy = (c & 2) ? hi[1] + 1 : lo[1];
+        int iz = (c & 1) ? hi[2] + 1 : lo[2];
+        int sgn = (__popc(c) & 1) ? -1 : 1;
+        atomicAdd(diff + (size_t)ix * sx + (size_t)iy * sy + iz, sgn);
+    }
+}
+
+// Axis-wise inclusive prefix sums of the (nx+1)(ny+1)(nz+1) difference array.
+__global__ void k_prefix_z(int* __restrict__ diff, int nxp, int nyp, int nzp) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nxp * nyp) return;
+    int* row = diff + (size_t)t * nzp;
+    int s = 0;
+    for (int k = 0; k < nzp; ++k) {
+        s += row[k];
+        row[k] = s;
+    }
+}
+
+__global__ void k_prefix_y(int* __restrict__ diff, int nxp, int nyp, int nzp) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nxp * nzp) return;
+    int i = t / nzp, k = t - i * nzp;
+    int* base = diff + (size_t)i * nyp * nzp + k;
+    int s = 0;
+    for (int j = 0; j < nyp; ++j) {
+        s += base[(size_t)j * nzp];
+        base[(size_t)j * nzp] = s;
+    }
+}
+
+// Last axis, fused with the write of V_n (dropping the padding row of each axis).
+__global__ void k_prefix_x(const int* __restrict__ diff, int* __restrict__ v_n, int nx, int ny, int nz) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ny * nz) return;
+    int j = t / nz, k = t - j * nz;
+    const int nzp = nz + 1, nyp = ny + 1;
+    int s = 0;
+    for (int i = 0; i < nx; ++i) {
+        s += diff[((size_t)i * nyp + j) * nzp + k];
+        v_n[((size_t)i * ny + j) * nz + k] = s;
+    }
+}
+
+// -------------------------------------------------------------- exclusive scan
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* sh, long long& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        long long w = (lane < (blockDim.x >> 5)) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    long long before = (wid > 0) ? sh[wid - 1] : 0;
+    total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const int* __restrict__ v_n, long long nvox,
+                                                              long long* __restrict__ tile_sums) {
+    __shared__ long long sh[32];
+    long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i)
+        if (base + i < nvox) s += v_n[base + i];
+    long long total;
+    block_excl_scan(s, sh, total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// One CTA: exclusive scan of the tile sums (grid-stride over tiles), total P,
+// capacity check.
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(long long* __restrict__ tile_sums, int n_tiles,
+                                                             long long capacity, long long* __restrict__ p_total,
+                                                             int* __restrict__ status) {
+    __shared__ long long sh[32];
+    long long carry = 0;
+    for (int b = 0; b < n_tiles; b += SCAN_THREADS) {
+        int i = b + threadIdx.x;
+        long long v = (i < n_tiles) ? tile_sums[i] : 0;
+        long long total;
+        long long ex = block_excl_scan(v, sh, total);
+        if (i < n_tiles) tile_sums[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        *p_total = carry;
+        if (carry > capacity || carry >= 2147483647LL) *status = SQ_ERR_CAPACITY;
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int* __restrict__ v_n, long long nvox,
+                                                             const long long* __restrict__ tile_off,
+                                                             int* __restrict__ v_f) {
+    __shared__ long long sh[32];
+    long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
+    int vals[SCAN_ITEMS];
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        vals[i] = (base + i < nvox) ? v_n[base + i] : 0;
+        s += vals[i];
+    }
+    long long total;
+    long long ex = block_excl_scan(s, sh, total) + tile_off[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i < nvox) v_f[base + i] = (int)ex;
+        ex += vals[i];
+    }
+}
+
+// -------------------------------------------------------------- scatter
+__global__ void __launch_bounds__(256) k_scatter(const int* __restrict__ ranges, int n, int ny, int nz,
+                                                 const int* __restrict__ v_f, int* __restrict__ cursor,
+                                                 int* __restrict__ v_sq, long long capacity,
+                                                 const int* __restrict__ status) {
+    if (*status != SQ_OK) return;
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int* r = ranges + 6 * k;
+        int dx = r[1] - r[0] + 1, dy = r[3] - r[2] + 1, dz = r[5] - r[4] + 1;
+        if (dx <= 0 || dy <= 0 || dz <= 0) continue;
+        long long vol = (long long)dx * dy * dz;
+        for (long long l = threadIdx.x; l < vol; l += blockDim.x) {
+            int iz = (int)(l % dz);
+            long long q = l / dz;
+            int iy = (int)(q % dy);
+            int ix = (int)(q / dy);
+            int v = ((r[0] + ix) * ny + (r[2] + iy)) * nz + (r[4] + iz);
+            int pos = atomicAdd(cursor + v, 1);
+            long long at = (long long)v_f[v] + pos;
+            if (at < capacity) v_sq[at] = k;
+        }
+    }
+}
+
+// -------------------------------------------------------------- per-voxel sort
+// Ascending bitonic network for any length n: merge steps compare (i, mirror of i)
+// then half-cleaners compare (i, i + stride).  Slots >= n act as +inf and are
+// never touched (their comparisons cannot swap).
+template <typename Load, typename Store>
+__device__ void warp_bitonic(int n, int lane, Load ld, Store st) {
+    int npow = 1;
+    while (npow < n) npow <<= 1;
+    const int pairs = npow >> 1;
+    for (int size = 2; size <= npow; size <<= 1) {
+        const int half = size >> 1;
+        for (int t = lane; t < pairs; t += 32) {
+            int blk = t / half, pos = t - blk * half;
+            int i = blk * size + pos, p = blk * size + size - 1 - pos;
+            if (p < n) {
+                int a = ld(i), b = ld(p);
+                if (a > b) { st(i, b); st(p, a); }
+            }
+        }
+        __syncwarp();
+        for (int stride = half >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < pairs; t += 32) {
+                int blk = t / stride, pos = t - blk * stride;
+                int i = blk * 2 * stride + pos, p = i + stride;
+                if (p < n) {
+                    int a = ld(i), b = ld(p);
+                    if (a > b) { st(i, b); st(p, a); }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(SORT_WARPS * 32) k_sort(const int* __restrict__ v_n, const int* __restrict__ v_f,
+                                                          int* __restrict__ v_sq, long long nvox,
+                                                          const int* __restrict__ status) {
+    __shared__ int sh[SORT_WARPS][SORT_SMEM];
+    if (*status != SQ_OK) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long nwarps = (long long)gridDim.x * SORT_WARPS;
+    for (long long v = (long long)blockIdx.x * SORT_WARPS + wid; v < nvox; v += nwarps) {
+        const int n = v_n[v];
+        if (n <= 1) continue;
+        int* list = v_sq + v_f[v];
+        if (n <= 32) {
+            int x = lane < n ? list[lane] : 0x7fffffff;
+#pragma unroll
+            for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    int y = __shfl_xor_sync(0xffffffffu, x, stride);
+                    bool up = ((lane & size) == 0);
+                    bool lower = ((lane & stride) == 0);
+                    int lo = min(x, y), hi = max(x, y);
+                    x = (lower == up) ? lo : hi;
+                }
+            }
+            if (lane < n) list[lane] = x;
+        } else if (n <= SORT_SMEM) {
+            int* s = sh[wid];
+            for (int i = lane; i < n; i += 32) s[i] = list[i];
+            __syncwarp();
+            warp_bitonic(n, lane, [&](int i) { return s[i]; }, [&](int i, int val) { s[i] = val; });
+            for (int i = lane; i < n; i += 32) list[i] = s[i];
+            __syncwarp();
+        } else {
+            volatile int* g = list;
+            warp_bitonic(n, lane, [&](int i) { return g[i]; }, [&](int i, int val) { g[i] = val; });
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- workspace
+struct IndexWs {
+    size_t diff_off, cursor_off, tiles_off, total;
+};
+
+static IndexWs index_ws(const sq_grid_t* g) {
+    IndexWs w;
+    size_t ndiff = (size_t)(g->nx + 1) * (g->ny + 1) * (g->nz + 1);
+    size_t nvox = (size_t)g->nx * g->ny * g->nz;
+    size_t ntiles = (nvox + SCAN_TILE - 1) / SCAN_TILE;
+    w.diff_off = 0;
+    w.cursor_off = align_up(w.diff_off + ndiff * sizeof(int), 256);
+    w.tiles_off = align_up(w.cursor_off + nvox * sizeof(int), 256);
+    w.total = align_up(w.tiles_off + ntiles * sizeof(long long), 256);
+    return w;
+}
+
+size_t index_workspace_size(const sq_grid_t* g) { return index_ws(g).total; }
+
+sq_status_t build_index_impl(const sq_prims_t* prims, const sq_grid_t* grid, const sq_index_opts_t* opts,
+                             sq_index_t* idx, void* ws, size_t ws_bytes, cudaStream_t st) {
+    IndexWs w = index_ws(grid);
+    if (ws_bytes < w.total || (w.total > 0 && ws == nullptr)) {
+        set_last_error("sq_build_index: workspace of %zu bytes given, %zu needed", ws_bytes, w.total);
+        return SQ_ERR_INVALID_ARG;
+    }
+    char* base = (char*)ws;
+    int* diff = (int*)(base + w.diff_off);
+    int* cursor = (int*)(base + w.cursor_off);
+    long long* tiles = (long long*)(base + w.tiles_off);
+    const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+    const long long nvox = (long long)nx * ny * nz;
+    const size_t ndiff = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+    const int n_tiles = (int)((nvox + SCAN_TILE - 1) / SCAN_TILE);
+
+    cudaError_t e;
+    e = cudaMemsetAsync(diff, 0, ndiff * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_status(e, "memset diff");
+    e = cudaMemsetAsync(cursor, 0, (size_t)nvox * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_status(e, "memset cursor");
+    e = cudaMemsetAsync(idx->status, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_status(e, "memset status");
+
+    RangeArgs a;
+    a.means = prims->means; a.quats = prims->quats; a.scales = prims->scales; a.eps = prims->eps;
+    a.n = prims->n; a.mode = opts->mode; a.nv = opts->nv;
+    a.log_kc = (opts->mode == SQ_INDEX_OBB) ? log(-log((double)opts->tau_cut)) : 0.0;
+    a.gn[0] = nx; a.gn[1] = ny; a.gn[2] = nz;
+    for (int i = 0; i < 3; ++i) { a.glo[i] = grid->lo[i]; a.gvs[i] = grid->vs[i]; }
+
+    if (prims->n > 0) {
+        k_ranges<<<(prims->n + 127) / 128, 128, 0, st>>>(a, idx->ranges, diff);
+        SQ_CHECK_LAUNCH("k_ranges");
+    }
+    const int nxp = nx + 1, nyp = ny + 1, nzp = nz + 1;
+    k_prefix_z<<<(nxp * nyp + 255) / 256, 256, 0, st>>>(diff, nxp, nyp, nzp);
+    SQ_CHECK_LAUNCH("k_prefix_z");
+    k_prefix_y<<<(nxp * nzp + 255) / 256, 256, 0, st>>>(diff, nxp, nyp, nzp);
+    SQ_CHECK_LAUNCH("k_prefix_y");
+    k_prefix_x<<<(ny * nz + 255) / 256, 256, 0, st>>>(diff, idx->v_n, nx, ny, nz);
+    SQ_CHECK_LAUNCH("k_prefix_x");
+    k_scan_reduce<<<n_tiles, SCAN_THREADS, 0, st>>>(idx->v_n, nvox, tiles);
+    SQ_CHECK_LAUNCH("k_scan_reduce");
+    k_scan_tiles<<<1, SCAN_THREADS, 0, st>>>(tiles, n_tiles, idx->capacity, idx->p_total, idx->status);
+    SQ_CHECK_LAUNCH("k_scan_tiles");
+    k_scan_apply<<<n_tiles, SCAN_THREADS, 0, st>>>(idx->v_n, nvox, tiles, idx->v_f);
+    SQ_CHECK_LAUNCH("k_scan_apply");
+    if (prims->n > 0) {
+        int blocks = prims->n < 65535 ? prims->n : 65535;
+        k_scatter<<<blocks, 256, 0, st>>>(idx->ranges, prims->n, ny, nz, idx->v_f, cursor, idx->v_sq, idx->capacity,
+                                          idx->status);
+        SQ_CHECK_LAUNCH("k_scatter");
+        long long want = (nvox + SORT_WARPS - 1) / SORT_WARPS;
+        int sblocks = (int)(want < 152 * 64 ? want : 152 * 64);
+        k_sort<<<sblocks, SORT_WARPS * 32, 0, st>>>(idx->v_n, idx->v_f, idx->v_sq, nvox, idx->status);
+        SQ_CHECK_LAUNCH("k_sort");
+    }
+    return SQ_OK;
+}
+
+}  // namespace sqr

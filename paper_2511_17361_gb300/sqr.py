@@ -1,0 +1,336 @@
+"""Thin Python binding of libsqr (include/sqr.h) over ctypes.
+
+Only argument marshalling lives here: every step of the renderer runs in the
+CUDA library.  PyTorch provides device memory and the current stream.  The
+library is loaded from the package's ``_lib/libsqr.so``; if it is missing the
+import fails (there is no CPU fallback).
+
+Names follow the C ABI: :func:`build_index`, :func:`render_fwd`,
+:func:`render_bwd`, :func:`query_grid`, :func:`loss_ce_mse`, and
+:class:`SQRender`, the ``torch.autograd.Function`` around forward/backward.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libsqr.so")
+
+SQ_OK, SQ_ERR_INVALID_ARG, SQ_ERR_CAPACITY, SQ_ERR_CUDA, SQ_ERR_TIMEOUT, SQ_ERR_NUMERIC = range(6)
+SQ_INDEX_OBB, SQ_INDEX_CUBE = 0, 1
+SQ_OP_INDEX, SQ_OP_FWD, SQ_OP_BWD, SQ_OP_QUERY = 0, 1, 2, 3
+
+_vp = ctypes.c_void_p
+
+
+class SqGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("lo", ctypes.c_float * 3),
+                ("vs", ctypes.c_float * 3)]
+
+
+class SqPrims(ctypes.Structure):
+    _fields_ = [("means", _vp), ("quats", _vp), ("scales", _vp), ("eps", _vp), ("opacity", _vp), ("logits", _vp),
+                ("n", ctypes.c_int), ("n_classes", ctypes.c_int)]
+
+
+class SqIndexOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("tau_cut", ctypes.c_float), ("nv", ctypes.c_int)]
+
+
+class SqIndex(ctypes.Structure):
+    _fields_ = [("v_n", _vp), ("v_f", _vp), ("v_sq", _vp), ("ranges", _vp), ("capacity", ctypes.c_longlong),
+                ("p_total", _vp), ("status", _vp)]
+
+
+class SqRays(ctypes.Structure):
+    _fields_ = [("n_cam", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int), ("K", _vp), ("cam2world", _vp),
+                ("t", _vp), ("L", ctypes.c_int), ("kappa", ctypes.c_float), ("alpha_max", ctypes.c_float)]
+
+
+class SqrError(RuntimeError):
+    pass
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsqr.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                          "python -m paper_2511_17361_gb300._build")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    lib.sq_workspace_size.restype = ctypes.c_size_t
+    lib.sq_workspace_size.argtypes = [ctypes.c_int, P(SqPrims), P(SqGrid), P(SqRays)]
+    lib.sq_build_index.argtypes = [P(SqPrims), P(SqGrid), P(SqIndexOpts), P(SqIndex), _vp, ctypes.c_size_t, _vp]
+    lib.sq_render_fwd.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), P(SqRays), _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                  _vp]
+    lib.sq_render_bwd.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), P(SqRays), _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                  _vp, _vp, ctypes.c_size_t, _vp]
+    lib.sq_query_grid.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), ctypes.c_float, _vp, _vp, _vp, _vp,
+                                  ctypes.c_size_t, _vp]
+    lib.sq_loss_ce_mse.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_float,
+                                   ctypes.c_float, _vp, _vp, _vp, _vp]
+    lib.sq_count_pairs.argtypes = [P(SqIndex), P(SqGrid), P(SqRays), _vp, _vp]
+    for f in ("sq_build_index", "sq_render_fwd", "sq_render_bwd", "sq_query_grid", "sq_loss_ce_mse",
+              "sq_count_pairs"):
+        getattr(lib, f).restype = ctypes.c_int
+    lib.sq_status_string.restype = ctypes.c_char_p
+    lib.sq_status_string.argtypes = [ctypes.c_int]
+    lib.sq_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int, what: str):
+    if status != SQ_OK:
+        raise SqrError(f"{what}: {lib.sq_status_string(status).decode()} ({lib.sq_last_error().decode()})")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need_cuda_f32(t, name):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise SqrError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+PRIM_KEYS = ("means", "quats", "scales", "eps", "opacity", "logits")
+
+
+def prims_struct(prims: dict) -> SqPrims:
+    for k in PRIM_KEYS:
+        _need_cuda_f32(prims[k], k)
+    n, C = prims["logits"].shape
+    return SqPrims(*[_ptr(prims[k]) for k in PRIM_KEYS], n, C)
+
+
+def grid_struct(grid: dict) -> SqGrid:
+    nx, ny, nz = (int(v) for v in grid["n"])
+    return SqGrid(nx, ny, nz, (ctypes.c_float * 3)(*[float(v) for v in grid["lo"]]),
+                  (ctypes.c_float * 3)(*[float(v) for v in grid["vs"]]))
+
+
+@dataclass
+class Rays:
+    """Camera rig and samples on the device: K [n_cam,4], cam2world [n_cam,3,4], t [L]."""
+    K: torch.Tensor
+    cam2world: torch.Tensor
+    t: torch.Tensor
+    H: int
+    W: int
+    kappa: float = 0.0
+    alpha_max: float = 1.0
+
+    @property
+    def n_cam(self):
+        return self.K.shape[0]
+
+    @property
+    def R(self):
+        return self.n_cam * self.H * self.W
+
+    def struct(self) -> SqRays:
+        for name in ("K", "cam2world", "t"):
+            _need_cuda_f32(getattr(self, name), name)
+        return SqRays(self.n_cam, self.H, self.W, _ptr(self.K), _ptr(self.cam2world), _ptr(self.t), self.t.numel(),
+                      self.kappa, self.alpha_max)
+
+    @staticmethod
+    def from_rig(rig: dict, t, device="cuda", kappa=0.0, alpha_max=1.0) -> "Rays":
+        f = lambda a: torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
+        return Rays(f(rig["K"]), f(rig["cam2world"]), f(t), int(rig["H"]), int(rig["W"]), kappa, alpha_max)
+
+
+class _Workspace:
+    """Per-device scratch buffers, grown on demand and reused across calls."""
+
+    def __init__(self):
+        self.bufs = {}
+
+    def get(self, key, nbytes, device):
+        nbytes = max(int(nbytes), 256)
+        b = self.bufs.get((key, device))
+        if b is None or b.numel() < nbytes:
+            b = torch.empty(nbytes, dtype=torch.uint8, device=device)
+            self.bufs[(key, device)] = b
+        return b
+
+
+_ws = _Workspace()
+
+
+def workspace_size(op, prims=None, grid=None, rays=None) -> int:
+    p = prims_struct(prims) if prims is not None else None
+    g = grid_struct(grid) if grid is not None else None
+    r = rays.struct() if rays is not None else None
+    return int(lib.sq_workspace_size(op, ctypes.byref(p) if p else None, ctypes.byref(g) if g else None,
+                                     ctypes.byref(r) if r else None))
+
+
+# ------------------------------------------------------------------ index
+class Index:
+    """Device buffers of the voxel -> superquadric index (V_n, V_f, V_sq, ranges)."""
+
+    def __init__(self, grid: dict, n: int, capacity: int, device):
+        nvox = int(grid["n"][0]) * int(grid["n"][1]) * int(grid["n"][2])
+        self.grid = grid
+        self.v_n = torch.empty(nvox, dtype=torch.int32, device=device)
+        self.v_f = torch.empty(nvox, dtype=torch.int32, device=device)
+        self.v_sq = torch.empty(max(int(capacity), 1), dtype=torch.int32, device=device)
+        self.capacity = int(capacity)
+        self.ranges = torch.empty((max(n, 1), 6), dtype=torch.int32, device=device)
+        self.p_total = torch.zeros(1, dtype=torch.int64, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def struct(self) -> SqIndex:
+        return SqIndex(_ptr(self.v_n), _ptr(self.v_f), _ptr(self.v_sq), _ptr(self.ranges), self.capacity,
+                       _ptr(self.p_total), _ptr(self.status))
+
+    def P(self) -> int:
+        return int(self.p_total.item())
+
+    def check(self):
+        s = int(self.status.item())
+        if s != SQ_OK:
+            raise SqrError(f"index: {lib.sq_status_string(s).decode()} (needed {self.P()}, have {self.capacity})")
+
+
+def build_index(prims: dict, grid: dict, mode: int = SQ_INDEX_OBB, tau_cut: float = 0.01, nv: int = 5,
+                capacity: int | None = None, index: Index | None = None, sync: bool = True) -> Index:
+    """Builds the index on the current stream.  With ``sync`` the host reads P and
+    re-runs once with a large enough V_sq when the capacity was too small."""
+    device = prims["means"].device
+    n = prims["means"].shape[0]
+    if index is None:
+        if capacity is None:
+            nvox = int(grid["n"][0]) * int(grid["n"][1]) * int(grid["n"][2])
+            capacity = max(4 * nvox, 1024)
+        index = Index(grid, n, capacity, device)
+    p, g = prims_struct(prims), grid_struct(grid)
+    opts = SqIndexOpts(mode, tau_cut, nv)
+    wsz = lib.sq_workspace_size(SQ_OP_INDEX, ctypes.byref(p), ctypes.byref(g), None)
+    ws = _ws.get("index", wsz, device)
+    idx_s = index.struct()
+    _check(lib.sq_build_index(ctypes.byref(p), ctypes.byref(g), ctypes.byref(opts), ctypes.byref(idx_s),
+                              _ptr(ws), ws.numel(), _stream()), "sq_build_index")
+    if sync:
+        P = index.P()
+        if P > index.capacity:
+            index = Index(grid, n, int(P * 1.25) + 1024, device)
+            return build_index(prims, grid, mode, tau_cut, nv, index=index, sync=True)
+        index.check()
+    return index
+
+
+# ------------------------------------------------------------------ render
+def render_fwd(prims: dict, index: Index, grid: dict, rays: Rays, out=None):
+    """Returns depth [R], sem [R, C], t_final [R] (Eq. 4-6)."""
+    device = prims["means"].device
+    C = prims["logits"].shape[1]
+    R = rays.R
+    if out is None:
+        out = (torch.empty(R, device=device), torch.empty((R, C), device=device), torch.empty(R, device=device))
+    depth, sem, tf = out
+    p, g, r, ix = prims_struct(prims), grid_struct(grid), rays.struct(), index.struct()
+    wsz = lib.sq_workspace_size(SQ_OP_FWD, ctypes.byref(p), ctypes.byref(g), ctypes.byref(r))
+    ws = _ws.get("fwd", wsz, device)
+    _check(lib.sq_render_fwd(ctypes.byref(p), ctypes.byref(ix), ctypes.byref(g), ctypes.byref(r), _ptr(depth),
+                             _ptr(sem), _ptr(tf), _ptr(ws), ws.numel(), _stream()), "sq_render_fwd")
+    return depth, sem, tf
+
+
+def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, grad_sem, out=None) -> dict:
+    """Gradients of sum(gD * depth) + sum(gS * sem) w.r.t. every parameter."""
+    device = prims["means"].device
+    grad_depth = _need_cuda_f32(grad_depth.contiguous(), "grad_depth")
+    grad_sem = _need_cuda_f32(grad_sem.contiguous(), "grad_sem")
+    if out is None:
+        out = {k: torch.empty_like(prims[k]) for k in PRIM_KEYS}
+    p, g, r, ix = prims_struct(prims), grid_struct(grid), rays.struct(), index.struct()
+    wsz = lib.sq_workspace_size(SQ_OP_BWD, ctypes.byref(p), ctypes.byref(g), ctypes.byref(r))
+    ws = _ws.get("bwd", wsz, device)
+    _check(lib.sq_render_bwd(ctypes.byref(p), ctypes.byref(ix), ctypes.byref(g), ctypes.byref(r), _ptr(grad_depth),
+                             _ptr(grad_sem), *[_ptr(out[k]) for k in PRIM_KEYS], _ptr(ws), ws.numel(), _stream()),
+           "sq_render_bwd")
+    return out
+
+
+def query_grid(prims: dict, index: Index, grid: dict, tau: float = 0.05, with_label: bool = True):
+    """Supp. A.4 voxelisation: density [V], sem [V, C], label [V] uint8 (C = free)."""
+    device = prims["means"].device
+    C = prims["logits"].shape[1]
+    nvox = index.v_n.numel()
+    dens = torch.empty(nvox, device=device)
+    sem = torch.empty((nvox, C), device=device)
+    lab = torch.empty(nvox, dtype=torch.uint8, device=device) if with_label else None
+    p, g, ix = prims_struct(prims), grid_struct(grid), index.struct()
+    wsz = lib.sq_workspace_size(SQ_OP_QUERY, ctypes.byref(p), ctypes.byref(g), None)
+    ws = _ws.get("query", wsz, device)
+    _check(lib.sq_query_grid(ctypes.byref(p), ctypes.byref(ix), ctypes.byref(g), tau, _ptr(dens), _ptr(sem),
+                             _ptr(lab), _ptr(ws), ws.numel(), _stream()), "sq_query_grid")
+    return dens, sem, lab
+
+
+def loss_ce_mse(depth, sem, target_depth, target_label, lambda_s=2.0, lambda_d=0.05, out=None):
+    """Supp. A.5 loss (Eq. 8) and its gradients w.r.t. depth and sem."""
+    R, C = sem.shape
+    if out is None:
+        out = (torch.empty(1, device=sem.device), torch.empty_like(depth), torch.empty_like(sem))
+    loss, gd, gs = out
+    _check(lib.sq_loss_ce_mse(_ptr(depth), _ptr(sem), _ptr(target_depth), _ptr(target_label), R, C, lambda_s,
+                              lambda_d, _ptr(loss), _ptr(gd), _ptr(gs), _stream()), "sq_loss_ce_mse")
+    return loss, gd, gs
+
+
+def count_pairs(index: Index, grid: dict, rays: Rays):
+    """(Q, in-grid samples): pairs the forward evaluates over all L samples."""
+    out = torch.zeros(2, dtype=torch.int64, device=index.v_n.device)
+    g, r, ix = grid_struct(grid), rays.struct(), index.struct()
+    _check(lib.sq_count_pairs(ctypes.byref(ix), ctypes.byref(g), ctypes.byref(r), _ptr(out), _stream()),
+           "sq_count_pairs")
+    q, s = out.tolist()
+    return int(q), int(s)
+
+
+class SQRender(torch.autograd.Function):
+    """(means, quats, scales, eps, opacity, logits) -> (depth [R], sem [R, C]).
+
+    The index and rays are constants of the call; the backward runs
+    sq_render_bwd with the incoming cotangents."""
+
+    @staticmethod
+    def forward(ctx, means, quats, scales, eps, opacity, logits, index: Index, grid: dict, rays: Rays):
+        prims = dict(zip(PRIM_KEYS, (t.contiguous() for t in (means, quats, scales, eps, opacity, logits))))
+        depth, sem, _ = render_fwd(prims, index, grid, rays)
+        ctx.save_for_backward(*[prims[k] for k in PRIM_KEYS])
+        ctx.index, ctx.grid, ctx.rays = index, grid, rays
+        return depth, sem
+
+    @staticmethod
+    def backward(ctx, g_depth, g_sem):
+        prims = dict(zip(PRIM_KEYS, ctx.saved_tensors))
+        if g_depth is None:
+            g_depth = torch.zeros(ctx.rays.R, device=prims["means"].device)
+        if g_sem is None:
+            g_sem = torch.zeros((ctx.rays.R, prims["logits"].shape[1]), device=prims["means"].device)
+        g = render_bwd(prims, ctx.index, ctx.grid, ctx.rays, g_depth, g_sem)
+        return (g["means"], g["quats"], g["scales"], g["eps"], g["opacity"], g["logits"], None, None, None)
+
+
+def render(prims: dict, index: Index, grid: dict, rays: Rays):
+    """Differentiable render of ``prims`` (tensors may require grad)."""
+    return SQRender.apply(*[prims[k] for k in PRIM_KEYS], index, grid, rays)
+
+
+def to_device(prims_np: dict, device="cuda") -> dict:
+    return {k: torch.as_tensor(prims_np[k], dtype=torch.float32).contiguous().to(device) for k in PRIM_KEYS}

@@ -103,7 +103,7 @@ def prims_driving(n, seed, ground_frac=0.7, n_classes=N_CLASSES) -> dict:
     return _pack(means[perm], quats[perm], scales[perm], eps[perm], opacity[perm], logits[perm])
 
 
-def prims_clustered(n, seed, n_clusters=512, spread=1.5, s_range=(0.2, 1.2), eps_range=(0.1, 1.9),
+def prims_clustered(n, seed, n_clusters=512, spread=1.5, s_range=(0.15, 0.6), eps_range=(0.1, 1.9),
                     n_classes=N_CLASSES) -> dict:
     """Heavy-overlap stress set: ``n_clusters`` cluster centres uniform in the scene
     box (z in [-1, 3]), members offset by N(0, spread) m, scales U(s_range)^3, random

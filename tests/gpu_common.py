@@ -1,0 +1,68 @@
+"""Helpers for the GPU parity tests: build/load the CUDA library, move seeded
+inputs to the device, and the tolerance checks (each stated where it is used)."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2511_17361_gb300 import synth
+
+
+def lib():
+    from paper_2511_17361_gb300 import _build
+    _build.build()
+    from paper_2511_17361_gb300 import sqr
+    return sqr
+
+
+def dev_grid(grid):
+    return {"n": tuple(int(v) for v in grid["n"]), "lo": [float(v) for v in grid["lo"]],
+            "vs": [float(v) for v in grid["vs"]]}
+
+
+def scene_to_gpu(sqr, prims, rig, t, kappa=0.0, alpha_max=1.0):
+    return sqr.to_device(prims), sqr.Rays.from_rig(rig, t, kappa=kappa, alpha_max=alpha_max)
+
+
+def np_index(ix):
+    P = ix.P()
+    return {"v_n": ix.v_n.cpu().numpy(), "v_f": ix.v_f.cpu().numpy(), "v_sq": ix.v_sq[:P].cpu().numpy(),
+            "ranges": ix.ranges.cpu().numpy(), "P": P}
+
+
+def softmax(x):
+    x = np.asarray(x, np.float64)
+    e = np.exp(x - x.max(-1, keepdims=True))
+    return e / e.sum(-1, keepdims=True)
+
+
+def check_depth(d_gpu, d_ref, t_near):
+    """Depth within 1e-4 relative: |dD| <= 1e-4 * max(D_ref, t_near)."""
+    d_gpu = np.asarray(d_gpu, np.float64)
+    tol = 1e-4 * np.maximum(np.abs(d_ref), t_near)
+    bad = np.abs(d_gpu - d_ref) > tol
+    assert not bad.any(), f"{bad.sum()} depths off; worst {np.max(np.abs(d_gpu - d_ref) / tol):.3g} x tol"
+
+
+def check_sem(s_gpu, s_ref, raw_tol=5e-5):
+    """Class probabilities softmax(S) within 1e-5 absolute; raw S within
+    raw_tol * max(1, |S_ref|) (FP32 accumulation of ~10^3 SFU-evaluated terms)."""
+    s_gpu = np.asarray(s_gpu, np.float64)
+    dp = np.abs(softmax(s_gpu) - softmax(s_ref))
+    assert dp.max() <= 1e-5, f"class probabilities off by {dp.max():.3g}"
+    rel = np.abs(s_gpu - s_ref) / np.maximum(1.0, np.abs(s_ref))
+    assert rel.max() <= raw_tol, f"raw semantics off by {rel.max():.3g} (rel)"
+
+
+def check_grad(g_gpu, g_ref, name, rtol=1e-3):
+    """Per element |g - g_ref| <= rtol * max(|g_ref|, 1e-3 * max|g_ref| over the tensor)."""
+    g_gpu = np.asarray(g_gpu, np.float64)
+    g_ref = np.asarray(g_ref, np.float64)
+    scale = np.max(np.abs(g_ref)) if g_ref.size else 0.0
+    tol = rtol * np.maximum(np.abs(g_ref), 1e-3 * scale)
+    err = np.abs(g_gpu - g_ref)
+    bad = err > tol + 1e-30
+    assert not bad.any(), (f"{name}: {bad.sum()}/{bad.size} elements off; worst ratio "
+                           f"{np.max(err / (tol + 1e-30)):.3g}; norm ratio "
+                           f"{np.linalg.norm(g_gpu) / max(np.linalg.norm(g_ref), 1e-300):.6f}")

@@ -1,0 +1,346 @@
+"""CUDA path vs the FP64 oracle on the same seeded inputs (needs a GPU).
+
+Index contents are compared bit for bit; renders, grid queries and gradients
+element by element at the tolerances in tests/gpu_common.py.  Small workloads
+are compared in full; the 540,000-ray frames on sampled rays (sparse
+cotangents for the backward), which the oracle computes one by one."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2511_17361_gb300 import synth
+from tests.gpu_common import check_depth, check_grad, check_sem, dev_grid, lib, np_index, scene_to_gpu
+from tests.helpers import prims_from, small_scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sqr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    oracle.build()
+    return lib()
+
+
+def _index_pair(sqr, cfg, mode=0, tau=0.01, nv=5):
+    prims_d = sqr.to_device(cfg["prims"])
+    ix = sqr.build_index(prims_d, dev_grid(cfg["grid"]), mode=mode, tau_cut=tau, nv=nv)
+    ref = oracle.build_index(cfg["prims"], cfg["grid"], mode, tau, nv)
+    return prims_d, ix, ref
+
+
+def _assert_index_equal(ix, ref):
+    got = np_index(ix)
+    assert ref["ties"] == 0, "seeded workload has a voxel-boundary near-tie"
+    assert got["P"] == ref["P"]
+    assert np.array_equal(got["ranges"][:len(ref["ranges"])], ref["ranges"])
+    assert np.array_equal(got["v_n"], ref["v_n"])
+    assert np.array_equal(got["v_f"], ref["v_f"])
+    assert np.array_equal(got["v_sq"], ref["v_sq"])
+
+
+# ----------------------------------------------------------------------- index
+@pytest.mark.parametrize("ci", [0, 1, 2, 4])
+def test_index_bit_exact(sqr, ci):
+    cfg = synth.make_config(ci)
+    _, ix, ref = _index_pair(sqr, cfg)
+    _assert_index_equal(ix, ref)
+
+
+def test_index_cube_mode_bit_exact(sqr):
+    cfg = synth.make_config(0)
+    _, ix, ref = _index_pair(sqr, cfg, mode=1, nv=5)
+    _assert_index_equal(ix, ref)
+
+
+def test_index_long_lists_sorted(sqr):
+    """Lists longer than a warp (33..2000 entries) take the shared- and global-memory
+    sort paths; still identical to the oracle."""
+    rng = np.random.default_rng(5)
+    for n in (40, 300, 2000):
+        pr = prims_from(rng.uniform(0, 4, (n, 3)), rng.standard_normal((n, 4)), rng.uniform(0.5, 3.0, (n, 3)),
+                        rng.uniform(0.3, 1.8, (n, 2)), rng.uniform(0, 1, n), rng.standard_normal((n, 3)))
+        grid = synth.grid_spec(4, 3, 2, lo=(0, 0, 0), hi=(4, 3, 2))
+        _, ix, ref = _index_pair(sqr, {"prims": pr, "grid": grid})
+        _assert_index_equal(ix, ref)
+        assert ref["v_n"].max() > 32
+
+
+def test_index_empty_and_outside(sqr):
+    """N = 0, and primitives entirely outside the grid, give empty lists."""
+    grid = synth.grid_spec(5, 5, 5, lo=(0, 0, 0), hi=(5, 5, 5))
+    pr = prims_from([[50, 50, 50], [-30, 2, 2]], [[1, 0, 0, 0]] * 2, [[1, 1, 1]] * 2, [[1, 1]] * 2, [0.5] * 2,
+                    np.zeros((2, 3)))
+    _, ix, ref = _index_pair(sqr, {"prims": pr, "grid": grid})
+    _assert_index_equal(ix, ref)
+    assert ref["P"] == 0
+    pr0 = prims_from(np.zeros((0, 3)), np.zeros((0, 4)), np.zeros((0, 3)), np.zeros((0, 2)), np.zeros(0),
+                     np.zeros((0, 3)))
+    _, ix0, ref0 = _index_pair(sqr, {"prims": pr0, "grid": grid})
+    assert ix0.P() == 0 and np.all(ix0.v_n.cpu().numpy() == 0)
+
+
+def test_index_capacity_overflow_reported(sqr):
+    """Too small a V_sq: status = SQ_ERR_CAPACITY and p_total = the needed size."""
+    cfg = synth.make_config(0)
+    prims_d = sqr.to_device(cfg["prims"])
+    ix = sqr.build_index(prims_d, dev_grid(cfg["grid"]), capacity=1000, sync=False)
+    torch.cuda.synchronize()
+    assert int(ix.status.item()) == sqr.SQ_ERR_CAPACITY
+    ref = oracle.build_index(cfg["prims"], cfg["grid"])
+    assert ix.P() == ref["P"]
+    with pytest.raises(sqr.SqrError):
+        ix.check()
+    # render on an overflowed index does no work (outputs left as given)
+    rays = sqr.Rays.from_rig(cfg["rig"], cfg["t"])
+    depth = torch.full((rays.R,), -7.0, device="cuda")
+    sem = torch.zeros((rays.R, 18), device="cuda")
+    tf = torch.zeros(rays.R, device="cuda")
+    sqr.render_fwd(prims_d, ix, dev_grid(cfg["grid"]), rays, out=(depth, sem, tf))
+    assert torch.all(depth == -7.0)
+    # the auto-growing path recovers
+    ix2 = sqr.build_index(prims_d, dev_grid(cfg["grid"]), capacity=1000)
+    _assert_index_equal(ix2, ref)
+
+
+# ----------------------------------------------------------------------- forward
+def _fwd_pair(sqr, prims, grid, rig, t, kappa=0.0, alpha_max=1.0, ray_ids=None, mode=0, tau=0.01, nv=5):
+    prims_d, rays = scene_to_gpu(sqr, prims, rig, t, kappa, alpha_max)
+    g = dev_grid(grid)
+    ix = sqr.build_index(prims_d, g, mode=mode, tau_cut=tau, nv=nv)
+    depth, sem, tf = sqr.render_fwd(prims_d, ix, g, rays)
+    torch.cuda.synchronize()
+    ref_ix = np_index(ix)
+    D, S, T, NU = oracle.render_fwd(prims, grid, ref_ix, rig, t, kappa, alpha_max, ray_ids=ray_ids)
+    sel = slice(None) if ray_ids is None else np.asarray(ray_ids)
+    return depth.cpu().numpy()[sel], sem.cpu().numpy()[sel], tf.cpu().numpy()[sel], D, S, T, NU
+
+
+def test_forward_small_workload_full(sqr):
+    cfg = synth.make_config(0)
+    d, s, tf, D, S, T, _ = _fwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"])
+    check_depth(d, D, 0.5)
+    check_sem(s, S)
+    assert np.max(np.abs(tf - T)) < 1e-5
+    # transmittance identity on the GPU side: sum w + T = 1 is implied by D, T
+    assert np.all((tf >= 0) & (tf <= 1))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_forward_ragged_small_scenes(sqr, seed):
+    """Odd image sizes (ragged warps and tiles), several class counts."""
+    C = [5, 3, 18][seed]
+    pr, grid, rig, t = small_scene(seed, n=9, H=7, W=13, L=[24, 33, 48][seed], C=C, sigma_max=0.9)
+    d, s, tf, D, S, T, _ = _fwd_pair(sqr, pr, grid, rig, t)
+    check_depth(d, D, 0.5)
+    check_sem(s, S)
+    assert np.max(np.abs(tf - T)) < 1e-5
+
+
+def test_forward_clamp_active(sqr):
+    """Dense overlapping primitives: alpha = min(sum, 1) saturates."""
+    pr, grid, rig, t = small_scene(4, n=12, sigma_max=3.0, s_range=(1.0, 2.5))
+    d, s, tf, D, S, T, _ = _fwd_pair(sqr, pr, grid, rig, t)
+    check_depth(d, D, 0.5)
+    check_sem(s, S)
+    assert np.any(T == 0.0)
+
+
+def test_forward_heavy_voxels(sqr):
+    """Voxel lists longer than a chunk's pair buffer (> 256 primitives)."""
+    rng = np.random.default_rng(9)
+    n = 400
+    pr = prims_from(np.c_[rng.uniform(2, 6, n), rng.uniform(-1, 1, n), rng.uniform(0, 2, n)],
+                    rng.standard_normal((n, 4)), rng.uniform(0.5, 2.0, (n, 3)), rng.uniform(0.3, 1.8, (n, 2)),
+                    rng.uniform(0.0, 0.02, n), rng.standard_normal((n, 4)))
+    grid = synth.grid_spec(4, 4, 2, lo=(-8, -8, -1), hi=(8, 8, 3))
+    rig = synth.rig_single(H=5, W=9, f=6.0, centre=(-1.0, 0.0, 1.0))
+    t = synth.sample_depths(30, 0.5, 9.5)
+    d, s, tf, D, S, T, _ = _fwd_pair(sqr, pr, grid, rig, t)
+    check_depth(d, D, 0.5)
+    check_sem(s, S, raw_tol=2e-4)
+
+
+def test_forward_early_termination(sqr):
+    """kappa > 0: rays stop after T < kappa; compared on rays whose T is not within
+    1e-4 (relative) of kappa at any sample."""
+    cfg = synth.make_config(0)
+    kappa = 1e-2
+    d, s, tf, D, S, T, NU = _fwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], kappa=kappa)
+    assert (NU < 48).any()
+    ok = np.ones(len(D), bool)
+    ix_ref = oracle.build_index(cfg["prims"], cfg["grid"])
+    for r in np.flatnonzero(NU < 48):
+        tr = oracle.trace_ray(cfg["prims"], cfg["grid"], ix_ref, cfg["rig"], cfg["t"], r, kappa=kappa)
+        if np.any(np.abs(tr["T"][:tr["used"] + 1] - kappa) < 1e-4 * kappa):
+            ok[r] = False
+    check_depth(d[ok], D[ok], 0.5)
+    check_sem(s[ok], S[ok])
+
+
+@pytest.mark.parametrize("ci", [1, 2])
+def test_forward_full_frame_sampled_rays(sqr, ci):
+    """Six-camera 225x400 frames (540,000 rays), 3000 sampled rays vs the oracle."""
+    cfg = synth.make_config(ci)
+    R = synth.n_rays(cfg["rig"])
+    rng = np.random.default_rng(ci)
+    rays = np.unique(np.r_[rng.integers(0, R, 2990), [0, R - 1, 399, 400, 90000, 89999]])
+    d, s, tf, D, S, T, _ = _fwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], ray_ids=rays)
+    check_depth(d, D, 0.5)
+    check_sem(s, S)
+    assert np.max(np.abs(tf - T)) < 2e-5
+
+
+def test_forward_cube_index(sqr):
+    cfg = synth.make_config(0)
+    d, s, tf, D, S, T, _ = _fwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], mode=1, nv=3)
+    check_depth(d, D, 0.5)
+    check_sem(s, S)
+
+
+# ----------------------------------------------------------------------- backward
+def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0):
+    prims_d, rays = scene_to_gpu(sqr, prims, rig, t, 0.0, alpha_max)
+    g = dev_grid(grid)
+    ix = sqr.build_index(prims_d, g)
+    R = rays.R
+    gd_full = np.zeros(R, np.float32)
+    gs_full = np.zeros((R, prims["logits"].shape[1]), np.float32)
+    sel = np.arange(R) if ray_ids is None else np.asarray(ray_ids)
+    gd_full[sel] = gd
+    gs_full[sel] = gs
+    out = sqr.render_bwd(prims_d, ix, g, rays, torch.from_numpy(gd_full).cuda(), torch.from_numpy(gs_full).cuda())
+    torch.cuda.synchronize()
+    ref = oracle.render_bwd(prims, grid, np_index(ix), rig, t, gd_full[sel].astype(np.float64),
+                            gs_full[sel].astype(np.float64), alpha_max=alpha_max,
+                            ray_ids=None if ray_ids is None else sel)
+    return {k: v.cpu().numpy() for k, v in out.items()}, ref
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_backward_small_scene_full(sqr, seed):
+    pr, grid, rig, t = small_scene(seed, n=8, H=9, W=11, L=32, C=[5, 18][seed], sigma_max=0.6)
+    R = 9 * 11
+    rng = np.random.default_rng(seed)
+    gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, pr["logits"].shape[1])).astype(
+        np.float32)
+    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs)
+    for k in ref:
+        check_grad(got[k], ref[k], k)
+
+
+def test_backward_clamp_active(sqr):
+    pr, grid, rig, t = small_scene(6, n=12, sigma_max=2.5, s_range=(1.0, 2.5))
+    R = rig["H"] * rig["W"]
+    rng = np.random.default_rng(6)
+    gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, 5)).astype(np.float32)
+    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs)
+    for k in ref:
+        check_grad(got[k], ref[k], k)
+
+
+def test_backward_stress_crop(sqr):
+    """16,384 clustered superquadrics, 32x32-ray crop of camera 0 (cotangents zero
+    elsewhere): every parameter's gradient vs the FP64 oracle."""
+    cfg = synth.make_config(2)
+    H, W = cfg["rig"]["H"], cfg["rig"]["W"]
+    v0, u0 = 96, 184
+    rays = np.array([(v0 + i) * W + (u0 + j) for i in range(32) for j in range(32)])
+    rng = np.random.default_rng(2)
+    gd = rng.standard_normal(len(rays)).astype(np.float32)
+    gs = rng.standard_normal((len(rays), 18)).astype(np.float32)
+    got, ref = _bwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], gd, gs, ray_ids=rays)
+    touched = np.abs(ref["opacity"]) > 0
+    assert touched.sum() > 100
+    for k in ref:
+        check_grad(got[k], ref[k], k)
+
+
+def test_backward_full_frame_sparse_cotangents(sqr):
+    """540,000-ray frame, cotangents on 400 sampled rays only."""
+    cfg = synth.make_config(1)
+    R = synth.n_rays(cfg["rig"])
+    rng = np.random.default_rng(11)
+    rays = np.unique(rng.integers(0, R, 400))
+    gd = rng.standard_normal(len(rays)).astype(np.float32)
+    gs = rng.standard_normal((len(rays), 18)).astype(np.float32)
+    got, ref = _bwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], gd, gs, ray_ids=rays)
+    for k in ref:
+        check_grad(got[k], ref[k], k)
+
+
+def test_autograd_function_matches_entry_point(sqr):
+    """SQRender (torch.autograd.Function) routes the cotangents of a loss into
+    sq_render_bwd: its .grad equals the direct call."""
+    pr, grid, rig, t = small_scene(3, n=7, C=4)
+    prims_d, rays = scene_to_gpu(sqr, pr, rig, t)
+    g = dev_grid(grid)
+    ix = sqr.build_index(prims_d, g)
+    leaves = {k: v.clone().requires_grad_(True) for k, v in prims_d.items()}
+    depth, sem = sqr.render(leaves, ix, g, rays)
+    tgt = torch.linspace(1, 5, rays.R, device="cuda")
+    loss = ((depth - tgt) ** 2).sum() + (sem[:, 1] * 0.3).sum()
+    loss.backward()
+    gd = 2 * (depth.detach() - tgt)
+    gs = torch.zeros_like(sem)
+    gs[:, 1] = 0.3
+    direct = sqr.render_bwd(prims_d, ix, g, rays, gd, gs)
+    for k in direct:
+        torch.testing.assert_close(leaves[k].grad, direct[k], rtol=1e-5, atol=1e-6)
+
+
+# ----------------------------------------------------------------------- grid query
+def test_query_grid_full(sqr):
+    """Supp. A.4 voxelisation of 8192 superquadrics at all 640,000 voxel centres."""
+    cfg = synth.make_config(4)
+    prims_d = sqr.to_device(cfg["prims"])
+    g = dev_grid(cfg["grid"])
+    ix = sqr.build_index(prims_d, g)
+    dens, sem, lab = sqr.query_grid(prims_d, ix, g, tau=0.05)
+    torch.cuda.synchronize()
+    rd, rs, rl = oracle.query_grid(cfg["prims"], cfg["grid"], np_index(ix), tau=0.05)
+    dens, sem, lab = dens.cpu().numpy(), sem.cpu().numpy(), lab.cpu().numpy()
+    assert np.max(np.abs(dens - rd) / np.maximum(1.0, rd)) < 5e-5
+    assert np.max(np.abs(sem - rs) / np.maximum(1.0, np.abs(rs))) < 5e-5
+    # labels: the GPU's own FP32 decision must be self-consistent everywhere ...
+    own = np.where(dens >= 0.05, np.argmax(sem, 1), 18)
+    assert np.array_equal(own, lab)
+    # ... and equal the FP64 label wherever the decision has a clear margin
+    srt = np.sort(rs, 1)
+    clear = (np.abs(rd - 0.05) > 1e-4) & (srt[:, -1] - srt[:, -2] > 1e-4)
+    assert clear.mean() > 0.99
+    assert np.array_equal(lab[clear], rl[clear])
+
+
+# ----------------------------------------------------------------------- loss
+def test_loss_kernel_matches_torch(sqr):
+    rng = np.random.default_rng(0)
+    R, C = 1000, 18
+    d = torch.from_numpy(rng.uniform(0, 40, R).astype(np.float32)).cuda()
+    s = torch.from_numpy(rng.standard_normal((R, C)).astype(np.float32)).cuda()
+    td = torch.from_numpy(rng.uniform(0.5, 45, R).astype(np.float32)).cuda()
+    tl = torch.from_numpy(rng.integers(0, C, R).astype(np.int32)).cuda()
+    loss, gd, gs = sqr.loss_ce_mse(d, s, td, tl)
+    dc, sc = d.cpu().double().requires_grad_(), s.cpu().double().requires_grad_()
+    ref = 2.0 * torch.nn.functional.cross_entropy(sc, tl.cpu().long()) + 0.05 * ((dc - td.cpu().double()) ** 2).mean()
+    ref.backward()
+    assert abs(loss.item() - ref.item()) < 1e-4 * abs(ref.item())
+    torch.testing.assert_close(gd.cpu().double(), dc.grad, rtol=1e-5, atol=1e-9)
+    torch.testing.assert_close(gs.cpu().double(), sc.grad, rtol=1e-4, atol=1e-9)
+
+
+# ----------------------------------------------------------------------- argument errors
+def test_invalid_arguments_rejected_on_host(sqr):
+    cfg = synth.make_config(0)
+    prims_d = sqr.to_device(cfg["prims"])
+    g = dev_grid(cfg["grid"])
+    with pytest.raises(sqr.SqrError):
+        sqr.build_index(prims_d, g, tau_cut=1.5)
+    with pytest.raises(sqr.SqrError):
+        sqr.build_index(prims_d, {"n": (0, 5, 5), "lo": [0, 0, 0], "vs": [1, 1, 1]})
+    ix = sqr.build_index(prims_d, g)
+    rays = sqr.Rays.from_rig(cfg["rig"], np.linspace(0.5, 45, 2000))
+    with pytest.raises(sqr.SqrError):
+        sqr.render_fwd(prims_d, ix, g, rays)  # L > SQ_MAX_SAMPLES
