@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(Q_THREADS) k_query(QueryArgs a) {
 }  // namespace
 
 size_t render_workspace_size(const sq_prims_t* p);
+size_t render_logits_offset(const sq_prims_t* p);
 
 template <int CP>
 static sq_status_t launch_query_cp(const QueryArgs& a, cudaStream_t st) {
@@ -117,11 +118,10 @@ sq_status_t query_grid_impl(const sq_prims_t* prims, const sq_index_t* idx, cons
         set_last_error("sq_query_grid: workspace of %zu bytes given, %zu needed", ws_bytes, need);
         return SQ_ERR_INVALID_ARG;
     }
-    const size_t n = (size_t)prims->n;
     const int cp = cpad(prims->n_classes);
     char* base = (char*)ws;
     float4* rec = (float4*)base;
-    float* lpad = (float*)(base + align_up(align_up(n * REC4 * sizeof(float4), 256) + n * AUX4 * sizeof(float4), 256));
+    float* lpad = (float*)(base + render_logits_offset(prims));
     sq_status_t s = launch_pack(prims, rec, nullptr, lpad, cp, st);
     if (s != SQ_OK) return s;
     QueryArgs a;

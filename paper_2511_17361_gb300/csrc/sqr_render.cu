@@ -1,24 +1,24 @@
 // sqr_render.cu -- forward and backward superquadric volume rendering (Sec. 3.3.2,
 // 3.3.3) on sm_103a.
 //
-// Work decomposition (both passes): one warp marches one ray.  The ray's samples
-// are taken in chunks of up to 32 consecutive samples (lane i owns sample j0+i)
-// whose voxel lists together hold at most PB (sample, primitive) pairs.  The
-// chunk's lists are staged from V_sq into shared memory (coalesced), then the
-// lanes sweep the flattened pair list 32 pairs at a time: each lane gathers one
-// packed primitive record (4 x float4) and evaluates p_o with the SFU; the pair
-// values of one sample are summed with a segmented warp reduction.  Compositing
-// of the chunk is a warp product-scan of (1 - alpha).  A single sample whose
-// list alone exceeds PB is streamed straight from global memory (occupancies
-// recomputed instead of buffered).
+// Forward (and the replay phase of the backward): a warp marches four rays at a
+// time, eight lanes per ray, one lane per sample.  Each lane walks its own voxel
+// list (Sec. 3.3.1), so the sums of Eq. 4 (alpha = sum p sigma, s = sum p c) stay
+// in the lane's registers; compositing (Eq. 5-6) of the eight samples is an
+// 8-lane product scan of (1 - alpha).  Rays are handed out by a global counter,
+// so a lane group whose ray ends early takes the next ray.
 //
-// Backward: phase 1 replays the forward for the ray and keeps, per sample,
-// alpha_j, the clamp flag and v_j = gD t_j + <gS, s_j> in shared memory; phase 2
-// sweeps back to front (U_j = alpha_{j+1} v_{j+1} + (1 - alpha_{j+1}) U_{j+1},
-// dL/dalpha_j = T_j (v_j - U_j)); phase 3 re-walks the pairs, chains dL/dalpha and
-// dL/ds_j through Eq. 1-2 to every parameter, and accumulates the per-primitive
-// gradients in a shared-memory hash table owned by the CTA (one table for the
-// CTA's tile of rays), flushed to global memory with atomics when the tile ends.
+// Backward gradients: one warp per ray.  Along a ray the samples that list a
+// given primitive are contiguous (a ray crosses a primitive's voxel box once), so
+// every primitive of the current sample's list is given an owner slot in a lane;
+// the owner accumulates that primitive's parameter gradients in registers for as
+// long as it stays in the lists and flushes them once when it leaves, as one
+// coalesced 32-wide atomic add into a [N, 32] accumulator.  The replay that
+// precedes it keeps per sample alpha_j, v_j = gD t_j + <gS, s_j> and T_j in shared
+// memory; the back-to-front sweep U_j = alpha_{j+1} v_{j+1} + (1 - alpha_{j+1}) U_{j+1}
+// then gives dL/dalpha_j = T_j (v_j - U_j) (zero where the clamp is active) and
+// w_j = T_j alpha_j.
+#include <limits.h>
 #include <math.h>
 
 #include "sqr_common.cuh"
@@ -27,12 +27,14 @@ namespace sqr {
 
 namespace {
 
-constexpr int PB = 256;        // pair buffer per warp (pairs per chunk)
-constexpr int FWD_WARPS = 8;   // warps (rays in flight) per CTA, forward
-constexpr int BWD_WARPS = 8;   // warps per CTA, backward
-constexpr int BWD_RAYS_X = 8;  // backward CTA tile: 8 x 4 pixels
-constexpr int BWD_RAYS_Y = 4;
-constexpr int TABLE_SLOTS = 512;
+constexpr int GS = 8;         // lanes (samples) per ray in the lane-per-sample layout
+constexpr int NG = 32 / GS;   // rays per warp in that layout
+constexpr int FWD_WARPS = 8;  // warps per CTA, forward
+constexpr int OWN = 64;       // owner slots per warp (two per lane)
+constexpr int QCAP = 64;      // pending gradient flushes per warp
+constexpr int QW = 16;        // words per pending flush: key, 12 geometry, sigma, W, pad
+constexpr int GF = 32;        // floats per primitive in the gradient accumulator
+constexpr int NGEO = 13;      // m3 q4 s3 eps2 sigma1
 
 // ------------------------------------------------------------------ packing
 __global__ void k_pack(sq_prims_t P, float4* __restrict__ rec, float4* __restrict__ aux, float* __restrict__ lpad,
@@ -84,19 +86,7 @@ struct RenderArgs {
     int n_cam, H, W, L, C;
     long long R;
     float kappa, alpha_max;
-};
-
-struct ChunkSmem {
-    int kbuf[PB];
-    float pbuf[PB];
-    unsigned char sidx[PB];
-    float x[3][32];
-    float asum[32];
-    float aux[32];
-    float wbuf[32];
-    int lst[32];
-    int cnt[32];
-    int off[32];
+    int* ray_ctr;  // work counter, zeroed before the launch
 };
 
 __device__ __forceinline__ void ray_of(const RenderArgs& a, long long r, float o[3], float d[3]) {
@@ -107,92 +97,39 @@ __device__ __forceinline__ void ray_of(const RenderArgs& a, long long r, float o
     pixel_ray(a.K + 4 * cam, a.c2w + 12 * cam, u, v, o, d);
 }
 
-// Sets up the chunk starting at sample j0: per-lane sample voxel, list start and
-// count; returns m (samples in the chunk), pc (pairs), heavy (single sample with
-// more than PB pairs).  Stages the lists into shared memory unless heavy.
-__device__ __forceinline__ void chunk_setup(const RenderArgs& a, ChunkSmem& sm, const float o[3], const float d[3],
-                                            int j0, int lane, int& m, int& pc, bool& heavy) {
-    const int j = j0 + lane;
-    float x[3] = {0.f, 0.f, 0.f};
-    int vox = -1;
-    if (j < a.L) vox = sample_voxel(a.g, o, d, __ldg(a.t + j), x);
-    int n = 0, f = 0;
-    if (vox >= 0) {
-        n = __ldg(a.v_n + vox);
-        f = __ldg(a.v_f + vox);
-    }
-    int cum = warp_incl_scan(n, lane);
-    unsigned ok = __ballot_sync(0xffffffffu, (cum <= PB) && (j < a.L));
-    m = __popc(ok);
-    if (m == 0) m = 1;
-    pc = __shfl_sync(0xffffffffu, cum, m - 1);
-    heavy = pc > PB;
-    if (lane < m) {
-        sm.x[0][lane] = x[0];
-        sm.x[1][lane] = x[1];
-        sm.x[2][lane] = x[2];
-        sm.asum[lane] = 0.f;
-        sm.aux[lane] = 0.f;
-        sm.lst[lane] = f;
-        sm.cnt[lane] = n;
-        sm.off[lane] = cum - n;
-    }
-    __syncwarp();
-    if (!heavy) {
-        for (int i = 0; i < m; ++i) {
-            const int ni = sm.cnt[i], fi = sm.lst[i], oi = sm.off[i];
-            for (int l = lane; l < ni; l += 32) {
-                sm.kbuf[oi + l] = __ldg(a.v_sq + fi + l);
-                sm.sidx[oi + l] = (unsigned char)i;
-            }
-        }
-    }
-    __syncwarp();
-}
-
-// Segmented (by sample slot) suffix sum across a 32-pair batch; the first lane of
-// each segment ends with the segment total.  Pairs are sorted by slot.
-__device__ __forceinline__ float seg_sum(float v, int slot, int lane, bool valid) {
+// Inclusive product scan within aligned groups of GS lanes.
+__device__ __forceinline__ float group_incl_prod(float v, int s) {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        float y = __shfl_down_sync(0xffffffffu, v, o);
-        int sy = __shfl_down_sync(0xffffffffu, slot, o);
-        bool vy = __shfl_down_sync(0xffffffffu, valid, o);
-        if (lane + o < 32 && vy && sy == slot) v += y;
+    for (int o = 1; o < GS; o <<= 1) {
+        float y = __shfl_up_sync(0xffffffffu, v, o, GS);
+        if (s >= o) v *= y;
     }
     return v;
 }
 
-__device__ __forceinline__ bool seg_head(int slot, int lane, bool valid) {
-    int sp = __shfl_up_sync(0xffffffffu, slot, 1);
-    return valid && (lane == 0 || sp != slot);
-}
-
-// Front-to-back compositing of the chunk (Eq. 5): lane i < m holds alpha_i.
-// Updates T; returns the lane's weight (0 for lanes >= m or past termination) and
-// the number of samples composited in this chunk; sets done on termination.
-__device__ __forceinline__ float composite(float alpha, int lane, int m, float kappa, float& T, float& Tbefore,
-                                           int& used, bool& done) {
-    float om = (lane < m) ? 1.f - alpha : 1.f;
-    float incl = warp_incl_prod(om, lane);
-    float excl = __shfl_up_sync(0xffffffffu, incl, 1);
-    if (lane == 0) excl = 1.f;
-    Tbefore = T * excl;
-    float w = (lane < m) ? Tbefore * alpha : 0.f;
-    used = m;
-    if (kappa > 0.f) {
-        unsigned stop = __ballot_sync(0xffffffffu, lane < m && T * incl < kappa);
-        if (stop) {
-            int ls = __ffs(stop) - 1;
-            if (lane > ls) w = 0.f;
-            used = ls + 1;
-            done = true;
-            T = T * __shfl_sync(0xffffffffu, incl, ls);
-            return w;
-        }
+// Compositing (Eq. 5) of a group's GS consecutive samples.  Lane s holds alpha
+// (0 for lanes past L or outside the grid).  Returns w = T_before * alpha (0 past
+// an early termination) and T_before; advances T (uniform in the group); `stop`
+// when kappa > 0 ends the ray inside this chunk, `used` = samples composited.
+__device__ __forceinline__ float group_composite(float alpha, int s, int gbase, float kappa, float& T, float& Tb,
+                                                 bool valid, int& used, bool& stop) {
+    const float incl = group_incl_prod(1.f - alpha, s);
+    float excl = __shfl_up_sync(0xffffffffu, incl, 1, GS);
+    if (s == 0) excl = 1.f;
+    Tb = T * excl;
+    float w = Tb * alpha;
+    used = GS;
+    stop = false;
+    const unsigned kill = __ballot_sync(0xffffffffu, valid && kappa > 0.f && T * incl < kappa);
+    const unsigned gk = (kill >> gbase) & ((1u << GS) - 1u);
+    if (gk) {
+        const int ls = __ffs(gk) - 1;
+        if (s > ls) w = 0.f;
+        used = ls + 1;
+        stop = true;
     }
-    T = T * __shfl_sync(0xffffffffu, incl, 31);
-    if (T == 0.f) done = true;  // every later weight is exactly zero
+    const float tot = __shfl_sync(0xffffffffu, incl, gbase + (gk ? (__ffs(gk) - 1) : GS - 1));
+    T = T * tot;
     return w;
 }
 
@@ -200,93 +137,101 @@ __device__ __forceinline__ float composite(float alpha, int lane, int m, float k
 template <int CP>
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward(RenderArgs a, float* __restrict__ depth,
                                                             float* __restrict__ sem, float* __restrict__ t_final) {
-    __shared__ ChunkSmem smem[FWD_WARPS];
     if (*a.status != SQ_OK) return;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    ChunkSmem& sm = smem[wid];
-    const long long nwarps = (long long)gridDim.x * FWD_WARPS;
+    const int lane = threadIdx.x & 31;
+    const int s = lane & (GS - 1), gbase = lane & ~(GS - 1);
     const float4* lp4 = reinterpret_cast<const float4*>(a.lpad);
 
-    for (long long r = (long long)blockIdx.x * FWD_WARPS + wid; r < a.R; r += nwarps) {
-        float o[3], d[3];
-        ray_of(a, r, o, d);
-        float T = 1.f, Dp = 0.f;
-        float acc[CP];
+    int rn = 0;
+    if (s == 0) rn = atomicAdd(a.ray_ctr, 1);
+    long long r = __shfl_sync(0xffffffffu, rn, gbase);
+    float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f};
+    if (r < a.R) ray_of(a, r, o, d);
+    float T = 1.f, Dp = 0.f;
+    int j0 = 0;
+    float acc[CP];
 #pragma unroll
-        for (int c = 0; c < CP; ++c) acc[c] = 0.f;
-        bool done = false;
-        for (int j0 = 0; j0 < a.L && !done;) {
-            int m, pc;
-            bool heavy;
-            chunk_setup(a, sm, o, d, j0, lane, m, pc, heavy);
-            // pass A: occupancies and alpha sums
-            for (int b = 0; b < pc; b += 32) {
-                const int gi = b + lane;
-                const bool valid = gi < pc;
-                int slot = 0;
-                float v = 0.f;
-                if (valid) {
-                    int k;
-                    if (!heavy) { k = sm.kbuf[gi]; slot = sm.sidx[gi]; }
-                    else k = __ldg(a.v_sq + sm.lst[0] + gi);
-                    Prim p = load_prim(a.rec, k);
-                    float xs[3] = {sm.x[0][slot], sm.x[1][slot], sm.x[2][slot]};
-                    float po = occupancy(p, xs);
-                    if (!heavy) sm.pbuf[gi] = po;
-                    v = po * p.sigma;
-                }
-                v = seg_sum(v, slot, lane, valid);
-                if (seg_head(slot, lane, valid)) sm.asum[slot] += v;
-                __syncwarp();
-            }
-            __syncwarp();
-            float alpha = (lane < m) ? fminf(sm.asum[lane], a.alpha_max) : 0.f;
-            float Tb;
-            int used;
-            float w = composite(alpha, lane, m, a.kappa, T, Tb, used, done);
-            if (lane < m) Dp += w * __ldg(a.t + j0 + lane);
-            sm.wbuf[lane] = w;
-            __syncwarp();
-            // pass B: semantics, acc += w_j p c_k
-            for (int gi = lane; gi < pc; gi += 32) {
-                int k, slot = 0;
-                float po;
-                if (!heavy) {
-                    k = sm.kbuf[gi];
-                    slot = sm.sidx[gi];
-                    po = sm.pbuf[gi];
-                } else {
-                    k = __ldg(a.v_sq + sm.lst[0] + gi);
-                    Prim p = load_prim(a.rec, k);
-                    float xs[3] = {sm.x[0][0], sm.x[1][0], sm.x[2][0]};
-                    po = occupancy(p, xs);
-                }
-                float om = sm.wbuf[slot] * po;
-                if (om != 0.f) {
-                    const float4* cr = lp4 + (size_t)k * (CP / 4);
+    for (int c = 0; c < CP; ++c) acc[c] = 0.f;
+
+    while (__any_sync(0xffffffffu, r < a.R)) {
+        const bool live = r < a.R;
+        const int j = j0 + s;
+        const bool valid = live && j < a.L;
+        float x[3] = {0.f, 0.f, 0.f};
+        int vox = -1;
+        float tj = 0.f;
+        if (valid) {
+            tj = __ldg(a.t + j);
+            vox = sample_voxel(a.g, o, d, tj, x);
+        }
+        int n = 0, f = 0;
+        if (vox >= 0) {
+            n = __ldg(a.v_n + vox);
+            f = __ldg(a.v_f + vox);
+        }
+        float asum = 0.f;
+        float sacc[CP];
 #pragma unroll
-                    for (int q = 0; q < CP / 4; ++q) {
-                        float4 cv = __ldg(cr + q);
-                        acc[4 * q + 0] = fmaf(om, cv.x, acc[4 * q + 0]);
-                        acc[4 * q + 1] = fmaf(om, cv.y, acc[4 * q + 1]);
-                        acc[4 * q + 2] = fmaf(om, cv.z, acc[4 * q + 2]);
-                        acc[4 * q + 3] = fmaf(om, cv.w, acc[4 * q + 3]);
-                    }
+        for (int c = 0; c < CP; ++c) sacc[c] = 0.f;
+        const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
+        for (int e = 0; e < nmax; ++e) {
+            if (e < n) {
+                const int k = __ldg(a.v_sq + f + e);
+                const Prim p = load_prim(a.rec, k);
+                const float po = occupancy(p, x);
+                asum = fmaf(po, p.sigma, asum);
+                const float4* cr = lp4 + (size_t)k * (CP / 4);
+#pragma unroll
+                for (int q = 0; q < CP / 4; ++q) {
+                    const float4 cv = __ldg(cr + q);
+                    sacc[4 * q + 0] = fmaf(po, cv.x, sacc[4 * q + 0]);
+                    sacc[4 * q + 1] = fmaf(po, cv.y, sacc[4 * q + 1]);
+                    sacc[4 * q + 2] = fmaf(po, cv.z, sacc[4 * q + 2]);
+                    sacc[4 * q + 3] = fmaf(po, cv.w, sacc[4 * q + 3]);
                 }
             }
-            __syncwarp();
-            j0 += m;
         }
-        float Dsum = warp_sum(Dp);
+        const float alpha = valid ? fminf(asum, a.alpha_max) : 0.f;
+        float Tb;
+        int used;
+        bool stop;
+        const float w = group_composite(alpha, s, gbase, a.kappa, T, Tb, valid, used, stop);
+        if (valid) {
+            Dp = fmaf(w, tj, Dp);
 #pragma unroll
-        for (int c = 0; c < CP; ++c) acc[c] = warp_sum(acc[c]);
-        if (lane == 0) {
-            depth[r] = Dsum;
-            if (t_final) t_final[r] = T;
+            for (int c = 0; c < CP; ++c) acc[c] = fmaf(w, sacc[c], acc[c]);
         }
+        j0 += GS;
+        // a ray ends at L, on early termination, or once T is exactly 0 (every later weight is 0)
+        const bool fin = live && (j0 >= a.L || stop || T == 0.f);
+        if (__any_sync(0xffffffffu, fin)) {
+            float Dsum = Dp;
 #pragma unroll
-        for (int c = 0; c < CP; ++c)
-            if (lane == c && c < a.C) sem[r * a.C + c] = acc[c];
+            for (int o2 = GS / 2; o2 > 0; o2 >>= 1) Dsum += __shfl_xor_sync(0xffffffffu, Dsum, o2, GS);
+#pragma unroll
+            for (int c = 0; c < CP; ++c) {
+                float v = acc[c];
+#pragma unroll
+                for (int o2 = GS / 2; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2, GS);
+                if (fin && (c % GS) == s && c < a.C) sem[r * a.C + c] = v;
+            }
+            if (fin && s == 0) {
+                depth[r] = Dsum;
+                if (t_final) t_final[r] = T;
+            }
+            int nr = 0;
+            if (fin && s == 0) nr = atomicAdd(a.ray_ctr, 1);
+            nr = __shfl_sync(0xffffffffu, nr, gbase);
+            if (fin) {
+                r = nr;
+                if (r < a.R) ray_of(a, r, o, d);
+                T = 1.f;
+                Dp = 0.f;
+                j0 = 0;
+#pragma unroll
+                for (int c = 0; c < CP; ++c) acc[c] = 0.f;
+            }
+        }
     }
 }
 
@@ -371,229 +316,316 @@ __device__ __forceinline__ float occupancy_grad(const BwdPrim& P, const float x[
     return po;
 }
 
+
 struct BwdArgs {
     RenderArgs r;
     const float* grad_depth;
     const float* grad_sem;
-    float* g_means;
-    float* g_quats;
-    float* g_scales;
-    float* g_eps;
-    float* g_opacity;
-    float* g_logits;
-    int tiles_x, tiles_y;  // CTA tiles per camera
+    float* gacc;  // [N, GF] gradient accumulator, zeroed before the launch
 };
 
-template <int CP>
-struct BwdShared {
-    static constexpr int NF = 13 + CP;
-    static constexpr int STRIDE = NF | 1;
-    int keys[TABLE_SLOTS];
-    float vals[TABLE_SLOTS * STRIDE];
-};
-
-__device__ __forceinline__ unsigned hash_slot(int k) { return ((unsigned)k * 2654435761u) >> 23; }  // 9 bits
-
-template <int CP>
-__device__ __forceinline__ void flush_field(const BwdArgs& a, int k, int f, float v) {
-    if (v == 0.f) return;
-    float* dst;
-    if (f < 3) dst = a.g_means + 3 * k + f;
-    else if (f < 7) dst = a.g_quats + 4 * k + (f - 3);
-    else if (f < 10) dst = a.g_scales + 3 * k + (f - 7);
-    else if (f < 12) dst = a.g_eps + 2 * k + (f - 10);
-    else if (f == 12) dst = a.g_opacity + k;
-    else {
-        if (f - 13 >= a.r.C) return;
-        dst = a.g_logits + (size_t)k * a.r.C + (f - 13);
-    }
-    red_add(dst, v);
+// Lower-bound membership test in a sorted 64-entry shared array padded with INT_MAX.
+__device__ __forceinline__ bool sorted64_has(const int* __restrict__ arr, int key) {
+    int pos = 0;
+#pragma unroll
+    for (int step = 32; step > 0; step >>= 1)
+        if (arr[pos + step - 1] < key) pos += step;
+    return pos < OWN && arr[pos] == key;
 }
 
 template <int CP>
-__global__ void __launch_bounds__(BWD_WARPS * 32) k_backward(BwdArgs a) {
-    using SH = BwdShared<CP>;
+__device__ __forceinline__ float logit_dot(const float* __restrict__ lpad, int k, const float gS[CP]) {
+    const float4* cr = reinterpret_cast<const float4*>(lpad) + (size_t)k * (CP / 4);
+    float cd = 0.f;
+#pragma unroll
+    for (int q = 0; q < CP / 4; ++q) {
+        const float4 c4 = __ldg(cr + q);
+        cd = fmaf(gS[4 * q + 0], c4.x, cd);
+        cd = fmaf(gS[4 * q + 1], c4.y, cd);
+        cd = fmaf(gS[4 * q + 2], c4.z, cd);
+        cd = fmaf(gS[4 * q + 3], c4.w, cd);
+    }
+    return cd;
+}
+
+// Writes the pending flushes of the warp into the accumulator: one coalesced
+// 32-wide atomic add per entry (lane f adds field f).  gsl = gS[lane - 13] of the
+// current ray for the logit fields (dL/dc_k = W_k gS).
+__device__ __forceinline__ void drain_queue(float* __restrict__ gacc, const float* __restrict__ q, int qn, int lane,
+                                            float gsl, int C) {
+    for (int e = 0; e < qn; ++e) {
+        const float* ent = q + e * QW;
+        const int k = __float_as_int(ent[0]);
+        float v = 0.f;
+        if (lane < NGEO) v = ent[1 + lane];
+        else if (lane < NGEO + C) v = ent[1 + NGEO] * gsl;
+        if (v != 0.f) red_add(gacc + (size_t)k * GF + lane, v);
+    }
+}
+
+// Per-warp shared memory of the backward kernel (dynamic; L-dependent part last).
+struct WarpBwd {
+    int keys[2][OWN];
+    float queue[QCAP * QW];
+};
+
+template <int CP>
+__global__ void __launch_bounds__(256, 2) k_backward(BwdArgs A) {
     extern __shared__ __align__(16) unsigned char dyn[];
-    SH& tab = *reinterpret_cast<SH*>(dyn);
-    ChunkSmem* chunks = reinterpret_cast<ChunkSmem*>(dyn + align16(sizeof(SH)));
-    if (*a.r.status != SQ_OK) return;
-    const RenderArgs& ra = a.r;
+    const RenderArgs& a = A.r;
+    if (*a.status != SQ_OK) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    ChunkSmem& sm = chunks[wid];
-    const int L = ra.L;
-    float* samp = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(chunks) + BWD_WARPS * sizeof(ChunkSmem)) +
-                  (size_t)wid * 3 * L;
-    float* sA = samp;          // alpha_j, negated where the clamp is active; reused as w_j
-    float* sV = samp + L;      // v_j; reused as G_j = dL/dalpha_j (0 where clamped)
-    float* sT = samp + 2 * L;  // T_j (transmittance before sample j)
-    const float4* lp4 = reinterpret_cast<const float4*>(ra.lpad);
-    const int tiles_per_cam = a.tiles_x * a.tiles_y;
-    const int n_tiles = tiles_per_cam * ra.n_cam;
+    const int nw = blockDim.x >> 5;
+    const int s = lane & (GS - 1), gbase = lane & ~(GS - 1), g = lane / GS;
+    const int L = a.L;
+    WarpBwd& wb = reinterpret_cast<WarpBwd*>(dyn)[wid];
+    float* samp = reinterpret_cast<float*>(dyn + (size_t)nw * sizeof(WarpBwd)) + (size_t)wid * NG * 3 * L;
+    const unsigned lt = (1u << lane) - 1u;
 
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        for (int s = threadIdx.x; s < TABLE_SLOTS; s += blockDim.x) tab.keys[s] = -1;
-        for (int s = threadIdx.x; s < TABLE_SLOTS * SH::STRIDE; s += blockDim.x) tab.vals[s] = 0.f;
-        __syncthreads();
-        const int cam = tile / tiles_per_cam;
-        const int tl = tile - cam * tiles_per_cam;
-        const int ty = tl / a.tiles_x, tx = tl - ty * a.tiles_x;
-        for (int q = wid; q < BWD_RAYS_X * BWD_RAYS_Y; q += BWD_WARPS) {
-            const int u = tx * BWD_RAYS_X + (q % BWD_RAYS_X), v = ty * BWD_RAYS_Y + (q / BWD_RAYS_X);
-            if (u >= ra.W || v >= ra.H) continue;
-            const long long r = ((long long)cam * ra.H + v) * ra.W + u;
-            float o[3], d[3];
-            pixel_ray(ra.K + 4 * cam, ra.c2w + 12 * cam, u, v, o, d);
-            const float gD = __ldg(a.grad_depth + r);
-            float gS[CP];
-#pragma unroll
-            for (int c = 0; c < CP; ++c) gS[c] = c < ra.C ? __ldg(a.grad_sem + r * ra.C + c) : 0.f;
+    for (;;) {
+        int r0 = 0;
+        if (lane == 0) r0 = atomicAdd(a.ray_ctr, NG);
+        r0 = __shfl_sync(0xffffffffu, r0, 0);
+        if (r0 >= a.R) break;
 
-            // ---- phase 1: replay alpha_j and v_j
-            float T = 1.f;
-            bool done = false;
-            int Leff = 0;
-            for (int j0 = 0; j0 < L && !done;) {
-                int m, pc;
-                bool heavy;
-                chunk_setup(ra, sm, o, d, j0, lane, m, pc, heavy);
-                for (int b = 0; b < pc; b += 32) {
-                    const int gi = b + lane;
-                    const bool valid = gi < pc;
-                    int slot = 0;
-                    float va = 0.f, vs = 0.f;
-                    if (valid) {
-                        int k;
-                        if (!heavy) { k = sm.kbuf[gi]; slot = sm.sidx[gi]; }
-                        else k = __ldg(ra.v_sq + sm.lst[0] + gi);
-                        Prim p = load_prim(ra.rec, k);
-                        float xs[3] = {sm.x[0][slot], sm.x[1][slot], sm.x[2][slot]};
-                        float po = occupancy(p, xs);
-                        const float4* cr = lp4 + (size_t)k * (CP / 4);
-                        float cd = 0.f;
+        // ------------------------------------------------ phase 1: replay (lane = sample)
+        const long long r = (long long)r0 + g;
+        const bool live = r < a.R;
+        float* sA = samp + (size_t)g * 3 * L;  // +-alpha_j (negative where clamped), then w_j
+        float* sV = sA + L;                    // v_j, then G_j = dL/dalpha_j
+        float* sT = sA + 2 * L;                // T_j
+        float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f};
+        float gD = 0.f;
+        float gS[CP];
 #pragma unroll
-                        for (int qq = 0; qq < CP / 4; ++qq) {
-                            float4 cv = __ldg(cr + qq);
-                            cd = fmaf(gS[4 * qq + 0], cv.x, cd);
-                            cd = fmaf(gS[4 * qq + 1], cv.y, cd);
-                            cd = fmaf(gS[4 * qq + 2], cv.z, cd);
-                            cd = fmaf(gS[4 * qq + 3], cv.w, cd);
-                        }
-                        va = po * p.sigma;
-                        vs = po * cd;
-                    }
-                    va = seg_sum(va, slot, lane, valid);
-                    vs = seg_sum(vs, slot, lane, valid);
-                    if (seg_head(slot, lane, valid)) {
-                        sm.asum[slot] += va;
-                        sm.aux[slot] += vs;
-                    }
-                    __syncwarp();
-                }
-                __syncwarp();
-                float raw = (lane < m) ? sm.asum[lane] : 0.f;
-                float alpha = fminf(raw, ra.alpha_max);
-                float Tb;
-                int used;
-                composite(alpha, lane, m, ra.kappa, T, Tb, used, done);
-                if (lane < used) {
-                    const int j = j0 + lane;
-                    // alpha_max > 0, so a clamped alpha is positive and its sign is free
-                    sA[j] = (raw > ra.alpha_max) ? -alpha : alpha;
-                    sV[j] = fmaf(gD, __ldg(ra.t + j), sm.aux[lane]);
-                    sT[j] = Tb;
-                }
-                __syncwarp();
-                j0 += used;
-                Leff = j0;
+        for (int c = 0; c < CP; ++c) gS[c] = 0.f;
+        if (live) {
+            ray_of(a, r, o, d);
+            gD = __ldg(A.grad_depth + r);
+#pragma unroll
+            for (int c = 0; c < CP; ++c)
+                if (c < a.C) gS[c] = __ldg(A.grad_sem + r * a.C + c);
+        }
+        float T = 1.f;
+        int j0 = 0, Leff = 0;
+        bool run = live;
+        while (__any_sync(0xffffffffu, run)) {
+            const int j = j0 + s;
+            const bool valid = run && j < L;
+            float x[3] = {0.f, 0.f, 0.f};
+            int vox = -1;
+            float tj = 0.f;
+            if (valid) {
+                tj = __ldg(a.t + j);
+                vox = sample_voxel(a.g, o, d, tj, x);
             }
-            // ---- phase 2: back-to-front sweep (lane 0), G_j and w_j
-            if (lane == 0) {
-                float U = 0.f;
-                for (int j = Leff - 1; j >= 0; --j) {
-                    float sa = sA[j], vj = sV[j], Tj = sT[j];
-                    bool clamped = sa < 0.f;
-                    float al = fabsf(sa);
-                    float G = clamped ? 0.f : Tj * (vj - U);
-                    U = fmaf(al, vj, (1.f - al) * U);
-                    sV[j] = G;
-                    sA[j] = Tj * al;
+            int n = 0, f = 0;
+            if (vox >= 0) {
+                n = __ldg(a.v_n + vox);
+                f = __ldg(a.v_f + vox);
+            }
+            float asum = 0.f, vsum = 0.f;
+            const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
+            for (int e = 0; e < nmax; ++e) {
+                if (e < n) {
+                    const int k = __ldg(a.v_sq + f + e);
+                    const Prim p = load_prim(a.rec, k);
+                    const float po = occupancy(p, x);
+                    asum = fmaf(po, p.sigma, asum);
+                    vsum = fmaf(po, logit_dot<CP>(a.lpad, k, gS), vsum);
                 }
+            }
+            const float alpha = valid ? fminf(asum, a.alpha_max) : 0.f;
+            float Tb;
+            int used;
+            bool stop;
+            group_composite(alpha, s, gbase, a.kappa, T, Tb, valid, used, stop);
+            if (valid && s < used) {
+                sA[j] = (asum > a.alpha_max) ? -alpha : alpha;
+                sV[j] = fmaf(gD, tj, vsum);
+                sT[j] = Tb;
+            }
+            if (run) {
+                Leff = min(j0 + used, L);
+                j0 += GS;
+                if (j0 >= L || stop || T == 0.f) run = false;
+            }
+        }
+        __syncwarp();
+        // ------------------------------------------------ phase 2: back-to-front sweep
+        if (live && s == 0) {
+            float U = 0.f;
+            for (int j = Leff - 1; j >= 0; --j) {
+                const float sa = sA[j], vj = sV[j], Tj = sT[j];
+                const bool clamped = sa < 0.f;
+                const float al = fabsf(sa);
+                sV[j] = clamped ? 0.f : Tj * (vj - U);
+                U = fmaf(al, vj, (1.f - al) * U);
+                sA[j] = Tj * al;
+            }
+        }
+        __syncwarp();
+        // ------------------------------------------------ phase 3: gradients (lane = owner)
+        for (int gg = 0; gg < NG; ++gg) {
+            const long long rr = (long long)r0 + gg;
+            if (rr >= a.R) break;
+            const int Le = __shfl_sync(0xffffffffu, Leff, gg * GS);
+            const float* wA = samp + (size_t)gg * 3 * L;  // w_j
+            const float* wG = wA + L;                      // G_j
+            float ro[3], rd[3];
+            ray_of(a, rr, ro, rd);
+            float gSr[CP];
+#pragma unroll
+            for (int c = 0; c < CP; ++c) gSr[c] = (c < a.C) ? __ldg(A.grad_sem + rr * a.C + c) : 0.f;
+            const float gsl = (lane >= NGEO && lane < NGEO + a.C) ? __ldg(A.grad_sem + rr * a.C + (lane - NGEO)) : 0.f;
+
+            int key[2] = {-1, -1};
+            float acc[2][14];
+            float cdk[2] = {0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int i = 0; i < 14; ++i) acc[q][i] = 0.f;
+            int* kold = wb.keys[0];
+            int* knew = wb.keys[1];
+            kold[lane] = INT_MAX;
+            kold[lane + 32] = INT_MAX;
+            int qn = 0;
+            __syncwarp();
+
+            for (int j = 0; j <= Le; ++j) {
+                // j == Le: a final empty list flushes every owner
+                float G = 0.f, w = 0.f;
+                int n = 0, f = 0;
+                float x[3] = {0.f, 0.f, 0.f};
+                if (j < Le) {
+                    G = wG[j];
+                    w = wA[j];
+                    if (G == 0.f && w == 0.f) continue;
+                    const int vox = sample_voxel(a.g, ro, rd, __ldg(a.t + j), x);
+                    if (vox >= 0) {
+                        n = __ldg(a.v_n + vox);
+                        f = __ldg(a.v_f + vox);
+                    }
+                }
+                const int m = min(n, OWN);
+                const int kn0 = lane < m ? __ldg(a.v_sq + f + lane) : INT_MAX;
+                const int kn1 = lane + 32 < m ? __ldg(a.v_sq + f + 32 + lane) : INT_MAX;
+                knew[lane] = kn0;
+                knew[lane + 32] = kn1;
+                __syncwarp();
+                // owners whose primitive left the list flush and free their slot
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const bool del = key[q] >= 0 && !sorted64_has(knew, key[q]);
+                    const unsigned dm = __ballot_sync(0xffffffffu, del);
+                    if (dm) {
+                        if (qn + __popc(dm) > QCAP) {
+                            __syncwarp();
+                            drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C);
+                            __syncwarp();
+                            qn = 0;
+                        }
+                        if (del) {
+                            float* ent = wb.queue + (qn + __popc(dm & lt)) * QW;
+                            ent[0] = __int_as_float(key[q]);
+#pragma unroll
+                            for (int i = 0; i < 14; ++i) ent[1 + i] = acc[q][i];
+                            key[q] = -1;
+                        }
+                        qn += __popc(dm);
+                    }
+                }
+                // new entries take free slots in rank order
+                const bool new0 = lane < m && !sorted64_has(kold, kn0);
+                const bool new1 = lane + 32 < m && !sorted64_has(kold, kn1);
+                const unsigned nm0 = __ballot_sync(0xffffffffu, new0), nm1 = __ballot_sync(0xffffffffu, new1);
+                const int c0 = __popc(nm0), nnew = c0 + __popc(nm1);
+                if (nnew) {
+                    const unsigned fr0 = __ballot_sync(0xffffffffu, key[0] < 0);
+                    const unsigned fr1 = __ballot_sync(0xffffffffu, key[1] < 0);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int rk = (q == 0) ? __popc(fr0 & lt) : __popc(fr0) + __popc(fr1 & lt);
+                        const bool want = key[q] < 0 && rk < nnew;
+                        int src = lane;
+                        bool hi = false;
+                        if (want) {
+                            if (rk < c0) src = __fns(nm0, 0, rk + 1);
+                            else { src = __fns(nm1, 0, rk - c0 + 1); hi = true; }
+                        }
+                        const int va = __shfl_sync(0xffffffffu, kn0, src);
+                        const int vb = __shfl_sync(0xffffffffu, kn1, src);
+                        if (want) {
+                            key[q] = hi ? vb : va;
+#pragma unroll
+                            for (int i = 0; i < 14; ++i) acc[q][i] = 0.f;
+                            cdk[q] = logit_dot<CP>(a.lpad, key[q], gSr);
+                        }
+                    }
+                }
+                int* tmp = kold;
+                kold = knew;
+                knew = tmp;
+                if (j == Le) break;
+                // each owner evaluates its pair with sample j
+                const bool any1 = __any_sync(0xffffffffu, key[1] >= 0);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    if (q == 1 && !any1) break;
+                    if (key[q] >= 0) {
+                        const BwdPrim P = load_bwd(a.rec, a.aux, key[q]);
+                        float gg12[12];
+                        const float po = occupancy_grad(P, x, gg12);
+                        if (po != 0.f) {
+                            const float gf = -po * fmaf(G, P.f.sigma, w * cdk[q]);
+#pragma unroll
+                            for (int i = 0; i < 12; ++i) acc[q][i] = fmaf(gf, gg12[i], acc[q][i]);
+                            acc[q][12] = fmaf(G, po, acc[q][12]);
+                            acc[q][13] = fmaf(w, po, acc[q][13]);
+                        }
+                    }
+                }
+                // list entries beyond the owner slots: per-pair atomics
+                for (int e = OWN + lane; e < n; e += 32) {
+                    const int k = __ldg(a.v_sq + f + e);
+                    const BwdPrim P = load_bwd(a.rec, a.aux, k);
+                    float gg12[12];
+                    const float po = occupancy_grad(P, x, gg12);
+                    if (po == 0.f) continue;
+                    const float cd = logit_dot<CP>(a.lpad, k, gSr);
+                    const float gf = -po * fmaf(G, P.f.sigma, w * cd);
+                    float* dst = A.gacc + (size_t)k * GF;
+#pragma unroll
+                    for (int i = 0; i < 12; ++i) red_add(dst + i, gf * gg12[i]);
+                    red_add(dst + 12, G * po);
+#pragma unroll
+                    for (int c = 0; c < CP; ++c)
+                        if (c < a.C) red_add(dst + NGEO + c, w * po * gSr[c]);
+                }
+                __syncwarp();
             }
             __syncwarp();
-            // ---- phase 3: per-pair gradients into the CTA table
-            for (int j0 = 0; j0 < Leff;) {
-                int m, pc;
-                bool heavy;
-                chunk_setup(ra, sm, o, d, j0, lane, m, pc, heavy);
-                if (j0 + m > Leff) m = Leff - j0;  // pairs of samples past termination are skipped below
-                for (int gi = lane; gi < pc; gi += 32) {
-                    int k, slot = 0;
-                    if (!heavy) { k = sm.kbuf[gi]; slot = sm.sidx[gi]; }
-                    else k = __ldg(ra.v_sq + sm.lst[0] + gi);
-                    if (slot >= m) continue;
-                    const int j = j0 + slot;
-                    const float G = sV[j], w = sA[j];
-                    if (G == 0.f && w == 0.f) continue;
-                    BwdPrim P = load_bwd(ra.rec, ra.aux, k);
-                    float xs[3] = {sm.x[0][slot], sm.x[1][slot], sm.x[2][slot]};
-                    float gg[12];
-                    float po = occupancy_grad(P, xs, gg);
-                    if (po == 0.f) continue;
-                    const float4* cr = lp4 + (size_t)k * (CP / 4);
-                    float cv[CP];
-                    float cd = 0.f;
-#pragma unroll
-                    for (int qq = 0; qq < CP / 4; ++qq) {
-                        float4 c4 = __ldg(cr + qq);
-                        cv[4 * qq + 0] = c4.x; cv[4 * qq + 1] = c4.y; cv[4 * qq + 2] = c4.z; cv[4 * qq + 3] = c4.w;
-                        cd = fmaf(gS[4 * qq + 0], c4.x, cd);
-                        cd = fmaf(gS[4 * qq + 1], c4.y, cd);
-                        cd = fmaf(gS[4 * qq + 2], c4.z, cd);
-                        cd = fmaf(gS[4 * qq + 3], c4.w, cd);
-                    }
-                    const float dLdp = fmaf(G, P.f.sigma, w * cd);
-                    const float gf = -po * dLdp;
-                    const float wp = w * po;
-                    // find / claim the table slot of primitive k
-                    unsigned h = hash_slot(k) & (TABLE_SLOTS - 1);
-                    int slotk = -1;
-                    for (int probe = 0; probe < TABLE_SLOTS; ++probe) {
-                        int key = tab.keys[h];
-                        if (key == k) { slotk = (int)h; break; }
-                        if (key == -1) {
-                            int old = atomicCAS(&tab.keys[h], -1, k);
-                            if (old == -1 || old == k) { slotk = (int)h; break; }
-                        }
-                        h = (h + 1) & (TABLE_SLOTS - 1);
-                    }
-                    if (slotk >= 0) {
-                        float* dst = tab.vals + slotk * SH::STRIDE;
-#pragma unroll
-                        for (int f = 0; f < 12; ++f) atomicAdd(dst + f, gf * gg[f]);
-                        atomicAdd(dst + 12, G * po);
-#pragma unroll
-                        for (int c = 0; c < CP; ++c)
-                            if (c < ra.C) atomicAdd(dst + 13 + c, wp * gS[c]);
-                    } else {
-#pragma unroll
-                        for (int f = 0; f < 12; ++f) flush_field<CP>(a, k, f, gf * gg[f]);
-                        flush_field<CP>(a, k, 12, G * po);
-#pragma unroll
-                        for (int c = 0; c < CP; ++c) flush_field<CP>(a, k, 13 + c, wp * gS[c]);
-                    }
-                }
-                __syncwarp();
-                j0 += m;
-            }
+            drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C);
+            __syncwarp();
         }
-        __syncthreads();
-        // flush the tile's table
-        for (int e = threadIdx.x; e < TABLE_SLOTS * SH::NF; e += blockDim.x) {
-            int s = e / SH::NF, f = e - s * SH::NF;
-            int k = tab.keys[s];
-            if (k >= 0) flush_field<CP>(a, k, f, tab.vals[s * SH::STRIDE + f]);
-        }
-        __syncthreads();
+    }
+}
+
+// Scatter of the [N, GF] accumulator into the six gradient outputs.
+__global__ void k_grad_out(const float* __restrict__ gacc, int n, int C, float* __restrict__ gm, float* __restrict__ gq,
+                           float* __restrict__ gs, float* __restrict__ ge, float* __restrict__ go,
+                           float* __restrict__ gl) {
+    const long long total = (long long)n * GF;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / GF), fld = (int)(i - (long long)k * GF);
+        const float v = gacc[i];
+        if (fld < 3) gm[3 * k + fld] = v;
+        else if (fld < 7) gq[4 * k + fld - 3] = v;
+        else if (fld < 10) gs[3 * k + fld - 7] = v;
+        else if (fld < 12) ge[2 * k + fld - 10] = v;
+        else if (fld == 12) go[k] = v;
+        else if (fld - NGEO < C) gl[(size_t)k * C + fld - NGEO] = v;
     }
 }
 
@@ -634,6 +666,14 @@ __global__ void __launch_bounds__(256) k_count_pairs(RenderArgs a, unsigned long
 
 }  // namespace
 
+// ------------------------------------------------------------------ host side
+static int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 152;
+    return sms;
+}
+
 sq_status_t count_pairs_impl(const sq_index_t* idx, const sq_grid_t* grid, const sq_rays_t* rays, long long* out,
                              cudaStream_t st) {
     RenderArgs a{};
@@ -657,7 +697,6 @@ sq_status_t count_pairs_impl(const sq_index_t* idx, const sq_grid_t* grid, const
     return SQ_OK;
 }
 
-// ------------------------------------------------------------------ host side
 sq_status_t launch_pack(const sq_prims_t* prims, float4* rec, float4* aux, float* lpad, int cp, cudaStream_t st) {
     if (prims->n == 0) return SQ_OK;
     k_pack<<<(prims->n + 127) / 128, 128, 0, st>>>(*prims, rec, aux, lpad, cp);
@@ -665,8 +704,10 @@ sq_status_t launch_pack(const sq_prims_t* prims, float4* rec, float4* aux, float
     return SQ_OK;
 }
 
+// Render workspace: packed records, backward extras, padded logits, gradient
+// accumulator [N, 32] and the work counter.
 struct RenderWs {
-    size_t rec_off, aux_off, lpad_off, total;
+    size_t rec_off, aux_off, lpad_off, gacc_off, ctr_off, total;
 };
 
 static RenderWs render_ws(const sq_prims_t* p) {
@@ -676,19 +717,27 @@ static RenderWs render_ws(const sq_prims_t* p) {
     w.rec_off = 0;
     w.aux_off = align_up(n * REC4 * sizeof(float4), 256);
     w.lpad_off = align_up(w.aux_off + n * AUX4 * sizeof(float4), 256);
-    w.total = align_up(w.lpad_off + n * cp * sizeof(float), 256);
-    if (w.total == 0) w.total = 256;
+    w.gacc_off = align_up(w.lpad_off + n * cp * sizeof(float), 256);
+    w.ctr_off = align_up(w.gacc_off + n * GF * sizeof(float), 256);
+    w.total = w.ctr_off + 256;
     return w;
 }
 
 size_t render_workspace_size(const sq_prims_t* p) { return render_ws(p).total; }
 
+size_t render_logits_offset(const sq_prims_t* p) { return render_ws(p).lpad_off; }
+
 static sq_status_t setup_render(const sq_prims_t* prims, const sq_index_t* idx, const sq_grid_t* grid,
                                 const sq_rays_t* rays, void* ws, size_t ws_bytes, cudaStream_t st, bool need_aux,
-                                RenderArgs& a, const char* who) {
+                                RenderArgs& a, float** gacc, const char* who) {
     RenderWs w = render_ws(prims);
     if (ws == nullptr || ws_bytes < w.total) {
         set_last_error("%s: workspace of %zu bytes given, %zu needed", who, ws_bytes, w.total);
+        return SQ_ERR_INVALID_ARG;
+    }
+    const long long R = (long long)rays->n_cam * rays->H * rays->W;
+    if (R >= 2147483647LL - 64) {
+        set_last_error("%s: %lld rays, at most 2^31 - 64 supported per call", who, R);
         return SQ_ERR_INVALID_ARG;
     }
     char* base = (char*)ws;
@@ -698,6 +747,8 @@ static sq_status_t setup_render(const sq_prims_t* prims, const sq_index_t* idx, 
     const int cp = cpad(prims->n_classes);
     sq_status_t s = launch_pack(prims, rec, aux, lpad, cp, st);
     if (s != SQ_OK) return s;
+    cudaError_t e = cudaMemsetAsync(base + w.ctr_off, 0, 256, st);
+    if (e != cudaSuccess) return cuda_status(e, "memset counter");
     a.rec = rec;
     a.aux = (float4*)(base + w.aux_off);
     a.lpad = lpad;
@@ -714,24 +765,30 @@ static sq_status_t setup_render(const sq_prims_t* prims, const sq_index_t* idx, 
     a.W = rays->W;
     a.L = rays->L;
     a.C = prims->n_classes;
-    a.R = (long long)rays->n_cam * rays->H * rays->W;
+    a.R = R;
     a.kappa = rays->kappa;
     a.alpha_max = rays->alpha_max;
+    a.ray_ctr = (int*)(base + w.ctr_off);
+    if (gacc) *gacc = (float*)(base + w.gacc_off);
     return SQ_OK;
 }
 
 template <int CP>
 static sq_status_t launch_fwd_cp(const RenderArgs& a, float* depth, float* sem, float* t_final, cudaStream_t st) {
-    long long want = (a.R + FWD_WARPS - 1) / FWD_WARPS;
-    int blocks = (int)(want < 152LL * 32 ? want : 152LL * 32);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward<CP>, FWD_WARPS * 32, 0);
+    if (e != cudaSuccess) return cuda_status(e, "k_forward occupancy");
+    long long need = (a.R + FWD_WARPS * NG - 1) / (FWD_WARPS * NG);
+    long long blocks = (long long)sm_count() * (per_sm > 0 ? per_sm : 1);
+    if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    k_forward<CP><<<blocks, FWD_WARPS * 32, 0, st>>>(a, depth, sem, t_final);
+    k_forward<CP><<<(int)blocks, FWD_WARPS * 32, 0, st>>>(a, depth, sem, t_final);
     SQ_CHECK_LAUNCH("k_forward");
     return SQ_OK;
 }
 
-#define SQ_DISPATCH_CP(cp, CALL)        \
-    switch (cp) {                       \
+#define SQ_DISPATCH_CP(cp, CALL)                          \
+    switch (cp) {                                         \
         case 4: { constexpr int CPV = 4; return CALL; }   \
         case 8: { constexpr int CPV = 8; return CALL; }   \
         case 12: { constexpr int CPV = 12; return CALL; } \
@@ -740,32 +797,42 @@ static sq_status_t launch_fwd_cp(const RenderArgs& a, float* depth, float* sem, 
         case 24: { constexpr int CPV = 24; return CALL; } \
         case 28: { constexpr int CPV = 28; return CALL; } \
         case 32: { constexpr int CPV = 32; return CALL; } \
-        default: return SQ_ERR_INVALID_ARG;                \
+        default: return SQ_ERR_INVALID_ARG;               \
     }
 
 sq_status_t render_fwd_impl(const sq_prims_t* prims, const sq_index_t* idx, const sq_grid_t* grid,
                             const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* ws,
                             size_t ws_bytes, cudaStream_t st) {
     RenderArgs a;
-    sq_status_t s = setup_render(prims, idx, grid, rays, ws, ws_bytes, st, false, a, "sq_render_fwd");
+    sq_status_t s = setup_render(prims, idx, grid, rays, ws, ws_bytes, st, false, a, nullptr, "sq_render_fwd");
     if (s != SQ_OK) return s;
     if (a.R == 0) return SQ_OK;
     const int cp = cpad(prims->n_classes);
     SQ_DISPATCH_CP(cp, (launch_fwd_cp<CPV>(a, depth, sem, t_final, st)));
 }
 
-template <int CP>
-static size_t bwd_smem_bytes(int L) {
-    return align16(sizeof(BwdShared<CP>)) + BWD_WARPS * sizeof(ChunkSmem) + (size_t)BWD_WARPS * 3 * L * sizeof(float);
+static int bwd_warps(int L) {
+    const size_t per_warp = sizeof(WarpBwd) + (size_t)NG * 3 * L * sizeof(float);
+    int nw = (int)((200 * 1024) / per_warp);
+    if (nw > 8) nw = 8;
+    if (nw < 1) nw = 1;
+    return nw;
 }
 
 template <int CP>
-static sq_status_t launch_bwd_cp(const BwdArgs& a, cudaStream_t st) {
-    size_t smem = bwd_smem_bytes<CP>(a.r.L);
+static sq_status_t launch_bwd_cp(const BwdArgs& A, cudaStream_t st) {
+    const int nw = bwd_warps(A.r.L);
+    const size_t smem = (size_t)nw * (sizeof(WarpBwd) + (size_t)NG * 3 * A.r.L * sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(k_backward<CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e, "k_backward smem attribute");
-    int n_tiles = a.tiles_x * a.tiles_y * a.r.n_cam;
-    k_backward<CP><<<n_tiles, BWD_WARPS * 32, smem, st>>>(a);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward<CP>, nw * 32, smem);
+    if (e != cudaSuccess) return cuda_status(e, "k_backward occupancy");
+    long long need = (A.r.R + (long long)nw * NG - 1) / ((long long)nw * NG);
+    long long blocks = (long long)sm_count() * (per_sm > 0 ? per_sm : 1);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    k_backward<CP><<<(int)blocks, nw * 32, smem, st>>>(A);
     SQ_CHECK_LAUNCH("k_backward");
     return SQ_OK;
 }
@@ -774,31 +841,39 @@ sq_status_t render_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, cons
                             const sq_rays_t* rays, const float* grad_depth, const float* grad_sem, float* g_means,
                             float* g_quats, float* g_scales, float* g_eps, float* g_opacity, float* g_logits,
                             void* ws, size_t ws_bytes, cudaStream_t st) {
-    BwdArgs a;
-    sq_status_t s = setup_render(prims, idx, grid, rays, ws, ws_bytes, st, true, a.r, "sq_render_bwd");
+    BwdArgs A;
+    float* gacc = nullptr;
+    sq_status_t s = setup_render(prims, idx, grid, rays, ws, ws_bytes, st, true, A.r, &gacc, "sq_render_bwd");
     if (s != SQ_OK) return s;
-    const size_t n = (size_t)prims->n;
+    const int n = prims->n;
     const int C = prims->n_classes;
-    struct { float* p; size_t count; } outs[6] = {{g_means, 3 * n}, {g_quats, 4 * n}, {g_scales, 3 * n},
-                                                {g_eps, 2 * n},   {g_opacity, n},    {g_logits, C * n}};
-    for (auto& o : outs) {
-        if (o.count == 0) continue;
-        cudaError_t e = cudaMemsetAsync(o.p, 0, o.count * sizeof(float), st);
-        if (e != cudaSuccess) return cuda_status(e, "memset gradients");
+    if (n == 0) return SQ_OK;
+    cudaError_t e = cudaMemsetAsync(gacc, 0, (size_t)n * GF * sizeof(float), st);
+    if (e != cudaSuccess) return cuda_status(e, "memset gradient accumulator");
+    A.grad_depth = grad_depth;
+    A.grad_sem = grad_sem;
+    A.gacc = gacc;
+    if (A.r.R > 0) {
+        const int cp = cpad(C);
+        sq_status_t ls;
+        switch (cp) {
+            case 4: ls = launch_bwd_cp<4>(A, st); break;
+            case 8: ls = launch_bwd_cp<8>(A, st); break;
+            case 12: ls = launch_bwd_cp<12>(A, st); break;
+            case 16: ls = launch_bwd_cp<16>(A, st); break;
+            case 20: ls = launch_bwd_cp<20>(A, st); break;
+            case 24: ls = launch_bwd_cp<24>(A, st); break;
+            case 28: ls = launch_bwd_cp<28>(A, st); break;
+            case 32: ls = launch_bwd_cp<32>(A, st); break;
+            default: return SQ_ERR_INVALID_ARG;
+        }
+        if (ls != SQ_OK) return ls;
     }
-    if (a.r.R == 0 || n == 0) return SQ_OK;
-    a.grad_depth = grad_depth;
-    a.grad_sem = grad_sem;
-    a.g_means = g_means;
-    a.g_quats = g_quats;
-    a.g_scales = g_scales;
-    a.g_eps = g_eps;
-    a.g_opacity = g_opacity;
-    a.g_logits = g_logits;
-    a.tiles_x = (rays->W + BWD_RAYS_X - 1) / BWD_RAYS_X;
-    a.tiles_y = (rays->H + BWD_RAYS_Y - 1) / BWD_RAYS_Y;
-    const int cp = cpad(C);
-    SQ_DISPATCH_CP(cp, (launch_bwd_cp<CPV>(a, st)));
+    long long total = (long long)n * GF;
+    int blocks = (int)((total + 255) / 256 < 152LL * 16 ? (total + 255) / 256 : 152LL * 16);
+    k_grad_out<<<blocks, 256, 0, st>>>(gacc, n, C, g_means, g_quats, g_scales, g_eps, g_opacity, g_logits);
+    SQ_CHECK_LAUNCH("k_grad_out");
+    return SQ_OK;
 }
 
 }  // namespace sqr
