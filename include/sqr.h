@@ -139,28 +139,40 @@ size_t sq_workspace_size(int op, const sq_prims_t* prims, const sq_grid_t* grid,
 sq_status_t sq_build_index(const sq_prims_t* prims, const sq_grid_t* grid, const sq_index_opts_t* opts,
                            sq_index_t* index, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Bytes of the forward state that sq_render_fwd saves for sq_render_bwd:
+ * T [R, L] FP32 (transmittance before every sample) and the per-ray count of
+ * composited samples [R] int32, each 256-byte aligned.  0 on invalid rays. */
+size_t sq_saved_size(const sq_rays_t* rays);
+
 /* Sec. 3.3.2 forward pass (Eq. 2, 4-6).  Per ray r:
  *   depth[r]   = sum_j w_j t_j,                  w_j = T_j alpha_j, T_j = prod_{l<j} (1 - alpha_l)
  *   sem[r, :]  = sum_j w_j s_j,                  alpha_j = min(sum_k p_o sigma_k, alpha_max),
  *                                                 s_j = sum_k p_o c_k over k in Q(voxel of sample j)
  *   t_final[r] = transmittance after the last composited sample (nullable).
- * With kappa > 0 a ray stops after the first sample whose following T < kappa.
- * Outputs: depth [R], sem [R, n_classes], t_final [R]; R = n_cam*H*W. */
+ * With kappa > 0 a ray stops after the first sample whose following T < kappa;
+ * a ray also stops once T is exactly 0 (all later weights vanish).
+ * t must be non-decreasing (the paper's uniform samples are): a ray that has
+ * left the grid is not followed further.
+ * Outputs: depth [R], sem [R, n_classes], t_final [R]; R = n_cam*H*W.
+ * saved (nullable, sq_saved_size bytes, caller-owned device memory) receives the
+ * state the backward pass needs; pass NULL for inference. */
 sq_status_t sq_render_fwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
-                          const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* workspace,
-                          size_t workspace_bytes, void* stream);
+                          const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* saved,
+                          size_t saved_bytes, void* workspace, size_t workspace_bytes, void* stream);
 
-/* Sec. 3.3.3 backward pass: given dL/d depth [R] and dL/d sem [R, n_classes],
- * overwrites g_means [n,3], g_quats [n,4] (w.r.t. the raw, unnormalised
- * quaternion), g_scales [n,3], g_eps [n,2], g_opacity [n], g_logits [n, C]
- * with dL/d(parameter).  The forward quantities are recomputed (the sample
- * alphas replayed front to back, then swept back to front), so no forward
- * state is needed.  The index is treated as constant.  Where the alpha clamp
- * is active (sum > alpha_max) no gradient flows through that sample's alpha. */
+/* Sec. 3.3.3 backward pass: given dL/d depth [R] and dL/d sem [R, n_classes]
+ * and the state a forward call with the same inputs saved, overwrites
+ * g_means [n,3], g_quats [n,4] (w.r.t. the raw, unnormalised quaternion),
+ * g_scales [n,3], g_eps [n,2], g_opacity [n], g_logits [n, C] with
+ * dL/d(parameter).  Samples are swept back to front, so that
+ * dL/dalpha_j = T_j (v_j - U_j) with v_j = gD t_j + <gS, s_j> and
+ * U_j = alpha_{j+1} v_{j+1} + (1 - alpha_{j+1}) U_{j+1} needs no division by
+ * (1 - alpha).  The index is treated as constant.  Where the alpha clamp is
+ * active (sum > alpha_max) no gradient flows through that sample's alpha. */
 sq_status_t sq_render_bwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
-                          const sq_rays_t* rays, const float* grad_depth, const float* grad_sem, float* g_means,
-                          float* g_quats, float* g_scales, float* g_eps, float* g_opacity, float* g_logits,
-                          void* workspace, size_t workspace_bytes, void* stream);
+                          const sq_rays_t* rays, const void* saved, size_t saved_bytes, const float* grad_depth,
+                          const float* grad_sem, float* g_means, float* g_quats, float* g_scales, float* g_eps,
+                          float* g_opacity, float* g_logits, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Supp. A.4 voxelisation at every voxel centre p = lo + (i + 0.5) vs (FP32):
  *   density[v] = sum_{k in Q(v)} p_o(p, S_k) sigma_k, sem[v, :] = sum p_o c_k,

@@ -108,9 +108,11 @@ size_t render_workspace_size(const sq_prims_t* p);
 sq_status_t build_index_impl(const sq_prims_t*, const sq_grid_t*, const sq_index_opts_t*, sq_index_t*, void*, size_t,
                              cudaStream_t);
 sq_status_t render_fwd_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, const sq_rays_t*, float*, float*,
-                            float*, void*, size_t, cudaStream_t);
-sq_status_t render_bwd_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, const sq_rays_t*, const float*,
-                            const float*, float*, float*, float*, float*, float*, float*, void*, size_t, cudaStream_t);
+                            float*, void*, size_t, void*, size_t, cudaStream_t);
+sq_status_t render_bwd_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, const sq_rays_t*, const void*,
+                            size_t, const float*, const float*, float*, float*, float*, float*, float*, float*, void*,
+                            size_t, cudaStream_t);
+size_t saved_size(const sq_rays_t* r);
 sq_status_t query_grid_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, float, float*, float*,
                             unsigned char*, void*, size_t, cudaStream_t);
 sq_status_t count_pairs_impl(const sq_index_t*, const sq_grid_t*, const sq_rays_t*, long long*, cudaStream_t);
@@ -207,9 +209,14 @@ sq_status_t sq_build_index(const sq_prims_t* prims, const sq_grid_t* grid, const
     return build_index_impl(prims, grid, opts, index, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+size_t sq_saved_size(const sq_rays_t* rays) {
+    if (check_rays(rays) != SQ_OK) return 0;
+    return saved_size(rays);
+}
+
 sq_status_t sq_render_fwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
-                          const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* ws, size_t ws_bytes,
-                          void* stream) {
+                          const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* saved,
+                          size_t saved_bytes, void* ws, size_t ws_bytes, void* stream) {
     sq_status_t s;
     if ((s = check_prims(prims)) != SQ_OK) return s;
     if ((s = check_grid(grid)) != SQ_OK) return s;
@@ -219,11 +226,13 @@ sq_status_t sq_render_fwd(const sq_prims_t* prims, const sq_index_t* index, cons
         set_last_error("sq_render_fwd: depth/sem output is NULL");
         return SQ_ERR_INVALID_ARG;
     }
-    return render_fwd_impl(prims, index, grid, rays, depth, sem, t_final, ws, ws_bytes, (cudaStream_t)stream);
+    return render_fwd_impl(prims, index, grid, rays, depth, sem, t_final, saved, saved_bytes, ws, ws_bytes,
+                           (cudaStream_t)stream);
 }
 
 sq_status_t sq_render_bwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
-                          const sq_rays_t* rays, const float* grad_depth, const float* grad_sem, float* g_means,
+                          const sq_rays_t* rays, const void* saved, size_t saved_bytes, const float* grad_depth,
+                          const float* grad_sem, float* g_means,
                           float* g_quats, float* g_scales, float* g_eps, float* g_opacity, float* g_logits, void* ws,
                           size_t ws_bytes, void* stream) {
     sq_status_t s;
@@ -239,8 +248,8 @@ sq_status_t sq_render_bwd(const sq_prims_t* prims, const sq_index_t* index, cons
         set_last_error("sq_render_bwd: a gradient output is NULL");
         return SQ_ERR_INVALID_ARG;
     }
-    return render_bwd_impl(prims, index, grid, rays, grad_depth, grad_sem, g_means, g_quats, g_scales, g_eps,
-                           g_opacity, g_logits, ws, ws_bytes, (cudaStream_t)stream);
+    return render_bwd_impl(prims, index, grid, rays, saved, saved_bytes, grad_depth, grad_sem, g_means, g_quats,
+                           g_scales, g_eps, g_opacity, g_logits, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 sq_status_t sq_query_grid(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid, float tau,

@@ -27,14 +27,14 @@ namespace sqr {
 
 namespace {
 
-constexpr int GS = 8;         // lanes (samples) per ray in the lane-per-sample layout
-constexpr int NG = 32 / GS;   // rays per warp in that layout
-constexpr int FWD_WARPS = 8;  // warps per CTA, forward
-constexpr int OWN = 64;       // owner slots per warp (two per lane)
-constexpr int QCAP = 64;      // pending gradient flushes per warp
-constexpr int QW = 16;        // words per pending flush: key, 12 geometry, sigma, W, pad
-constexpr int GF = 32;        // floats per primitive in the gradient accumulator
-constexpr int NGEO = 13;      // m3 q4 s3 eps2 sigma1
+constexpr int OWN = 64;     // owner slots per warp (two per lane)
+constexpr int QCAP = 64;    // pending gradient flushes per warp (backward)
+constexpr int QW = 16;      // words per pending flush: key, 12 geometry, sigma, W, pad
+constexpr int FQCAP = 32;   // pending semantic flushes per warp (forward)
+constexpr int GF = 48;      // floats per primitive in the gradient accumulator (13 + up to 32 classes)
+constexpr int NGEO = 13;    // m3 q4 s3 eps2 sigma1
+constexpr int FWD_WARPS = 8;
+constexpr int BWD_WARPS = 8;
 
 // ------------------------------------------------------------------ packing
 __global__ void k_pack(sq_prims_t P, float4* __restrict__ rec, float4* __restrict__ aux, float* __restrict__ lpad,
@@ -49,12 +49,12 @@ __global__ void k_pack(sq_prims_t P, float4* __restrict__ rec, float4* __restric
     R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z); R[0][2] = 2.f * (x * z + w * y);
     R[1][0] = 2.f * (x * y + w * z); R[1][1] = 1.f - 2.f * (x * x + z * z); R[1][2] = 2.f * (y * z - w * x);
     R[2][0] = 2.f * (x * z - w * y); R[2][1] = 2.f * (y * z + w * x); R[2][2] = 1.f - 2.f * (x * x + y * y);
-    float s[3] = {P.scales[3 * k + 0], P.scales[3 * k + 1], P.scales[3 * k + 2]};
+    float is[3] = {1.f / P.scales[3 * k + 0], 1.f / P.scales[3 * k + 1], 1.f / P.scales[3 * k + 2]};
     float e1 = P.eps[2 * k + 0], e2 = P.eps[2 * k + 1];
     float ea = 2.f / e2, eb = e2 / e1, ec = 2.f / e1;
     float M[3][3];
     for (int j = 0; j < 3; ++j)
-        for (int i = 0; i < 3; ++i) M[j][i] = R[i][j] / s[j];
+        for (int i = 0; i < 3; ++i) M[j][i] = R[i][j] * is[j];
     float4* r = rec + (size_t)k * REC4;
     r[0] = make_float4(P.means[3 * k + 0], P.means[3 * k + 1], P.means[3 * k + 2], P.opacity[k]);
     r[1] = make_float4(M[0][0], M[0][1], M[0][2], ea);
@@ -63,7 +63,7 @@ __global__ void k_pack(sq_prims_t P, float4* __restrict__ rec, float4* __restric
     if (aux) {
         float4* a = aux + (size_t)k * AUX4;
         a[0] = make_float4(w, x, y, z);
-        a[1] = make_float4(inq, s[0], s[1], s[2]);
+        a[1] = make_float4(inq, is[0], is[1], is[2]);
         a[2] = make_float4(e1, e2, 1.f / e1, 1.f / e2);
     }
     const int C = P.n_classes;
@@ -86,7 +86,9 @@ struct RenderArgs {
     int n_cam, H, W, L, C;
     long long R;
     float kappa, alpha_max;
-    int* ray_ctr;  // work counter, zeroed before the launch
+    int* ray_ctr;     // work counter, zeroed before the launch
+    float* save_T;    // [R, L] transmittance before each sample (forward writes, backward reads)
+    int* save_n;      // [R] samples composited
 };
 
 __device__ __forceinline__ void ray_of(const RenderArgs& a, long long r, float o[3], float d[3]) {
@@ -97,233 +99,6 @@ __device__ __forceinline__ void ray_of(const RenderArgs& a, long long r, float o
     pixel_ray(a.K + 4 * cam, a.c2w + 12 * cam, u, v, o, d);
 }
 
-// Inclusive product scan within aligned groups of GS lanes.
-__device__ __forceinline__ float group_incl_prod(float v, int s) {
-#pragma unroll
-    for (int o = 1; o < GS; o <<= 1) {
-        float y = __shfl_up_sync(0xffffffffu, v, o, GS);
-        if (s >= o) v *= y;
-    }
-    return v;
-}
-
-// Compositing (Eq. 5) of a group's GS consecutive samples.  Lane s holds alpha
-// (0 for lanes past L or outside the grid).  Returns w = T_before * alpha (0 past
-// an early termination) and T_before; advances T (uniform in the group); `stop`
-// when kappa > 0 ends the ray inside this chunk, `used` = samples composited.
-__device__ __forceinline__ float group_composite(float alpha, int s, int gbase, float kappa, float& T, float& Tb,
-                                                 bool valid, int& used, bool& stop) {
-    const float incl = group_incl_prod(1.f - alpha, s);
-    float excl = __shfl_up_sync(0xffffffffu, incl, 1, GS);
-    if (s == 0) excl = 1.f;
-    Tb = T * excl;
-    float w = Tb * alpha;
-    used = GS;
-    stop = false;
-    const unsigned kill = __ballot_sync(0xffffffffu, valid && kappa > 0.f && T * incl < kappa);
-    const unsigned gk = (kill >> gbase) & ((1u << GS) - 1u);
-    if (gk) {
-        const int ls = __ffs(gk) - 1;
-        if (s > ls) w = 0.f;
-        used = ls + 1;
-        stop = true;
-    }
-    const float tot = __shfl_sync(0xffffffffu, incl, gbase + (gk ? (__ffs(gk) - 1) : GS - 1));
-    T = T * tot;
-    return w;
-}
-
-// ------------------------------------------------------------------ forward
-template <int CP>
-__global__ void __launch_bounds__(FWD_WARPS * 32) k_forward(RenderArgs a, float* __restrict__ depth,
-                                                            float* __restrict__ sem, float* __restrict__ t_final) {
-    if (*a.status != SQ_OK) return;
-    const int lane = threadIdx.x & 31;
-    const int s = lane & (GS - 1), gbase = lane & ~(GS - 1);
-    const float4* lp4 = reinterpret_cast<const float4*>(a.lpad);
-
-    int rn = 0;
-    if (s == 0) rn = atomicAdd(a.ray_ctr, 1);
-    long long r = __shfl_sync(0xffffffffu, rn, gbase);
-    float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f};
-    if (r < a.R) ray_of(a, r, o, d);
-    float T = 1.f, Dp = 0.f;
-    int j0 = 0;
-    float acc[CP];
-#pragma unroll
-    for (int c = 0; c < CP; ++c) acc[c] = 0.f;
-
-    while (__any_sync(0xffffffffu, r < a.R)) {
-        const bool live = r < a.R;
-        const int j = j0 + s;
-        const bool valid = live && j < a.L;
-        float x[3] = {0.f, 0.f, 0.f};
-        int vox = -1;
-        float tj = 0.f;
-        if (valid) {
-            tj = __ldg(a.t + j);
-            vox = sample_voxel(a.g, o, d, tj, x);
-        }
-        int n = 0, f = 0;
-        if (vox >= 0) {
-            n = __ldg(a.v_n + vox);
-            f = __ldg(a.v_f + vox);
-        }
-        float asum = 0.f;
-        float sacc[CP];
-#pragma unroll
-        for (int c = 0; c < CP; ++c) sacc[c] = 0.f;
-        const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
-        for (int e = 0; e < nmax; ++e) {
-            if (e < n) {
-                const int k = __ldg(a.v_sq + f + e);
-                const Prim p = load_prim(a.rec, k);
-                const float po = occupancy(p, x);
-                asum = fmaf(po, p.sigma, asum);
-                const float4* cr = lp4 + (size_t)k * (CP / 4);
-#pragma unroll
-                for (int q = 0; q < CP / 4; ++q) {
-                    const float4 cv = __ldg(cr + q);
-                    sacc[4 * q + 0] = fmaf(po, cv.x, sacc[4 * q + 0]);
-                    sacc[4 * q + 1] = fmaf(po, cv.y, sacc[4 * q + 1]);
-                    sacc[4 * q + 2] = fmaf(po, cv.z, sacc[4 * q + 2]);
-                    sacc[4 * q + 3] = fmaf(po, cv.w, sacc[4 * q + 3]);
-                }
-            }
-        }
-        const float alpha = valid ? fminf(asum, a.alpha_max) : 0.f;
-        float Tb;
-        int used;
-        bool stop;
-        const float w = group_composite(alpha, s, gbase, a.kappa, T, Tb, valid, used, stop);
-        if (valid) {
-            Dp = fmaf(w, tj, Dp);
-#pragma unroll
-            for (int c = 0; c < CP; ++c) acc[c] = fmaf(w, sacc[c], acc[c]);
-        }
-        j0 += GS;
-        // a ray ends at L, on early termination, or once T is exactly 0 (every later weight is 0)
-        const bool fin = live && (j0 >= a.L || stop || T == 0.f);
-        if (__any_sync(0xffffffffu, fin)) {
-            float Dsum = Dp;
-#pragma unroll
-            for (int o2 = GS / 2; o2 > 0; o2 >>= 1) Dsum += __shfl_xor_sync(0xffffffffu, Dsum, o2, GS);
-#pragma unroll
-            for (int c = 0; c < CP; ++c) {
-                float v = acc[c];
-#pragma unroll
-                for (int o2 = GS / 2; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2, GS);
-                if (fin && (c % GS) == s && c < a.C) sem[r * a.C + c] = v;
-            }
-            if (fin && s == 0) {
-                depth[r] = Dsum;
-                if (t_final) t_final[r] = T;
-            }
-            int nr = 0;
-            if (fin && s == 0) nr = atomicAdd(a.ray_ctr, 1);
-            nr = __shfl_sync(0xffffffffu, nr, gbase);
-            if (fin) {
-                r = nr;
-                if (r < a.R) ray_of(a, r, o, d);
-                T = 1.f;
-                Dp = 0.f;
-                j0 = 0;
-#pragma unroll
-                for (int c = 0; c < CP; ++c) acc[c] = 0.f;
-            }
-        }
-    }
-}
-
-// ------------------------------------------------------------------ backward
-struct BwdPrim {
-    Prim f;
-    float qn[4];
-    float inv_qn;
-    float s[3];
-    float e1, e2, ie1, ie2;
-};
-
-__device__ __forceinline__ BwdPrim load_bwd(const float4* __restrict__ rec, const float4* __restrict__ aux, int k) {
-    BwdPrim b;
-    b.f = load_prim(rec, k);
-    const float4* a = aux + (size_t)k * AUX4;
-    float4 a0 = __ldg(a + 0), a1 = __ldg(a + 1), a2 = __ldg(a + 2);
-    b.qn[0] = a0.x; b.qn[1] = a0.y; b.qn[2] = a0.z; b.qn[3] = a0.w;
-    b.inv_qn = a1.x; b.s[0] = a1.y; b.s[1] = a1.z; b.s[2] = a1.w;
-    b.e1 = a2.x; b.e2 = a2.y; b.ie1 = a2.z; b.ie2 = a2.w;
-    return b;
-}
-
-// df/d(parameters) at point x.  Outputs p_o and the 12 geometric partials
-// g[0..2] = df/dm, g[3..6] = df/dq (raw quaternion), g[7..9] = df/ds, g[10..11] = df/d(eps1, eps2).
-__device__ __forceinline__ float occupancy_grad(const BwdPrim& P, const float x[3], float g[12]) {
-    const Prim& p = P.f;
-    float d[3] = {x[0] - p.m[0], x[1] - p.m[1], x[2] - p.m[2]};
-    float u[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) u[j] = fmaf(p.M[j][0], d[0], fmaf(p.M[j][1], d[1], p.M[j][2] * d[2]));
-    float la = lg2(fabsf(u[0])), lb = lg2(fabsf(u[1])), lc = lg2(fabsf(u[2]));
-    float pa = ex2(p.ea * la), pb = ex2(p.ea * lb), pc = ex2(p.ec * lc);
-    float A = pa + pb;
-    float lA = lg2(A);
-    float PA = ex2(p.eb * lA);
-    float f = PA + pc;
-    float po = ex2(-f * LOG2E);
-
-    float rA = A > 0.f ? rcp(A) : 0.f;
-    float t0 = p.ec * PA * rA;
-    float ta = t0 * pa, tb = t0 * pb, tc = p.ec * pc;  // = dfu_j * u_j
-    float dfu[3];
-    dfu[0] = u[0] != 0.f ? ta * rcp(u[0]) : 0.f;
-    dfu[1] = u[1] != 0.f ? tb * rcp(u[1]) : 0.f;
-    dfu[2] = u[2] != 0.f ? tc * rcp(u[2]) : 0.f;
-    // d f / d x (world) = sum_j dfu_j M_j ; df/dm = -that
-    float gd[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) gd[i] = dfu[0] * p.M[0][i] + dfu[1] * p.M[1][i] + dfu[2] * p.M[2][i];
-    g[0] = -gd[0]; g[1] = -gd[1]; g[2] = -gd[2];
-    // scales: u_j = (R^T d)_j / s_j  =>  df/ds_j = -dfu_j u_j / s_j
-    g[7] = -ta / P.s[0];
-    g[8] = -tb / P.s[1];
-    g[9] = -tc / P.s[2];
-    // exponents
-    float e1term = (PA > 0.f ? p.eb * PA * lA : 0.f) + (pc > 0.f ? p.ec * pc * lc : 0.f);
-    g[10] = -LN2 * P.ie1 * e1term;
-    float pl = (pa > 0.f ? pa * la : 0.f) + (pb > 0.f ? pb * lb : 0.f);
-    g[11] = PA > 0.f ? PA * LN2 * (lA * P.ie1 - p.ec * P.ie2 * pl * rA) : 0.f;
-    // rotation: x_S = R^T d, df/dxS_j = dfu_j / s_j, df/dR_ij = d_i df/dxS_j
-    float gl[3] = {dfu[0] / P.s[0], dfu[1] / P.s[1], dfu[2] / P.s[2]};
-    float gR[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) gR[3 * i + j] = d[i] * gl[j];
-    const float w = P.qn[0], qx = P.qn[1], qy = P.qn[2], qz = P.qn[3];
-    float gq[4];
-    gq[0] = 2.f * (-qz * gR[1] + qy * gR[2] + qz * gR[3] - qx * gR[5] - qy * gR[6] + qx * gR[7]);
-    gq[1] = 2.f * (qy * gR[1] + qz * gR[2] + qy * gR[3] - 2.f * qx * gR[4] - w * gR[5] + qz * gR[6] + w * gR[7] -
-                   2.f * qx * gR[8]);
-    gq[2] = 2.f * (-2.f * qy * gR[0] + qx * gR[1] + w * gR[2] + qx * gR[3] + qz * gR[5] - w * gR[6] + qz * gR[7] -
-                   2.f * qy * gR[8]);
-    gq[3] = 2.f * (-2.f * qz * gR[0] - w * gR[1] + qx * gR[2] + w * gR[3] - 2.f * qz * gR[4] + qy * gR[5] +
-                   qx * gR[6] + qy * gR[7]);
-    float dot = gq[0] * w + gq[1] * qx + gq[2] * qy + gq[3] * qz;
-    g[3] = (gq[0] - w * dot) * P.inv_qn;
-    g[4] = (gq[1] - qx * dot) * P.inv_qn;
-    g[5] = (gq[2] - qy * dot) * P.inv_qn;
-    g[6] = (gq[3] - qz * dot) * P.inv_qn;
-    return po;
-}
-
-
-struct BwdArgs {
-    RenderArgs r;
-    const float* grad_depth;
-    const float* grad_sem;
-    float* gacc;  // [N, GF] gradient accumulator, zeroed before the launch
-};
-
 // Lower-bound membership test in a sorted 64-entry shared array padded with INT_MAX.
 __device__ __forceinline__ bool sorted64_has(const int* __restrict__ arr, int key) {
     int pos = 0;
@@ -333,282 +108,485 @@ __device__ __forceinline__ bool sorted64_has(const int* __restrict__ arr, int ke
     return pos < OWN && arr[pos] == key;
 }
 
+// ------------------------------------------------------------------ owner slots
+// The primitives of the current sample's list (its first OWN entries, ascending)
+// are owned by lane slots (lane, q), q = 0, 1.  Moving to the next sample's list:
+// owners whose primitive is absent leave (on_leave(q) is called on that lane and
+// the slot is freed), then the list's new primitives take free slots in rank
+// order (on_enter(q, k)).  kold holds the previous list, knew the current one,
+// both sorted and padded with INT_MAX; the caller swaps them afterwards.
+template <class Leave, class Enter>
+__device__ __forceinline__ void owners_update(int key[2], const int* __restrict__ kold, const int* __restrict__ knew,
+                                              int m, int kn0, int kn1, int lane, unsigned lt, Leave&& on_leave,
+                                              Enter&& on_enter) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const bool del = key[q] >= 0 && !sorted64_has(knew, key[q]);
+        on_leave(q, del, __ballot_sync(0xffffffffu, del));
+        if (del) key[q] = -1;
+    }
+    const bool new0 = lane < m && !sorted64_has(kold, kn0);
+    const bool new1 = lane + 32 < m && !sorted64_has(kold, kn1);
+    const unsigned nm0 = __ballot_sync(0xffffffffu, new0), nm1 = __ballot_sync(0xffffffffu, new1);
+    const int c0 = __popc(nm0), nnew = c0 + __popc(nm1);
+    if (nnew == 0) return;
+    const unsigned fr0 = __ballot_sync(0xffffffffu, key[0] < 0);
+    const unsigned fr1 = __ballot_sync(0xffffffffu, key[1] < 0);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int rk = (q == 0) ? __popc(fr0 & lt) : __popc(fr0) + __popc(fr1 & lt);
+        const bool want = key[q] < 0 && rk < nnew;
+        int src = lane;
+        bool hi = false;
+        if (want) {
+            if (rk < c0) src = __fns(nm0, 0, rk + 1);
+            else { src = __fns(nm1, 0, rk - c0 + 1); hi = true; }
+        }
+        const int va = __shfl_sync(0xffffffffu, kn0, src);
+        const int vb = __shfl_sync(0xffffffffu, kn1, src);
+        if (want) {
+            key[q] = hi ? vb : va;
+            on_enter(q, key[q]);
+        }
+    }
+}
+
+// Loads the first min(n, OWN) entries of a voxel list into knew (padded) and
+// returns them per lane (entries lane and lane + 32).
+__device__ __forceinline__ int load_list(const int* __restrict__ v_sq, int f, int m, int lane, int* knew, int& kn1) {
+    const int kn0 = lane < m ? __ldg(v_sq + f + lane) : INT_MAX;
+    kn1 = lane + 32 < m ? __ldg(v_sq + f + 32 + lane) : INT_MAX;
+    knew[lane] = kn0;
+    knew[lane + 32] = kn1;
+    __syncwarp();
+    return kn0;
+}
+
 template <int CP>
-__device__ __forceinline__ float logit_dot(const float* __restrict__ lpad, int k, const float gS[CP]) {
+__device__ __forceinline__ void add_logits(float acc[CP], const float* __restrict__ lpad, int k, float wgt) {
+    const float4* cr = reinterpret_cast<const float4*>(lpad) + (size_t)k * (CP / 4);
+#pragma unroll
+    for (int q = 0; q < CP / 4; ++q) {
+        const float4 cv = __ldg(cr + q);
+        acc[4 * q + 0] = fmaf(wgt, cv.x, acc[4 * q + 0]);
+        acc[4 * q + 1] = fmaf(wgt, cv.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(wgt, cv.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(wgt, cv.w, acc[4 * q + 3]);
+    }
+}
+
+// ------------------------------------------------------------------ forward
+// One warp per ray, samples front to back.  Owners keep W_k = sum_j w_j p_jk of
+// their primitive; when it leaves, (k, W_k) is queued and later folded into the
+// lane-local semantic accumulator as W_k c_k (Eq. 6 regrouped by primitive).
+struct WarpFwd {
+    int keys[2][OWN];
+    int qk[FQCAP];
+    float qw[FQCAP];
+};
+
+template <int CP>
+__global__ void __launch_bounds__(FWD_WARPS * 32) k_forward(RenderArgs a, float* __restrict__ depth,
+                                                            float* __restrict__ sem, float* __restrict__ t_final) {
+    __shared__ WarpFwd smem[FWD_WARPS];
+    if (*a.status != SQ_OK) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    WarpFwd& sm = smem[wid];
+
+    for (;;) {
+        int rr = 0;
+        if (lane == 0) rr = atomicAdd(a.ray_ctr, 1);
+        const long long r = __shfl_sync(0xffffffffu, rr, 0);
+        if (r >= a.R) break;
+        float o[3], d[3];
+        ray_of(a, r, o, d);
+        float acc[CP];
+#pragma unroll
+        for (int c = 0; c < CP; ++c) acc[c] = 0.f;
+        int key[2] = {-1, -1};
+        float Wk[2] = {0.f, 0.f};
+        int* kold = sm.keys[0];
+        int* knew = sm.keys[1];
+        kold[lane] = INT_MAX;
+        kold[lane + 32] = INT_MAX;
+        int qn = 0;
+        float T = 1.f, D = 0.f;
+        bool inside_seen = false;
+        int used = 0;
+        __syncwarp();
+
+        auto drain = [&]() {
+            __syncwarp();
+            if (lane < qn) add_logits<CP>(acc, a.lpad, sm.qk[lane], sm.qw[lane]);
+            __syncwarp();
+            qn = 0;
+        };
+        auto leave = [&](int q, bool del, unsigned dm) {
+            if (!dm) return;
+            if (qn + __popc(dm) > FQCAP) drain();
+            if (del) {
+                const int pos = qn + __popc(dm & lt);
+                sm.qk[pos] = key[q];
+                sm.qw[pos] = Wk[q];
+            }
+            qn += __popc(dm);
+        };
+        auto enter = [&](int q, int) { Wk[q] = 0.f; };
+
+        for (int j = 0; j <= a.L; ++j) {
+            // j == L: an empty list releases every owner
+            int n = 0, f = 0;
+            float x[3] = {0.f, 0.f, 0.f};
+            float tj = 0.f;
+            bool last = (j == a.L);
+            if (!last) {
+                tj = __ldg(a.t + j);
+                const int vox = sample_voxel(a.g, o, d, tj, x);
+                if (vox >= 0) {
+                    n = __ldg(a.v_n + vox);
+                    f = __ldg(a.v_f + vox);
+                    inside_seen = true;
+                } else if (inside_seen) {
+                    last = true;  // samples are non-decreasing in t: the ray has left the grid for good
+                }
+                if (a.save_T && lane == 0) a.save_T[r * a.L + j] = T;
+            }
+            const bool owners = __any_sync(0xffffffffu, key[0] >= 0 || key[1] >= 0);
+            if (n == 0 && !owners) {
+                if (last) { used = j; break; }
+                used = j + 1;
+                continue;  // empty sample with no owners: alpha = 0, T unchanged
+            }
+            const int m = min(n, OWN);
+            int kn1;
+            const int kn0 = load_list(a.v_sq, f, m, lane, knew, kn1);
+            owners_update(key, kold, knew, m, kn0, kn1, lane, lt, leave, enter);
+            int* tmp = kold; kold = knew; knew = tmp;
+            if (last) { used = j; break; }
+            // occupancies of owned pairs, alpha = sum p sigma
+            float po[2] = {0.f, 0.f};
+            float part = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (key[q] >= 0) {
+                    const Prim p = load_prim(a.rec, key[q]);
+                    po[q] = occupancy(p, x);
+                    part = fmaf(po[q], p.sigma, part);
+                }
+            }
+            for (int e = OWN + lane; e < n; e += 32) {
+                const Prim p = load_prim(a.rec, __ldg(a.v_sq + f + e));
+                part = fmaf(occupancy(p, x), p.sigma, part);
+            }
+            const float raw = warp_sum(part);
+            const float alpha = fminf(raw, a.alpha_max);
+            const float w = T * alpha;
+            D = fmaf(w, tj, D);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) Wk[q] = fmaf(w, po[q], Wk[q]);
+            for (int e = OWN + lane; e < n; e += 32) {
+                const int k = __ldg(a.v_sq + f + e);
+                const Prim p = load_prim(a.rec, k);
+                add_logits<CP>(acc, a.lpad, k, w * occupancy(p, x));
+            }
+            T = T * (1.f - alpha);
+            used = j + 1;
+            __syncwarp();
+            if ((a.kappa > 0.f && T < a.kappa) || T == 0.f) {
+                // terminated: release every owner through an empty list
+                knew[lane] = INT_MAX;
+                knew[lane + 32] = INT_MAX;
+                __syncwarp();
+                owners_update(key, kold, knew, 0, INT_MAX, INT_MAX, lane, lt, leave, enter);
+                break;
+            }
+        }
+        drain();
+#pragma unroll
+        for (int c = 0; c < CP; ++c) {
+            const float v = warp_sum(acc[c]);
+            if (lane == c && c < a.C) sem[r * a.C + c] = v;
+        }
+        if (lane == 0) {
+            depth[r] = D;
+            if (t_final) t_final[r] = T;
+            if (a.save_n) a.save_n[r] = used;
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ backward
+struct BwdPrim {
+    Prim f;
+    float qn[4];
+    float inv_qn;
+    float is[3];  // 1 / s
+    float e1, e2, ie1, ie2;
+};
+
+__device__ __forceinline__ BwdPrim load_bwd(const float4* __restrict__ rec, const float4* __restrict__ aux, int k) {
+    BwdPrim b;
+    b.f = load_prim(rec, k);
+    const float4* a = aux + (size_t)k * AUX4;
+    float4 a0 = __ldg(a + 0), a1 = __ldg(a + 1), a2 = __ldg(a + 2);
+    b.qn[0] = a0.x; b.qn[1] = a0.y; b.qn[2] = a0.z; b.qn[3] = a0.w;
+    b.inv_qn = a1.x; b.is[0] = a1.y; b.is[1] = a1.z; b.is[2] = a1.w;
+    b.e1 = a2.x; b.e2 = a2.y; b.ie1 = a2.z; b.ie2 = a2.w;
+    return b;
+}
+
+// p_o and df/d(parameters) at point x.  g[0..2] = df/dm, g[3..6] = df/dq (raw,
+// unnormalised quaternion), g[7..9] = df/ds, g[10..11] = df/d(eps1, eps2).
+//   u_j = (R^T (x - m))_j / s_j,  a = |u_0|, b = |u_1|, c = |u_2|,
+//   f = A^eb + c^ec with A = a^ea + b^ea (ea = 2/eps2, eb = eps2/eps1, ec = 2/eps1),
+//   u_j df/du_j = ec A^(eb-1) a^ea (j = 0), likewise b (j = 1), ec c^ec (j = 2);
+//   the rotation part uses x_S = d - 2w (v x d) + 2 v (v.d) - 2 d (v.v) for q = (w, v).
+__device__ __forceinline__ float occupancy_grad(const BwdPrim& P, const float x[3], float g[12]) {
+    const Prim& p = P.f;
+    const float d[3] = {x[0] - p.m[0], x[1] - p.m[1], x[2] - p.m[2]};
+    float u[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) u[j] = fmaf(p.M[j][0], d[0], fmaf(p.M[j][1], d[1], p.M[j][2] * d[2]));
+    const float la = lg2(fabsf(u[0])), lb = lg2(fabsf(u[1])), lc = lg2(fabsf(u[2]));
+    const float pa = ex2(p.ea * la), pb = ex2(p.ea * lb), pc = ex2(p.ec * lc);
+    const float A = pa + pb;
+    const float lA = lg2(A);
+    const float PA = ex2(p.eb * lA);
+    const float po = ex2(-(PA + pc) * LOG2E);
+
+    const float rA = A > 0.f ? rcp(A) : 0.f;
+    const float t0 = p.ec * PA * rA;
+    const float tu[3] = {t0 * pa, t0 * pb, p.ec * pc};  // u_j df/du_j
+    float dfu[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dfu[j] = u[j] != 0.f ? tu[j] * rcp(u[j]) : 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) g[i] = -(dfu[0] * p.M[0][i] + dfu[1] * p.M[1][i] + dfu[2] * p.M[2][i]);
+    // s_j enters through u_j = x_S,j / s_j: df/ds_j = -u_j df/du_j / s_j
+#pragma unroll
+    for (int j = 0; j < 3; ++j) g[7 + j] = -tu[j] * P.is[j];
+    // exponents
+    const float e1term = (PA > 0.f ? p.eb * PA * lA : 0.f) + (pc > 0.f ? p.ec * pc * lc : 0.f);
+    g[10] = -LN2 * P.ie1 * e1term;
+    const float pl = (pa > 0.f ? pa * la : 0.f) + (pb > 0.f ? pb * lb : 0.f);
+    g[11] = PA > 0.f ? PA * LN2 * (lA * P.ie1 - p.ec * P.ie2 * pl * rA) : 0.f;
+    // rotation: gl = df/dx_S
+    const float gl[3] = {dfu[0] * P.is[0], dfu[1] * P.is[1], dfu[2] * P.is[2]};
+    const float w = P.qn[0];
+    const float v[3] = {P.qn[1], P.qn[2], P.qn[3]};
+    const float cx[3] = {d[1] * gl[2] - d[2] * gl[1], d[2] * gl[0] - d[0] * gl[2], d[0] * gl[1] - d[1] * gl[0]};
+    const float vd = v[0] * d[0] + v[1] * d[1] + v[2] * d[2];
+    const float gv = gl[0] * v[0] + gl[1] * v[1] + gl[2] * v[2];
+    const float gd = gl[0] * d[0] + gl[1] * d[1] + gl[2] * d[2];
+    const float gw = -2.f * (v[0] * cx[0] + v[1] * cx[1] + v[2] * cx[2]);
+    float gu[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gu[i] = 2.f * (-w * cx[i] + vd * gl[i] + gv * d[i] - 2.f * gd * v[i]);
+    const float dot = w * gw + v[0] * gu[0] + v[1] * gu[1] + v[2] * gu[2];
+    g[3] = (gw - w * dot) * P.inv_qn;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) g[4 + i] = (gu[i] - v[i] * dot) * P.inv_qn;
+    return po;
+}
+
+struct BwdArgs {
+    RenderArgs r;
+    const float* grad_depth;
+    const float* grad_sem;
+    float* gacc;  // [N, GF] gradient accumulator, zeroed before the launch
+};
+
+template <int CP>
+__device__ __forceinline__ float logit_dot(const float* __restrict__ lpad, int k, const float* __restrict__ gS, int C) {
     const float4* cr = reinterpret_cast<const float4*>(lpad) + (size_t)k * (CP / 4);
     float cd = 0.f;
 #pragma unroll
     for (int q = 0; q < CP / 4; ++q) {
         const float4 c4 = __ldg(cr + q);
-        cd = fmaf(gS[4 * q + 0], c4.x, cd);
-        cd = fmaf(gS[4 * q + 1], c4.y, cd);
-        cd = fmaf(gS[4 * q + 2], c4.z, cd);
-        cd = fmaf(gS[4 * q + 3], c4.w, cd);
+        const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (4 * q + i < C) cd = fmaf(__ldg(gS + 4 * q + i), cc[i], cd);
     }
     return cd;
 }
 
-// Writes the pending flushes of the warp into the accumulator: one coalesced
-// 32-wide atomic add per entry (lane f adds field f).  gsl = gS[lane - 13] of the
-// current ray for the logit fields (dL/dc_k = W_k gS).
+// Writes the pending flushes of the warp into the accumulator: coalesced atomic
+// adds, lane f adding field f (and f + 32 when C > 19).  gsl[b] = gS[32 b + lane - 13]
+// of the current ray for the logit fields (dL/dc_k = W_k gS).
 __device__ __forceinline__ void drain_queue(float* __restrict__ gacc, const float* __restrict__ q, int qn, int lane,
-                                            float gsl, int C) {
+                                            const float gsl[2], int C) {
     for (int e = 0; e < qn; ++e) {
         const float* ent = q + e * QW;
         const int k = __float_as_int(ent[0]);
+        float* row = gacc + (size_t)k * GF;
         float v = 0.f;
         if (lane < NGEO) v = ent[1 + lane];
-        else if (lane < NGEO + C) v = ent[1 + NGEO] * gsl;
-        if (v != 0.f) red_add(gacc + (size_t)k * GF + lane, v);
+        else if (lane < NGEO + C) v = ent[1 + NGEO] * gsl[0];
+        if (v != 0.f) red_add(row + lane, v);
+        if (NGEO + C > 32 && lane + 32 < NGEO + C) {
+            const float v2 = ent[1 + NGEO] * gsl[1];
+            if (v2 != 0.f) red_add(row + 32 + lane, v2);
+        }
     }
 }
 
-// Per-warp shared memory of the backward kernel (dynamic; L-dependent part last).
 struct WarpBwd {
     int keys[2][OWN];
     float queue[QCAP * QW];
 };
 
+// One warp per ray, samples back to front (Sec. 3.3.3): with T_j saved by the
+// forward, U_j is carried from the back, so one sweep gives alpha_j, v_j, G_j and
+// every pair's gradient.
 template <int CP>
-__global__ void __launch_bounds__(256, 2) k_backward(BwdArgs A) {
-    extern __shared__ __align__(16) unsigned char dyn[];
+__global__ void __launch_bounds__(BWD_WARPS * 32, 2) k_backward(BwdArgs A) {
+    __shared__ WarpBwd smem[BWD_WARPS];
     const RenderArgs& a = A.r;
     if (*a.status != SQ_OK) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    const int s = lane & (GS - 1), gbase = lane & ~(GS - 1), g = lane / GS;
-    const int L = a.L;
-    WarpBwd& wb = reinterpret_cast<WarpBwd*>(dyn)[wid];
-    float* samp = reinterpret_cast<float*>(dyn + (size_t)nw * sizeof(WarpBwd)) + (size_t)wid * NG * 3 * L;
     const unsigned lt = (1u << lane) - 1u;
+    WarpBwd& wb = smem[wid];
 
     for (;;) {
-        int r0 = 0;
-        if (lane == 0) r0 = atomicAdd(a.ray_ctr, NG);
-        r0 = __shfl_sync(0xffffffffu, r0, 0);
-        if (r0 >= a.R) break;
+        int rr = 0;
+        if (lane == 0) rr = atomicAdd(a.ray_ctr, 1);
+        const long long r = __shfl_sync(0xffffffffu, rr, 0);
+        if (r >= a.R) break;
+        const int Le = __ldg(a.save_n + r);
+        float o[3], d[3];
+        ray_of(a, r, o, d);
+        const float gD = __ldg(A.grad_depth + r);
+        const float* gS = A.grad_sem + r * a.C;
+        float gsl[2];
+        gsl[0] = (lane >= NGEO && lane < NGEO + a.C) ? __ldg(gS + (lane - NGEO)) : 0.f;
+        gsl[1] = (lane + 32 < NGEO + a.C) ? __ldg(gS + (lane + 32 - NGEO)) : 0.f;
 
-        // ------------------------------------------------ phase 1: replay (lane = sample)
-        const long long r = (long long)r0 + g;
-        const bool live = r < a.R;
-        float* sA = samp + (size_t)g * 3 * L;  // +-alpha_j (negative where clamped), then w_j
-        float* sV = sA + L;                    // v_j, then G_j = dL/dalpha_j
-        float* sT = sA + 2 * L;                // T_j
-        float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f};
-        float gD = 0.f;
-        float gS[CP];
+        int key[2] = {-1, -1};
+        float acc[2][14];
+        float cdk[2] = {0.f, 0.f};
 #pragma unroll
-        for (int c = 0; c < CP; ++c) gS[c] = 0.f;
-        if (live) {
-            ray_of(a, r, o, d);
-            gD = __ldg(A.grad_depth + r);
+        for (int q = 0; q < 2; ++q)
 #pragma unroll
-            for (int c = 0; c < CP; ++c)
-                if (c < a.C) gS[c] = __ldg(A.grad_sem + r * a.C + c);
-        }
-        float T = 1.f;
-        int j0 = 0, Leff = 0;
-        bool run = live;
-        while (__any_sync(0xffffffffu, run)) {
-            const int j = j0 + s;
-            const bool valid = run && j < L;
-            float x[3] = {0.f, 0.f, 0.f};
-            int vox = -1;
-            float tj = 0.f;
-            if (valid) {
-                tj = __ldg(a.t + j);
-                vox = sample_voxel(a.g, o, d, tj, x);
+            for (int i = 0; i < 14; ++i) acc[q][i] = 0.f;
+        int* kold = wb.keys[0];
+        int* knew = wb.keys[1];
+        kold[lane] = INT_MAX;
+        kold[lane + 32] = INT_MAX;
+        int qn = 0;
+        float U = 0.f;
+        __syncwarp();
+
+        auto leave = [&](int q, bool del, unsigned dm) {
+            if (!dm) return;
+            if (qn + __popc(dm) > QCAP) {
+                __syncwarp();
+                drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C);
+                __syncwarp();
+                qn = 0;
             }
+            if (del) {
+                float* ent = wb.queue + (qn + __popc(dm & lt)) * QW;
+                ent[0] = __int_as_float(key[q]);
+#pragma unroll
+                for (int i = 0; i < 14; ++i) ent[1 + i] = acc[q][i];
+            }
+            qn += __popc(dm);
+        };
+        auto enter = [&](int q, int k) {
+#pragma unroll
+            for (int i = 0; i < 14; ++i) acc[q][i] = 0.f;
+            cdk[q] = logit_dot<CP>(a.lpad, k, gS, a.C);
+        };
+
+        for (int j = Le - 1; j >= -1; --j) {
+            // j == -1: an empty list releases every owner
             int n = 0, f = 0;
-            if (vox >= 0) {
-                n = __ldg(a.v_n + vox);
-                f = __ldg(a.v_f + vox);
-            }
-            float asum = 0.f, vsum = 0.f;
-            const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
-            for (int e = 0; e < nmax; ++e) {
-                if (e < n) {
-                    const int k = __ldg(a.v_sq + f + e);
-                    const Prim p = load_prim(a.rec, k);
-                    const float po = occupancy(p, x);
-                    asum = fmaf(po, p.sigma, asum);
-                    vsum = fmaf(po, logit_dot<CP>(a.lpad, k, gS), vsum);
+            float x[3] = {0.f, 0.f, 0.f};
+            float tj = 0.f;
+            if (j >= 0) {
+                tj = __ldg(a.t + j);
+                const int vox = sample_voxel(a.g, o, d, tj, x);
+                if (vox >= 0) {
+                    n = __ldg(a.v_n + vox);
+                    f = __ldg(a.v_f + vox);
                 }
             }
-            const float alpha = valid ? fminf(asum, a.alpha_max) : 0.f;
-            float Tb;
-            int used;
-            bool stop;
-            group_composite(alpha, s, gbase, a.kappa, T, Tb, valid, used, stop);
-            if (valid && s < used) {
-                sA[j] = (asum > a.alpha_max) ? -alpha : alpha;
-                sV[j] = fmaf(gD, tj, vsum);
-                sT[j] = Tb;
+            const bool owners = __any_sync(0xffffffffu, key[0] >= 0 || key[1] >= 0);
+            if (n == 0 && !owners) {
+                if (j < 0) break;
+                continue;  // no primitive here: alpha_j = 0 leaves U unchanged
             }
-            if (run) {
-                Leff = min(j0 + used, L);
-                j0 += GS;
-                if (j0 >= L || stop || T == 0.f) run = false;
+            const int m = min(n, OWN);
+            int kn1;
+            const int kn0 = load_list(a.v_sq, f, m, lane, knew, kn1);
+            owners_update(key, kold, knew, m, kn0, kn1, lane, lt, leave, enter);
+            int* tmp = kold; kold = knew; knew = tmp;
+            if (j < 0) break;
+            if (n == 0) {
+                __syncwarp();
+                continue;
             }
+            // owned pairs: occupancy and its partials; alpha_j and <gS, s_j> by warp sums
+            float po[2] = {0.f, 0.f};
+            float gg[2][12];
+            float pa = 0.f, pv = 0.f;
+            float sig[2] = {0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (key[q] >= 0) {
+                    const BwdPrim P = load_bwd(a.rec, a.aux, key[q]);
+                    po[q] = occupancy_grad(P, x, gg[q]);
+                    sig[q] = P.f.sigma;
+                    pa = fmaf(po[q], sig[q], pa);
+                    pv = fmaf(po[q], cdk[q], pv);
+                }
+            }
+            for (int e = OWN + lane; e < n; e += 32) {
+                const int k = __ldg(a.v_sq + f + e);
+                const Prim p = load_prim(a.rec, k);
+                const float pe = occupancy(p, x);
+                pa = fmaf(pe, p.sigma, pa);
+                pv = fmaf(pe, logit_dot<CP>(a.lpad, k, gS, a.C), pv);
+            }
+            const float raw = warp_sum(pa);
+            const float vs = warp_sum(pv);
+            const float alpha = fminf(raw, a.alpha_max);
+            const float Tj = __ldg(a.save_T + r * a.L + j);
+            const float vj = fmaf(gD, tj, vs);
+            const float G = raw > a.alpha_max ? 0.f : Tj * (vj - U);  // dL/dalpha_j
+            const float w = Tj * alpha;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (key[q] >= 0 && po[q] != 0.f) {
+                    const float gf = -po[q] * fmaf(G, sig[q], w * cdk[q]);
+#pragma unroll
+                    for (int i = 0; i < 12; ++i) acc[q][i] = fmaf(gf, gg[q][i], acc[q][i]);
+                    acc[q][12] = fmaf(G, po[q], acc[q][12]);
+                    acc[q][13] = fmaf(w, po[q], acc[q][13]);
+                }
+            }
+            for (int e = OWN + lane; e < n; e += 32) {
+                const int k = __ldg(a.v_sq + f + e);
+                const BwdPrim P = load_bwd(a.rec, a.aux, k);
+                float g12[12];
+                const float pe = occupancy_grad(P, x, g12);
+                if (pe == 0.f) continue;
+                const float gf = -pe * fmaf(G, P.f.sigma, w * logit_dot<CP>(a.lpad, k, gS, a.C));
+                float* dst = A.gacc + (size_t)k * GF;
+#pragma unroll
+                for (int i = 0; i < 12; ++i) red_add(dst + i, gf * g12[i]);
+                red_add(dst + 12, G * pe);
+                for (int c = 0; c < a.C; ++c) red_add(dst + NGEO + c, w * pe * __ldg(gS + c));
+            }
+            U = fmaf(alpha, vj, (1.f - alpha) * U);
+            __syncwarp();
         }
         __syncwarp();
-        // ------------------------------------------------ phase 2: back-to-front sweep
-        if (live && s == 0) {
-            float U = 0.f;
-            for (int j = Leff - 1; j >= 0; --j) {
-                const float sa = sA[j], vj = sV[j], Tj = sT[j];
-                const bool clamped = sa < 0.f;
-                const float al = fabsf(sa);
-                sV[j] = clamped ? 0.f : Tj * (vj - U);
-                U = fmaf(al, vj, (1.f - al) * U);
-                sA[j] = Tj * al;
-            }
-        }
+        drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C);
         __syncwarp();
-        // ------------------------------------------------ phase 3: gradients (lane = owner)
-        for (int gg = 0; gg < NG; ++gg) {
-            const long long rr = (long long)r0 + gg;
-            if (rr >= a.R) break;
-            const int Le = __shfl_sync(0xffffffffu, Leff, gg * GS);
-            const float* wA = samp + (size_t)gg * 3 * L;  // w_j
-            const float* wG = wA + L;                      // G_j
-            float ro[3], rd[3];
-            ray_of(a, rr, ro, rd);
-            float gSr[CP];
-#pragma unroll
-            for (int c = 0; c < CP; ++c) gSr[c] = (c < a.C) ? __ldg(A.grad_sem + rr * a.C + c) : 0.f;
-            const float gsl = (lane >= NGEO && lane < NGEO + a.C) ? __ldg(A.grad_sem + rr * a.C + (lane - NGEO)) : 0.f;
-
-            int key[2] = {-1, -1};
-            float acc[2][14];
-            float cdk[2] = {0.f, 0.f};
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-#pragma unroll
-                for (int i = 0; i < 14; ++i) acc[q][i] = 0.f;
-            int* kold = wb.keys[0];
-            int* knew = wb.keys[1];
-            kold[lane] = INT_MAX;
-            kold[lane + 32] = INT_MAX;
-            int qn = 0;
-            __syncwarp();
-
-            for (int j = 0; j <= Le; ++j) {
-                // j == Le: a final empty list flushes every owner
-                float G = 0.f, w = 0.f;
-                int n = 0, f = 0;
-                float x[3] = {0.f, 0.f, 0.f};
-                if (j < Le) {
-                    G = wG[j];
-                    w = wA[j];
-                    if (G == 0.f && w == 0.f) continue;
-                    const int vox = sample_voxel(a.g, ro, rd, __ldg(a.t + j), x);
-                    if (vox >= 0) {
-                        n = __ldg(a.v_n + vox);
-                        f = __ldg(a.v_f + vox);
-                    }
-                }
-                const int m = min(n, OWN);
-                const int kn0 = lane < m ? __ldg(a.v_sq + f + lane) : INT_MAX;
-                const int kn1 = lane + 32 < m ? __ldg(a.v_sq + f + 32 + lane) : INT_MAX;
-                knew[lane] = kn0;
-                knew[lane + 32] = kn1;
-                __syncwarp();
-                // owners whose primitive left the list flush and free their slot
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const bool del = key[q] >= 0 && !sorted64_has(knew, key[q]);
-                    const unsigned dm = __ballot_sync(0xffffffffu, del);
-                    if (dm) {
-                        if (qn + __popc(dm) > QCAP) {
-                            __syncwarp();
-                            drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C);
-                            __syncwarp();
-                            qn = 0;
-                        }
-                        if (del) {
-                            float* ent = wb.queue + (qn + __popc(dm & lt)) * QW;
-                            ent[0] = __int_as_float(key[q]);
-#pragma unroll
-                            for (int i = 0; i < 14; ++i) ent[1 + i] = acc[q][i];
-                            key[q] = -1;
-                        }
-                        qn += __popc(dm);
-                    }
-                }
-                // new entries take free slots in rank order
-                const bool new0 = lane < m && !sorted64_has(kold, kn0);
-                const bool new1 = lane + 32 < m && !sorted64_has(kold, kn1);
-                const unsigned nm0 = __ballot_sync(0xffffffffu, new0), nm1 = __ballot_sync(0xffffffffu, new1);
-                const int c0 = __popc(nm0), nnew = c0 + __popc(nm1);
-                if (nnew) {
-                    const unsigned fr0 = __ballot_sync(0xffffffffu, key[0] < 0);
-                    const unsigned fr1 = __ballot_sync(0xffffffffu, key[1] < 0);
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int rk = (q == 0) ? __popc(fr0 & lt) : __popc(fr0) + __popc(fr1 & lt);
-                        const bool want = key[q] < 0 && rk < nnew;
-                        int src = lane;
-                        bool hi = false;
-                        if (want) {
-                            if (rk < c0) src = __fns(nm0, 0, rk + 1);
-                            else { src = __fns(nm1, 0, rk - c0 + 1); hi = true; }
-                        }
-                        const int va = __shfl_sync(0xffffffffu, kn0, src);
-                        const int vb = __shfl_sync(0xffffffffu, kn1, src);
-                        if (want) {
-                            key[q] = hi ? vb : va;
-#pragma unroll
-                            for (int i = 0; i < 14; ++i) acc[q][i] = 0.f;
-                            cdk[q] = logit_dot<CP>(a.lpad, key[q], gSr);
-                        }
-                    }
-                }
-                int* tmp = kold;
-                kold = knew;
-                knew = tmp;
-                if (j == Le) break;
-                // each owner evaluates its pair with sample j
-                const bool any1 = __any_sync(0xffffffffu, key[1] >= 0);
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    if (q == 1 && !any1) break;
-                    if (key[q] >= 0) {
-                        const BwdPrim P = load_bwd(a.rec, a.aux, key[q]);
-                        float gg12[12];
-                        const float po = occupancy_grad(P, x, gg12);
-                        if (po != 0.f) {
-                            const float gf = -po * fmaf(G, P.f.sigma, w * cdk[q]);
-#pragma unroll
-                            for (int i = 0; i < 12; ++i) acc[q][i] = fmaf(gf, gg12[i], acc[q][i]);
-                            acc[q][12] = fmaf(G, po, acc[q][12]);
-                            acc[q][13] = fmaf(w, po, acc[q][13]);
-                        }
-                    }
-                }
-                // list entries beyond the owner slots: per-pair atomics
-                for (int e = OWN + lane; e < n; e += 32) {
-                    const int k = __ldg(a.v_sq + f + e);
-                    const BwdPrim P = load_bwd(a.rec, a.aux, k);
-                    float gg12[12];
-                    const float po = occupancy_grad(P, x, gg12);
-                    if (po == 0.f) continue;
-                    const float cd = logit_dot<CP>(a.lpad, k, gSr);
-                    const float gf = -po * fmaf(G, P.f.sigma, w * cd);
-                    float* dst = A.gacc + (size_t)k * GF;
-#pragma unroll
-                    for (int i = 0; i < 12; ++i) red_add(dst + i, gf * gg12[i]);
-                    red_add(dst + 12, G * po);
-#pragma unroll
-                    for (int c = 0; c < CP; ++c)
-                        if (c < a.C) red_add(dst + NGEO + c, w * po * gSr[c]);
-                }
-                __syncwarp();
-            }
-            __syncwarp();
-            drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C);
-            __syncwarp();
-        }
     }
 }
 
@@ -769,22 +747,44 @@ static sq_status_t setup_render(const sq_prims_t* prims, const sq_index_t* idx, 
     a.kappa = rays->kappa;
     a.alpha_max = rays->alpha_max;
     a.ray_ctr = (int*)(base + w.ctr_off);
+    a.save_T = nullptr;
+    a.save_n = nullptr;
     if (gacc) *gacc = (float*)(base + w.gacc_off);
     return SQ_OK;
 }
 
+// Saved forward state: T [R, L] (transmittance before each sample) then n [R].
+size_t saved_size(const sq_rays_t* r) {
+    const size_t R = (size_t)r->n_cam * r->H * r->W;
+    return align_up(R * r->L * sizeof(float), 256) + align_up(R * sizeof(int), 256);
+}
+
+static void saved_ptrs(const sq_rays_t* r, void* saved, float** T, int** n) {
+    const size_t R = (size_t)r->n_cam * r->H * r->W;
+    *T = (float*)saved;
+    *n = (int*)((char*)saved + align_up(R * r->L * sizeof(float), 256));
+}
+
 template <int CP>
-static sq_status_t launch_fwd_cp(const RenderArgs& a, float* depth, float* sem, float* t_final, cudaStream_t st) {
+static sq_status_t launch_persistent(const void* fn, int threads, size_t smem, long long work, int per_block,
+                                     void** args, cudaStream_t st, const char* who) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward<CP>, FWD_WARPS * 32, 0);
-    if (e != cudaSuccess) return cuda_status(e, "k_forward occupancy");
-    long long need = (a.R + FWD_WARPS * NG - 1) / (FWD_WARPS * NG);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    if (e != cudaSuccess) return cuda_status(e, who);
+    long long need = (work + per_block - 1) / per_block;
     long long blocks = (long long)sm_count() * (per_sm > 0 ? per_sm : 1);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    k_forward<CP><<<(int)blocks, FWD_WARPS * 32, 0, st>>>(a, depth, sem, t_final);
-    SQ_CHECK_LAUNCH("k_forward");
+    e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(threads), args, smem, st);
+    if (e != cudaSuccess) return cuda_status(e, who);
     return SQ_OK;
+}
+
+template <int CP>
+static sq_status_t launch_fwd_cp(RenderArgs a, float* depth, float* sem, float* t_final, cudaStream_t st) {
+    void* args[] = {&a, &depth, &sem, &t_final};
+    return launch_persistent<CP>((const void*)k_forward<CP>, FWD_WARPS * 32, 0, a.R, FWD_WARPS, args, st,
+                                 "k_forward");
 }
 
 #define SQ_DISPATCH_CP(cp, CALL)                          \
@@ -801,50 +801,41 @@ static sq_status_t launch_fwd_cp(const RenderArgs& a, float* depth, float* sem, 
     }
 
 sq_status_t render_fwd_impl(const sq_prims_t* prims, const sq_index_t* idx, const sq_grid_t* grid,
-                            const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* ws,
-                            size_t ws_bytes, cudaStream_t st) {
+                            const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* saved,
+                            size_t saved_bytes, void* ws, size_t ws_bytes, cudaStream_t st) {
     RenderArgs a;
+    if (saved && saved_bytes < saved_size(rays)) {
+        set_last_error("sq_render_fwd: saved state of %zu bytes given, %zu needed", saved_bytes, saved_size(rays));
+        return SQ_ERR_INVALID_ARG;
+    }
     sq_status_t s = setup_render(prims, idx, grid, rays, ws, ws_bytes, st, false, a, nullptr, "sq_render_fwd");
     if (s != SQ_OK) return s;
+    if (saved) saved_ptrs(rays, saved, &a.save_T, &a.save_n);
     if (a.R == 0) return SQ_OK;
     const int cp = cpad(prims->n_classes);
     SQ_DISPATCH_CP(cp, (launch_fwd_cp<CPV>(a, depth, sem, t_final, st)));
 }
 
-static int bwd_warps(int L) {
-    const size_t per_warp = sizeof(WarpBwd) + (size_t)NG * 3 * L * sizeof(float);
-    int nw = (int)((200 * 1024) / per_warp);
-    if (nw > 8) nw = 8;
-    if (nw < 1) nw = 1;
-    return nw;
-}
-
 template <int CP>
-static sq_status_t launch_bwd_cp(const BwdArgs& A, cudaStream_t st) {
-    const int nw = bwd_warps(A.r.L);
-    const size_t smem = (size_t)nw * (sizeof(WarpBwd) + (size_t)NG * 3 * A.r.L * sizeof(float));
-    cudaError_t e = cudaFuncSetAttribute(k_backward<CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_status(e, "k_backward smem attribute");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward<CP>, nw * 32, smem);
-    if (e != cudaSuccess) return cuda_status(e, "k_backward occupancy");
-    long long need = (A.r.R + (long long)nw * NG - 1) / ((long long)nw * NG);
-    long long blocks = (long long)sm_count() * (per_sm > 0 ? per_sm : 1);
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
-    k_backward<CP><<<(int)blocks, nw * 32, smem, st>>>(A);
-    SQ_CHECK_LAUNCH("k_backward");
-    return SQ_OK;
+static sq_status_t launch_bwd_cp(BwdArgs A, cudaStream_t st) {
+    void* args[] = {&A};
+    return launch_persistent<CP>((const void*)k_backward<CP>, BWD_WARPS * 32, 0, A.r.R, BWD_WARPS, args, st,
+                                 "k_backward");
 }
 
 sq_status_t render_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, const sq_grid_t* grid,
-                            const sq_rays_t* rays, const float* grad_depth, const float* grad_sem, float* g_means,
-                            float* g_quats, float* g_scales, float* g_eps, float* g_opacity, float* g_logits,
-                            void* ws, size_t ws_bytes, cudaStream_t st) {
+                            const sq_rays_t* rays, const void* saved, size_t saved_bytes, const float* grad_depth,
+                            const float* grad_sem, float* g_means, float* g_quats, float* g_scales, float* g_eps,
+                            float* g_opacity, float* g_logits, void* ws, size_t ws_bytes, cudaStream_t st) {
     BwdArgs A;
+    if (!saved || saved_bytes < saved_size(rays)) {
+        set_last_error("sq_render_bwd: saved state of %zu bytes given, %zu needed", saved_bytes, saved_size(rays));
+        return SQ_ERR_INVALID_ARG;
+    }
     float* gacc = nullptr;
     sq_status_t s = setup_render(prims, idx, grid, rays, ws, ws_bytes, st, true, A.r, &gacc, "sq_render_bwd");
     if (s != SQ_OK) return s;
+    saved_ptrs(rays, const_cast<void*>(saved), &A.r.save_T, &A.r.save_n);
     const int n = prims->n;
     const int C = prims->n_classes;
     if (n == 0) return SQ_OK;

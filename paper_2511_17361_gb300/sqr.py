@@ -64,10 +64,12 @@ def _load():
     lib.sq_workspace_size.restype = ctypes.c_size_t
     lib.sq_workspace_size.argtypes = [ctypes.c_int, P(SqPrims), P(SqGrid), P(SqRays)]
     lib.sq_build_index.argtypes = [P(SqPrims), P(SqGrid), P(SqIndexOpts), P(SqIndex), _vp, ctypes.c_size_t, _vp]
+    lib.sq_saved_size.restype = ctypes.c_size_t
+    lib.sq_saved_size.argtypes = [P(SqRays)]
     lib.sq_render_fwd.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), P(SqRays), _vp, _vp, _vp, _vp, ctypes.c_size_t,
-                                  _vp]
-    lib.sq_render_bwd.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), P(SqRays), _vp, _vp, _vp, _vp, _vp, _vp, _vp,
-                                  _vp, _vp, ctypes.c_size_t, _vp]
+                                  _vp, ctypes.c_size_t, _vp]
+    lib.sq_render_bwd.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), P(SqRays), _vp, ctypes.c_size_t, _vp, _vp, _vp,
+                                  _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
     lib.sq_query_grid.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), ctypes.c_float, _vp, _vp, _vp, _vp,
                                   ctypes.c_size_t, _vp]
     lib.sq_loss_ce_mse.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_float,
@@ -148,6 +150,9 @@ class Rays:
     @staticmethod
     def from_rig(rig: dict, t, device="cuda", kappa=0.0, alpha_max=1.0) -> "Rays":
         f = lambda a: torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
+        t_host = torch.as_tensor(t, dtype=torch.float32)
+        if t_host.numel() > 1 and bool((t_host[1:] < t_host[:-1]).any()):
+            raise SqrError("sample depths t must be non-decreasing")
         return Rays(f(rig["K"]), f(rig["cam2world"]), f(t), int(rig["H"]), int(rig["W"]), kappa, alpha_max)
 
 
@@ -233,8 +238,16 @@ def build_index(prims: dict, grid: dict, mode: int = SQ_INDEX_OBB, tau_cut: floa
 
 
 # ------------------------------------------------------------------ render
-def render_fwd(prims: dict, index: Index, grid: dict, rays: Rays, out=None):
-    """Returns depth [R], sem [R, C], t_final [R] (Eq. 4-6)."""
+def saved_size(rays: Rays) -> int:
+    """Bytes of forward state the backward pass needs (T per sample, samples per ray)."""
+    r = rays.struct()
+    return int(lib.sq_saved_size(ctypes.byref(r)))
+
+
+def render_fwd(prims: dict, index: Index, grid: dict, rays: Rays, out=None, saved=None):
+    """Returns depth [R], sem [R, C], t_final [R] (Eq. 4-6).  ``saved``: a uint8
+    device tensor of saved_size(rays) bytes that receives the state for
+    render_bwd, or None (inference)."""
     device = prims["means"].device
     C = prims["logits"].shape[1]
     R = rays.R
@@ -244,24 +257,34 @@ def render_fwd(prims: dict, index: Index, grid: dict, rays: Rays, out=None):
     p, g, r, ix = prims_struct(prims), grid_struct(grid), rays.struct(), index.struct()
     wsz = lib.sq_workspace_size(SQ_OP_FWD, ctypes.byref(p), ctypes.byref(g), ctypes.byref(r))
     ws = _ws.get("fwd", wsz, device)
+    sv_n = 0 if saved is None else saved.numel() * saved.element_size()
     _check(lib.sq_render_fwd(ctypes.byref(p), ctypes.byref(ix), ctypes.byref(g), ctypes.byref(r), _ptr(depth),
-                             _ptr(sem), _ptr(tf), _ptr(ws), ws.numel(), _stream()), "sq_render_fwd")
+                             _ptr(sem), _ptr(tf), _ptr(saved), sv_n, _ptr(ws), ws.numel(), _stream()),
+           "sq_render_fwd")
     return depth, sem, tf
 
 
-def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, grad_sem, out=None) -> dict:
-    """Gradients of sum(gD * depth) + sum(gS * sem) w.r.t. every parameter."""
+def new_saved(rays: Rays, device="cuda"):
+    return torch.empty(saved_size(rays), dtype=torch.uint8, device=device)
+
+
+def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, grad_sem, saved=None, out=None) -> dict:
+    """Gradients of sum(gD * depth) + sum(gS * sem) w.r.t. every parameter.  ``saved``
+    comes from render_fwd on the same inputs; when None the forward is run here."""
     device = prims["means"].device
     grad_depth = _need_cuda_f32(grad_depth.contiguous(), "grad_depth")
     grad_sem = _need_cuda_f32(grad_sem.contiguous(), "grad_sem")
+    if saved is None:
+        saved = new_saved(rays, device)
+        render_fwd(prims, index, grid, rays, saved=saved)
     if out is None:
         out = {k: torch.empty_like(prims[k]) for k in PRIM_KEYS}
     p, g, r, ix = prims_struct(prims), grid_struct(grid), rays.struct(), index.struct()
     wsz = lib.sq_workspace_size(SQ_OP_BWD, ctypes.byref(p), ctypes.byref(g), ctypes.byref(r))
     ws = _ws.get("bwd", wsz, device)
-    _check(lib.sq_render_bwd(ctypes.byref(p), ctypes.byref(ix), ctypes.byref(g), ctypes.byref(r), _ptr(grad_depth),
-                             _ptr(grad_sem), *[_ptr(out[k]) for k in PRIM_KEYS], _ptr(ws), ws.numel(), _stream()),
-           "sq_render_bwd")
+    _check(lib.sq_render_bwd(ctypes.byref(p), ctypes.byref(ix), ctypes.byref(g), ctypes.byref(r), _ptr(saved),
+                             saved.numel() * saved.element_size(), _ptr(grad_depth), _ptr(grad_sem),
+                             *[_ptr(out[k]) for k in PRIM_KEYS], _ptr(ws), ws.numel(), _stream()), "sq_render_bwd")
     return out
 
 
@@ -311,19 +334,21 @@ class SQRender(torch.autograd.Function):
     @staticmethod
     def forward(ctx, means, quats, scales, eps, opacity, logits, index: Index, grid: dict, rays: Rays):
         prims = dict(zip(PRIM_KEYS, (t.contiguous() for t in (means, quats, scales, eps, opacity, logits))))
-        depth, sem, _ = render_fwd(prims, index, grid, rays)
-        ctx.save_for_backward(*[prims[k] for k in PRIM_KEYS])
+        saved = new_saved(rays, means.device)
+        depth, sem, _ = render_fwd(prims, index, grid, rays, saved=saved)
+        ctx.save_for_backward(*[prims[k] for k in PRIM_KEYS], saved)
         ctx.index, ctx.grid, ctx.rays = index, grid, rays
         return depth, sem
 
     @staticmethod
     def backward(ctx, g_depth, g_sem):
-        prims = dict(zip(PRIM_KEYS, ctx.saved_tensors))
+        prims = dict(zip(PRIM_KEYS, ctx.saved_tensors[:6]))
+        saved = ctx.saved_tensors[6]
         if g_depth is None:
             g_depth = torch.zeros(ctx.rays.R, device=prims["means"].device)
         if g_sem is None:
             g_sem = torch.zeros((ctx.rays.R, prims["logits"].shape[1]), device=prims["means"].device)
-        g = render_bwd(prims, ctx.index, ctx.grid, ctx.rays, g_depth, g_sem)
+        g = render_bwd(prims, ctx.index, ctx.grid, ctx.rays, g_depth, g_sem, saved=saved)
         return (g["means"], g["quats"], g["scales"], g["eps"], g["opacity"], g["logits"], None, None, None)
 
 

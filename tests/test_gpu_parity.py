@@ -201,8 +201,8 @@ def test_forward_cube_index(sqr):
 
 
 # ----------------------------------------------------------------------- backward
-def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0):
-    prims_d, rays = scene_to_gpu(sqr, prims, rig, t, 0.0, alpha_max)
+def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0, kappa=0.0):
+    prims_d, rays = scene_to_gpu(sqr, prims, rig, t, kappa, alpha_max)
     g = dev_grid(grid)
     ix = sqr.build_index(prims_d, g)
     R = rays.R
@@ -214,14 +214,16 @@ def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0):
     out = sqr.render_bwd(prims_d, ix, g, rays, torch.from_numpy(gd_full).cuda(), torch.from_numpy(gs_full).cuda())
     torch.cuda.synchronize()
     ref = oracle.render_bwd(prims, grid, np_index(ix), rig, t, gd_full[sel].astype(np.float64),
-                            gs_full[sel].astype(np.float64), alpha_max=alpha_max,
+                            gs_full[sel].astype(np.float64), alpha_max=alpha_max, kappa=kappa,
                             ray_ids=None if ray_ids is None else sel)
     return {k: v.cpu().numpy() for k, v in out.items()}, ref
 
 
-@pytest.mark.parametrize("seed", [0, 1])
+@pytest.mark.parametrize("seed", [0, 1, 2])
 def test_backward_small_scene_full(sqr, seed):
-    pr, grid, rig, t = small_scene(seed, n=8, H=9, W=11, L=32, C=[5, 18][seed], sigma_max=0.6)
+    """Every gradient of a small scene, for 5, 18 and 32 classes (the logit
+    gradients of 32 classes span two 32-lane blocks of the accumulator)."""
+    pr, grid, rig, t = small_scene(seed, n=8, H=9, W=11, L=32, C=[5, 18, 32][seed], sigma_max=0.6)
     R = 9 * 11
     rng = np.random.default_rng(seed)
     gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, pr["logits"].shape[1])).astype(
@@ -237,6 +239,28 @@ def test_backward_clamp_active(sqr):
     rng = np.random.default_rng(6)
     gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, 5)).astype(np.float32)
     got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs)
+    for k in ref:
+        check_grad(got[k], ref[k], k)
+
+
+def test_backward_early_termination(sqr):
+    """kappa > 0: gradients flow only through the composited samples; cotangents on
+    rays whose T stays clear of kappa (1e-4 relative) at every sample."""
+    cfg = synth.make_config(0)
+    kappa = 1e-2
+    ix_ref = oracle.build_index(cfg["prims"], cfg["grid"])
+    D, S, T, NU = oracle.render_fwd(cfg["prims"], cfg["grid"], ix_ref, cfg["rig"], cfg["t"], kappa=kappa)
+    safe = []
+    for r in range(0, len(D), 7):
+        tr = oracle.trace_ray(cfg["prims"], cfg["grid"], ix_ref, cfg["rig"], cfg["t"], r, kappa=kappa)
+        if not np.any(np.abs(tr["T"][:tr["used"] + 1] - kappa) < 1e-4 * kappa):
+            safe.append(r)
+    safe = np.array(safe)
+    assert (NU[safe] < 48).sum() > 20
+    rng = np.random.default_rng(8)
+    gd = rng.standard_normal(len(safe)).astype(np.float32)
+    gs = rng.standard_normal((len(safe), 18)).astype(np.float32)
+    got, ref = _bwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], gd, gs, ray_ids=safe, kappa=kappa)
     for k in ref:
         check_grad(got[k], ref[k], k)
 
