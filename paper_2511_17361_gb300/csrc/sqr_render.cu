@@ -27,10 +27,10 @@ namespace sqr {
 
 namespace {
 
+constexpr int GS = 8;       // lanes (samples) per ray in the forward
 constexpr int OWN = 64;     // owner slots per warp (two per lane)
 constexpr int QCAP = 64;    // pending gradient flushes per warp (backward)
 constexpr int QW = 16;      // words per pending flush: key, 12 geometry, sigma, W, pad
-constexpr int FQCAP = 32;   // pending semantic flushes per warp (forward)
 constexpr int GF = 48;      // floats per primitive in the gradient accumulator (13 + up to 32 classes)
 constexpr int NGEO = 13;    // m3 q4 s3 eps2 sigma1
 constexpr int FWD_WARPS = 8;
@@ -99,251 +99,186 @@ __device__ __forceinline__ void ray_of(const RenderArgs& a, long long r, float o
     pixel_ray(a.K + 4 * cam, a.c2w + 12 * cam, u, v, o, d);
 }
 
-// Lower-bound membership test in a sorted 64-entry shared array padded with INT_MAX.
-__device__ __forceinline__ bool sorted64_has(const int* __restrict__ arr, int key) {
-    int pos = 0;
+// Inclusive product scan within aligned groups of GS lanes.
+__device__ __forceinline__ float group_incl_prod(float v, int s) {
 #pragma unroll
-    for (int step = 32; step > 0; step >>= 1)
-        if (arr[pos + step - 1] < key) pos += step;
-    return pos < OWN && arr[pos] == key;
+    for (int o = 1; o < GS; o <<= 1) {
+        float y = __shfl_up_sync(0xffffffffu, v, o, GS);
+        if (s >= o) v *= y;
+    }
+    return v;
 }
 
-// ------------------------------------------------------------------ owner slots
-// The primitives of the current sample's list (its first OWN entries, ascending)
-// are owned by lane slots (lane, q), q = 0, 1.  Moving to the next sample's list:
-// owners whose primitive is absent leave (on_leave(q) is called on that lane and
-// the slot is freed), then the list's new primitives take free slots in rank
-// order (on_enter(q, k)).  kold holds the previous list, knew the current one,
-// both sorted and padded with INT_MAX; the caller swaps them afterwards.
-template <class Leave, class Enter>
-__device__ __forceinline__ void owners_update(int key[2], const int* __restrict__ kold, const int* __restrict__ knew,
-                                              int m, int kn0, int kn1, int lane, unsigned lt, Leave&& on_leave,
-                                              Enter&& on_enter) {
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const bool del = key[q] >= 0 && !sorted64_has(knew, key[q]);
-        on_leave(q, del, __ballot_sync(0xffffffffu, del));
-        if (del) key[q] = -1;
+// Compositing (Eq. 5) of a group's GS consecutive samples.  Lane s holds alpha
+// (0 for lanes past L or outside the grid).  Returns w = T_before * alpha (0 past
+// an early termination) and T_before; advances T (uniform in the group); `stop`
+// when kappa > 0 ends the ray inside this chunk, `used` = samples composited.
+__device__ __forceinline__ float group_composite(float alpha, int s, int gbase, float kappa, float& T, float& Tb,
+                                                 bool valid, int& used, bool& stop) {
+    const float incl = group_incl_prod(1.f - alpha, s);
+    float excl = __shfl_up_sync(0xffffffffu, incl, 1, GS);
+    if (s == 0) excl = 1.f;
+    Tb = T * excl;
+    float w = Tb * alpha;
+    used = GS;
+    stop = false;
+    const unsigned kill = __ballot_sync(0xffffffffu, valid && kappa > 0.f && T * incl < kappa);
+    const unsigned gk = (kill >> gbase) & ((1u << GS) - 1u);
+    if (gk) {
+        const int ls = __ffs(gk) - 1;
+        if (s > ls) w = 0.f;
+        used = ls + 1;
+        stop = true;
     }
-    const bool new0 = lane < m && !sorted64_has(kold, kn0);
-    const bool new1 = lane + 32 < m && !sorted64_has(kold, kn1);
-    const unsigned nm0 = __ballot_sync(0xffffffffu, new0), nm1 = __ballot_sync(0xffffffffu, new1);
-    const int c0 = __popc(nm0), nnew = c0 + __popc(nm1);
-    if (nnew == 0) return;
-    const unsigned fr0 = __ballot_sync(0xffffffffu, key[0] < 0);
-    const unsigned fr1 = __ballot_sync(0xffffffffu, key[1] < 0);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int rk = (q == 0) ? __popc(fr0 & lt) : __popc(fr0) + __popc(fr1 & lt);
-        const bool want = key[q] < 0 && rk < nnew;
-        int src = lane;
-        bool hi = false;
-        if (want) {
-            if (rk < c0) src = __fns(nm0, 0, rk + 1);
-            else { src = __fns(nm1, 0, rk - c0 + 1); hi = true; }
-        }
-        const int va = __shfl_sync(0xffffffffu, kn0, src);
-        const int vb = __shfl_sync(0xffffffffu, kn1, src);
-        if (want) {
-            key[q] = hi ? vb : va;
-            on_enter(q, key[q]);
-        }
-    }
-}
-
-// Loads the first min(n, OWN) entries of a voxel list into knew (padded) and
-// returns them per lane (entries lane and lane + 32).
-__device__ __forceinline__ int load_list(const int* __restrict__ v_sq, int f, int m, int lane, int* knew, int& kn1) {
-    const int kn0 = lane < m ? __ldg(v_sq + f + lane) : INT_MAX;
-    kn1 = lane + 32 < m ? __ldg(v_sq + f + 32 + lane) : INT_MAX;
-    knew[lane] = kn0;
-    knew[lane + 32] = kn1;
-    __syncwarp();
-    return kn0;
-}
-
-template <int CP>
-__device__ __forceinline__ void add_logits(float acc[CP], const float* __restrict__ lpad, int k, float wgt) {
-    const float4* cr = reinterpret_cast<const float4*>(lpad) + (size_t)k * (CP / 4);
-#pragma unroll
-    for (int q = 0; q < CP / 4; ++q) {
-        const float4 cv = __ldg(cr + q);
-        acc[4 * q + 0] = fmaf(wgt, cv.x, acc[4 * q + 0]);
-        acc[4 * q + 1] = fmaf(wgt, cv.y, acc[4 * q + 1]);
-        acc[4 * q + 2] = fmaf(wgt, cv.z, acc[4 * q + 2]);
-        acc[4 * q + 3] = fmaf(wgt, cv.w, acc[4 * q + 3]);
-    }
+    const float tot = __shfl_sync(0xffffffffu, incl, gbase + (gk ? (__ffs(gk) - 1) : GS - 1));
+    T = T * tot;
+    return w;
 }
 
 // ------------------------------------------------------------------ forward
-// One warp per ray, samples front to back.  Owners keep W_k = sum_j w_j p_jk of
-// their primitive; when it leaves, (k, W_k) is queued and later folded into the
-// lane-local semantic accumulator as W_k c_k (Eq. 6 regrouped by primitive).
-struct WarpFwd {
-    int keys[2][OWN];
-    int qk[FQCAP];
-    float qw[FQCAP];
-};
-
+// Four rays per warp, eight lanes per ray, one lane per sample: each lane walks
+// its own voxel list with alpha and s_j in registers (Eq. 4), the group composites
+// its eight samples with a product scan (Eq. 5-6), and saves T_j for the backward.
 template <int CP>
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward(RenderArgs a, float* __restrict__ depth,
                                                             float* __restrict__ sem, float* __restrict__ t_final) {
-    __shared__ WarpFwd smem[FWD_WARPS];
     if (*a.status != SQ_OK) return;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    WarpFwd& sm = smem[wid];
+    const int lane = threadIdx.x & 31;
+    const int s = lane & (GS - 1), gbase = lane & ~(GS - 1);
+    const float4* lp4 = reinterpret_cast<const float4*>(a.lpad);
 
-    for (;;) {
-        int rr = 0;
-        if (lane == 0) rr = atomicAdd(a.ray_ctr, 1);
-        const long long r = __shfl_sync(0xffffffffu, rr, 0);
-        if (r >= a.R) break;
-        float o[3], d[3];
-        ray_of(a, r, o, d);
-        float acc[CP];
+    int rn = 0;
+    if (s == 0) rn = atomicAdd(a.ray_ctr, 1);
+    long long r = __shfl_sync(0xffffffffu, rn, gbase);
+    float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f};
+    if (r < a.R) ray_of(a, r, o, d);
+    float T = 1.f, Dp = 0.f;
+    int j0 = 0, used_total = 0;
+    bool seen_inside = false;
+    float acc[CP];
 #pragma unroll
-        for (int c = 0; c < CP; ++c) acc[c] = 0.f;
-        int key[2] = {-1, -1};
-        float Wk[2] = {0.f, 0.f};
-        int* kold = sm.keys[0];
-        int* knew = sm.keys[1];
-        kold[lane] = INT_MAX;
-        kold[lane + 32] = INT_MAX;
-        int qn = 0;
-        float T = 1.f, D = 0.f;
-        bool inside_seen = false;
-        int used = 0;
-        __syncwarp();
+    for (int c = 0; c < CP; ++c) acc[c] = 0.f;
 
-        auto drain = [&]() {
-            __syncwarp();
-            if (lane < qn) add_logits<CP>(acc, a.lpad, sm.qk[lane], sm.qw[lane]);
-            __syncwarp();
-            qn = 0;
-        };
-        auto leave = [&](int q, bool del, unsigned dm) {
-            if (!dm) return;
-            if (qn + __popc(dm) > FQCAP) drain();
-            if (del) {
-                const int pos = qn + __popc(dm & lt);
-                sm.qk[pos] = key[q];
-                sm.qw[pos] = Wk[q];
-            }
-            qn += __popc(dm);
-        };
-        auto enter = [&](int q, int) { Wk[q] = 0.f; };
-
-        for (int j = 0; j <= a.L; ++j) {
-            // j == L: an empty list releases every owner
-            int n = 0, f = 0;
-            float x[3] = {0.f, 0.f, 0.f};
-            float tj = 0.f;
-            bool last = (j == a.L);
-            if (!last) {
-                tj = __ldg(a.t + j);
-                const int vox = sample_voxel(a.g, o, d, tj, x);
-                if (vox >= 0) {
-                    n = __ldg(a.v_n + vox);
-                    f = __ldg(a.v_f + vox);
-                    inside_seen = true;
-                } else if (inside_seen) {
-                    last = true;  // samples are non-decreasing in t: the ray has left the grid for good
-                }
-                if (a.save_T && lane == 0) a.save_T[r * a.L + j] = T;
-            }
-            const bool owners = __any_sync(0xffffffffu, key[0] >= 0 || key[1] >= 0);
-            if (n == 0 && !owners) {
-                if (last) { used = j; break; }
-                used = j + 1;
-                continue;  // empty sample with no owners: alpha = 0, T unchanged
-            }
-            const int m = min(n, OWN);
-            int kn1;
-            const int kn0 = load_list(a.v_sq, f, m, lane, knew, kn1);
-            owners_update(key, kold, knew, m, kn0, kn1, lane, lt, leave, enter);
-            int* tmp = kold; kold = knew; knew = tmp;
-            if (last) { used = j; break; }
-            // occupancies of owned pairs, alpha = sum p sigma
-            float po[2] = {0.f, 0.f};
-            float part = 0.f;
+    while (__any_sync(0xffffffffu, r < a.R)) {
+        const bool live = r < a.R;
+        const int j = j0 + s;
+        const bool valid = live && j < a.L;
+        float x[3] = {0.f, 0.f, 0.f};
+        int vox = -1;
+        float tj = 0.f;
+        if (valid) {
+            tj = __ldg(a.t + j);
+            vox = sample_voxel(a.g, o, d, tj, x);
+        }
+        int n = 0, f = 0;
+        if (vox >= 0) {
+            n = __ldg(a.v_n + vox);
+            f = __ldg(a.v_f + vox);
+        }
+        float asum = 0.f;
+        float sacc[CP];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (key[q] >= 0) {
-                    const Prim p = load_prim(a.rec, key[q]);
-                    po[q] = occupancy(p, x);
-                    part = fmaf(po[q], p.sigma, part);
-                }
-            }
-            for (int e = OWN + lane; e < n; e += 32) {
-                const Prim p = load_prim(a.rec, __ldg(a.v_sq + f + e));
-                part = fmaf(occupancy(p, x), p.sigma, part);
-            }
-            const float raw = warp_sum(part);
-            const float alpha = fminf(raw, a.alpha_max);
-            const float w = T * alpha;
-            D = fmaf(w, tj, D);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) Wk[q] = fmaf(w, po[q], Wk[q]);
-            for (int e = OWN + lane; e < n; e += 32) {
+        for (int c = 0; c < CP; ++c) sacc[c] = 0.f;
+        const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
+        for (int e = 0; e < nmax; ++e) {
+            if (e < n) {
                 const int k = __ldg(a.v_sq + f + e);
                 const Prim p = load_prim(a.rec, k);
-                add_logits<CP>(acc, a.lpad, k, w * occupancy(p, x));
-            }
-            T = T * (1.f - alpha);
-            used = j + 1;
-            __syncwarp();
-            if ((a.kappa > 0.f && T < a.kappa) || T == 0.f) {
-                // terminated: release every owner through an empty list
-                knew[lane] = INT_MAX;
-                knew[lane + 32] = INT_MAX;
-                __syncwarp();
-                owners_update(key, kold, knew, 0, INT_MAX, INT_MAX, lane, lt, leave, enter);
-                break;
-            }
-        }
-        drain();
+                const float po = occupancy(p, x);
+                asum = fmaf(po, p.sigma, asum);
+                const float4* cr = lp4 + (size_t)k * (CP / 4);
 #pragma unroll
-        for (int c = 0; c < CP; ++c) {
-            const float v = warp_sum(acc[c]);
-            if (lane == c && c < a.C) sem[r * a.C + c] = v;
+                for (int q = 0; q < CP / 4; ++q) {
+                    const float4 cv = __ldg(cr + q);
+                    sacc[4 * q + 0] = fmaf(po, cv.x, sacc[4 * q + 0]);
+                    sacc[4 * q + 1] = fmaf(po, cv.y, sacc[4 * q + 1]);
+                    sacc[4 * q + 2] = fmaf(po, cv.z, sacc[4 * q + 2]);
+                    sacc[4 * q + 3] = fmaf(po, cv.w, sacc[4 * q + 3]);
+                }
+            }
         }
-        if (lane == 0) {
-            depth[r] = D;
-            if (t_final) t_final[r] = T;
-            if (a.save_n) a.save_n[r] = used;
+        const float alpha = valid ? fminf(asum, a.alpha_max) : 0.f;
+        float Tb;
+        int used;
+        bool stop;
+        const float w = group_composite(alpha, s, gbase, a.kappa, T, Tb, valid, used, stop);
+        if (valid) {
+            if (s < used && a.save_T) a.save_T[r * a.L + j] = Tb;
+            Dp = fmaf(w, tj, Dp);
+#pragma unroll
+            for (int c = 0; c < CP; ++c) acc[c] = fmaf(w, sacc[c], acc[c]);
         }
-        __syncwarp();
+        // the group's samples: inside the grid anywhere?  t is non-decreasing, so a
+        // chunk fully outside after an inside one means the ray has left for good
+        const unsigned ins = (__ballot_sync(0xffffffffu, vox >= 0) >> gbase) & ((1u << GS) - 1u);
+        const bool left = seen_inside && ins == 0u;
+        seen_inside = seen_inside || ins != 0u;
+        if (live) used_total = min(j0 + used, a.L);
+        j0 += GS;
+        // a ray ends at L, on early termination, once T is exactly 0 (every later
+        // weight is 0), or when it has left the grid
+        const bool fin = live && (j0 >= a.L || stop || T == 0.f || left);
+        if (__any_sync(0xffffffffu, fin)) {
+            float Dsum = Dp;
+#pragma unroll
+            for (int o2 = GS / 2; o2 > 0; o2 >>= 1) Dsum += __shfl_xor_sync(0xffffffffu, Dsum, o2, GS);
+#pragma unroll
+            for (int c = 0; c < CP; ++c) {
+                float v = acc[c];
+#pragma unroll
+                for (int o2 = GS / 2; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2, GS);
+                if (fin && (c % GS) == s && c < a.C) sem[r * a.C + c] = v;
+            }
+            if (fin && s == 0) {
+                depth[r] = Dsum;
+                if (t_final) t_final[r] = T;
+                if (a.save_n) a.save_n[r] = used_total;
+            }
+            int nr = 0;
+            if (fin && s == 0) nr = atomicAdd(a.ray_ctr, 1);
+            nr = __shfl_sync(0xffffffffu, nr, gbase);
+            if (fin) {
+                r = nr;
+                if (r < a.R) ray_of(a, r, o, d);
+                T = 1.f;
+                Dp = 0.f;
+                j0 = 0;
+                used_total = 0;
+                seen_inside = false;
+#pragma unroll
+                for (int c = 0; c < CP; ++c) acc[c] = 0.f;
+            }
+        }
     }
 }
 
 // ------------------------------------------------------------------ backward
 struct BwdPrim {
     Prim f;
-    float qn[4];
-    float inv_qn;
     float is[3];  // 1 / s
-    float e1, e2, ie1, ie2;
+    float ie1, ie2;
 };
 
 __device__ __forceinline__ BwdPrim load_bwd(const float4* __restrict__ rec, const float4* __restrict__ aux, int k) {
     BwdPrim b;
     b.f = load_prim(rec, k);
     const float4* a = aux + (size_t)k * AUX4;
-    float4 a0 = __ldg(a + 0), a1 = __ldg(a + 1), a2 = __ldg(a + 2);
-    b.qn[0] = a0.x; b.qn[1] = a0.y; b.qn[2] = a0.z; b.qn[3] = a0.w;
-    b.inv_qn = a1.x; b.is[0] = a1.y; b.is[1] = a1.z; b.is[2] = a1.w;
-    b.e1 = a2.x; b.e2 = a2.y; b.ie1 = a2.z; b.ie2 = a2.w;
+    const float4 a1 = __ldg(a + 1), a2 = __ldg(a + 2);
+    b.is[0] = a1.y; b.is[1] = a1.z; b.is[2] = a1.w;
+    b.ie1 = a2.z; b.ie2 = a2.w;
     return b;
 }
 
-// p_o and df/d(parameters) at point x.  g[0..2] = df/dm, g[3..6] = df/dq (raw,
-// unnormalised quaternion), g[7..9] = df/ds, g[10..11] = df/d(eps1, eps2).
-//   u_j = (R^T (x - m))_j / s_j,  a = |u_0|, b = |u_1|, c = |u_2|,
-//   f = A^eb + c^ec with A = a^ea + b^ea (ea = 2/eps2, eb = eps2/eps1, ec = 2/eps1),
-//   u_j df/du_j = ec A^(eb-1) a^ea (j = 0), likewise b (j = 1), ec c^ec (j = 2);
-//   the rotation part uses x_S = d - 2w (v x d) + 2 v (v.d) - 2 d (v.v) for q = (w, v).
-__device__ __forceinline__ float occupancy_grad(const BwdPrim& P, const float x[3], float g[12]) {
+// Per-pair partial derivatives of f, in the form that is summed per (ray,
+// primitive) and turned into parameter gradients once at the flush:
+//   r[0..2]  gx = df/dx (world), so df/dm = -gx
+//   r[3..5]  tau = gx x (x - m), the torque of a world-frame rotation of the primitive
+//   r[6..8]  u_j df/du_j, so df/ds_j = -(u_j df/du_j) / s_j
+//   r[9..10] df/deps1, df/deps2
+// with u_j = (R^T (x - m))_j / s_j, a = |u_0|, b = |u_1|, c = |u_2|,
+// f = A^eb + c^ec, A = a^ea + b^ea (ea = 2/eps2, eb = eps2/eps1, ec = 2/eps1).
+// Returns p_o = exp(-f).
+__device__ __forceinline__ float occupancy_partials(const BwdPrim& P, const float x[3], float r[11]) {
     const Prim& p = P.f;
     const float d[3] = {x[0] - p.m[0], x[1] - p.m[1], x[2] - p.m[2]};
     float u[3];
@@ -355,39 +290,23 @@ __device__ __forceinline__ float occupancy_grad(const BwdPrim& P, const float x[
     const float lA = lg2(A);
     const float PA = ex2(p.eb * lA);
     const float po = ex2(-(PA + pc) * LOG2E);
-
     const float rA = A > 0.f ? rcp(A) : 0.f;
     const float t0 = p.ec * PA * rA;
-    const float tu[3] = {t0 * pa, t0 * pb, p.ec * pc};  // u_j df/du_j
+    r[6] = t0 * pa;
+    r[7] = t0 * pb;
+    r[8] = p.ec * pc;
     float dfu[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) dfu[j] = u[j] != 0.f ? tu[j] * rcp(u[j]) : 0.f;
+    for (int j = 0; j < 3; ++j) dfu[j] = u[j] != 0.f ? r[6 + j] * rcp(u[j]) : 0.f;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) g[i] = -(dfu[0] * p.M[0][i] + dfu[1] * p.M[1][i] + dfu[2] * p.M[2][i]);
-    // s_j enters through u_j = x_S,j / s_j: df/ds_j = -u_j df/du_j / s_j
-#pragma unroll
-    for (int j = 0; j < 3; ++j) g[7 + j] = -tu[j] * P.is[j];
-    // exponents
+    for (int i = 0; i < 3; ++i) r[i] = dfu[0] * p.M[0][i] + dfu[1] * p.M[1][i] + dfu[2] * p.M[2][i];
+    r[3] = r[1] * d[2] - r[2] * d[1];
+    r[4] = r[2] * d[0] - r[0] * d[2];
+    r[5] = r[0] * d[1] - r[1] * d[0];
     const float e1term = (PA > 0.f ? p.eb * PA * lA : 0.f) + (pc > 0.f ? p.ec * pc * lc : 0.f);
-    g[10] = -LN2 * P.ie1 * e1term;
+    r[9] = -LN2 * P.ie1 * e1term;
     const float pl = (pa > 0.f ? pa * la : 0.f) + (pb > 0.f ? pb * lb : 0.f);
-    g[11] = PA > 0.f ? PA * LN2 * (lA * P.ie1 - p.ec * P.ie2 * pl * rA) : 0.f;
-    // rotation: gl = df/dx_S
-    const float gl[3] = {dfu[0] * P.is[0], dfu[1] * P.is[1], dfu[2] * P.is[2]};
-    const float w = P.qn[0];
-    const float v[3] = {P.qn[1], P.qn[2], P.qn[3]};
-    const float cx[3] = {d[1] * gl[2] - d[2] * gl[1], d[2] * gl[0] - d[0] * gl[2], d[0] * gl[1] - d[1] * gl[0]};
-    const float vd = v[0] * d[0] + v[1] * d[1] + v[2] * d[2];
-    const float gv = gl[0] * v[0] + gl[1] * v[1] + gl[2] * v[2];
-    const float gd = gl[0] * d[0] + gl[1] * d[1] + gl[2] * d[2];
-    const float gw = -2.f * (v[0] * cx[0] + v[1] * cx[1] + v[2] * cx[2]);
-    float gu[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) gu[i] = 2.f * (-w * cx[i] + vd * gl[i] + gv * d[i] - 2.f * gd * v[i]);
-    const float dot = w * gw + v[0] * gu[0] + v[1] * gu[1] + v[2] * gu[2];
-    g[3] = (gw - w * dot) * P.inv_qn;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) g[4 + i] = (gu[i] - v[i] * dot) * P.inv_qn;
+    r[10] = PA > 0.f ? PA * LN2 * (lA * P.ie1 - p.ec * P.ie2 * pl * rA) : 0.f;
     return po;
 }
 
@@ -395,7 +314,8 @@ struct BwdArgs {
     RenderArgs r;
     const float* grad_depth;
     const float* grad_sem;
-    float* gacc;  // [N, GF] gradient accumulator, zeroed before the launch
+    const int* ranges;  // [N, 6] voxel boxes of the index
+    float* gacc;        // [N, GF] gradient accumulator, zeroed before the launch
 };
 
 template <int CP>
@@ -413,34 +333,62 @@ __device__ __forceinline__ float logit_dot(const float* __restrict__ lpad, int k
     return cd;
 }
 
-// Writes the pending flushes of the warp into the accumulator: coalesced atomic
-// adds, lane f adding field f (and f + 32 when C > 19).  gsl[b] = gS[32 b + lane - 13]
-// of the current ray for the logit fields (dL/dc_k = W_k gS).
+// Field f of a primitive's gradient row from its summed partials e[0..12]
+// (gx 3, tau 3, u df/du 3, eps 2, sigma 1, W 1):  0-2 dL/dm, 3-6 dL/dq (raw
+// quaternion, through the torque and the normalisation), 7-9 dL/ds, 10-11 dL/deps,
+// 12 dL/dsigma, 13.. dL/dc_c = W gS_c.
+__device__ __forceinline__ float grad_field(int fld, const float* __restrict__ e, const float4* __restrict__ aux,
+                                            int k, float gs_c) {
+    if (fld < 3) return -e[fld];
+    if (fld < 7) {
+        const float4 a0 = __ldg(aux + (size_t)k * AUX4), a1 = __ldg(aux + (size_t)k * AUX4 + 1);
+        const float w = a0.x, v[3] = {a0.y, a0.z, a0.w}, inq = a1.x;
+        const float t[3] = {e[3], e[4], e[5]};
+        if (fld == 3) return -2.f * (t[0] * v[0] + t[1] * v[1] + t[2] * v[2]) * inq;
+        const int i = fld - 4, i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+        return 2.f * (w * t[i] + t[i1] * v[i2] - t[i2] * v[i1]) * inq;
+    }
+    if (fld < 10) {
+        const float4 a1 = __ldg(aux + (size_t)k * AUX4 + 1);
+        const float is = fld == 7 ? a1.y : (fld == 8 ? a1.z : a1.w);
+        return -e[6 + (fld - 7)] * is;
+    }
+    if (fld < 13) return e[9 + (fld - 10)];
+    return e[12] * gs_c;
+}
+
+// Writes the warp's pending flushes: per entry, lane f computes field f (and
+// f + 32) and adds it to the accumulator row (coalesced atomics).
 __device__ __forceinline__ void drain_queue(float* __restrict__ gacc, const float* __restrict__ q, int qn, int lane,
-                                            const float gsl[2], int C) {
+                                            const float gsl[2], int C, const float4* __restrict__ aux) {
     for (int e = 0; e < qn; ++e) {
         const float* ent = q + e * QW;
         const int k = __float_as_int(ent[0]);
         float* row = gacc + (size_t)k * GF;
-        float v = 0.f;
-        if (lane < NGEO) v = ent[1 + lane];
-        else if (lane < NGEO + C) v = ent[1 + NGEO] * gsl[0];
-        if (v != 0.f) red_add(row + lane, v);
-        if (NGEO + C > 32 && lane + 32 < NGEO + C) {
-            const float v2 = ent[1 + NGEO] * gsl[1];
-            if (v2 != 0.f) red_add(row + 32 + lane, v2);
+        if (lane < NGEO + C) {
+            const float v = grad_field(lane, ent + 1, aux, k, gsl[0]);
+            if (v != 0.f) red_add(row + lane, v);
+        }
+        if (lane + 32 < NGEO + C) {
+            const float v = ent[1 + 12] * gsl[1];
+            if (v != 0.f) red_add(row + 32 + lane, v);
         }
     }
 }
 
 struct WarpBwd {
-    int keys[2][OWN];
     float queue[QCAP * QW];
 };
 
-// One warp per ray, samples back to front (Sec. 3.3.3): with T_j saved by the
+__device__ __forceinline__ bool box_has(const int b[6], int ix, int iy, int iz) {
+    return ix >= b[0] && ix <= b[1] && iy >= b[2] && iy <= b[3] && iz >= b[4] && iz <= b[5];
+}
+
+// One warp per ray, samples back to front (Sec. 3.3.3).  With T_j saved by the
 // forward, U_j is carried from the back, so one sweep gives alpha_j, v_j, G_j and
-// every pair's gradient.
+// every pair's gradient.  Owner bookkeeping uses the primitives' voxel boxes: an
+// owner leaves when the sample's voxel is outside its box, and a list entry is new
+// when the previous sample's voxel is outside its box.
 template <int CP>
 __global__ void __launch_bounds__(BWD_WARPS * 32, 2) k_backward(BwdArgs A) {
     __shared__ WarpBwd smem[BWD_WARPS];
@@ -449,6 +397,7 @@ __global__ void __launch_bounds__(BWD_WARPS * 32, 2) k_backward(BwdArgs A) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     WarpBwd& wb = smem[wid];
+    const int ny = a.g.n[1], nz = a.g.n[2];
 
     for (;;) {
         int rr = 0;
@@ -465,25 +414,25 @@ __global__ void __launch_bounds__(BWD_WARPS * 32, 2) k_backward(BwdArgs A) {
         gsl[1] = (lane + 32 < NGEO + a.C) ? __ldg(gS + (lane + 32 - NGEO)) : 0.f;
 
         int key[2] = {-1, -1};
-        float acc[2][14];
+        int box[2][6];
+        float acc[2][13];
         float cdk[2] = {0.f, 0.f};
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+        for (int q = 0; q < 2; ++q) {
 #pragma unroll
-            for (int i = 0; i < 14; ++i) acc[q][i] = 0.f;
-        int* kold = wb.keys[0];
-        int* knew = wb.keys[1];
-        kold[lane] = INT_MAX;
-        kold[lane + 32] = INT_MAX;
+            for (int i = 0; i < 6; ++i) box[q][i] = 0;
+#pragma unroll
+            for (int i = 0; i < 13; ++i) acc[q][i] = 0.f;
+        }
         int qn = 0;
         float U = 0.f;
-        __syncwarp();
+        int pvx = -1, piy = 0, piz = 0, pvox = -1;  // voxel of the previously processed sample (-1: none)
 
-        auto leave = [&](int q, bool del, unsigned dm) {
+        auto flush = [&](int q, bool del, unsigned dm) {
             if (!dm) return;
             if (qn + __popc(dm) > QCAP) {
                 __syncwarp();
-                drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C);
+                drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C, a.aux);
                 __syncwarp();
                 qn = 0;
             }
@@ -491,65 +440,149 @@ __global__ void __launch_bounds__(BWD_WARPS * 32, 2) k_backward(BwdArgs A) {
                 float* ent = wb.queue + (qn + __popc(dm & lt)) * QW;
                 ent[0] = __int_as_float(key[q]);
 #pragma unroll
-                for (int i = 0; i < 14; ++i) ent[1 + i] = acc[q][i];
+                for (int i = 0; i < 13; ++i) ent[1 + i] = acc[q][i];
+                key[q] = -1;
             }
             qn += __popc(dm);
-        };
-        auto enter = [&](int q, int k) {
-#pragma unroll
-            for (int i = 0; i < 14; ++i) acc[q][i] = 0.f;
-            cdk[q] = logit_dot<CP>(a.lpad, k, gS, a.C);
         };
 
         for (int j = Le - 1; j >= -1; --j) {
             // j == -1: an empty list releases every owner
-            int n = 0, f = 0;
+            int n = 0, f = 0, vox = -1, ix = -1, iy = 0, iz = 0;
             float x[3] = {0.f, 0.f, 0.f};
             float tj = 0.f;
             if (j >= 0) {
                 tj = __ldg(a.t + j);
-                const int vox = sample_voxel(a.g, o, d, tj, x);
+                vox = sample_voxel(a.g, o, d, tj, x);
                 if (vox >= 0) {
                     n = __ldg(a.v_n + vox);
                     f = __ldg(a.v_f + vox);
+                    iz = vox % nz;
+                    iy = (vox / nz) % ny;
+                    ix = vox / (ny * nz);
                 }
             }
-            const bool owners = __any_sync(0xffffffffu, key[0] >= 0 || key[1] >= 0);
-            if (n == 0 && !owners) {
-                if (j < 0) break;
-                continue;  // no primitive here: alpha_j = 0 leaves U unchanged
+            const bool heavy = n > OWN;
+            if (vox != pvox || heavy) {
+                // owners whose box misses this voxel leave (all of them on an empty or heavy list)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const bool del = key[q] >= 0 && (n == 0 || heavy || !box_has(box[q], ix, iy, iz));
+                    flush(q, del, __ballot_sync(0xffffffffu, del));
+                }
+                if (n > 0 && !heavy) {
+                    // slot-1 owners move to free slot-0 lanes
+                    const unsigned o1 = __ballot_sync(0xffffffffu, key[1] >= 0);
+                    if (o1) {
+                        const unsigned f0 = __ballot_sync(0xffffffffu, key[0] < 0);
+                        const int mv = min(__popc(o1), __popc(f0));
+                        if (mv > 0) {
+                            const int rk = __popc(f0 & lt);
+                            const bool take = key[0] < 0 && rk < mv;
+                            const int src = take ? __fns(o1, 0, rk + 1) : lane;
+                            const int k1 = __shfl_sync(0xffffffffu, key[1], src);
+                            const float c1 = __shfl_sync(0xffffffffu, cdk[1], src);
+                            int b1[6];
+                            float a1[13];
+#pragma unroll
+                            for (int i = 0; i < 6; ++i) b1[i] = __shfl_sync(0xffffffffu, box[1][i], src);
+#pragma unroll
+                            for (int i = 0; i < 13; ++i) a1[i] = __shfl_sync(0xffffffffu, acc[1][i], src);
+                            const bool given = key[1] >= 0 && __popc(o1 & lt) < mv;
+                            if (take) {
+                                key[0] = k1;
+                                cdk[0] = c1;
+#pragma unroll
+                                for (int i = 0; i < 6; ++i) box[0][i] = b1[i];
+#pragma unroll
+                                for (int i = 0; i < 13; ++i) acc[0][i] = a1[i];
+                            }
+                            if (given) key[1] = -1;
+                        }
+                    }
+                    // list entries whose box misses the previous voxel are new owners
+                    const int e0 = lane, e1 = lane + 32;
+                    int kn0 = -1, kn1 = -1;
+                    bool new0 = false, new1 = false;
+                    int nb0[6], nb1[6];
+                    if (e0 < n) {
+                        kn0 = __ldg(a.v_sq + f + e0);
+                        const int* bp = A.ranges + 6 * (size_t)kn0;
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) nb0[i] = __ldg(bp + i);
+                        new0 = pvox < 0 || !box_has(nb0, pvx, piy, piz);
+                    }
+                    if (e1 < n) {
+                        kn1 = __ldg(a.v_sq + f + e1);
+                        const int* bp = A.ranges + 6 * (size_t)kn1;
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) nb1[i] = __ldg(bp + i);
+                        new1 = pvox < 0 || !box_has(nb1, pvx, piy, piz);
+                    }
+                    const unsigned nm0 = __ballot_sync(0xffffffffu, new0), nm1 = __ballot_sync(0xffffffffu, new1);
+                    const int c0 = __popc(nm0), nnew = c0 + __popc(nm1);
+                    if (nnew) {
+                        const unsigned fr0 = __ballot_sync(0xffffffffu, key[0] < 0);
+                        const unsigned fr1 = __ballot_sync(0xffffffffu, key[1] < 0);
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const int rk = (q == 0) ? __popc(fr0 & lt) : __popc(fr0) + __popc(fr1 & lt);
+                            const bool want = key[q] < 0 && rk < nnew;
+                            int src = lane;
+                            bool hi = false;
+                            if (want) {
+                                if (rk < c0) src = __fns(nm0, 0, rk + 1);
+                                else { src = __fns(nm1, 0, rk - c0 + 1); hi = true; }
+                            }
+                            const int va = __shfl_sync(0xffffffffu, kn0, src);
+                            const int vb = __shfl_sync(0xffffffffu, kn1, src);
+                            if (want) {
+                                const int k = hi ? vb : va;
+                                key[q] = k;
+                                const int* bp = A.ranges + 6 * (size_t)k;
+#pragma unroll
+                                for (int i = 0; i < 6; ++i) box[q][i] = __ldg(bp + i);
+#pragma unroll
+                                for (int i = 0; i < 13; ++i) acc[q][i] = 0.f;
+                                cdk[q] = logit_dot<CP>(a.lpad, k, gS, a.C);
+                            }
+                        }
+                    }
+                }
+                pvox = (n > 0 && !heavy) ? vox : -1;
+                pvx = ix; piy = iy; piz = iz;
             }
-            const int m = min(n, OWN);
-            int kn1;
-            const int kn0 = load_list(a.v_sq, f, m, lane, knew, kn1);
-            owners_update(key, kold, knew, m, kn0, kn1, lane, lt, leave, enter);
-            int* tmp = kold; kold = knew; knew = tmp;
             if (j < 0) break;
-            if (n == 0) {
-                __syncwarp();
-                continue;
-            }
-            // owned pairs: occupancy and its partials; alpha_j and <gS, s_j> by warp sums
+            if (n == 0) continue;  // no primitive here: alpha_j = 0 leaves U unchanged
+            // owned (or, on a heavy list, all) pairs: partials, alpha_j and <gS, s_j>
             float po[2] = {0.f, 0.f};
-            float gg[2][12];
-            float pa = 0.f, pv = 0.f;
+            float pr[2][11];
             float sig[2] = {0.f, 0.f};
+            float pa = 0.f, pv = 0.f;
+            const bool any1 = __any_sync(0xffffffffu, key[1] >= 0);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
+                if (q == 1 && !any1) {
+#pragma unroll
+                    for (int i = 0; i < 11; ++i) pr[1][i] = 0.f;
+                    continue;
+                }
                 if (key[q] >= 0) {
                     const BwdPrim P = load_bwd(a.rec, a.aux, key[q]);
-                    po[q] = occupancy_grad(P, x, gg[q]);
+                    po[q] = occupancy_partials(P, x, pr[q]);
                     sig[q] = P.f.sigma;
                     pa = fmaf(po[q], sig[q], pa);
                     pv = fmaf(po[q], cdk[q], pv);
                 }
             }
-            for (int e = OWN + lane; e < n; e += 32) {
-                const int k = __ldg(a.v_sq + f + e);
-                const Prim p = load_prim(a.rec, k);
-                const float pe = occupancy(p, x);
-                pa = fmaf(pe, p.sigma, pa);
-                pv = fmaf(pe, logit_dot<CP>(a.lpad, k, gS, a.C), pv);
+            if (heavy) {
+                for (int e = lane; e < n; e += 32) {
+                    const int k = __ldg(a.v_sq + f + e);
+                    const Prim p = load_prim(a.rec, k);
+                    const float pe = occupancy(p, x);
+                    pa = fmaf(pe, p.sigma, pa);
+                    pv = fmaf(pe, logit_dot<CP>(a.lpad, k, gS, a.C), pv);
+                }
             }
             const float raw = warp_sum(pa);
             const float vs = warp_sum(pv);
@@ -563,29 +596,36 @@ __global__ void __launch_bounds__(BWD_WARPS * 32, 2) k_backward(BwdArgs A) {
                 if (key[q] >= 0 && po[q] != 0.f) {
                     const float gf = -po[q] * fmaf(G, sig[q], w * cdk[q]);
 #pragma unroll
-                    for (int i = 0; i < 12; ++i) acc[q][i] = fmaf(gf, gg[q][i], acc[q][i]);
-                    acc[q][12] = fmaf(G, po[q], acc[q][12]);
-                    acc[q][13] = fmaf(w, po[q], acc[q][13]);
+                    for (int i = 0; i < 11; ++i) acc[q][i] = fmaf(gf, pr[q][i], acc[q][i]);
+                    acc[q][11] = fmaf(G, po[q], acc[q][11]);
+                    acc[q][12] = fmaf(w, po[q], acc[q][12]);
                 }
             }
-            for (int e = OWN + lane; e < n; e += 32) {
-                const int k = __ldg(a.v_sq + f + e);
-                const BwdPrim P = load_bwd(a.rec, a.aux, k);
-                float g12[12];
-                const float pe = occupancy_grad(P, x, g12);
-                if (pe == 0.f) continue;
-                const float gf = -pe * fmaf(G, P.f.sigma, w * logit_dot<CP>(a.lpad, k, gS, a.C));
-                float* dst = A.gacc + (size_t)k * GF;
+            if (heavy) {
+                // per-pair atomics for the whole list
+                for (int e = lane; e < n; e += 32) {
+                    const int k = __ldg(a.v_sq + f + e);
+                    const BwdPrim P = load_bwd(a.rec, a.aux, k);
+                    float pp[11];
+                    const float pe = occupancy_partials(P, x, pp);
+                    if (pe == 0.f) continue;
+                    const float gf = -pe * fmaf(G, P.f.sigma, w * logit_dot<CP>(a.lpad, k, gS, a.C));
+                    float ent[13];
 #pragma unroll
-                for (int i = 0; i < 12; ++i) red_add(dst + i, gf * g12[i]);
-                red_add(dst + 12, G * pe);
-                for (int c = 0; c < a.C; ++c) red_add(dst + NGEO + c, w * pe * __ldg(gS + c));
+                    for (int i = 0; i < 11; ++i) ent[i] = gf * pp[i];
+                    ent[11] = G * pe;
+                    ent[12] = w * pe;
+                    float* row = A.gacc + (size_t)k * GF;
+                    for (int fld = 0; fld < NGEO + a.C; ++fld) {
+                        const float v = grad_field(fld, ent, a.aux, k, fld >= NGEO ? __ldg(gS + fld - NGEO) : 0.f);
+                        if (v != 0.f) red_add(row + fld, v);
+                    }
+                }
             }
             U = fmaf(alpha, vj, (1.f - alpha) * U);
-            __syncwarp();
         }
         __syncwarp();
-        drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C);
+        drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C, a.aux);
         __syncwarp();
     }
 }
@@ -783,7 +823,7 @@ static sq_status_t launch_persistent(const void* fn, int threads, size_t smem, l
 template <int CP>
 static sq_status_t launch_fwd_cp(RenderArgs a, float* depth, float* sem, float* t_final, cudaStream_t st) {
     void* args[] = {&a, &depth, &sem, &t_final};
-    return launch_persistent<CP>((const void*)k_forward<CP>, FWD_WARPS * 32, 0, a.R, FWD_WARPS, args, st,
+    return launch_persistent<CP>((const void*)k_forward<CP>, FWD_WARPS * 32, 0, a.R, FWD_WARPS * 4, args, st,
                                  "k_forward");
 }
 
@@ -843,6 +883,7 @@ sq_status_t render_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, cons
     if (e != cudaSuccess) return cuda_status(e, "memset gradient accumulator");
     A.grad_depth = grad_depth;
     A.grad_sem = grad_sem;
+    A.ranges = idx->ranges;
     A.gacc = gacc;
     if (A.r.R > 0) {
         const int cp = cpad(C);
