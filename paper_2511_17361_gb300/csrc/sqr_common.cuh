@@ -36,9 +36,9 @@ GridC make_grid(const sq_grid_t* g);
 
 // Sample x = o + t d in FP32 (multiply, then add; no contraction) and its voxel
 // id, -1 when any axis falls outside [0, n).
-__device__ __forceinline__ int sample_voxel(const GridC& g, const float o[3], const float d[3], float t, float x[3]) {
+__device__ __forceinline__ int sample_voxel(const GridC& g, const float o[3], const float d[3], float t, float x[3],
+                                            int idx[3]) {
     bool inside = true;
-    int idx[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         x[i] = __fadd_rn(o[i], __fmul_rn(t, d[i]));
@@ -48,6 +48,11 @@ __device__ __forceinline__ int sample_voxel(const GridC& g, const float o[3], co
         idx[i] = in ? (int)floorf(u) : 0;
     }
     return inside ? (idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2] : -1;
+}
+
+__device__ __forceinline__ int sample_voxel(const GridC& g, const float o[3], const float d[3], float t, float x[3]) {
+    int idx[3];
+    return sample_voxel(g, o, d, t, x, idx);
 }
 
 // Pinhole ray through the centre of pixel (u, v): FP32, correctly rounded

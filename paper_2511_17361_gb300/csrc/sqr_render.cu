@@ -27,12 +27,16 @@ namespace sqr {
 
 namespace {
 
+#ifndef SQR_MIGRATE
+#define SQR_MIGRATE 0
+#endif
 constexpr int GS = 8;       // lanes (samples) per ray in the forward
 constexpr int OWN = 64;     // owner slots per warp (two per lane)
 constexpr int QCAP = 64;    // pending gradient flushes per warp (backward)
 constexpr int QW = 16;      // words per pending flush: key, 12 geometry, sigma, W, pad
 constexpr int GF = 48;      // floats per primitive in the gradient accumulator (13 + up to 32 classes)
 constexpr int NGEO = 13;    // m3 q4 s3 eps2 sigma1
+constexpr int NRAW = 12;    // summed partials: gx3 tau3 u.df/du 3 eps2 sigma1
 constexpr int FWD_WARPS = 8;
 constexpr int BWD_WARPS = 8;
 
@@ -87,6 +91,7 @@ struct RenderArgs {
     long long R;
     float kappa, alpha_max;
     int* ray_ctr;     // work counter, zeroed before the launch
+    int4* boxes;      // packed voxel boxes (backward)
     float* save_T;    // [R, L] transmittance before each sample (forward writes, backward reads)
     int* save_n;      // [R] samples composited
 };
@@ -314,7 +319,7 @@ struct BwdArgs {
     RenderArgs r;
     const float* grad_depth;
     const float* grad_sem;
-    const int* ranges;  // [N, 6] voxel boxes of the index
+    const int4* boxes;  // [N] voxel boxes of the index, 16-bit packed (lo | hi << 16 per axis)
     float* gacc;        // [N, GF] gradient accumulator, zeroed before the launch
 };
 
@@ -333,55 +338,166 @@ __device__ __forceinline__ float logit_dot(const float* __restrict__ lpad, int k
     return cd;
 }
 
-// Field f of a primitive's gradient row from its summed partials e[0..12]
-// (gx 3, tau 3, u df/du 3, eps 2, sigma 1, W 1):  0-2 dL/dm, 3-6 dL/dq (raw
-// quaternion, through the torque and the normalisation), 7-9 dL/ds, 10-11 dL/deps,
-// 12 dL/dsigma, 13.. dL/dc_c = W gS_c.
-__device__ __forceinline__ float grad_field(int fld, const float* __restrict__ e, const float4* __restrict__ aux,
-                                            int k, float gs_c) {
-    if (fld < 3) return -e[fld];
-    if (fld < 7) {
-        const float4 a0 = __ldg(aux + (size_t)k * AUX4), a1 = __ldg(aux + (size_t)k * AUX4 + 1);
-        const float w = a0.x, v[3] = {a0.y, a0.z, a0.w}, inq = a1.x;
-        const float t[3] = {e[3], e[4], e[5]};
-        if (fld == 3) return -2.f * (t[0] * v[0] + t[1] * v[1] + t[2] * v[2]) * inq;
-        const int i = fld - 4, i1 = (i + 1) % 3, i2 = (i + 2) % 3;
-        return 2.f * (w * t[i] + t[i1] * v[i2] - t[i2] * v[i1]) * inq;
+// <gS, c_k> with gS staged in shared memory (zero-padded to CP).
+template <int CP>
+__device__ __forceinline__ float logit_dot_sh(const float* __restrict__ lpad, int k, const float* gS) {
+    const float4* cr = reinterpret_cast<const float4*>(lpad) + (size_t)k * (CP / 4);
+    float cd = 0.f;
+#pragma unroll
+    for (int q = 0; q < CP / 4; ++q) {
+        const float4 c4 = __ldg(cr + q);
+        cd = fmaf(gS[4 * q + 0], c4.x, cd);
+        cd = fmaf(gS[4 * q + 1], c4.y, cd);
+        cd = fmaf(gS[4 * q + 2], c4.z, cd);
+        cd = fmaf(gS[4 * q + 3], c4.w, cd);
     }
-    if (fld < 10) {
-        const float4 a1 = __ldg(aux + (size_t)k * AUX4 + 1);
-        const float is = fld == 7 ? a1.y : (fld == 8 ? a1.z : a1.w);
-        return -e[6 + (fld - 7)] * is;
-    }
-    if (fld < 13) return e[9 + (fld - 10)];
-    return e[12] * gs_c;
+    return cd;
 }
 
-// Writes the warp's pending flushes: per entry, lane f computes field f (and
-// f + 32) and adds it to the accumulator row (coalesced atomics).
+// Writes the warp's pending flushes into the accumulator of raw partial sums:
+// per entry, lane f adds field f (and f + 32).  Fields 0-11 are the summed
+// partials (gx 3, tau 3, u df/du 3, eps 2, sigma 1), 12.. the logit gradients
+// W gS_c; gsl[b] = gS[32 b + lane - 12] of the current ray.
 __device__ __forceinline__ void drain_queue(float* __restrict__ gacc, const float* __restrict__ q, int qn, int lane,
-                                            const float gsl[2], int C, const float4* __restrict__ aux) {
+                                            const float gsl[2], int C) {
     for (int e = 0; e < qn; ++e) {
         const float* ent = q + e * QW;
         const int k = __float_as_int(ent[0]);
         float* row = gacc + (size_t)k * GF;
-        if (lane < NGEO + C) {
-            const float v = grad_field(lane, ent + 1, aux, k, gsl[0]);
-            if (v != 0.f) red_add(row + lane, v);
-        }
-        if (lane + 32 < NGEO + C) {
-            const float v = ent[1 + 12] * gsl[1];
-            if (v != 0.f) red_add(row + 32 + lane, v);
+        float v = 0.f;
+        if (lane < NRAW) v = ent[1 + lane];
+        else if (lane < NRAW + C) v = ent[1 + NRAW] * gsl[0];
+        if (v != 0.f) red_add(row + lane, v);
+        if (lane + 32 < NRAW + C) {
+            const float v2 = ent[1 + NRAW] * gsl[1];
+            if (v2 != 0.f) red_add(row + 32 + lane, v2);
         }
     }
 }
 
 struct WarpBwd {
     float queue[QCAP * QW];
+    float gs[32];  // dL/dS of the current ray
 };
 
-__device__ __forceinline__ bool box_has(const int b[6], int ix, int iy, int iz) {
-    return ix >= b[0] && ix <= b[1] && iy >= b[2] && iy <= b[3] && iz >= b[4] && iz <= b[5];
+// Packed inclusive box test; an empty box is stored as lo = 1, hi = 0.
+__device__ __forceinline__ bool box_has(const int4 b, int ix, int iy, int iz) {
+    return ix >= (b.x & 0xffff) && ix <= (b.x >> 16) && iy >= (b.y & 0xffff) && iy <= (b.y >> 16) &&
+           iz >= (b.z & 0xffff) && iz <= (b.z >> 16);
+}
+
+__device__ __forceinline__ int4 shfl_box(int4 b, int src) {
+    return make_int4(__shfl_sync(0xffffffffu, b.x, src), __shfl_sync(0xffffffffu, b.y, src),
+                     __shfl_sync(0xffffffffu, b.z, src), 0);
+}
+
+__global__ void k_pack_boxes(const int* __restrict__ ranges, int n, int4* __restrict__ boxes) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int* r = ranges + 6 * k;
+    int v[3];
+    const bool empty = r[1] < r[0] || r[3] < r[2] || r[5] < r[4];
+    for (int a = 0; a < 3; ++a) v[a] = empty ? 1 : (r[2 * a] | (r[2 * a + 1] << 16));
+    boxes[k] = make_int4(v[0], v[1], v[2], 0);
+}
+
+// Per-lane state of one owner slot.
+struct Slot {
+    int key;      // primitive id, -1 when free
+    int4 box;     // its voxel box (packed)
+    float cd;     // <gS, c_key> of the current ray
+    float acc[13];
+};
+
+// Pending flush queue of a warp (per-(ray, primitive) partial sums).
+struct FlushQ {
+    float* q;
+    int n;
+};
+
+__device__ __forceinline__ void queue_make_room(FlushQ& Q, unsigned dm, float* gacc, int lane, const float gsl[2],
+                                                int C, const float4* aux) {
+    if (Q.n + __popc(dm) > QCAP) {
+        __syncwarp();
+        drain_queue(gacc, Q.q, Q.n, lane, gsl, C);
+        __syncwarp();
+        Q.n = 0;
+    }
+}
+
+__device__ __forceinline__ void queue_push(FlushQ& Q, bool mine, unsigned dm, unsigned lt, int key, const float v[13]) {
+    if (mine) {
+        float* ent = Q.q + (Q.n + __popc(dm & lt)) * QW;
+        ent[0] = __int_as_float(key);
+#pragma unroll
+        for (int i = 0; i < 13; ++i) ent[1 + i] = v[i];
+    }
+    Q.n += __popc(dm);
+}
+
+// Owner of slot S leaves when `del`; its sums are queued and the slot freed.
+__device__ __forceinline__ void slot_leave(Slot& S, bool del, FlushQ& Q, float* gacc, int lane, unsigned lt,
+                                           const float gsl[2], int C, const float4* aux) {
+    const unsigned dm = __ballot_sync(0xffffffffu, del);
+    if (!dm) return;
+    queue_make_room(Q, dm, gacc, lane, gsl, C, aux);
+    queue_push(Q, del, dm, lt, S.key, S.acc);
+    if (del) S.key = -1;
+}
+
+__device__ __forceinline__ void slot_copy_from(Slot& dst, const Slot& src_lane_slot, int src, bool take) {
+    const int k = __shfl_sync(0xffffffffu, src_lane_slot.key, src);
+    const float c = __shfl_sync(0xffffffffu, src_lane_slot.cd, src);
+    int4 b;
+    float v[13];
+    b.x = __shfl_sync(0xffffffffu, src_lane_slot.box.x, src);
+    b.y = __shfl_sync(0xffffffffu, src_lane_slot.box.y, src);
+    b.z = __shfl_sync(0xffffffffu, src_lane_slot.box.z, src);
+    b.w = 0;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) v[i] = __shfl_sync(0xffffffffu, src_lane_slot.acc[i], src);
+    if (take) {
+        dst.key = k;
+        dst.cd = c;
+        dst.box = b;
+#pragma unroll
+        for (int i = 0; i < 13; ++i) dst.acc[i] = v[i];
+    }
+}
+
+template <int CP>
+__device__ __forceinline__ void slot_enter(Slot& S, int k, int4 box, const float* __restrict__ lpad,
+                                           const float* __restrict__ gS, int C) {
+    S.key = k;
+    S.box = box;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) S.acc[i] = 0.f;
+    S.cd = logit_dot_sh<CP>(lpad, k, gS);
+}
+
+// Evaluates the slot's pair at x: p_o and partials (kept for the accumulation
+// once G_j is known) and the slot's share of alpha_j and <gS, s_j>.
+__device__ __forceinline__ void slot_eval(const Slot& S, const RenderArgs& a, const float x[3], float& po, float pr[11],
+                                          float& sig, float& pa, float& pv) {
+    po = 0.f;
+    sig = 0.f;
+    if (S.key >= 0) {
+        const BwdPrim P = load_bwd(a.rec, a.aux, S.key);
+        po = occupancy_partials(P, x, pr);
+        sig = P.f.sigma;
+        pa = fmaf(po, sig, pa);
+        pv = fmaf(po, S.cd, pv);
+    }
+}
+
+__device__ __forceinline__ void slot_accumulate(Slot& S, float po, const float pr[11], float sig, float G, float w) {
+    if (S.key >= 0 && po != 0.f) {
+        const float gf = -po * fmaf(G, sig, w * S.cd);
+#pragma unroll
+        for (int i = 0; i < 11; ++i) S.acc[i] = fmaf(gf, pr[i], S.acc[i]);
+        S.acc[11] = fmaf(G, po, S.acc[11]);
+        S.acc[12] = fmaf(w, po, S.acc[12]);
+    }
 }
 
 // One warp per ray, samples back to front (Sec. 3.3.3).  With T_j saved by the
@@ -396,8 +512,7 @@ __global__ void __launch_bounds__(BWD_WARPS * 32, 2) k_backward(BwdArgs A) {
     if (*a.status != SQ_OK) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    WarpBwd& wb = smem[wid];
-    const int ny = a.g.n[1], nz = a.g.n[2];
+    float* gSs = smem[wid].gs;
 
     for (;;) {
         int rr = 0;
@@ -405,46 +520,23 @@ __global__ void __launch_bounds__(BWD_WARPS * 32, 2) k_backward(BwdArgs A) {
         const long long r = __shfl_sync(0xffffffffu, rr, 0);
         if (r >= a.R) break;
         const int Le = __ldg(a.save_n + r);
+        __syncwarp();
+        gSs[lane] = lane < a.C ? __ldg(A.grad_sem + r * a.C + lane) : 0.f;
+        __syncwarp();
         float o[3], d[3];
         ray_of(a, r, o, d);
         const float gD = __ldg(A.grad_depth + r);
         const float* gS = A.grad_sem + r * a.C;
         float gsl[2];
-        gsl[0] = (lane >= NGEO && lane < NGEO + a.C) ? __ldg(gS + (lane - NGEO)) : 0.f;
-        gsl[1] = (lane + 32 < NGEO + a.C) ? __ldg(gS + (lane + 32 - NGEO)) : 0.f;
+        gsl[0] = (lane >= NRAW && lane < NRAW + a.C) ? __ldg(gS + (lane - NRAW)) : 0.f;
+        gsl[1] = (lane + 32 < NRAW + a.C) ? __ldg(gS + (lane + 32 - NRAW)) : 0.f;
 
-        int key[2] = {-1, -1};
-        int box[2][6];
-        float acc[2][13];
-        float cdk[2] = {0.f, 0.f};
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) box[q][i] = 0;
-#pragma unroll
-            for (int i = 0; i < 13; ++i) acc[q][i] = 0.f;
-        }
-        int qn = 0;
+        Slot S0, S1;
+        S0.key = -1;
+        S1.key = -1;
+        FlushQ Q{smem[wid].queue, 0};
         float U = 0.f;
         int pvx = -1, piy = 0, piz = 0, pvox = -1;  // voxel of the previously processed sample (-1: none)
-
-        auto flush = [&](int q, bool del, unsigned dm) {
-            if (!dm) return;
-            if (qn + __popc(dm) > QCAP) {
-                __syncwarp();
-                drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C, a.aux);
-                __syncwarp();
-                qn = 0;
-            }
-            if (del) {
-                float* ent = wb.queue + (qn + __popc(dm & lt)) * QW;
-                ent[0] = __int_as_float(key[q]);
-#pragma unroll
-                for (int i = 0; i < 13; ++i) ent[1 + i] = acc[q][i];
-                key[q] = -1;
-            }
-            qn += __popc(dm);
-        };
 
         for (int j = Le - 1; j >= -1; --j) {
             // j == -1: an empty list releases every owner
@@ -453,81 +545,61 @@ __global__ void __launch_bounds__(BWD_WARPS * 32, 2) k_backward(BwdArgs A) {
             float tj = 0.f;
             if (j >= 0) {
                 tj = __ldg(a.t + j);
-                vox = sample_voxel(a.g, o, d, tj, x);
+                int vi[3];
+                vox = sample_voxel(a.g, o, d, tj, x, vi);
                 if (vox >= 0) {
                     n = __ldg(a.v_n + vox);
                     f = __ldg(a.v_f + vox);
-                    iz = vox % nz;
-                    iy = (vox / nz) % ny;
-                    ix = vox / (ny * nz);
+                    ix = vi[0];
+                    iy = vi[1];
+                    iz = vi[2];
                 }
             }
             const bool heavy = n > OWN;
             if (vox != pvox || heavy) {
                 // owners whose box misses this voxel leave (all of them on an empty or heavy list)
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const bool del = key[q] >= 0 && (n == 0 || heavy || !box_has(box[q], ix, iy, iz));
-                    flush(q, del, __ballot_sync(0xffffffffu, del));
-                }
-                if (n > 0 && !heavy) {
+                const bool gone = n == 0 || heavy;
+                slot_leave(S0, S0.key >= 0 && (gone || !box_has(S0.box, ix, iy, iz)), Q, A.gacc, lane, lt, gsl, a.C,
+                           a.aux);
+                slot_leave(S1, S1.key >= 0 && (gone || !box_has(S1.box, ix, iy, iz)), Q, A.gacc, lane, lt, gsl, a.C,
+                           a.aux);
+                if (!gone) {
                     // slot-1 owners move to free slot-0 lanes
-                    const unsigned o1 = __ballot_sync(0xffffffffu, key[1] >= 0);
-                    if (o1) {
-                        const unsigned f0 = __ballot_sync(0xffffffffu, key[0] < 0);
-                        const int mv = min(__popc(o1), __popc(f0));
-                        if (mv > 0) {
+                    const unsigned o1 = __ballot_sync(0xffffffffu, S1.key >= 0);
+                    if (SQR_MIGRATE && o1) {
+                        const unsigned f0 = __ballot_sync(0xffffffffu, S0.key < 0);
+                        const int mv = __popc(o1);
+                        if (mv <= __popc(f0)) {
                             const int rk = __popc(f0 & lt);
-                            const bool take = key[0] < 0 && rk < mv;
+                            const bool take = S0.key < 0 && rk < mv;
                             const int src = take ? __fns(o1, 0, rk + 1) : lane;
-                            const int k1 = __shfl_sync(0xffffffffu, key[1], src);
-                            const float c1 = __shfl_sync(0xffffffffu, cdk[1], src);
-                            int b1[6];
-                            float a1[13];
-#pragma unroll
-                            for (int i = 0; i < 6; ++i) b1[i] = __shfl_sync(0xffffffffu, box[1][i], src);
-#pragma unroll
-                            for (int i = 0; i < 13; ++i) a1[i] = __shfl_sync(0xffffffffu, acc[1][i], src);
-                            const bool given = key[1] >= 0 && __popc(o1 & lt) < mv;
-                            if (take) {
-                                key[0] = k1;
-                                cdk[0] = c1;
-#pragma unroll
-                                for (int i = 0; i < 6; ++i) box[0][i] = b1[i];
-#pragma unroll
-                                for (int i = 0; i < 13; ++i) acc[0][i] = a1[i];
-                            }
-                            if (given) key[1] = -1;
+                            const bool given = S1.key >= 0 && __popc(o1 & lt) < mv;
+                            slot_copy_from(S0, S1, src, take);
+                            if (given) S1.key = -1;
                         }
                     }
                     // list entries whose box misses the previous voxel are new owners
-                    const int e0 = lane, e1 = lane + 32;
                     int kn0 = -1, kn1 = -1;
+                    int4 bx0 = make_int4(1, 1, 1, 0), bx1 = make_int4(1, 1, 1, 0);
                     bool new0 = false, new1 = false;
-                    int nb0[6], nb1[6];
-                    if (e0 < n) {
-                        kn0 = __ldg(a.v_sq + f + e0);
-                        const int* bp = A.ranges + 6 * (size_t)kn0;
-#pragma unroll
-                        for (int i = 0; i < 6; ++i) nb0[i] = __ldg(bp + i);
-                        new0 = pvox < 0 || !box_has(nb0, pvx, piy, piz);
+                    if (lane < n) {
+                        kn0 = __ldg(a.v_sq + f + lane);
+                        bx0 = __ldg(A.boxes + kn0);
+                        new0 = pvox < 0 || !box_has(bx0, pvx, piy, piz);
                     }
-                    if (e1 < n) {
-                        kn1 = __ldg(a.v_sq + f + e1);
-                        const int* bp = A.ranges + 6 * (size_t)kn1;
-#pragma unroll
-                        for (int i = 0; i < 6; ++i) nb1[i] = __ldg(bp + i);
-                        new1 = pvox < 0 || !box_has(nb1, pvx, piy, piz);
+                    if (lane + 32 < n) {
+                        kn1 = __ldg(a.v_sq + f + lane + 32);
+                        bx1 = __ldg(A.boxes + kn1);
+                        new1 = pvox < 0 || !box_has(bx1, pvx, piy, piz);
                     }
                     const unsigned nm0 = __ballot_sync(0xffffffffu, new0), nm1 = __ballot_sync(0xffffffffu, new1);
                     const int c0 = __popc(nm0), nnew = c0 + __popc(nm1);
                     if (nnew) {
-                        const unsigned fr0 = __ballot_sync(0xffffffffu, key[0] < 0);
-                        const unsigned fr1 = __ballot_sync(0xffffffffu, key[1] < 0);
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            const int rk = (q == 0) ? __popc(fr0 & lt) : __popc(fr0) + __popc(fr1 & lt);
-                            const bool want = key[q] < 0 && rk < nnew;
+                        const unsigned fr0 = __ballot_sync(0xffffffffu, S0.key < 0);
+                        const unsigned fr1 = __ballot_sync(0xffffffffu, S1.key < 0);
+                        {
+                            const int rk = __popc(fr0 & lt);
+                            const bool want = S0.key < 0 && rk < nnew;
                             int src = lane;
                             bool hi = false;
                             if (want) {
@@ -536,45 +608,37 @@ __global__ void __launch_bounds__(BWD_WARPS * 32, 2) k_backward(BwdArgs A) {
                             }
                             const int va = __shfl_sync(0xffffffffu, kn0, src);
                             const int vb = __shfl_sync(0xffffffffu, kn1, src);
+                            const int4 ba = shfl_box(bx0, src), bb1 = shfl_box(bx1, src);
+                            const int4 bb = hi ? bb1 : ba;
+                            if (want) slot_enter<CP>(S0, hi ? vb : va, bb, a.lpad, gSs, a.C);
+                        }
+                        if (nnew > __popc(fr0)) {
+                            const int rk = __popc(fr0) + __popc(fr1 & lt);
+                            const bool want = S1.key < 0 && rk < nnew;
+                            int src = lane;
+                            bool hi = false;
                             if (want) {
-                                const int k = hi ? vb : va;
-                                key[q] = k;
-                                const int* bp = A.ranges + 6 * (size_t)k;
-#pragma unroll
-                                for (int i = 0; i < 6; ++i) box[q][i] = __ldg(bp + i);
-#pragma unroll
-                                for (int i = 0; i < 13; ++i) acc[q][i] = 0.f;
-                                cdk[q] = logit_dot<CP>(a.lpad, k, gS, a.C);
+                                if (rk < c0) src = __fns(nm0, 0, rk + 1);
+                                else { src = __fns(nm1, 0, rk - c0 + 1); hi = true; }
                             }
+                            const int va = __shfl_sync(0xffffffffu, kn0, src);
+                            const int vb = __shfl_sync(0xffffffffu, kn1, src);
+                            const int4 ba = shfl_box(bx0, src), bb1 = shfl_box(bx1, src);
+                            const int4 bb = hi ? bb1 : ba;
+                            if (want) slot_enter<CP>(S1, hi ? vb : va, bb, a.lpad, gSs, a.C);
                         }
                     }
                 }
-                pvox = (n > 0 && !heavy) ? vox : -1;
+                pvox = gone ? -1 : vox;
                 pvx = ix; piy = iy; piz = iz;
             }
             if (j < 0) break;
             if (n == 0) continue;  // no primitive here: alpha_j = 0 leaves U unchanged
-            // owned (or, on a heavy list, all) pairs: partials, alpha_j and <gS, s_j>
-            float po[2] = {0.f, 0.f};
-            float pr[2][11];
-            float sig[2] = {0.f, 0.f};
+            float po0, po1 = 0.f, pr0[11], pr1[11], sg0, sg1 = 0.f;
             float pa = 0.f, pv = 0.f;
-            const bool any1 = __any_sync(0xffffffffu, key[1] >= 0);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (q == 1 && !any1) {
-#pragma unroll
-                    for (int i = 0; i < 11; ++i) pr[1][i] = 0.f;
-                    continue;
-                }
-                if (key[q] >= 0) {
-                    const BwdPrim P = load_bwd(a.rec, a.aux, key[q]);
-                    po[q] = occupancy_partials(P, x, pr[q]);
-                    sig[q] = P.f.sigma;
-                    pa = fmaf(po[q], sig[q], pa);
-                    pv = fmaf(po[q], cdk[q], pv);
-                }
-            }
+            slot_eval(S0, a, x, po0, pr0, sg0, pa, pv);
+            const bool any1 = __any_sync(0xffffffffu, S1.key >= 0);
+            if (any1) slot_eval(S1, a, x, po1, pr1, sg1, pa, pv);
             if (heavy) {
                 for (int e = lane; e < n; e += 32) {
                     const int k = __ldg(a.v_sq + f + e);
@@ -591,60 +655,67 @@ __global__ void __launch_bounds__(BWD_WARPS * 32, 2) k_backward(BwdArgs A) {
             const float vj = fmaf(gD, tj, vs);
             const float G = raw > a.alpha_max ? 0.f : Tj * (vj - U);  // dL/dalpha_j
             const float w = Tj * alpha;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (key[q] >= 0 && po[q] != 0.f) {
-                    const float gf = -po[q] * fmaf(G, sig[q], w * cdk[q]);
-#pragma unroll
-                    for (int i = 0; i < 11; ++i) acc[q][i] = fmaf(gf, pr[q][i], acc[q][i]);
-                    acc[q][11] = fmaf(G, po[q], acc[q][11]);
-                    acc[q][12] = fmaf(w, po[q], acc[q][12]);
-                }
-            }
+            slot_accumulate(S0, po0, pr0, sg0, G, w);
+            if (any1) slot_accumulate(S1, po1, pr1, sg1, G, w);
             if (heavy) {
-                // per-pair atomics for the whole list
-                for (int e = lane; e < n; e += 32) {
-                    const int k = __ldg(a.v_sq + f + e);
-                    const BwdPrim P = load_bwd(a.rec, a.aux, k);
-                    float pp[11];
-                    const float pe = occupancy_partials(P, x, pp);
-                    if (pe == 0.f) continue;
-                    const float gf = -pe * fmaf(G, P.f.sigma, w * logit_dot<CP>(a.lpad, k, gS, a.C));
-                    float ent[13];
+                // every pair of a heavy list is queued on its own
+                for (int e0 = 0; e0 < n; e0 += 32) {
+                    const int e = e0 + lane;
+                    float v[13];
+                    int k = -1;
+                    bool mine = false;
+                    if (e < n) {
+                        k = __ldg(a.v_sq + f + e);
+                        const BwdPrim P = load_bwd(a.rec, a.aux, k);
+                        float pp[11];
+                        const float pe = occupancy_partials(P, x, pp);
+                        const float gf = -pe * fmaf(G, P.f.sigma, w * logit_dot<CP>(a.lpad, k, gS, a.C));
 #pragma unroll
-                    for (int i = 0; i < 11; ++i) ent[i] = gf * pp[i];
-                    ent[11] = G * pe;
-                    ent[12] = w * pe;
-                    float* row = A.gacc + (size_t)k * GF;
-                    for (int fld = 0; fld < NGEO + a.C; ++fld) {
-                        const float v = grad_field(fld, ent, a.aux, k, fld >= NGEO ? __ldg(gS + fld - NGEO) : 0.f);
-                        if (v != 0.f) red_add(row + fld, v);
+                        for (int i = 0; i < 11; ++i) v[i] = gf * pp[i];
+                        v[11] = G * pe;
+                        v[12] = w * pe;
+                        mine = pe != 0.f;
+                    }
+                    const unsigned dm = __ballot_sync(0xffffffffu, mine);
+                    if (dm) {
+                        queue_make_room(Q, dm, A.gacc, lane, gsl, a.C, a.aux);
+                        queue_push(Q, mine, dm, lt, k, v);
                     }
                 }
             }
             U = fmaf(alpha, vj, (1.f - alpha) * U);
         }
         __syncwarp();
-        drain_queue(A.gacc, wb.queue, qn, lane, gsl, a.C, a.aux);
+        drain_queue(A.gacc, Q.q, Q.n, lane, gsl, a.C);
         __syncwarp();
     }
 }
 
-// Scatter of the [N, GF] accumulator into the six gradient outputs.
-__global__ void k_grad_out(const float* __restrict__ gacc, int n, int C, float* __restrict__ gm, float* __restrict__ gq,
-                           float* __restrict__ gs, float* __restrict__ ge, float* __restrict__ go,
-                           float* __restrict__ gl) {
-    const long long total = (long long)n * GF;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(i / GF), fld = (int)(i - (long long)k * GF);
-        const float v = gacc[i];
-        if (fld < 3) gm[3 * k + fld] = v;
-        else if (fld < 7) gq[4 * k + fld - 3] = v;
-        else if (fld < 10) gs[3 * k + fld - 7] = v;
-        else if (fld < 12) ge[2 * k + fld - 10] = v;
-        else if (fld == 12) go[k] = v;
-        else if (fld - NGEO < C) gl[(size_t)k * C + fld - NGEO] = v;
+// Converts each primitive's summed partials into the six gradient outputs:
+//   dL/dm = -sum gx;  dL/dq = (0, 2 tau) (x) qn / |q| (the torque of a world-frame
+//   rotation mapped onto the tangent of the unit quaternion, then through q/|q|);
+//   dL/ds_j = -sum(u_j df/du_j) / s_j;  dL/deps, dL/dsigma as summed;
+//   dL/dc as accumulated.  One thread per primitive.
+__global__ void k_grad_out(const float* __restrict__ gacc, const float4* __restrict__ aux, int n, int C,
+                           float* __restrict__ gm, float* __restrict__ gq, float* __restrict__ gs,
+                           float* __restrict__ ge, float* __restrict__ go, float* __restrict__ gl) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float* e = gacc + (size_t)k * GF;
+    const float4 a0 = aux[(size_t)k * AUX4], a1 = aux[(size_t)k * AUX4 + 1];
+    const float w = a0.x, v[3] = {a0.y, a0.z, a0.w}, inq = a1.x, is[3] = {a1.y, a1.z, a1.w};
+    for (int i = 0; i < 3; ++i) gm[3 * k + i] = -e[i];
+    const float t[3] = {e[3], e[4], e[5]};
+    gq[4 * k + 0] = -2.f * (t[0] * v[0] + t[1] * v[1] + t[2] * v[2]) * inq;
+    for (int i = 0; i < 3; ++i) {
+        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+        gq[4 * k + 1 + i] = 2.f * (w * t[i] + t[i1] * v[i2] - t[i2] * v[i1]) * inq;
     }
+    for (int i = 0; i < 3; ++i) gs[3 * k + i] = -e[6 + i] * is[i];
+    ge[2 * k + 0] = e[9];
+    ge[2 * k + 1] = e[10];
+    go[k] = e[11];
+    for (int c = 0; c < C; ++c) gl[(size_t)k * C + c] = e[NRAW + c];
 }
 
 // ------------------------------------------------------------------ pair counter
@@ -725,7 +796,7 @@ sq_status_t launch_pack(const sq_prims_t* prims, float4* rec, float4* aux, float
 // Render workspace: packed records, backward extras, padded logits, gradient
 // accumulator [N, 32] and the work counter.
 struct RenderWs {
-    size_t rec_off, aux_off, lpad_off, gacc_off, ctr_off, total;
+    size_t rec_off, aux_off, lpad_off, gacc_off, box_off, ctr_off, total;
 };
 
 static RenderWs render_ws(const sq_prims_t* p) {
@@ -736,7 +807,8 @@ static RenderWs render_ws(const sq_prims_t* p) {
     w.aux_off = align_up(n * REC4 * sizeof(float4), 256);
     w.lpad_off = align_up(w.aux_off + n * AUX4 * sizeof(float4), 256);
     w.gacc_off = align_up(w.lpad_off + n * cp * sizeof(float), 256);
-    w.ctr_off = align_up(w.gacc_off + n * GF * sizeof(float), 256);
+    w.box_off = align_up(w.gacc_off + n * GF * sizeof(float), 256);
+    w.ctr_off = align_up(w.box_off + n * sizeof(int4), 256);
     w.total = w.ctr_off + 256;
     return w;
 }
@@ -790,6 +862,7 @@ static sq_status_t setup_render(const sq_prims_t* prims, const sq_index_t* idx, 
     a.save_T = nullptr;
     a.save_n = nullptr;
     if (gacc) *gacc = (float*)(base + w.gacc_off);
+    a.boxes = (int4*)(base + w.box_off);
     return SQ_OK;
 }
 
@@ -883,8 +956,14 @@ sq_status_t render_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, cons
     if (e != cudaSuccess) return cuda_status(e, "memset gradient accumulator");
     A.grad_depth = grad_depth;
     A.grad_sem = grad_sem;
-    A.ranges = idx->ranges;
+    A.boxes = A.r.boxes;
     A.gacc = gacc;
+    if (grid->nx > 65535 || grid->ny > 65535 || grid->nz > 65535) {
+        set_last_error("sq_render_bwd: grid dims above 65535 per axis are not supported");
+        return SQ_ERR_INVALID_ARG;
+    }
+    k_pack_boxes<<<(n + 127) / 128, 128, 0, st>>>(idx->ranges, n, A.r.boxes);
+    SQ_CHECK_LAUNCH("k_pack_boxes");
     if (A.r.R > 0) {
         const int cp = cpad(C);
         sq_status_t ls;
@@ -901,9 +980,8 @@ sq_status_t render_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, cons
         }
         if (ls != SQ_OK) return ls;
     }
-    long long total = (long long)n * GF;
-    int blocks = (int)((total + 255) / 256 < 152LL * 16 ? (total + 255) / 256 : 152LL * 16);
-    k_grad_out<<<blocks, 256, 0, st>>>(gacc, n, C, g_means, g_quats, g_scales, g_eps, g_opacity, g_logits);
+    k_grad_out<<<(n + 127) / 128, 128, 0, st>>>(gacc, A.r.aux, n, C, g_means, g_quats, g_scales, g_eps, g_opacity,
+                                                g_logits);
     SQ_CHECK_LAUNCH("k_grad_out");
     return SQ_OK;
 }
