@@ -160,6 +160,23 @@ sq_status_t sq_render_fwd(const sq_prims_t* prims, const sq_index_t* index, cons
                           const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* saved,
                           size_t saved_bytes, void* workspace, size_t workspace_bytes, void* stream);
 
+/* No counterpart in the paper.  The forward render of sq_render_fwd for callers
+ * that cannot allocate device memory when they render and have no workspace to
+ * lend the library -- for instance a real-time loop that forbids allocation after
+ * start-up (cudaMalloc can block and synchronise the device), or a plugin whose
+ * host framework owns every device buffer.  Same arguments and outputs as
+ * sq_render_fwd without saved state or workspace: the scratch comes from a
+ * buffer built into the library (a static device array of about 7.4 MB, held on
+ * every device that loads the library until exit).  Limits: prims->n at most
+ * SQ_NOALLOC_MAX_PRIMS (otherwise SQ_ERR_INVALID_ARG, no work done).  The first
+ * call on each device looks up the buffer's device address; make that first
+ * call before any stream capture.  All calls share the buffer, so calls that
+ * overlap on the GPU race; order them (one stream, or events).  Allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library call. */
+#define SQ_NOALLOC_MAX_PRIMS 16384
+sq_status_t sq_render_fwd_noalloc(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
+                                  const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* stream);
+
 /* Sec. 3.3.3 backward pass: given dL/d depth [R] and dL/d sem [R, n_classes]
  * and the state a forward call with the same inputs saved, overwrites
  * g_means [n,3], g_quats [n,4] (w.r.t. the raw, unnormalised quaternion),

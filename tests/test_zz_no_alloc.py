@@ -1,0 +1,72 @@
+"""sq_render_fwd_noalloc: the forward render for callers that cannot allocate device
+memory at render time (a real-time loop that forbids allocation after start-up,
+or a plugin whose host owns every device buffer).  Its scratch is a buffer built
+into the library, so the test checks that two calls in a row through the C ABI
+give the same depth, semantics and transmittance as sq_render_fwd with a
+caller-provided workspace, and that a scene beyond the built-in limit is refused.
+This file is collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2511_17361_gb300 import synth
+from tests.gpu_common import check_depth, check_sem, dev_grid, lib
+
+pytestmark = pytest.mark.gpu
+
+
+def _call_noalloc(sqr, prims_d, ix, grid, rays, C):
+    L = sqr.lib
+    P = ctypes.POINTER
+    L.sq_render_fwd_noalloc.argtypes = [P(sqr.SqPrims), P(sqr.SqIndex), P(sqr.SqGrid), P(sqr.SqRays),
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.sq_render_fwd_noalloc.restype = ctypes.c_int
+    depth = torch.full((rays.R,), -1.0, device="cuda")
+    sem = torch.full((rays.R, C), -1.0, device="cuda")
+    tf = torch.full((rays.R,), -1.0, device="cuda")
+    p, g, r, i = sqr.prims_struct(prims_d), sqr.grid_struct(grid), rays.struct(), ix.struct()
+    st = L.sq_render_fwd_noalloc(ctypes.byref(p), ctypes.byref(i), ctypes.byref(g), ctypes.byref(r),
+                                 ctypes.c_void_p(depth.data_ptr()), ctypes.c_void_p(sem.data_ptr()),
+                                 ctypes.c_void_p(tf.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return st, depth, sem, tf
+
+
+def test_noalloc_forward_matches_workspace_forward_twice():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sqr = lib()
+    cfg = synth.make_config(0)
+    C = cfg["prims"]["logits"].shape[1]
+    prims_d = sqr.to_device(cfg["prims"])
+    rays = sqr.Rays.from_rig(cfg["rig"], cfg["t"])
+    grid = dev_grid(cfg["grid"])
+    ix = sqr.build_index(prims_d, grid)
+    d_ref, s_ref, t_ref = sqr.render_fwd(prims_d, ix, grid, rays)
+    torch.cuda.synchronize()
+    d_ref, s_ref, t_ref = (x.cpu().numpy().astype(np.float64) for x in (d_ref, s_ref, t_ref))
+    for _ in range(2):
+        st, d, s, t = _call_noalloc(sqr, prims_d, ix, grid, rays, C)
+        assert st == sqr.SQ_OK, sqr.lib.sq_last_error()
+        torch.cuda.synchronize()
+        check_depth(d.cpu().numpy(), d_ref, 0.5)
+        check_sem(s.cpu().numpy(), s_ref)
+        assert np.max(np.abs(t.cpu().numpy() - t_ref)) <= 1e-6
+
+
+def test_noalloc_forward_refuses_scenes_beyond_its_scratch():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sqr = lib()
+    cfg = synth.make_config(0)
+    big = synth.prims_uniform(16385, 3)
+    prims_d = sqr.to_device(big)
+    rays = sqr.Rays.from_rig(cfg["rig"], cfg["t"])
+    grid = dev_grid(cfg["grid"])
+    ix = sqr.build_index(prims_d, grid)
+    st, d, _, _ = _call_noalloc(sqr, prims_d, ix, grid, rays, big["logits"].shape[1])
+    assert st == sqr.SQ_ERR_INVALID_ARG
+    assert b"16384" in sqr.lib.sq_last_error()
+    torch.cuda.synchronize()
+    assert torch.all(d == -1.0)
