@@ -323,6 +323,94 @@ def run_mine(args):
     return 0
 
 
+# ----------------------------------------------------------------------- batched workload
+def run_batch(args):
+    """Twelve uneven scenes: per-scene launches vs one batched persistent launch per
+    pass (autotuned), the whole step captured in a CUDA graph."""
+    import torch
+    from paper_2511_17361_gb300 import _build
+    _build.build()
+    from paper_2511_17361_gb300 import sqr
+    dev = torch.device("cuda", 0)
+    cfgs = synth.make_batch_config(3)
+    scenes, targets = [], []
+    for i, c in enumerate(cfgs):
+        prims = sqr.to_device(c["prims"], dev)
+        rays = sqr.Rays.from_rig(c["rig"], c["t"], device=dev)
+        grid = {"n": c["grid"]["n"], "lo": [float(v) for v in c["grid"]["lo"]], "vs": [float(v) for v in c["grid"]["vs"]]}
+        ix = sqr.build_index(prims, grid)
+        sc = sqr.Scene(prims, ix, grid, rays, training=True)
+        td, tl = synth.loss_targets(rays.R, 300 + i)
+        C = c["prims"]["logits"].shape[1]
+        targets.append((torch.from_numpy(td).to(dev), torch.from_numpy(tl).to(dev),
+                        (torch.empty(1, device=dev), torch.empty(rays.R, device=dev),
+                         torch.empty((rays.R, C), device=dev))))
+        scenes.append(sc)
+    samples = sum(sc.rays.R * sc.rays.t.numel() for sc in scenes)
+
+    def loss_all():
+        for sc, (td, tl, out) in zip(scenes, targets):
+            sqr.loss_ce_mse(sc.depth, sc.sem, td, tl, out=out)
+            sc.grad_depth.copy_(out[1])
+            sc.grad_sem.copy_(out[2])
+
+    def per_scene_step():
+        for sc, (td, tl, out) in zip(scenes, targets):
+            sqr.build_index(sc.prims, sc.grid, index=sc.index, sync=False)
+            sqr.render_fwd(sc.prims, sc.index, sc.grid, sc.rays, out=(sc.depth, sc.sem, sc.t_final), saved=sc.saved)
+            sqr.loss_ce_mse(sc.depth, sc.sem, td, tl, out=out)
+            sqr.render_bwd(sc.prims, sc.index, sc.grid, sc.rays, out[1], out[2], saved=sc.saved, out=sc.grads)
+
+    tuning = sqr.autotune(scenes, reps=2)
+
+    def batched_step():
+        for sc in scenes:
+            sqr.build_index(sc.prims, sc.grid, index=sc.index, sync=False)
+        sqr.render_batched(sqr.SQ_OP_FWD, scenes, tuning)
+        loss_all()
+        sqr.render_batched(sqr.SQ_OP_BWD, scenes, tuning)
+
+    def timed(fn, steps):
+        flush = torch.empty(64 * 1024 * 1024, device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for s in range(steps):
+            flush.fill_(float(s))
+            ev[s][0].record()
+            fn()
+            ev[s][1].record()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    for _ in range(args.warmup):
+        per_scene_step()
+        batched_step()
+    ms_per_scene = timed(per_scene_step, args.steps)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        batched_step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batched_step()
+    ms_graph = timed(graph.replay, args.steps)
+    ms_batched = timed(batched_step, args.steps)
+    line = {"metric": "ray-samples/s (forward + backward), 12-scene uneven batch", "value": samples / (ms_graph / 1e3),
+            "unit": "ray-samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch12_uneven", "scenes": len(scenes), "ray_samples": samples,
+                       "rays": [sc.rays.R for sc in scenes], "superquadrics": [int(sc.prims["means"].shape[0])
+                                                                             for sc in scenes],
+                       "samples_per_ray": [int(sc.rays.t.numel()) for sc in scenes], "tuning": tuning,
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "per_scene_launches": {"ms_per_step": ms_per_scene, "value": samples / (ms_per_scene / 1e3)},
+            "batched_eager": {"ms_per_step": ms_batched, "value": samples / (ms_batched / 1e3)},
+            "batched_graph": {"ms_per_step": ms_graph, "value": samples / (ms_graph / 1e3)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,11 +419,15 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--workload", choices=["frame", "batch"], default="frame",
+                    help="frame: one six-camera frame (default); batch: 12 uneven scenes, batched vs per scene")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_mine(args)
 
 

@@ -191,6 +191,65 @@ sq_status_t sq_render_bwd(const sq_prims_t* prims, const sq_index_t* index, cons
                           const float* grad_sem, float* g_means, float* g_quats, float* g_scales, float* g_eps,
                           float* g_opacity, float* g_logits, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Batched rendering of many scenes (uneven primitive, camera, ray and sample
+ * counts) in one persistent launch per pass: the rays of all scenes form one
+ * range handed out by a global work counter, so a launch stays busy until the
+ * last ray of the last scene.  The paper renders the 2T+1 frames of its temporal
+ * horizon per training step (Sec. 3.2); here any set of scenes sharing
+ * n_classes can be batched.  A scene carries what sq_render_fwd and
+ * sq_render_bwd take: for SQ_OP_FWD depth/sem/t_final outputs and an optional
+ * saved buffer; for SQ_OP_BWD the saved buffer written by the forward, the
+ * cotangents and the six gradient outputs.  Only kernel launches and async
+ * memsets are issued (the scene descriptors travel as kernel arguments), so a
+ * call can be captured in a CUDA graph. */
+#define SQ_MAX_BATCH 32
+typedef struct {
+    sq_prims_t prims;
+    sq_index_t index;
+    sq_grid_t grid;
+    sq_rays_t rays;
+    float* depth;        /* [R] forward outputs */
+    float* sem;          /* [R, C] */
+    float* t_final;      /* [R], nullable */
+    void* saved;         /* sq_saved_size(&rays) bytes; nullable for inference forwards */
+    size_t saved_bytes;
+    const float* grad_depth; /* [R] backward inputs */
+    const float* grad_sem;   /* [R, C] */
+    float* g_means;      /* backward outputs, as in sq_render_bwd */
+    float* g_quats;
+    float* g_scales;
+    float* g_eps;
+    float* g_opacity;
+    float* g_logits;
+} sq_scene_t;
+
+/* Launch configuration: lanes (= samples marched together) per ray in the
+ * forward (8 or 16), warps per CTA in the forward and backward (1..8).  The
+ * defaults are {8, 8, 8}. */
+typedef struct {
+    int fwd_lanes_per_ray;
+    int fwd_warps_per_cta;
+    int bwd_warps_per_cta;
+} sq_tuning_t;
+
+/* Workspace bytes for sq_render_batched / sq_autotune on these scenes. */
+size_t sq_batched_workspace_size(const sq_scene_t* scenes, int n_scenes);
+
+/* op = SQ_OP_FWD or SQ_OP_BWD over n_scenes (1..SQ_MAX_BATCH) scenes; tuning
+ * nullable (defaults).  Scenes must share n_classes. */
+sq_status_t sq_render_batched(int op, const sq_scene_t* scenes, int n_scenes, const sq_tuning_t* tuning,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
+/* Autotuner: times every forward configuration (lanes per ray x warps per CTA)
+ * and, when every scene has saved state and cotangents, every backward one on
+ * these scenes (reps timed launches each, CUDA events on the stream) and writes
+ * the fastest to *best.  fwd_ms[4] / bwd_ms[2] (nullable) receive the mean
+ * times of the candidates in the order {8,4},{8,8},{16,4},{16,8} and {4},{8}.
+ * Host-synchronous and overwrites the scenes' outputs; call it outside any
+ * stream capture. */
+sq_status_t sq_autotune(const sq_scene_t* scenes, int n_scenes, void* workspace, size_t workspace_bytes, void* stream,
+                        int reps, sq_tuning_t* best, float* fwd_ms, float* bwd_ms);
+
 /* Supp. A.4 voxelisation at every voxel centre p = lo + (i + 0.5) vs (FP32):
  *   density[v] = sum_{k in Q(v)} p_o(p, S_k) sigma_k, sem[v, :] = sum p_o c_k,
  *   label[v] = argmax_c sem[v, c] (lowest c on ties) if density >= tau, else

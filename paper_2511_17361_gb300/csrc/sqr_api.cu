@@ -116,6 +116,27 @@ size_t saved_size(const sq_rays_t* r);
 sq_status_t query_grid_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, float, float*, float*,
                             unsigned char*, void*, size_t, cudaStream_t);
 sq_status_t count_pairs_impl(const sq_index_t*, const sq_grid_t*, const sq_rays_t*, long long*, cudaStream_t);
+size_t batched_workspace_size(const sq_scene_t* scenes, int n);
+sq_status_t batched_api_impl(int op, const sq_scene_t* sc, int n, const sq_tuning_t* tuning, void* ws, size_t ws_bytes,
+                             cudaStream_t st);
+sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes, cudaStream_t st, sq_tuning_t* best,
+                          float* fwd_ms, float* bwd_ms, int reps);
+
+// Host checks of every scene of a batch.
+static sq_status_t check_scenes(const sq_scene_t* sc, int n) {
+    if (!sc || n < 1 || n > SQ_MAX_BATCH) {
+        set_last_error("scenes: %d scenes, 1..%d supported", n, SQ_MAX_BATCH);
+        return SQ_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n; ++i) {
+        sq_status_t s;
+        if ((s = check_prims(&sc[i].prims)) != SQ_OK) return s;
+        if ((s = check_grid(&sc[i].grid)) != SQ_OK) return s;
+        if ((s = check_index(&sc[i].index, &sc[i].grid, sc[i].prims.n)) != SQ_OK) return s;
+        if ((s = check_rays(&sc[i].rays)) != SQ_OK) return s;
+    }
+    return SQ_OK;
+}
 
 // ------------------------------------------------------------------ loss
 namespace {
@@ -292,6 +313,34 @@ sq_status_t sq_count_pairs(const sq_index_t* index, const sq_grid_t* grid, const
     if ((s = check_rays(rays)) != SQ_OK) return s;
     if (!out) { set_last_error("sq_count_pairs: out is NULL"); return SQ_ERR_INVALID_ARG; }
     return count_pairs_impl(index, grid, rays, out, (cudaStream_t)stream);
+}
+
+size_t sq_batched_workspace_size(const sq_scene_t* scenes, int n_scenes) {
+    if (check_scenes(scenes, n_scenes) != SQ_OK) return 0;
+    return batched_workspace_size(scenes, n_scenes);
+}
+
+sq_status_t sq_render_batched(int op, const sq_scene_t* scenes, int n_scenes, const sq_tuning_t* tuning,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+    sq_status_t s;
+    if ((s = check_scenes(scenes, n_scenes)) != SQ_OK) return s;
+    if (op != SQ_OP_FWD && op != SQ_OP_BWD) {
+        set_last_error("sq_render_batched: op %d is not SQ_OP_FWD or SQ_OP_BWD", op);
+        return SQ_ERR_INVALID_ARG;
+    }
+    return batched_api_impl(op, scenes, n_scenes, tuning, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+sq_status_t sq_autotune(const sq_scene_t* scenes, int n_scenes, void* workspace, size_t workspace_bytes, void* stream,
+                        int reps, sq_tuning_t* best, float* fwd_ms, float* bwd_ms) {
+    sq_status_t s;
+    if ((s = check_scenes(scenes, n_scenes)) != SQ_OK) return s;
+    if (!best) {
+        set_last_error("sq_autotune: best is NULL");
+        return SQ_ERR_INVALID_ARG;
+    }
+    return autotune_impl(scenes, n_scenes, workspace, workspace_bytes, (cudaStream_t)stream, best, fwd_ms, bwd_ms,
+                         reps);
 }
 
 }  // extern "C"

@@ -1,0 +1,226 @@
+// sqr_fwd.cu -- forward render (Sec. 3.3.2, Eq. 2, 4-6) on sm_103a.
+//
+// A warp marches 32/GS rays at a time, GS lanes per ray, one lane per sample.
+// Each lane walks its own sample's voxel list (Sec. 3.3.1), so the sums of Eq. 4
+// (alpha = sum p sigma, s = sum p c) stay in the lane's registers; compositing
+// (Eq. 5-6) of a group's GS samples is a GS-lane product scan of (1 - alpha).
+// Rays of all scenes of the batch are handed out by one global counter, so a
+// lane group whose ray ends early takes the next ray, from whichever scene.
+// The forward saves T_j before every sample and the number of composited
+// samples for the backward sweep.
+#include "sqr_render.cuh"
+
+namespace sqr {
+
+namespace {
+
+template <int GS>
+__device__ __forceinline__ float group_incl_prod(float v, int s) {
+#pragma unroll
+    for (int o = 1; o < GS; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, v, o, GS);
+        if (s >= o) v *= y;
+    }
+    return v;
+}
+
+// Compositing (Eq. 5) of a group's GS consecutive samples.  Lane s holds alpha
+// (0 for lanes past L or outside the grid).  Returns w = T_before * alpha (0 past
+// an early termination) and T_before; advances T (uniform in the group); `stop`
+// when kappa > 0 ends the ray inside this chunk, `used` = samples composited.
+template <int GS>
+__device__ __forceinline__ float group_composite(float alpha, int s, int gbase, float kappa, float& T, float& Tb,
+                                                 bool valid, int& used, bool& stop) {
+    const float incl = group_incl_prod<GS>(1.f - alpha, s);
+    float excl = __shfl_up_sync(0xffffffffu, incl, 1, GS);
+    if (s == 0) excl = 1.f;
+    Tb = T * excl;
+    float w = Tb * alpha;
+    used = GS;
+    stop = false;
+    const unsigned gmask = (GS == 32) ? 0xffffffffu : ((1u << GS) - 1u);
+    const unsigned kill = __ballot_sync(0xffffffffu, valid && kappa > 0.f && T * incl < kappa);
+    const unsigned gk = (kill >> gbase) & gmask;
+    if (gk) {
+        const int ls = __ffs(gk) - 1;
+        if (s > ls) w = 0.f;
+        used = ls + 1;
+        stop = true;
+    }
+    const float tot = __shfl_sync(0xffffffffu, incl, gbase + (gk ? (__ffs(gk) - 1) : GS - 1));
+    T = T * tot;
+    return w;
+}
+
+template <int CP, int GS>
+__global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
+    const int lane = threadIdx.x & 31;
+    const int s = lane & (GS - 1), gbase = lane & ~(GS - 1);
+    const unsigned gmask = (GS == 32) ? 0xffffffffu : ((1u << GS) - 1u);
+
+    // draw the group's first ray
+    int gn = 0;
+    if (s == 0) gn = atomicAdd(B.ctr, 1);
+    long long gr = __shfl_sync(0xffffffffu, gn, gbase);
+    int si = 0;
+    long long r = 0;
+    bool live = gr < B.total;
+    if (live) {
+        si = scene_of(B, gr);
+        r = gr - __ldg(B.off + si);
+        if (*B.d[si].status != SQ_OK) live = false;
+    }
+    float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f};
+    if (live) scene_ray(B.d[si], r, o, d);
+    float T = 1.f, Dp = 0.f;
+    int j0 = 0, used_total = 0;
+    bool seen_inside = false;
+    float acc[CP];
+#pragma unroll
+    for (int c = 0; c < CP; ++c) acc[c] = 0.f;
+
+    while (__any_sync(0xffffffffu, gr < B.total)) {
+        const SceneDesc& S = B.d[si];
+        const int L = S.L;
+        const int j = j0 + s;
+        const bool valid = live && j < L;
+        float x[3] = {0.f, 0.f, 0.f};
+        int vox = -1;
+        float tj = 0.f;
+        if (valid) {
+            tj = __ldg(S.t + j);
+            vox = sample_voxel(S.g, o, d, tj, x);
+        }
+        int n = 0, f = 0;
+        if (vox >= 0) {
+            n = __ldg(S.v_n + vox);
+            f = __ldg(S.v_f + vox);
+        }
+        float asum = 0.f;
+        float sacc[CP];
+#pragma unroll
+        for (int c = 0; c < CP; ++c) sacc[c] = 0.f;
+        const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
+        const float4* lp4 = reinterpret_cast<const float4*>(S.lpad);
+        for (int e = 0; e < nmax; ++e) {
+            if (e < n) {
+                const int k = __ldg(S.v_sq + f + e);
+                const Prim p = load_prim(S.rec, k);
+                const float po = occupancy(p, x);
+                asum = fmaf(po, p.sigma, asum);
+                const float4* cr = lp4 + (size_t)k * (CP / 4);
+#pragma unroll
+                for (int q = 0; q < CP / 4; ++q) {
+                    const float4 cv = __ldg(cr + q);
+                    sacc[4 * q + 0] = fmaf(po, cv.x, sacc[4 * q + 0]);
+                    sacc[4 * q + 1] = fmaf(po, cv.y, sacc[4 * q + 1]);
+                    sacc[4 * q + 2] = fmaf(po, cv.z, sacc[4 * q + 2]);
+                    sacc[4 * q + 3] = fmaf(po, cv.w, sacc[4 * q + 3]);
+                }
+            }
+        }
+        const float alpha = valid ? fminf(asum, S.alpha_max) : 0.f;
+        float Tb;
+        int used;
+        bool stop;
+        const float w = group_composite<GS>(alpha, s, gbase, S.kappa, T, Tb, valid, used, stop);
+        if (valid) {
+            if (s < used && S.save_T) S.save_T[r * L + j] = Tb;
+            Dp = fmaf(w, tj, Dp);
+#pragma unroll
+            for (int c = 0; c < CP; ++c) acc[c] = fmaf(w, sacc[c], acc[c]);
+        }
+        // t is non-decreasing, so a chunk fully outside the grid after an inside
+        // one means the ray has left the grid for good
+        const unsigned ins = (__ballot_sync(0xffffffffu, vox >= 0) >> gbase) & gmask;
+        const bool left = seen_inside && ins == 0u;
+        seen_inside = seen_inside || ins != 0u;
+        if (live) used_total = min(j0 + used, L);
+        j0 += GS;
+        // a ray ends at L, on early termination, once T is exactly 0 (every later
+        // weight is 0), or when it has left the grid
+        const bool fin = (gr < B.total) && (!live || j0 >= L || stop || T == 0.f || left);
+        if (__any_sync(0xffffffffu, fin)) {
+            float Dsum = Dp;
+#pragma unroll
+            for (int o2 = GS / 2; o2 > 0; o2 >>= 1) Dsum += __shfl_xor_sync(0xffffffffu, Dsum, o2, GS);
+#pragma unroll
+            for (int c = 0; c < CP; ++c) {
+                float v = acc[c];
+#pragma unroll
+                for (int o2 = GS / 2; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2, GS);
+                if (fin && live && (c % GS) == s && c < S.C) S.sem[r * S.C + c] = v;
+            }
+            if (fin && live && s == 0) {
+                S.depth[r] = Dsum;
+                if (S.t_final) S.t_final[r] = T;
+                if (S.save_n) S.save_n[r] = used_total;
+            }
+            int nr = 0;
+            if (fin && s == 0) nr = atomicAdd(B.ctr, 1);
+            nr = __shfl_sync(0xffffffffu, nr, gbase);
+            if (fin) {
+                gr = nr;
+                live = gr < B.total;
+                if (live) {
+                    si = scene_of(B, gr);
+                    r = gr - __ldg(B.off + si);
+                    if (*B.d[si].status != SQ_OK) live = false;
+                }
+                if (live) scene_ray(B.d[si], r, o, d);
+                T = 1.f;
+                Dp = 0.f;
+                j0 = 0;
+                used_total = 0;
+                seen_inside = false;
+#pragma unroll
+                for (int c = 0; c < CP; ++c) acc[c] = 0.f;
+            }
+        }
+    }
+}
+
+template <int CP, int GS>
+sq_status_t launch_cp_gs(const Batch& B, int warps, cudaStream_t st) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward<CP, GS>, warps * 32, 0);
+    if (e != cudaSuccess) return cuda_status(e, "k_forward occupancy");
+    const long long per_block = (long long)warps * (32 / GS);
+    const long long need = (B.total + per_block - 1) / per_block;
+    long long blocks = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    k_forward<CP, GS><<<(int)blocks, warps * 32, 0, st>>>(B);
+    SQ_CHECK_LAUNCH("k_forward");
+    return SQ_OK;
+}
+
+template <int CP>
+sq_status_t launch_cp(const Batch& B, const Tuning& tn, cudaStream_t st) {
+    if (tn.fwd_lanes == 16) return launch_cp_gs<CP, 16>(B, tn.fwd_warps, st);
+    return launch_cp_gs<CP, 8>(B, tn.fwd_warps, st);
+}
+
+}  // namespace
+
+sq_status_t launch_forward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st) {
+    if (B.total == 0) return SQ_OK;
+    if (tn.fwd_warps < 1 || tn.fwd_warps > MAX_WARPS || (tn.fwd_lanes != 8 && tn.fwd_lanes != 16)) {
+        set_last_error("forward tuning (lanes %d, warps %d) not supported", tn.fwd_lanes, tn.fwd_warps);
+        return SQ_ERR_INVALID_ARG;
+    }
+    switch (cp) {
+        case 4: return launch_cp<4>(B, tn, st);
+        case 8: return launch_cp<8>(B, tn, st);
+        case 12: return launch_cp<12>(B, tn, st);
+        case 16: return launch_cp<16>(B, tn, st);
+        case 20: return launch_cp<20>(B, tn, st);
+        case 24: return launch_cp<24>(B, tn, st);
+        case 28: return launch_cp<28>(B, tn, st);
+        case 32: return launch_cp<32>(B, tn, st);
+    }
+    set_last_error("n_classes padding %d not supported", cp);
+    return SQ_ERR_INVALID_ARG;
+}
+
+}  // namespace sqr

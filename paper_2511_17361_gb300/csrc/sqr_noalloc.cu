@@ -29,8 +29,9 @@ namespace {
 
 // Per primitive the render workspace holds 64 B of record, 48 B of backward
 // extras, 4 * 32 B of padded logits, 192 B of gradient accumulator and 16 B of
-// packed box; plus alignment padding and the work counter.
-constexpr size_t kNoallocBytes = (size_t)SQ_NOALLOC_MAX_PRIMS * (64 + 48 + 4 * 32 + 192 + 16) + 8 * 256;
+// packed box; plus a header (scene descriptors, ray offsets, work counter) and
+// alignment padding, covered by the 64 KB allowance.
+constexpr size_t kNoallocBytes = (size_t)SQ_NOALLOC_MAX_PRIMS * (64 + 48 + 4 * 32 + 192 + 16) + 64 * 1024;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 

@@ -98,7 +98,6 @@ __global__ void __launch_bounds__(Q_THREADS) k_query(QueryArgs a) {
 }  // namespace
 
 size_t render_workspace_size(const sq_prims_t* p);
-size_t render_logits_offset(const sq_prims_t* p);
 
 template <int CP>
 static sq_status_t launch_query_cp(const QueryArgs& a, cudaStream_t st) {
@@ -119,9 +118,10 @@ sq_status_t query_grid_impl(const sq_prims_t* prims, const sq_index_t* idx, cons
         return SQ_ERR_INVALID_ARG;
     }
     const int cp = cpad(prims->n_classes);
+    // packed records at the start of the workspace, padded logits after them
     char* base = (char*)ws;
     float4* rec = (float4*)base;
-    float* lpad = (float*)(base + render_logits_offset(prims));
+    float* lpad = (float*)(base + align_up((size_t)prims->n * REC4 * sizeof(float4), 256));
     sq_status_t s = launch_pack(prims, rec, nullptr, lpad, cp, st);
     if (s != SQ_OK) return s;
     QueryArgs a;

@@ -1,0 +1,92 @@
+// sqr_render.cuh -- internal interface between the render translation units:
+// per-scene descriptors (one or many scenes per launch), the packed-record
+// layout, and the kernel launchers implemented in sqr_fwd.cu and sqr_bwd.cu.
+#pragma once
+
+#include "sqr_common.cuh"
+
+namespace sqr {
+
+constexpr int MAX_BATCH = 32;  // scenes per launch (= SQ_MAX_BATCH)
+constexpr int GF = 48;         // floats per primitive in the gradient accumulator (12 partials + up to 32 classes)
+constexpr int NRAW = 12;       // summed partials: gx 3, tau 3, u df/du 3, eps 2, sigma 1
+constexpr int MAX_WARPS = 8;   // warps per CTA accepted by the render kernels
+
+// Everything a render kernel needs about one scene.  Built on the host, written
+// to device memory by k_write_desc (a by-value kernel argument, so batched
+// launches stay capturable in a CUDA graph without host copies).
+struct SceneDesc {
+    const float4* rec;   // [N, REC4] packed forward records
+    const float4* aux;   // [N, AUX4] backward extras
+    const float* lpad;   // [N, CP] logits padded to CP
+    const int4* boxes;   // [N] packed voxel boxes (backward)
+    const int* v_n;
+    const int* v_f;
+    const int* v_sq;
+    const int* status;
+    GridC g;
+    const float* K;
+    const float* c2w;
+    const float* t;
+    int n_cam, H, W, L, C, n;
+    long long R;
+    float kappa, alpha_max;
+    float* depth;        // forward outputs
+    float* sem;
+    float* t_final;
+    float* save_T;       // [R, L] saved transmittance before each sample (nullable in inference)
+    int* save_n;         // [R] samples composited
+    const float* grad_depth;  // backward inputs
+    const float* grad_sem;
+    float* gacc;         // [N, GF] gradient accumulator (zeroed per backward)
+};
+
+struct BatchParams {
+    int n;
+    long long off[MAX_BATCH + 1];  // ray offsets of the scenes in the concatenated ray range
+    SceneDesc s[MAX_BATCH];
+};
+
+// What the render kernels receive: descriptors and offsets in device memory and
+// a zeroed work counter over the concatenated rays.
+struct Batch {
+    const SceneDesc* d;
+    const long long* off;
+    int n;
+    long long total;
+    int* ctr;
+};
+
+__device__ __forceinline__ int scene_of(const Batch& B, long long g) {
+    int lo = 0, hi = B.n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(B.off + mid) <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void scene_ray(const SceneDesc& S, long long r, float o[3], float d[3]) {
+    const long long hw = (long long)S.H * S.W;
+    const int cam = (int)(r / hw);
+    const long long pix = r - (long long)cam * hw;
+    const int v = (int)(pix / S.W), u = (int)(pix - (long long)v * S.W);
+    pixel_ray(S.K + 4 * cam, S.c2w + 12 * cam, u, v, o, d);
+}
+
+// Launch configuration picked by the autotuner (or the defaults).
+struct Tuning {
+    int fwd_lanes;  // lanes (samples) per ray in the forward: 8 or 16
+    int fwd_warps;  // warps per CTA, forward: 4 or 8
+    int bwd_warps;  // warps per CTA, backward: 4 or 8
+};
+
+int device_sm_count();
+sq_status_t launch_forward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st);
+sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st);
+sq_status_t launch_grad_out(const SceneDesc& S, float* gm, float* gq, float* gs, float* ge, float* go, float* gl,
+                            cudaStream_t st);
+sq_status_t launch_pack_boxes(const int* ranges, int n, int4* boxes, cudaStream_t st);
+
+}  // namespace sqr

@@ -51,6 +51,18 @@ class SqRays(ctypes.Structure):
                 ("t", _vp), ("L", ctypes.c_int), ("kappa", ctypes.c_float), ("alpha_max", ctypes.c_float)]
 
 
+class SqScene(ctypes.Structure):
+    _fields_ = [("prims", SqPrims), ("index", SqIndex), ("grid", SqGrid), ("rays", SqRays), ("depth", _vp),
+                ("sem", _vp), ("t_final", _vp), ("saved", _vp), ("saved_bytes", ctypes.c_size_t), ("grad_depth", _vp),
+                ("grad_sem", _vp), ("g_means", _vp), ("g_quats", _vp), ("g_scales", _vp), ("g_eps", _vp),
+                ("g_opacity", _vp), ("g_logits", _vp)]
+
+
+class SqTuning(ctypes.Structure):
+    _fields_ = [("fwd_lanes_per_ray", ctypes.c_int), ("fwd_warps_per_cta", ctypes.c_int),
+                ("bwd_warps_per_cta", ctypes.c_int)]
+
+
 class SqrError(RuntimeError):
     pass
 
@@ -75,8 +87,13 @@ def _load():
     lib.sq_loss_ce_mse.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_float,
                                    ctypes.c_float, _vp, _vp, _vp, _vp]
     lib.sq_count_pairs.argtypes = [P(SqIndex), P(SqGrid), P(SqRays), _vp, _vp]
+    lib.sq_batched_workspace_size.restype = ctypes.c_size_t
+    lib.sq_batched_workspace_size.argtypes = [P(SqScene), ctypes.c_int]
+    lib.sq_render_batched.argtypes = [ctypes.c_int, P(SqScene), ctypes.c_int, P(SqTuning), _vp, ctypes.c_size_t, _vp]
+    lib.sq_autotune.argtypes = [P(SqScene), ctypes.c_int, _vp, ctypes.c_size_t, _vp, ctypes.c_int, P(SqTuning),
+                                _vp, _vp]
     for f in ("sq_build_index", "sq_render_fwd", "sq_render_bwd", "sq_query_grid", "sq_loss_ce_mse",
-              "sq_count_pairs"):
+              "sq_count_pairs", "sq_render_batched", "sq_autotune"):
         getattr(lib, f).restype = ctypes.c_int
     lib.sq_status_string.restype = ctypes.c_char_p
     lib.sq_status_string.argtypes = [ctypes.c_int]
@@ -359,3 +376,100 @@ def render(prims: dict, index: Index, grid: dict, rays: Rays):
 
 def to_device(prims_np: dict, device="cuda") -> dict:
     return {k: torch.as_tensor(prims_np[k], dtype=torch.float32).contiguous().to(device) for k in PRIM_KEYS}
+
+
+# ------------------------------------------------------------------ batched scenes
+class Scene:
+    """One scene of a batch: its parameters, index, grid and rays plus the device
+    buffers the batched forward and backward read and write."""
+
+    def __init__(self, prims: dict, index: Index, grid: dict, rays: Rays, training: bool = True):
+        device = prims["means"].device
+        C = prims["logits"].shape[1]
+        R = rays.R
+        self.prims, self.index, self.grid, self.rays = prims, index, grid, rays
+        self.depth = torch.empty(R, device=device)
+        self.sem = torch.empty((R, C), device=device)
+        self.t_final = torch.empty(R, device=device)
+        self.saved = new_saved(rays, device) if training else None
+        self.grad_depth = torch.zeros(R, device=device) if training else None
+        self.grad_sem = torch.zeros((R, C), device=device) if training else None
+        self.grads = {k: torch.empty_like(prims[k]) for k in PRIM_KEYS} if training else None
+
+    def struct(self) -> SqScene:
+        sc = SqScene()
+        sc.prims = prims_struct(self.prims)
+        sc.index = self.index.struct()
+        sc.grid = grid_struct(self.grid)
+        sc.rays = self.rays.struct()
+        sc.depth, sc.sem, sc.t_final = _ptr(self.depth), _ptr(self.sem), _ptr(self.t_final)
+        if self.saved is not None:
+            sc.saved, sc.saved_bytes = _ptr(self.saved), self.saved.numel()
+            sc.grad_depth, sc.grad_sem = _ptr(self.grad_depth), _ptr(self.grad_sem)
+            for k in PRIM_KEYS:
+                setattr(sc, "g_" + k, _ptr(self.grads[k]))
+        return sc
+
+
+def _scene_array(scenes):
+    arr = (SqScene * len(scenes))(*[s.struct() for s in scenes])
+    return arr
+
+
+def batched_workspace_size(scenes) -> int:
+    arr = _scene_array(scenes)
+    return int(lib.sq_batched_workspace_size(arr, len(scenes)))
+
+
+def render_batched(op: int, scenes, tuning: dict | None = None):
+    """One persistent launch over all scenes (op = SQ_OP_FWD or SQ_OP_BWD)."""
+    arr = _scene_array(scenes)
+    device = scenes[0].prims["means"].device
+    ws = _ws.get("batched", lib.sq_batched_workspace_size(arr, len(scenes)), device)
+    tn = None if tuning is None else SqTuning(tuning["fwd_lanes_per_ray"], tuning["fwd_warps_per_cta"],
+                                              tuning["bwd_warps_per_cta"])
+    _check(lib.sq_render_batched(op, arr, len(scenes), ctypes.byref(tn) if tn else None, _ptr(ws), ws.numel(),
+                                 _stream()), "sq_render_batched")
+
+
+TUNING_CACHE = os.path.join(_PKG, "_lib", "autotune.json")
+
+
+def batch_signature(scenes) -> str:
+    """Workload key for the tuning cache: scene sizes, rays, samples, classes."""
+    parts = [f"{s.prims['means'].shape[0]}x{s.rays.R}x{s.rays.t.numel()}" for s in scenes]
+    return f"C{scenes[0].prims['logits'].shape[1]}:" + ",".join(parts)
+
+
+def autotune(scenes, reps: int = 3, use_cache: bool = True) -> dict:
+    """Picks the fastest launch configuration for this batch with sq_autotune and
+    caches it (JSON next to the library) under the batch signature."""
+    import json
+    key = batch_signature(scenes)
+    cache = {}
+    if use_cache and os.path.exists(TUNING_CACHE):
+        try:
+            cache = json.load(open(TUNING_CACHE))
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        return cache[key]
+    arr = _scene_array(scenes)
+    device = scenes[0].prims["means"].device
+    ws = _ws.get("batched", lib.sq_batched_workspace_size(arr, len(scenes)), device)
+    best = SqTuning()
+    fms = (ctypes.c_float * 4)()
+    bms = (ctypes.c_float * 2)()
+    _check(lib.sq_autotune(arr, len(scenes), _ptr(ws), ws.numel(), _stream(), reps, ctypes.byref(best), fms, bms),
+           "sq_autotune")
+    out = {"fwd_lanes_per_ray": best.fwd_lanes_per_ray, "fwd_warps_per_cta": best.fwd_warps_per_cta,
+           "bwd_warps_per_cta": best.bwd_warps_per_cta, "fwd_ms": list(fms), "bwd_ms": list(bms)}
+    if use_cache:
+        cache[key] = out
+        try:
+            os.makedirs(os.path.dirname(TUNING_CACHE), exist_ok=True)
+            with open(TUNING_CACHE, "w") as f:
+                json.dump(cache, f, indent=1)
+        except OSError:
+            pass
+    return out

@@ -1,0 +1,161 @@
+"""Batched persistent launches (many scenes of uneven size in one launch), the
+launch-configuration autotuner and CUDA-graph capture (needs a GPU).  The batched
+path is checked against per-scene calls (themselves checked against the FP64
+oracle in test_gpu_parity.py) and against the oracle directly on every scene.
+Gradients of two GPU runs differ by the order of FP32 atomic additions, so they
+are compared at the gradient tolerance."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2511_17361_gb300 import synth
+from tests.gpu_common import check_depth, check_grad, check_sem, dev_grid, lib, np_index
+from tests.helpers import small_scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sqr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    oracle.build()
+    return lib()
+
+
+def _scenes(sqr, seed=0):
+    """Four scenes of uneven size sharing 18 classes: different N, cameras, image
+    sizes and sample counts."""
+    rng = np.random.default_rng(seed)
+    cfgs = []
+    c0 = synth.make_config(0)
+    cfgs.append((c0["prims"], c0["grid"], c0["rig"], c0["t"]))
+    pr, g, rig, t = small_scene(seed + 1, n=30, H=21, W=35, L=40, C=18, sigma_max=0.8)
+    cfgs.append((pr, g, rig, t))
+    pr = synth.prims_driving(900, seed + 2)
+    cfgs.append((pr, synth.grid_spec(100, 100, 8), synth.rig_ring(n_cam=2, H=30, W=52, f=35.0), synth.sample_depths(33)))
+    pr = synth.prims_uniform(500, seed + 3)
+    cfgs.append((pr, synth.grid_spec(50, 50, 8), synth.rig_ring(n_cam=3, H=17, W=23, f=14.0), synth.sample_depths(61)))
+    scenes, host = [], []
+    for pr, g, rig, t in cfgs:
+        prims_d = sqr.to_device(pr)
+        rays = sqr.Rays.from_rig(rig, t)
+        gd = dev_grid(g)
+        ix = sqr.build_index(prims_d, gd)
+        sc = sqr.Scene(prims_d, ix, gd, rays, training=True)
+        R = rays.R
+        sc.grad_depth.copy_(torch.from_numpy(rng.standard_normal(R).astype(np.float32)))
+        sc.grad_sem.copy_(torch.from_numpy(rng.standard_normal((R, 18)).astype(np.float32)))
+        scenes.append(sc)
+        host.append((pr, g, rig, t))
+    return scenes, host
+
+
+def _per_scene(sqr, sc):
+    saved = sqr.new_saved(sc.rays)
+    d, s, tf = sqr.render_fwd(sc.prims, sc.index, sc.grid, sc.rays, saved=saved)
+    g = sqr.render_bwd(sc.prims, sc.index, sc.grid, sc.rays, sc.grad_depth, sc.grad_sem, saved=saved)
+    return d.clone(), s.clone(), tf.clone(), {k: v.clone() for k, v in g.items()}
+
+
+def test_batched_equals_per_scene(sqr):
+    scenes, _ = _scenes(sqr)
+    refs = [_per_scene(sqr, sc) for sc in scenes]
+    sqr.render_batched(sqr.SQ_OP_FWD, scenes)
+    sqr.render_batched(sqr.SQ_OP_BWD, scenes)
+    torch.cuda.synchronize()
+    for sc, (d, s, tf, g) in zip(scenes, refs):
+        assert torch.equal(sc.depth, d) and torch.equal(sc.sem, s) and torch.equal(sc.t_final, tf)
+        for k in g:
+            check_grad(sc.grads[k].cpu().numpy(), g[k].cpu().numpy(), k)
+
+
+def test_batched_scene_against_oracle(sqr):
+    scenes, host = _scenes(sqr, seed=5)
+    sqr.render_batched(sqr.SQ_OP_FWD, scenes)
+    sqr.render_batched(sqr.SQ_OP_BWD, scenes)
+    torch.cuda.synchronize()
+    for sc, (pr, g, rig, t) in zip(scenes, host):
+        idx = np_index(sc.index)
+        D, S, T, _ = oracle.render_fwd(pr, g, idx, rig, t)
+        check_depth(sc.depth.cpu().numpy(), D, 0.5)
+        check_sem(sc.sem.cpu().numpy(), S)
+        ref = oracle.render_bwd(pr, g, idx, rig, t, sc.grad_depth.cpu().numpy().astype(np.float64),
+                                sc.grad_sem.cpu().numpy().astype(np.float64))
+        for k in ref:
+            check_grad(sc.grads[k].cpu().numpy(), ref[k], k)
+
+
+@pytest.mark.parametrize("lanes,fw,bw", [(8, 4, 4), (8, 8, 8), (16, 4, 8), (16, 8, 4)])
+def test_every_tuning_gives_the_same_render(sqr, lanes, fw, bw):
+    scenes, _ = _scenes(sqr, seed=2)
+    sqr.render_batched(sqr.SQ_OP_FWD, scenes)
+    sqr.render_batched(sqr.SQ_OP_BWD, scenes)
+    base = [(sc.depth.clone(), sc.sem.clone(), {k: v.clone() for k, v in sc.grads.items()}) for sc in scenes]
+    tn = {"fwd_lanes_per_ray": lanes, "fwd_warps_per_cta": fw, "bwd_warps_per_cta": bw}
+    sqr.render_batched(sqr.SQ_OP_FWD, scenes, tn)
+    sqr.render_batched(sqr.SQ_OP_BWD, scenes, tn)
+    torch.cuda.synchronize()
+    for sc, (d, s, g) in zip(scenes, base):
+        torch.testing.assert_close(sc.depth, d, rtol=1e-5, atol=1e-5)
+        torch.testing.assert_close(sc.sem, s, rtol=1e-5, atol=1e-5)
+        for k in g:
+            check_grad(sc.grads[k].cpu().numpy(), g[k].cpu().numpy(), k)
+
+
+def test_autotuner_picks_a_measured_candidate(sqr):
+    scenes, _ = _scenes(sqr, seed=3)
+    best = sqr.autotune(scenes, reps=2, use_cache=False)
+    assert best["fwd_lanes_per_ray"] in (8, 16) and best["fwd_warps_per_cta"] in (4, 8)
+    assert best["bwd_warps_per_cta"] in (4, 8)
+    assert all(ms > 0 for ms in best["fwd_ms"]) and all(ms > 0 for ms in best["bwd_ms"])
+    cands = [(8, 4), (8, 8), (16, 4), (16, 8)]
+    i = cands.index((best["fwd_lanes_per_ray"], best["fwd_warps_per_cta"]))
+    assert best["fwd_ms"][i] == min(best["fwd_ms"])
+
+
+def test_cuda_graph_replay_matches_eager(sqr):
+    """The whole training step of a batch (index rebuilds, batched forward, loss
+    gradient, batched backward) captured once and replayed."""
+    scenes, _ = _scenes(sqr, seed=4)
+    targets = []
+    for sc in scenes:
+        R = sc.rays.R
+        rng = np.random.default_rng(R)
+        targets.append((torch.from_numpy(rng.uniform(0.5, 40, R).astype(np.float32)).cuda(),
+                        torch.from_numpy(rng.integers(0, 18, R).astype(np.int32)).cuda(),
+                        (torch.empty(1, device="cuda"), torch.empty(R, device="cuda"),
+                         torch.empty((R, 18), device="cuda"))))
+
+    def step():
+        for sc in scenes:
+            sqr.build_index(sc.prims, sc.grid, index=sc.index, sync=False)
+        sqr.render_batched(sqr.SQ_OP_FWD, scenes)
+        for sc, (td, tl, out) in zip(scenes, targets):
+            sqr.loss_ce_mse(sc.depth, sc.sem, td, tl, out=out)
+            sc.grad_depth.copy_(out[1])
+            sc.grad_sem.copy_(out[2])
+        sqr.render_batched(sqr.SQ_OP_BWD, scenes)
+
+    step()
+    torch.cuda.synchronize()
+    eager = [(sc.depth.clone(), sc.sem.clone(), {k: v.clone() for k, v in sc.grads.items()}) for sc in scenes]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()  # warm-up on the capture stream (workspaces already sized)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for sc in scenes:
+        sc.depth.zero_()
+        for v in sc.grads.values():
+            v.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for sc, (d, s, gr) in zip(scenes, eager):
+        assert torch.equal(sc.depth, d) and torch.equal(sc.sem, s)
+        for k in gr:
+            check_grad(sc.grads[k].cpu().numpy(), gr[k].cpu().numpy(), k)
