@@ -32,7 +32,7 @@ from paper_2511_17361_gb300 import synth  # noqa: E402
 
 WORKLOAD = 1
 MUFU_PER_PAIR = {"fwd": 9, "bwd": 13}  # SFU ops per (sample, primitive) pair in each kernel
-LAUNCHES_PER_STEP = 14                  # index 9, forward 2, loss 1, backward 2
+LAUNCHES_PER_STEP = 18                  # index 9, forward 3, loss 1, backward 5
 # DRAM traffic per launch from the committed ncu summaries, valid only while the
 # kernel source is unchanged (sha256 of the file holding it).
 NCU_TRAFFIC = {}
@@ -44,6 +44,22 @@ def _sha(path):
 
 def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The slowest rank's value (timings are reported as the max over ranks)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, total_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / (total_ms / 1e3)
 
 
 # ----------------------------------------------------------------------- clocks
@@ -221,13 +237,10 @@ def run_mine(args):
     clocks = sampler.stop()
     phase = np.array([[evs[s][i].elapsed_time(evs[s][i + 1]) for i in range(4)] for s in range(args.steps)])
     step_ms = phase.sum(1)
-    total_ms = float(step_ms.sum())
+    total_ms = max_over_ranks(float(step_ms.sum()), world, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
-    value = world * R * L * args.steps / (total_ms / 1e3)
+    value = job_throughput(R * L * args.steps, world, total_ms)
 
     # ---- end to end through the public API: pinned host inputs in, gradients + loss out
     host_in = {k: torch.from_numpy(np.ascontiguousarray(cfg["prims"][k])).pin_memory() for k in sqr.PRIM_KEYS}
@@ -264,11 +277,8 @@ def run_mine(args):
         e1.record()
         torch.cuda.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * R * L * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e_value = job_throughput(R * L * args.steps, world, e2e_ms)
 
     # ---- roofline of the dominant kernel (SFU-bound: MUFU ops per pair)
     mean_phase = phase.mean(0)

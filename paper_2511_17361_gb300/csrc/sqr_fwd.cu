@@ -81,7 +81,11 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
 
     while (__any_sync(0xffffffffu, gr < B.total)) {
         const SceneDesc& S = B.d[si];
+        // scene constants of this group's ray, kept in registers for the list walk
         const int L = S.L;
+        const float4* __restrict__ rec = S.rec;
+        const float4* __restrict__ lp4 = reinterpret_cast<const float4*>(S.lpad);
+        const int* __restrict__ v_sq = S.v_sq;
         const int j = j0 + s;
         const bool valid = live && j < L;
         float x[3] = {0.f, 0.f, 0.f};
@@ -89,7 +93,8 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
         float tj = 0.f;
         if (valid) {
             tj = __ldg(S.t + j);
-            vox = sample_voxel(S.g, o, d, tj, x);
+            const GridC g = S.g;
+            vox = sample_voxel(g, o, d, tj, x);
         }
         int n = 0, f = 0;
         if (vox >= 0) {
@@ -101,11 +106,10 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
 #pragma unroll
         for (int c = 0; c < CP; ++c) sacc[c] = 0.f;
         const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
-        const float4* lp4 = reinterpret_cast<const float4*>(S.lpad);
         for (int e = 0; e < nmax; ++e) {
             if (e < n) {
-                const int k = __ldg(S.v_sq + f + e);
-                const Prim p = load_prim(S.rec, k);
+                const int k = __ldg(v_sq + f + e);
+                const Prim p = load_prim(rec, k);
                 const float po = occupancy(p, x);
                 asum = fmaf(po, p.sigma, asum);
                 const float4* cr = lp4 + (size_t)k * (CP / 4);

@@ -2,8 +2,9 @@
 launch-configuration autotuner and CUDA-graph capture (needs a GPU).  The batched
 path is checked against per-scene calls (themselves checked against the FP64
 oracle in test_gpu_parity.py) and against the oracle directly on every scene.
-Gradients of two GPU runs differ by the order of FP32 atomic additions, so they
-are compared at the gradient tolerance."""
+Gradients of two GPU runs differ by the order of FP32 atomic additions; each is
+within the gradient tolerance of the FP64 result, so two runs are compared at
+twice that tolerance."""
 import numpy as np
 import pytest
 import torch
@@ -68,7 +69,7 @@ def test_batched_equals_per_scene(sqr):
     for sc, (d, s, tf, g) in zip(scenes, refs):
         assert torch.equal(sc.depth, d) and torch.equal(sc.sem, s) and torch.equal(sc.t_final, tf)
         for k in g:
-            check_grad(sc.grads[k].cpu().numpy(), g[k].cpu().numpy(), k)
+            check_grad(sc.grads[k].cpu().numpy(), g[k].cpu().numpy(), k, rtol=2e-3)
 
 
 def test_batched_scene_against_oracle(sqr):
@@ -101,7 +102,7 @@ def test_every_tuning_gives_the_same_render(sqr, lanes, fw, bw):
         torch.testing.assert_close(sc.depth, d, rtol=1e-5, atol=1e-5)
         torch.testing.assert_close(sc.sem, s, rtol=1e-5, atol=1e-5)
         for k in g:
-            check_grad(sc.grads[k].cpu().numpy(), g[k].cpu().numpy(), k)
+            check_grad(sc.grads[k].cpu().numpy(), g[k].cpu().numpy(), k, rtol=2e-3)
 
 
 def test_autotuner_picks_a_measured_candidate(sqr):
@@ -158,4 +159,4 @@ def test_cuda_graph_replay_matches_eager(sqr):
     for sc, (d, s, gr) in zip(scenes, eager):
         assert torch.equal(sc.depth, d) and torch.equal(sc.sem, s)
         for k in gr:
-            check_grad(sc.grads[k].cpu().numpy(), gr[k].cpu().numpy(), k)
+            check_grad(sc.grads[k].cpu().numpy(), gr[k].cpu().numpy(), k, rtol=2e-3)
