@@ -35,7 +35,10 @@ MUFU_PER_PAIR = {"fwd": 9, "bwd": 13}  # SFU ops per (sample, primitive) pair in
 LAUNCHES_PER_STEP = 18                  # index 9, forward 3, loss 1, backward 5
 # DRAM traffic per launch from the committed ncu summaries, valid only while the
 # kernel source is unchanged (sha256 of the file holding it).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "k_backward": {"src": "sqr_bwd.cu", "src_sha": "53b0e8338b23d8b7", "bytes_per_launch": 235353088},
+    "k_forward": {"src": "sqr_fwd.cu", "src_sha": "3473c5f9e9e13720", "bytes_per_launch": 160511232},
+}
 
 
 def _sha(path):
@@ -291,10 +294,11 @@ def run_mine(args):
     roof = None
     if names[dom] in MUFU_PER_PAIR:
         achieved = Q * MUFU_PER_PAIR[names[dom]] / (mean_phase[dom] / 1e3) / 1e9
-        src = os.path.join(ROOT, "paper_2511_17361_gb300", "csrc", "sqr_render.cu")
         kname = "k_" + ("forward" if names[dom] == "fwd" else "backward")
         tr = NCU_TRAFFIC.get(kname)
-        traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _sha(src) else None
+        traffic = None
+        if tr and tr["src_sha"] == _sha(os.path.join(ROOT, "paper_2511_17361_gb300", "csrc", tr["src"])):
+            traffic = tr["bytes_per_launch"]
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GMUFUop/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{sm_count} SMs x 16 SFU ops/clk x {peak_mhz:.0f} MHz (max SM clock seen)"}
