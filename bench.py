@@ -208,7 +208,7 @@ def run_mine(args):
     tf = torch.empty(R, device=dev)
     loss_out = (torch.empty(1, device=dev), torch.empty(R, device=dev), torch.empty((R, C), device=dev))
     grads = {k: torch.empty_like(prims[k]) for k in sqr.PRIM_KEYS}
-    saved = sqr.new_saved(rays, dev)
+    saved = sqr.new_saved(rays, C, dev)
 
     def step(ev=None):
         if ev: ev[0].record()

@@ -139,10 +139,13 @@ size_t sq_workspace_size(int op, const sq_prims_t* prims, const sq_grid_t* grid,
 sq_status_t sq_build_index(const sq_prims_t* prims, const sq_grid_t* grid, const sq_index_opts_t* opts,
                            sq_index_t* index, void* workspace, size_t workspace_bytes, void* stream);
 
-/* Bytes of the forward state that sq_render_fwd saves for sq_render_bwd:
- * T [R, L] FP32 (transmittance before every sample) and the per-ray count of
- * composited samples [R] int32, each 256-byte aligned.  0 on invalid rays. */
-size_t sq_saved_size(const sq_rays_t* rays);
+/* Bytes of the forward state that sq_render_fwd saves for sq_render_bwd, per
+ * composited sample of every ray: T_j [R, L] FP32 (transmittance before the
+ * sample), alpha_j [R, L] FP32 (negated where the alpha_max clamp was active),
+ * s_j [R, n_classes, L] FP32 (Eq. 4, sample index fastest); then the per-ray
+ * count of composited samples [R] int32.  Each block 256-byte aligned:
+ * about R * L * (n_classes + 2) * 4 bytes.  0 on invalid rays or n_classes. */
+size_t sq_saved_size(const sq_rays_t* rays, int n_classes);
 
 /* Sec. 3.3.2 forward pass (Eq. 2, 4-6).  Per ray r:
  *   depth[r]   = sum_j w_j t_j,                  w_j = T_j alpha_j, T_j = prod_{l<j} (1 - alpha_l)
@@ -211,7 +214,7 @@ typedef struct {
     float* depth;        /* [R] forward outputs */
     float* sem;          /* [R, C] */
     float* t_final;      /* [R], nullable */
-    void* saved;         /* sq_saved_size(&rays) bytes; nullable for inference forwards */
+    void* saved;         /* sq_saved_size(&rays, n_classes) bytes; nullable for inference forwards */
     size_t saved_bytes;
     const float* grad_depth; /* [R] backward inputs */
     const float* grad_sem;   /* [R, C] */

@@ -112,7 +112,7 @@ sq_status_t render_fwd_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_
 sq_status_t render_bwd_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, const sq_rays_t*, const void*,
                             size_t, const float*, const float*, float*, float*, float*, float*, float*, float*, void*,
                             size_t, cudaStream_t);
-size_t saved_size(const sq_rays_t* r);
+size_t saved_size(const sq_rays_t* r, int n_classes);
 sq_status_t query_grid_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, float, float*, float*,
                             unsigned char*, void*, size_t, cudaStream_t);
 sq_status_t count_pairs_impl(const sq_index_t*, const sq_grid_t*, const sq_rays_t*, long long*, cudaStream_t);
@@ -230,9 +230,13 @@ sq_status_t sq_build_index(const sq_prims_t* prims, const sq_grid_t* grid, const
     return build_index_impl(prims, grid, opts, index, ws, ws_bytes, (cudaStream_t)stream);
 }
 
-size_t sq_saved_size(const sq_rays_t* rays) {
+size_t sq_saved_size(const sq_rays_t* rays, int n_classes) {
     if (check_rays(rays) != SQ_OK) return 0;
-    return saved_size(rays);
+    if (n_classes < 1 || n_classes > SQ_MAX_CLASSES) {
+        set_last_error("n_classes = %d outside 1..%d", n_classes, SQ_MAX_CLASSES);
+        return 0;
+    }
+    return saved_size(rays, n_classes);
 }
 
 sq_status_t sq_render_fwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,

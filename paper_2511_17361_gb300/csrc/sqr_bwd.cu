@@ -1,30 +1,33 @@
 // sqr_bwd.cu -- backward render (Sec. 3.3.3) on sm_103a.
 //
-// One warp per ray, samples back to front.  With T_j saved by the forward, the
-// back-to-front carry U_j = alpha_{j+1} v_{j+1} + (1 - alpha_{j+1}) U_{j+1} gives
-// dL/dalpha_j = T_j (v_j - U_j) (v_j = gD t_j + <gS, s_j>, zero where the alpha
-// clamp is active) in the same sweep that evaluates every pair's gradient.
+// One warp per bundle of RB rays.  Per ray, the warp first rebuilds the ray's
+// sample table in shared memory: from the forward's saved alpha_j, s_j and T_j it
+// forms v_j = gD t_j + <gS, s_j> and the back-to-front carry
+// U_j = alpha_{j+1} v_{j+1} + (1 - alpha_{j+1}) U_{j+1} (a 32-lane suffix scan of
+// affine maps per chunk of 32 samples), so dL/dalpha_j = T_j (v_j - U_j) (zero
+// where the alpha clamp is active) and w_j = T_j alpha_j; next to them the sample
+// point, its voxel and the voxel's list (V_n, V_f).
 //
-// Along a ray the samples listing a given primitive are contiguous (a ray
-// crosses a primitive's voxel box once), so each primitive of the current
-// sample's list has an owner slot in a lane that accumulates the primitive's
-// partial derivatives in registers while it stays in the lists and flushes them
-// once when it leaves (queued, then one coalesced 32-wide atomic add).  Owner
-// bookkeeping uses the primitives' voxel boxes: an owner leaves when the sample's
-// voxel is outside its box; a list entry is new when the previously processed
-// sample's voxel is outside its box.  Lists longer than the 64 owner slots are
-// evaluated pair by pair.
-#include <limits.h>
-
+// Along a ray the samples whose lists hold a given primitive are consecutive (the
+// voxel coordinates of the samples are monotone in t and the primitive is listed
+// in exactly the voxels of its box), so every (ray, primitive) pair is one run of
+// samples.  The warp lists the runs that start at each sample (list entries whose
+// box misses the previous sample's voxel) and then every lane walks runs on its
+// own: it holds the primitive's record in registers, evaluates dp_o/d(params) at
+// each sample of the run, weights it by dL/dp_o = G_j sigma + w_j <gS, c>, sums in
+// registers and flushes once per run (queued in shared memory, then coalesced
+// atomic adds of raw partial sums).  A lane whose run ends takes the next listed
+// run at once.  k_grad_out turns the sums into parameter gradients.
 #include "sqr_render.cuh"
 
 namespace sqr {
 
 namespace {
 
-constexpr int OWN = 64;   // owner slots per warp (two per lane)
-constexpr int QCAP = 64;  // pending flushes per warp
-constexpr int QW = 16;    // words per pending flush: key, 11 partials, sigma, W, pad
+constexpr int RB = 2;      // rays per bundle
+constexpr int TCAP = 384;  // runs listed per pass
+constexpr int QCAP = 32;   // pending flushes per warp
+constexpr int QW = 16;     // words per flush: key, 11 partials, sigma, W, ray slot, pad
 
 struct BwdPrim {
     Prim f;
@@ -83,74 +86,6 @@ __device__ __forceinline__ float occupancy_partials(const BwdPrim& P, const floa
     return po;
 }
 
-template <int CP>
-__device__ __forceinline__ float logit_dot(const float* __restrict__ lpad, int k, const float* __restrict__ gS, int C) {
-    const float4* cr = reinterpret_cast<const float4*>(lpad) + (size_t)k * (CP / 4);
-    float cd = 0.f;
-#pragma unroll
-    for (int q = 0; q < CP / 4; ++q) {
-        const float4 c4 = __ldg(cr + q);
-        const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (4 * q + i < C) cd = fmaf(__ldg(gS + 4 * q + i), cc[i], cd);
-    }
-    return cd;
-}
-
-// <gS, c_k> with gS staged in shared memory (zero-padded to CP).
-template <int CP>
-__device__ __forceinline__ float logit_dot_sh(const float* __restrict__ lpad, int k, const float* gS) {
-    const float4* cr = reinterpret_cast<const float4*>(lpad) + (size_t)k * (CP / 4);
-    float cd = 0.f;
-#pragma unroll
-    for (int q = 0; q < CP / 4; ++q) {
-        const float4 c4 = __ldg(cr + q);
-        cd = fmaf(gS[4 * q + 0], c4.x, cd);
-        cd = fmaf(gS[4 * q + 1], c4.y, cd);
-        cd = fmaf(gS[4 * q + 2], c4.z, cd);
-        cd = fmaf(gS[4 * q + 3], c4.w, cd);
-    }
-    return cd;
-}
-
-// Writes the warp's pending flushes into the accumulator of raw partial sums:
-// per entry, lane f adds field f (and f + 32).  Fields 0-11 are the summed
-// partials (gx 3, tau 3, u df/du 3, eps 2, sigma 1), 12.. the logit gradients
-// W gS_c; gsl[b] = gS[32 b + lane - 12] of the current ray.
-__device__ __forceinline__ void drain_queue(float* __restrict__ gacc, const float* __restrict__ q, int qn, int lane,
-                                            const float gsl[2], int C) {
-    for (int e = 0; e < qn; ++e) {
-        const float* ent = q + e * QW;
-        const int k = __float_as_int(ent[0]);
-        float* row = gacc + (size_t)k * GF;
-        float v = 0.f;
-        if (lane < NRAW) v = ent[1 + lane];
-        else if (lane < NRAW + C) v = ent[1 + NRAW] * gsl[0];
-        if (v != 0.f) red_add(row + lane, v);
-        if (lane + 32 < NRAW + C) {
-            const float v2 = ent[1 + NRAW] * gsl[1];
-            if (v2 != 0.f) red_add(row + 32 + lane, v2);
-        }
-    }
-}
-
-struct WarpBwd {
-    float queue[QCAP * QW];
-    float gs[32];  // dL/dS of the current ray
-};
-
-// Packed inclusive box test; an empty box is stored as lo = 1, hi = 0.
-__device__ __forceinline__ bool box_has(const int4 b, int ix, int iy, int iz) {
-    return ix >= (b.x & 0xffff) && ix <= (b.x >> 16) && iy >= (b.y & 0xffff) && iy <= (b.y >> 16) &&
-           iz >= (b.z & 0xffff) && iz <= (b.z >> 16);
-}
-
-__device__ __forceinline__ int4 shfl_box(int4 b, int src) {
-    return make_int4(__shfl_sync(0xffffffffu, b.x, src), __shfl_sync(0xffffffffu, b.y, src),
-                     __shfl_sync(0xffffffffu, b.z, src), 0);
-}
-
 __global__ void k_pack_boxes(const int* __restrict__ ranges, int n, int4* __restrict__ boxes) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -161,255 +96,319 @@ __global__ void k_pack_boxes(const int* __restrict__ ranges, int n, int4* __rest
     boxes[k] = make_int4(v[0], v[1], v[2], 0);
 }
 
-// Per-lane state of one owner slot.
-struct Slot {
-    int key;      // primitive id, -1 when free
-    int4 box;     // its voxel box (packed)
-    float cd;     // <gS, c_key> of the current ray
-    float acc[13];
-};
 
-// Pending flush queue of a warp (per-(ray, primitive) partial sums).
-struct FlushQ {
-    float* q;
-    int n;
-};
-
-__device__ __forceinline__ void queue_make_room(FlushQ& Q, unsigned dm, float* gacc, int lane, const float gsl[2],
-                                                int C, const float4* aux) {
-    if (Q.n + __popc(dm) > QCAP) {
-        __syncwarp();
-        drain_queue(gacc, Q.q, Q.n, lane, gsl, C);
-        __syncwarp();
-        Q.n = 0;
-    }
+// Packed inclusive box test; an empty box is stored as lo = 1, hi = 0.  pv holds
+// a sample's voxel as (ix | iy << 16, iz), iz = -1 outside the grid.
+__device__ __forceinline__ bool box_has(const int4 b, int2 pv) {
+    if (pv.y < 0) return false;
+    const unsigned bx = (unsigned)b.x, by = (unsigned)b.y, bz = (unsigned)b.z, px = (unsigned)pv.x;
+    const unsigned ix = px & 0xffffu, iy = px >> 16, iz = (unsigned)pv.y;
+    return ix >= (bx & 0xffffu) && ix <= (bx >> 16) && iy >= (by & 0xffffu) && iy <= (by >> 16) &&
+           iz >= (bz & 0xffffu) && iz <= (bz >> 16);
 }
 
-__device__ __forceinline__ void queue_push(FlushQ& Q, bool mine, unsigned dm, unsigned lt, int key, const float v[13]) {
-    if (mine) {
-        float* ent = Q.q + (Q.n + __popc(dm & lt)) * QW;
-        ent[0] = __int_as_float(key);
+// <gS, c_k> with gS staged in shared memory (zero-padded to 32).
+template <int CP>
+__device__ __forceinline__ float logit_dot(const float* __restrict__ lpad, int k, const float* gs) {
+    const float4* cr = reinterpret_cast<const float4*>(lpad) + (size_t)k * (CP / 4);
+    float cd = 0.f;
 #pragma unroll
-        for (int i = 0; i < 13; ++i) ent[1 + i] = v[i];
+    for (int q = 0; q < CP / 4; ++q) {
+        const float4 c4 = __ldg(cr + q);
+        cd = fmaf(gs[4 * q + 0], c4.x, cd);
+        cd = fmaf(gs[4 * q + 1], c4.y, cd);
+        cd = fmaf(gs[4 * q + 2], c4.z, cd);
+        cd = fmaf(gs[4 * q + 3], c4.w, cd);
     }
-    Q.n += __popc(dm);
+    return cd;
 }
 
-// Owner of slot S leaves when `del`; its sums are queued and the slot freed.
-__device__ __forceinline__ void slot_leave(Slot& S, bool del, FlushQ& Q, float* gacc, int lane, unsigned lt,
-                                           const float gsl[2], int C, const float4* aux) {
-    const unsigned dm = __ballot_sync(0xffffffffu, del);
-    if (!dm) return;
-    queue_make_room(Q, dm, gacc, lane, gsl, C, aux);
-    queue_push(Q, del, dm, lt, S.key, S.acc);
-    if (del) S.key = -1;
+// Writes the warp's pending flushes into the accumulator of raw partial sums:
+// per entry, lane f adds field f (and f + 32).  Fields 0-11 are the summed
+// partials (gx 3, tau 3, u df/du 3, eps 2, sigma 1); fields 12.. the logit
+// gradients W gS_c of the entry's ray (gS of the bundle's rays in gsb).
+__device__ __forceinline__ void drain_queue(float* __restrict__ gacc, const float* __restrict__ q, int qn, int lane,
+                                            const float* __restrict__ gsb, int C) {
+    for (int e = 0; e < qn; ++e) {
+        const float* ent = q + e * QW;
+        const int k = __float_as_int(ent[0]);
+        const float* gs = gsb + __float_as_int(ent[14]) * 32;
+        float* row = gacc + (size_t)k * GF;
+        float v = 0.f;
+        if (lane < NRAW) v = ent[1 + lane];
+        else if (lane < NRAW + C) v = ent[1 + NRAW] * gs[lane - NRAW];
+        if (v != 0.f) red_add(row + lane, v);
+        if (lane + 32 < NRAW + C) {
+            const float v2 = ent[1 + NRAW] * gs[lane + 32 - NRAW];
+            if (v2 != 0.f) red_add(row + 32 + lane, v2);
+        }
+    }
+}
+
+// Fixed per-warp shared memory; the sample tables (RB * L entries) follow the
+// array of these in dynamic shared memory.
+struct alignas(16) WarpBwd {
+    int2 task[TCAP];  // listed runs: (primitive, ray slot << 16 | first sample)
+    float queue[QCAP * QW];
+    float gs[RB * 32];  // dL/dS of the bundle's rays, zero-padded
+    int pre[32];        // inclusive prefix of list lengths over a chunk of samples
+    int le[RB];         // composited samples of the bundle's rays
+};
+
+// Sample table of one warp, structure of arrays over RB * lmax samples.
+struct Table {
+    float4* xg;  // sample point, dL/dalpha_j
+    int2* pv;    // packed voxel
+    int2* nf;    // V_n, V_f of the voxel (0 outside)
+    float* w;    // w_j = T_j alpha_j
+};
+
+__host__ __device__ inline size_t table_stride(int lmax) { return ((size_t)RB * lmax * 36 + 15) / 16 * 16; }
+
+__device__ __forceinline__ Table table_at(unsigned char* base, int lmax) {
+    const size_t n = (size_t)RB * lmax;
+    Table t;
+    t.xg = reinterpret_cast<float4*>(base);
+    t.pv = reinterpret_cast<int2*>(base + n * 16);
+    t.nf = reinterpret_cast<int2*>(base + n * 24);
+    t.w = reinterpret_cast<float*>(base + n * 32);
+    return t;
+}
+
+// Fills ray slot q of the table (one warp, back to front in chunks of 32).
+__device__ __forceinline__ void build_table(const SceneDesc& S, long long r, int q, int Le, const Table& tb,
+                                            int lmax, const float* gs, int lane) {
+    float o[3], d[3];
+    scene_ray(S, r, o, d);
+    const int L = S.L, C = S.C;
+    const float gD = __ldg(S.grad_depth + r);
+    const float* __restrict__ sS = S.save_S + r * C * L;
+    const GridC g = S.g;
+    float carry = 0.f;  // U at the last sample of the chunk being processed
+    for (int jc = ((Le - 1) >> 5) << 5; Le > 0 && jc >= 0; jc -= 32) {
+        const int j = jc + lane;
+        const bool valid = j < Le;
+        float sa = 0.f, T = 0.f, v = 0.f, tj = 0.f;
+        if (valid) {
+            sa = __ldg(S.save_A + r * L + j);
+            T = __ldg(S.save_T + r * L + j);
+            tj = __ldg(S.t + j);
+            float dot = 0.f;
+#pragma unroll 4
+            for (int c = 0; c < C; ++c) dot = fmaf(gs[c], __ldg(sS + (long long)c * L + j), dot);
+            v = fmaf(gD, tj, dot);
+        }
+        const float al = fabsf(sa);
+        // f_j(U) = al v + (1 - al) U; after the scan (a, b) is f_j o ... o f_{jc+31}
+        float a = al * v, b = 1.f - al;
+#pragma unroll
+        for (int o2 = 1; o2 < 32; o2 <<= 1) {
+            const float a2 = __shfl_down_sync(0xffffffffu, a, o2);
+            const float b2 = __shfl_down_sync(0xffffffffu, b, o2);
+            if (lane + o2 < 32) {
+                a = fmaf(b, a2, a);
+                b *= b2;
+            }
+        }
+        float na = __shfl_down_sync(0xffffffffu, a, 1), nb = __shfl_down_sync(0xffffffffu, b, 1);
+        if (lane == 31) {
+            na = 0.f;
+            nb = 1.f;
+        }
+        const float U = fmaf(nb, carry, na);  // U_j
+        if (valid) {
+            const float G = sa < 0.f ? 0.f : T * (v - U);
+            float x[3];
+            int vi[3];
+            const int vox = sample_voxel(g, o, d, tj, x, vi);
+            int2 nf = make_int2(0, 0);
+            if (vox >= 0) nf = make_int2(__ldg(S.v_n + vox), __ldg(S.v_f + vox));
+            const int at = q * lmax + j;
+            tb.xg[at] = make_float4(x[0], x[1], x[2], G);
+            tb.pv[at] = vox >= 0 ? make_int2(vi[0] | (vi[1] << 16), vi[2]) : make_int2(0, -1);
+            tb.nf[at] = nf;
+            tb.w[at] = T * al;
+        }
+        const float a0 = __shfl_sync(0xffffffffu, a, 0), b0 = __shfl_sync(0xffffffffu, b, 0);
+        carry = fmaf(b0, carry, a0);
+    }
 }
 
 template <int CP>
-__device__ __forceinline__ void slot_enter(Slot& S, int k, int4 box, const float* __restrict__ lpad,
-                                           const float* __restrict__ gS, int C) {
-    S.key = k;
-    S.box = box;
-#pragma unroll
-    for (int i = 0; i < 13; ++i) S.acc[i] = 0.f;
-    S.cd = logit_dot_sh<CP>(lpad, k, gS);
-}
-
-// Evaluates the slot's pair at x: p_o and partials (kept for the accumulation
-// once G_j is known) and the slot's share of alpha_j and <gS, s_j>.
-__device__ __forceinline__ void slot_eval(const Slot& S, const SceneDesc& a, const float x[3], float& po, float pr[11],
-                                          float& sig, float& pa, float& pv) {
-    po = 0.f;
-    sig = 0.f;
-    if (S.key >= 0) {
-        const BwdPrim P = load_bwd(a.rec, a.aux, S.key);
-        po = occupancy_partials(P, x, pr);
-        sig = P.f.sigma;
-        pa = fmaf(po, sig, pa);
-        pv = fmaf(po, S.cd, pv);
-    }
-}
-
-__device__ __forceinline__ void slot_accumulate(Slot& S, float po, const float pr[11], float sig, float G, float w) {
-    if (S.key >= 0 && po != 0.f) {
-        const float gf = -po * fmaf(G, sig, w * S.cd);
-#pragma unroll
-        for (int i = 0; i < 11; ++i) S.acc[i] = fmaf(gf, pr[i], S.acc[i]);
-        S.acc[11] = fmaf(G, po, S.acc[11]);
-        S.acc[12] = fmaf(w, po, S.acc[12]);
-    }
-}
-
-template <int CP>
-__global__ void __launch_bounds__(MAX_WARPS * 32, 2) k_backward(Batch B) {
-    __shared__ WarpBwd smem[MAX_WARPS];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+__global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    float* gSs = smem[wid].gs;
+    const int lmax = B.lmax;
+    WarpBwd& sm = reinterpret_cast<WarpBwd*>(dyn)[wid];
+    const Table tb = table_at(dyn + (size_t)nw * sizeof(WarpBwd) + (size_t)wid * table_stride(lmax), lmax);
+    const long long nbund = __ldg(B.boff + B.n);
 
     for (;;) {
-        int rr = 0;
-        if (lane == 0) rr = atomicAdd(B.ctr, 1);
-        const long long gr = __shfl_sync(0xffffffffu, rr, 0);
-        if (gr >= B.total) break;
-        const int si = scene_of(B, gr);
-        const SceneDesc& a = B.d[si];
-        const long long r = gr - __ldg(B.off + si);
-        if (*a.status != SQ_OK) continue;
-        const int Le = __ldg(a.save_n + r);
+        int bb = 0;
+        if (lane == 0) bb = atomicAdd(B.ctr, 1);
+        const long long gb = __shfl_sync(0xffffffffu, bb, 0);
+        if (gb >= nbund) break;
+        int si = 0;
+        {
+            int lo = 0, hi = B.n;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(B.boff + mid) <= gb) lo = mid;
+                else hi = mid;
+            }
+            si = lo;
+        }
+        const SceneDesc& S = B.d[si];
+        if (*S.status != SQ_OK) continue;
+        const long long r0 = (gb - __ldg(B.boff + si)) * RB;
+        const int nr = (int)min((long long)RB, S.R - r0);
+        const int C = S.C;
         __syncwarp();
-        gSs[lane] = lane < a.C ? __ldg(a.grad_sem + r * a.C + lane) : 0.f;
-        __syncwarp();
-        float o[3], d[3];
-        scene_ray(a, r, o, d);
-        const float gD = __ldg(a.grad_depth + r);
-        const float* gS = a.grad_sem + r * a.C;
-        float gsl[2];
-        gsl[0] = (lane >= NRAW && lane < NRAW + a.C) ? __ldg(gS + (lane - NRAW)) : 0.f;
-        gsl[1] = (lane + 32 < NRAW + a.C) ? __ldg(gS + (lane + 32 - NRAW)) : 0.f;
-
-        Slot S0, S1;
-        S0.key = -1;
-        S1.key = -1;
-        FlushQ Q{smem[wid].queue, 0};
-        float U = 0.f;
-        int pvx = -1, piy = 0, piz = 0, pvox = -1;  // voxel of the previously processed sample (-1: none)
-
-        for (int j = Le - 1; j >= -1; --j) {
-            // j == -1: an empty list releases every owner
-            int n = 0, f = 0, vox = -1, ix = -1, iy = 0, iz = 0;
-            float x[3] = {0.f, 0.f, 0.f};
-            float tj = 0.f;
-            if (j >= 0) {
-                tj = __ldg(a.t + j);
-                int vi[3];
-                vox = sample_voxel(a.g, o, d, tj, x, vi);
-                if (vox >= 0) {
-                    n = __ldg(a.v_n + vox);
-                    f = __ldg(a.v_f + vox);
-                    ix = vi[0];
-                    iy = vi[1];
-                    iz = vi[2];
-                }
-            }
-            const bool heavy = n > OWN;
-            if (vox != pvox || heavy) {
-                // owners whose box misses this voxel leave (all of them on an empty or heavy list)
-                const bool gone = n == 0 || heavy;
-                slot_leave(S0, S0.key >= 0 && (gone || !box_has(S0.box, ix, iy, iz)), Q, a.gacc, lane, lt, gsl, a.C,
-                           a.aux);
-                slot_leave(S1, S1.key >= 0 && (gone || !box_has(S1.box, ix, iy, iz)), Q, a.gacc, lane, lt, gsl, a.C,
-                           a.aux);
-                if (!gone) {
-                    // list entries whose box misses the previous voxel are new owners
-                    int kn0 = -1, kn1 = -1;
-                    int4 bx0 = make_int4(1, 1, 1, 0), bx1 = make_int4(1, 1, 1, 0);
-                    bool new0 = false, new1 = false;
-                    if (lane < n) {
-                        kn0 = __ldg(a.v_sq + f + lane);
-                        bx0 = __ldg(a.boxes + kn0);
-                        new0 = pvox < 0 || !box_has(bx0, pvx, piy, piz);
-                    }
-                    if (lane + 32 < n) {
-                        kn1 = __ldg(a.v_sq + f + lane + 32);
-                        bx1 = __ldg(a.boxes + kn1);
-                        new1 = pvox < 0 || !box_has(bx1, pvx, piy, piz);
-                    }
-                    const unsigned nm0 = __ballot_sync(0xffffffffu, new0), nm1 = __ballot_sync(0xffffffffu, new1);
-                    const int c0 = __popc(nm0), nnew = c0 + __popc(nm1);
-                    if (nnew) {
-                        const unsigned fr0 = __ballot_sync(0xffffffffu, S0.key < 0);
-                        const unsigned fr1 = __ballot_sync(0xffffffffu, S1.key < 0);
-                        {
-                            const int rk = __popc(fr0 & lt);
-                            const bool want = S0.key < 0 && rk < nnew;
-                            int src = lane;
-                            bool hi = false;
-                            if (want) {
-                                if (rk < c0) src = __fns(nm0, 0, rk + 1);
-                                else { src = __fns(nm1, 0, rk - c0 + 1); hi = true; }
-                            }
-                            const int va = __shfl_sync(0xffffffffu, kn0, src);
-                            const int vb = __shfl_sync(0xffffffffu, kn1, src);
-                            const int4 ba = shfl_box(bx0, src), bb1 = shfl_box(bx1, src);
-                            const int4 bb = hi ? bb1 : ba;
-                            if (want) slot_enter<CP>(S0, hi ? vb : va, bb, a.lpad, gSs, a.C);
-                        }
-                        if (nnew > __popc(fr0)) {
-                            const int rk = __popc(fr0) + __popc(fr1 & lt);
-                            const bool want = S1.key < 0 && rk < nnew;
-                            int src = lane;
-                            bool hi = false;
-                            if (want) {
-                                if (rk < c0) src = __fns(nm0, 0, rk + 1);
-                                else { src = __fns(nm1, 0, rk - c0 + 1); hi = true; }
-                            }
-                            const int va = __shfl_sync(0xffffffffu, kn0, src);
-                            const int vb = __shfl_sync(0xffffffffu, kn1, src);
-                            const int4 ba = shfl_box(bx0, src), bb1 = shfl_box(bx1, src);
-                            const int4 bb = hi ? bb1 : ba;
-                            if (want) slot_enter<CP>(S1, hi ? vb : va, bb, a.lpad, gSs, a.C);
-                        }
-                    }
-                }
-                pvox = gone ? -1 : vox;
-                pvx = ix; piy = iy; piz = iz;
-            }
-            if (j < 0) break;
-            if (n == 0) continue;  // no primitive here: alpha_j = 0 leaves U unchanged
-            float po0, po1 = 0.f, pr0[11], pr1[11], sg0, sg1 = 0.f;
-            float pa = 0.f, pv = 0.f;
-            slot_eval(S0, a, x, po0, pr0, sg0, pa, pv);
-            const bool any1 = __any_sync(0xffffffffu, S1.key >= 0);
-            if (any1) slot_eval(S1, a, x, po1, pr1, sg1, pa, pv);
-            if (heavy) {
-                for (int e = lane; e < n; e += 32) {
-                    const int k = __ldg(a.v_sq + f + e);
-                    const Prim p = load_prim(a.rec, k);
-                    const float pe = occupancy(p, x);
-                    pa = fmaf(pe, p.sigma, pa);
-                    pv = fmaf(pe, logit_dot<CP>(a.lpad, k, gS, a.C), pv);
-                }
-            }
-            const float raw = warp_sum(pa);
-            const float vs = warp_sum(pv);
-            const float alpha = fminf(raw, a.alpha_max);
-            const float Tj = __ldg(a.save_T + r * a.L + j);
-            const float vj = fmaf(gD, tj, vs);
-            const float G = raw > a.alpha_max ? 0.f : Tj * (vj - U);  // dL/dalpha_j
-            const float w = Tj * alpha;
-            slot_accumulate(S0, po0, pr0, sg0, G, w);
-            if (any1) slot_accumulate(S1, po1, pr1, sg1, G, w);
-            if (heavy) {
-                // every pair of a heavy list is queued on its own
-                for (int e0 = 0; e0 < n; e0 += 32) {
-                    const int e = e0 + lane;
-                    float v[13];
-                    int k = -1;
-                    bool mine = false;
-                    if (e < n) {
-                        k = __ldg(a.v_sq + f + e);
-                        const BwdPrim P = load_bwd(a.rec, a.aux, k);
-                        float pp[11];
-                        const float pe = occupancy_partials(P, x, pp);
-                        const float gf = -pe * fmaf(G, P.f.sigma, w * logit_dot<CP>(a.lpad, k, gS, a.C));
-#pragma unroll
-                        for (int i = 0; i < 11; ++i) v[i] = gf * pp[i];
-                        v[11] = G * pe;
-                        v[12] = w * pe;
-                        mine = pe != 0.f;
-                    }
-                    const unsigned dm = __ballot_sync(0xffffffffu, mine);
-                    if (dm) {
-                        queue_make_room(Q, dm, a.gacc, lane, gsl, a.C, a.aux);
-                        queue_push(Q, mine, dm, lt, k, v);
-                    }
-                }
-            }
-            U = fmaf(alpha, vj, (1.f - alpha) * U);
+        for (int q = 0; q < RB; ++q) {
+            sm.gs[q * 32 + lane] = (q < nr && lane < C) ? __ldg(S.grad_sem + (r0 + q) * C + lane) : 0.f;
+            if (lane == 0) sm.le[q] = q < nr ? min(max(__ldg(S.save_n + r0 + q), 0), S.L) : 0;
         }
         __syncwarp();
-        drain_queue(a.gacc, Q.q, Q.n, lane, gsl, a.C);
+        for (int q = 0; q < nr; ++q) build_table(S, r0 + q, q, sm.le[q], tb, lmax, sm.gs + q * 32, lane);
+        __syncwarp();
+
+        int qn = 0;               // pending flushes
+        int eq = 0, ec = 0, ee = 0;  // where the run listing resumes: ray slot, chunk, entry
+        bool more = nr > 0;
+        while (more) {
+            // ---- list run starts until the task list is full or every run is listed
+            int nt = 0;
+            for (;;) {
+                if (eq >= nr) {
+                    more = false;
+                    break;
+                }
+                const int Lq = sm.le[eq];
+                if (ec * 32 >= Lq) {
+                    ++eq;
+                    ec = 0;
+                    ee = 0;
+                    continue;
+                }
+                const int j = ec * 32 + lane, at = eq * lmax + j;
+                int nj = 0, fj = 0;
+                if (j < Lq) {
+                    const int2 nf = tb.nf[at];
+                    nj = nf.x;
+                    fj = nf.y;
+                    // a sample in its predecessor's voxel starts no run
+                    if (j > 0 && nj > 0) {
+                        const int2 p0 = tb.pv[at - 1], p1 = tb.pv[at];
+                        if (p0.x == p1.x && p0.y == p1.y) nj = 0;
+                    }
+                }
+                const int incl = warp_incl_scan(nj, lane);
+                const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                sm.pre[lane] = incl;
+                __syncwarp();
+                bool full = false;
+                for (; ee < tot; ee += 32) {
+                    if (nt + 32 > TCAP) {
+                        full = true;
+                        break;
+                    }
+                    const int e = ee + lane;
+                    int l = 0;  // sample of entry e: number of prefixes <= e
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (sm.pre[l + step - 1] <= e) l += step;
+                    const int fl = __shfl_sync(0xffffffffu, fj, l);
+                    bool start = false;
+                    int k = 0;
+                    const int jl = ec * 32 + l;
+                    if (e < tot) {
+                        const int ex = l > 0 ? sm.pre[l - 1] : 0;
+                        k = __ldg(S.v_sq + fl + (e - ex));
+                        start = jl == 0 || !box_has(__ldg(S.boxes + k), tb.pv[eq * lmax + jl - 1]);
+                    }
+                    const unsigned bm = __ballot_sync(0xffffffffu, start);
+                    if (start) sm.task[nt + __popc(bm & lt)] = make_int2(k, (eq << 16) | jl);
+                    nt += __popc(bm);
+                }
+                __syncwarp();
+                if (full) break;
+                ++ec;
+                ee = 0;
+            }
+            __syncwarp();
+            // ---- walk the listed runs; idle lanes take the next run
+            int next = 0;
+            bool act = false;
+            int k = 0, rq = 0, jj = 0;
+            int4 box = make_int4(1, 0, 1, 0);
+            BwdPrim P;
+            float cd = 0.f;
+            float acc[13];
+#pragma unroll
+            for (int i = 0; i < 13; ++i) acc[i] = 0.f;
+            for (;;) {
+                const unsigned idle = __ballot_sync(0xffffffffu, !act);
+                if (idle != 0u && next < nt) {
+                    const int idx = next + __popc(idle & lt);
+                    if (!act && idx < nt) {
+                        const int2 tk = sm.task[idx];
+                        k = tk.x;
+                        rq = tk.y >> 16;
+                        jj = tk.y & 0xffff;
+                        P = load_bwd(S.rec, S.aux, k);
+                        box = __ldg(S.boxes + k);
+                        cd = logit_dot<CP>(S.lpad, k, sm.gs + rq * 32);
+#pragma unroll
+                        for (int i = 0; i < 13; ++i) acc[i] = 0.f;
+                        act = true;
+                    }
+                    next = min(next + __popc(idle), nt);
+                }
+                if (!__any_sync(0xffffffffu, act)) break;
+                bool ends = false;
+                if (act) {
+                    const int at = rq * lmax + jj;
+                    const float4 xg = tb.xg[at];
+                    const float w = tb.w[at], G = xg.w;
+                    if (G != 0.f || w != 0.f) {
+                        const float x[3] = {xg.x, xg.y, xg.z};
+                        float pr[11];
+                        const float po = occupancy_partials(P, x, pr);
+                        if (po != 0.f) {
+                            const float gf = -po * fmaf(G, P.f.sigma, w * cd);
+#pragma unroll
+                            for (int i = 0; i < 11; ++i) acc[i] = fmaf(gf, pr[i], acc[i]);
+                            acc[11] = fmaf(G, po, acc[11]);
+                            acc[12] = fmaf(w, po, acc[12]);
+                        }
+                    }
+                    ++jj;
+                    ends = jj >= sm.le[rq] || !box_has(box, tb.pv[at + 1]);
+                }
+                const unsigned dm = __ballot_sync(0xffffffffu, ends);
+                if (dm) {
+                    if (qn + __popc(dm) > QCAP) {
+                        __syncwarp();
+                        drain_queue(S.gacc, sm.queue, qn, lane, sm.gs, C);
+                        __syncwarp();
+                        qn = 0;
+                    }
+                    if (ends) {
+                        float* ent = sm.queue + (qn + __popc(dm & lt)) * QW;
+                        ent[0] = __int_as_float(k);
+#pragma unroll
+                        for (int i = 0; i < 13; ++i) ent[1 + i] = acc[i];
+                        ent[14] = __int_as_float(rq);
+                        act = false;
+                    }
+                    qn += __popc(dm);
+                }
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+        drain_queue(S.gacc, sm.queue, qn, lane, sm.gs, C);
         __syncwarp();
     }
 }
@@ -444,9 +443,11 @@ __global__ void k_grad_out(const float* __restrict__ gacc, const float4* __restr
 
 }  // namespace
 
+int bwd_rays_per_bundle() { return RB; }
+
 sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st) {
     if (B.total == 0) return SQ_OK;
-    const int warps = tn.bwd_warps;
+    int warps = tn.bwd_warps;
     if (warps < 1 || warps > MAX_WARPS) {
         set_last_error("backward tuning (warps %d) not supported", warps);
         return SQ_ERR_INVALID_ARG;
@@ -465,16 +466,27 @@ sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream
             set_last_error("n_classes padding %d not supported", cp);
             return SQ_ERR_INVALID_ARG;
     }
+    // per warp: fixed part plus a sample table of RB * lmax entries
+    const size_t per_warp = sizeof(WarpBwd) + table_stride(B.lmax);
+    const size_t kMaxSmem = 227 * 1024;
+    while (warps > 1 && (size_t)warps * per_warp > kMaxSmem) --warps;
+    const size_t smem = (size_t)warps * per_warp;
+    if (smem > kMaxSmem) {
+        set_last_error("backward: %d samples per ray need %zu bytes of shared memory", B.lmax, smem);
+        return SQ_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e, "k_backward shared memory");
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem);
     if (e != cudaSuccess) return cuda_status(e, "k_backward occupancy");
-    const long long need = (B.total + warps - 1) / warps;
+    const long long need = (B.total / RB + B.n + warps - 1) / warps;
     long long blocks = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     Batch arg = B;
     void* args[] = {&arg};
-    e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(warps * 32), args, 0, st);
+    e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(warps * 32), args, smem, st);
     if (e != cudaSuccess) return cuda_status(e, "k_backward");
     return SQ_OK;
 }

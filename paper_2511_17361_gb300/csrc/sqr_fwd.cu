@@ -6,8 +6,8 @@
 // (Eq. 5-6) of a group's GS samples is a GS-lane product scan of (1 - alpha).
 // Rays of all scenes of the batch are handed out by one global counter, so a
 // lane group whose ray ends early takes the next ray, from whichever scene.
-// The forward saves T_j before every sample and the number of composited
-// samples for the backward sweep.
+// For the backward the forward saves, per composited sample, T_j, alpha_j (sign
+// marking the clamp) and s_j, and per ray the number of composited samples.
 #include "sqr_render.cuh"
 
 namespace sqr {
@@ -129,7 +129,15 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
         bool stop;
         const float w = group_composite<GS>(alpha, s, gbase, S.kappa, T, Tb, valid, used, stop);
         if (valid) {
-            if (s < used && S.save_T) S.save_T[r * L + j] = Tb;
+            if (s < used && S.save_T) {
+                const long long sj = r * L + j;
+                S.save_T[sj] = Tb;
+                S.save_A[sj] = asum > S.alpha_max ? -alpha : alpha;
+                float* sv = S.save_S + r * S.C * L + j;
+#pragma unroll
+                for (int c = 0; c < CP; ++c)
+                    if (c < S.C) sv[(long long)c * L] = sacc[c];
+            }
             Dp = fmaf(w, tj, Dp);
 #pragma unroll
             for (int c = 0; c < CP; ++c) acc[c] = fmaf(w, sacc[c], acc[c]);

@@ -49,10 +49,14 @@ __global__ void k_pack(sq_prims_t P, float4* __restrict__ rec, float4* __restric
 }
 
 // Copies the by-value scene descriptors into device memory (one thread).
-__global__ void k_write_desc(BatchParams P, SceneDesc* __restrict__ d, long long* __restrict__ off) {
+__global__ void k_write_desc(BatchParams P, SceneDesc* __restrict__ d, long long* __restrict__ off,
+                             long long* __restrict__ boff) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (int i = 0; i < P.n; ++i) d[i] = P.s[i];
-    for (int i = 0; i <= P.n; ++i) off[i] = P.off[i];
+    for (int i = 0; i <= P.n; ++i) {
+        off[i] = P.off[i];
+        boff[i] = P.boff[i];
+    }
 }
 
 // ------------------------------------------------------------------ pair counter
@@ -99,7 +103,8 @@ struct SceneWs {
 
 constexpr size_t HDR_DESC = 0;
 constexpr size_t HDR_OFF = (MAX_BATCH * sizeof(SceneDesc) + 255) / 256 * 256;
-constexpr size_t HDR_CTR = HDR_OFF + ((MAX_BATCH + 1) * sizeof(long long) + 255) / 256 * 256;
+constexpr size_t HDR_BOFF = HDR_OFF + ((MAX_BATCH + 1) * sizeof(long long) + 255) / 256 * 256;
+constexpr size_t HDR_CTR = HDR_BOFF + ((MAX_BATCH + 1) * sizeof(long long) + 255) / 256 * 256;
 constexpr size_t HDR_END = HDR_CTR + 256;
 
 SceneWs scene_ws(const sq_prims_t* p, size_t base) {
@@ -121,16 +126,23 @@ size_t batch_ws_size(const sq_scene_t* sc, int n) {
     return at;
 }
 
-// Saved forward state: T [R, L] then n [R].
-size_t saved_bytes_of(const sq_rays_t* r) {
-    const size_t R = (size_t)r->n_cam * r->H * r->W;
-    return align_up(R * r->L * sizeof(float), 256) + align_up(R * sizeof(int), 256);
+// Saved forward state: T [R, L], signed alpha [R, L], s [R, C, L], then n [R].
+size_t saved_bytes_of(const sq_rays_t* r, int C) {
+    const size_t R = (size_t)r->n_cam * r->H * r->W, RL = R * (size_t)r->L;
+    return 2 * align_up(RL * sizeof(float), 256) + align_up(RL * (size_t)C * sizeof(float), 256) +
+           align_up(R * sizeof(int), 256);
 }
 
-void saved_ptrs(const sq_rays_t* r, void* saved, float** T, int** n) {
-    const size_t R = (size_t)r->n_cam * r->H * r->W;
-    *T = (float*)saved;
-    *n = (int*)((char*)saved + align_up(R * r->L * sizeof(float), 256));
+void saved_ptrs(const sq_rays_t* r, int C, void* saved, SceneDesc& D) {
+    const size_t R = (size_t)r->n_cam * r->H * r->W, RL = R * (size_t)r->L;
+    char* p = (char*)saved;
+    D.save_T = (float*)p;
+    p += align_up(RL * sizeof(float), 256);
+    D.save_A = (float*)p;
+    p += align_up(RL * sizeof(float), 256);
+    D.save_S = (float*)p;
+    p += align_up(RL * (size_t)C * sizeof(float), 256);
+    D.save_n = (int*)p;
 }
 
 Tuning default_tuning() { return Tuning{8, 8, 8}; }
@@ -151,7 +163,7 @@ sq_status_t launch_pack(const sq_prims_t* prims, float4* rec, float4* aux, float
     return SQ_OK;
 }
 
-size_t saved_size(const sq_rays_t* r) { return saved_bytes_of(r); }
+size_t saved_size(const sq_rays_t* r, int n_classes) { return saved_bytes_of(r, n_classes); }
 
 size_t batched_workspace_size(const sq_scene_t* scenes, int n) { return batch_ws_size(scenes, n); }
 
@@ -180,7 +192,9 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
     memset(&P, 0, sizeof(P));
     P.n = n;
     char* base = (char*)ws;
-    long long total = 0;
+    long long total = 0, btotal = 0;
+    const int RB = bwd_rays_per_bundle();
+    int lmax = 0;
     size_t at = HDR_END;
     for (int i = 0; i < n; ++i) {
         const sq_scene_t& s = sc[i];
@@ -193,15 +207,15 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
             set_last_error("scene %d: depth/sem output is NULL", i);
             return SQ_ERR_INVALID_ARG;
         }
-        if (op == SQ_OP_FWD && s.saved && s.saved_bytes < saved_bytes_of(&s.rays)) {
-            set_last_error("scene %d: saved state of %zu bytes given, %zu needed", i, s.saved_bytes,
-                           saved_bytes_of(&s.rays));
+        const size_t sneed = saved_bytes_of(&s.rays, C);
+        if (op == SQ_OP_FWD && s.saved && s.saved_bytes < sneed) {
+            set_last_error("scene %d: saved state of %zu bytes given, %zu needed", i, s.saved_bytes, sneed);
             return SQ_ERR_INVALID_ARG;
         }
         if (op == SQ_OP_BWD) {
-            if (!s.saved || s.saved_bytes < saved_bytes_of(&s.rays)) {
+            if (!s.saved || s.saved_bytes < sneed) {
                 set_last_error("scene %d: backward needs the saved forward state (%zu bytes given, %zu needed)", i,
-                               s.saved_bytes, saved_bytes_of(&s.rays));
+                               s.saved_bytes, sneed);
                 return SQ_ERR_INVALID_ARG;
             }
             if (R > 0 && (!s.grad_depth || !s.grad_sem)) {
@@ -245,14 +259,15 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
         D.depth = s.depth;
         D.sem = s.sem;
         D.t_final = s.t_final;
-        D.save_T = nullptr;
-        D.save_n = nullptr;
-        if (s.saved) saved_ptrs(&s.rays, s.saved, &D.save_T, &D.save_n);
+        if (s.saved) saved_ptrs(&s.rays, C, s.saved, D);
         D.grad_depth = s.grad_depth;
         D.grad_sem = s.grad_sem;
         D.gacc = (float*)(base + w.gacc);
         P.off[i] = total;
+        P.boff[i] = btotal;
         total += R;
+        btotal += (R + RB - 1) / RB;
+        if (s.rays.L > lmax) lmax = s.rays.L;
         if (total >= 2147483647LL - 4096) {
             set_last_error("a batch holds at most 2^31 - 4096 rays");
             return SQ_ERR_INVALID_ARG;
@@ -268,14 +283,16 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
         }
     }
     P.off[n] = total;
+    P.boff[n] = btotal;
     SceneDesc* d = (SceneDesc*)(base + HDR_DESC);
     long long* off = (long long*)(base + HDR_OFF);
+    long long* boff = (long long*)(base + HDR_BOFF);
     int* ctr = (int*)(base + HDR_CTR);
-    k_write_desc<<<1, 32, 0, st>>>(P, d, off);
+    k_write_desc<<<1, 32, 0, st>>>(P, d, off, boff);
     SQ_CHECK_LAUNCH("k_write_desc");
     cudaError_t e = cudaMemsetAsync(ctr, 0, 256, st);
     if (e != cudaSuccess) return cuda_status(e, "memset counter");
-    Batch B{d, off, n, total, ctr};
+    Batch B{d, off, boff, n, total, ctr, lmax};
     sq_status_t ls = (op == SQ_OP_FWD) ? launch_forward(B, cp, tn, st) : launch_backward(B, cp, tn, st);
     if (ls != SQ_OK) return ls;
     if (op == SQ_OP_BWD) {

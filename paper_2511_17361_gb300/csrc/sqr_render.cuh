@@ -35,6 +35,8 @@ struct SceneDesc {
     float* sem;
     float* t_final;
     float* save_T;       // [R, L] saved transmittance before each sample (nullable in inference)
+    float* save_A;       // [R, L] saved alpha_j, negated where the clamp was active
+    float* save_S;       // [R, C, L] saved semantic vector s_j of each sample (sample index fastest)
     int* save_n;         // [R] samples composited
     const float* grad_depth;  // backward inputs
     const float* grad_sem;
@@ -43,18 +45,21 @@ struct SceneDesc {
 
 struct BatchParams {
     int n;
-    long long off[MAX_BATCH + 1];  // ray offsets of the scenes in the concatenated ray range
+    long long off[MAX_BATCH + 1];   // ray offsets of the scenes in the concatenated ray range
+    long long boff[MAX_BATCH + 1];  // offsets of the scenes' ray bundles (backward)
     SceneDesc s[MAX_BATCH];
 };
 
 // What the render kernels receive: descriptors and offsets in device memory and
-// a zeroed work counter over the concatenated rays.
+// a zeroed work counter over the concatenated rays (or ray bundles).
 struct Batch {
     const SceneDesc* d;
     const long long* off;
+    const long long* boff;
     int n;
     long long total;
     int* ctr;
+    int lmax;  // largest L of the batch
 };
 
 __device__ __forceinline__ int scene_of(const Batch& B, long long g) {
@@ -83,6 +88,7 @@ struct Tuning {
 };
 
 int device_sm_count();
+int bwd_rays_per_bundle();
 sq_status_t launch_forward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st);
 sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st);
 sq_status_t launch_grad_out(const SceneDesc& S, float* gm, float* gq, float* gs, float* ge, float* go, float* gl,

@@ -77,7 +77,7 @@ def _load():
     lib.sq_workspace_size.argtypes = [ctypes.c_int, P(SqPrims), P(SqGrid), P(SqRays)]
     lib.sq_build_index.argtypes = [P(SqPrims), P(SqGrid), P(SqIndexOpts), P(SqIndex), _vp, ctypes.c_size_t, _vp]
     lib.sq_saved_size.restype = ctypes.c_size_t
-    lib.sq_saved_size.argtypes = [P(SqRays)]
+    lib.sq_saved_size.argtypes = [P(SqRays), ctypes.c_int]
     lib.sq_render_fwd.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), P(SqRays), _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                   _vp, ctypes.c_size_t, _vp]
     lib.sq_render_bwd.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), P(SqRays), _vp, ctypes.c_size_t, _vp, _vp, _vp,
@@ -255,15 +255,19 @@ def build_index(prims: dict, grid: dict, mode: int = SQ_INDEX_OBB, tau_cut: floa
 
 
 # ------------------------------------------------------------------ render
-def saved_size(rays: Rays) -> int:
-    """Bytes of forward state the backward pass needs (T per sample, samples per ray)."""
+def saved_size(rays: Rays, n_classes: int) -> int:
+    """Bytes of forward state the backward pass needs (T_j, alpha_j and s_j per
+    sample, samples per ray)."""
     r = rays.struct()
-    return int(lib.sq_saved_size(ctypes.byref(r)))
+    n = int(lib.sq_saved_size(ctypes.byref(r), int(n_classes)))
+    if n == 0 and rays.R > 0:
+        raise ValueError(f"sq_saved_size: {lib.sq_last_error().decode()}")
+    return n
 
 
 def render_fwd(prims: dict, index: Index, grid: dict, rays: Rays, out=None, saved=None):
     """Returns depth [R], sem [R, C], t_final [R] (Eq. 4-6).  ``saved``: a uint8
-    device tensor of saved_size(rays) bytes that receives the state for
+    device tensor of saved_size(rays, C) bytes that receives the state for
     render_bwd, or None (inference)."""
     device = prims["means"].device
     C = prims["logits"].shape[1]
@@ -281,8 +285,8 @@ def render_fwd(prims: dict, index: Index, grid: dict, rays: Rays, out=None, save
     return depth, sem, tf
 
 
-def new_saved(rays: Rays, device="cuda"):
-    return torch.empty(saved_size(rays), dtype=torch.uint8, device=device)
+def new_saved(rays: Rays, n_classes: int, device="cuda"):
+    return torch.empty(saved_size(rays, n_classes), dtype=torch.uint8, device=device)
 
 
 def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, grad_sem, saved=None, out=None) -> dict:
@@ -292,7 +296,7 @@ def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, gr
     grad_depth = _need_cuda_f32(grad_depth.contiguous(), "grad_depth")
     grad_sem = _need_cuda_f32(grad_sem.contiguous(), "grad_sem")
     if saved is None:
-        saved = new_saved(rays, device)
+        saved = new_saved(rays, prims["logits"].shape[1], device)
         render_fwd(prims, index, grid, rays, saved=saved)
     if out is None:
         out = {k: torch.empty_like(prims[k]) for k in PRIM_KEYS}
@@ -351,7 +355,7 @@ class SQRender(torch.autograd.Function):
     @staticmethod
     def forward(ctx, means, quats, scales, eps, opacity, logits, index: Index, grid: dict, rays: Rays):
         prims = dict(zip(PRIM_KEYS, (t.contiguous() for t in (means, quats, scales, eps, opacity, logits))))
-        saved = new_saved(rays, means.device)
+        saved = new_saved(rays, logits.shape[1], means.device)
         depth, sem, _ = render_fwd(prims, index, grid, rays, saved=saved)
         ctx.save_for_backward(*[prims[k] for k in PRIM_KEYS], saved)
         ctx.index, ctx.grid, ctx.rays = index, grid, rays
@@ -391,7 +395,7 @@ class Scene:
         self.depth = torch.empty(R, device=device)
         self.sem = torch.empty((R, C), device=device)
         self.t_final = torch.empty(R, device=device)
-        self.saved = new_saved(rays, device) if training else None
+        self.saved = new_saved(rays, C, device) if training else None
         self.grad_depth = torch.zeros(R, device=device) if training else None
         self.grad_sem = torch.zeros((R, C), device=device) if training else None
         self.grads = {k: torch.empty_like(prims[k]) for k in PRIM_KEYS} if training else None

@@ -54,7 +54,7 @@ def _scenes(sqr, seed=0):
 
 
 def _per_scene(sqr, sc):
-    saved = sqr.new_saved(sc.rays)
+    saved = sqr.new_saved(sc.rays, sc.prims["logits"].shape[1])
     d, s, tf = sqr.render_fwd(sc.prims, sc.index, sc.grid, sc.rays, saved=saved)
     g = sqr.render_bwd(sc.prims, sc.index, sc.grid, sc.rays, sc.grad_depth, sc.grad_sem, saved=saved)
     return d.clone(), s.clone(), tf.clone(), {k: v.clone() for k, v in g.items()}
