@@ -128,7 +128,9 @@ typedef struct {
 } sq_rays_t;
 
 /* Bytes of workspace an entry point needs (op = SQ_OP_*); rays may be NULL for
- * SQ_OP_INDEX and SQ_OP_QUERY.  Returns 0 on invalid arguments. */
+ * SQ_OP_INDEX, SQ_OP_FWD and SQ_OP_QUERY.  SQ_OP_BWD needs rays: besides the
+ * per-primitive records it holds 8 bytes per sample of every ray (dL/dalpha_j
+ * and w_j from the back-to-front sweep).  Returns 0 on invalid arguments. */
 size_t sq_workspace_size(int op, const sq_prims_t* prims, const sq_grid_t* grid, const sq_rays_t* rays);
 
 /* Sec. 3.3.1 "Preliminary Construction": per-primitive voxel ranges, V_n by a
@@ -235,7 +237,8 @@ typedef struct {
     int bwd_warps_per_cta;
 } sq_tuning_t;
 
-/* Workspace bytes for sq_render_batched / sq_autotune on these scenes. */
+/* Workspace bytes for sq_render_batched / sq_autotune on these scenes; when
+ * every scene has saved state it includes the backward's 8 bytes per sample. */
 size_t sq_batched_workspace_size(const sq_scene_t* scenes, int n_scenes);
 
 /* op = SQ_OP_FWD or SQ_OP_BWD over n_scenes (1..SQ_MAX_BATCH) scenes; tuning

@@ -1,23 +1,24 @@
-// sqr_bwd.cu -- backward render (Sec. 3.3.3) on sm_103a.
+// sqr_bwd.cu -- backward render (Sec. 3.3.3) on sm_103a, in two launches.
 //
-// One warp per bundle of RB rays.  Per ray, the warp first rebuilds the ray's
-// sample table in shared memory: from the forward's saved alpha_j, s_j and T_j it
-// forms v_j = gD t_j + <gS, s_j> and the back-to-front carry
+// k_bwd_sweep (one warp per ray, samples back to front): from the forward's saved
+// alpha_j, s_j and T_j it forms v_j = gD t_j + <gS, s_j> and the carry
 // U_j = alpha_{j+1} v_{j+1} + (1 - alpha_{j+1}) U_{j+1} (a 32-lane suffix scan of
-// affine maps per chunk of 32 samples), so dL/dalpha_j = T_j (v_j - U_j) (zero
-// where the alpha clamp is active) and w_j = T_j alpha_j; next to them the sample
-// point, its voxel and the voxel's list (V_n, V_f).
+// affine maps per chunk of 32 samples), and writes dL/dalpha_j = T_j (v_j - U_j)
+// (zero where the alpha clamp is active) and w_j = T_j alpha_j per sample.
 //
-// Along a ray the samples whose lists hold a given primitive are consecutive (the
-// voxel coordinates of the samples are monotone in t and the primitive is listed
-// in exactly the voxels of its box), so every (ray, primitive) pair is one run of
-// samples.  The warp lists the runs that start at each sample (list entries whose
-// box misses the previous sample's voxel) and then every lane walks runs on its
-// own: it holds the primitive's record in registers, evaluates dp_o/d(params) at
-// each sample of the run, weights it by dL/dp_o = G_j sigma + w_j <gS, c>, sums in
-// registers and flushes once per run (queued in shared memory, then coalesced
-// atomic adds of raw partial sums).  A lane whose run ends takes the next listed
-// run at once.  k_grad_out turns the sums into parameter gradients.
+// k_backward (one warp per bundle of RB rays): along a ray the samples whose lists
+// hold a given primitive are consecutive (the voxel coordinates of the samples are
+// monotone in t and the primitive is listed in exactly the voxels of its box), so
+// every (ray, primitive) pair is one run of samples.  Per bundle the warp builds a
+// sample table in shared memory (point, voxel, list, dL/dalpha_j, w_j), lists the
+// runs that start at each sample (list entries whose box misses the previous
+// sample's voxel), finds each run's end by a binary search, and then every lane
+// walks runs on its own: it holds the primitive's record in registers, evaluates
+// dp_o/d(params) at the run's samples (two per step), weights them by
+// dL/dp_o = G_j sigma + w_j <gS, c>, sums in registers and flushes once per run
+// (queued in shared memory, then coalesced atomic adds of raw partial sums).
+// Idle lanes take the next listed runs together.  k_grad_out turns the sums into
+// parameter gradients.
 #include "sqr_render.cuh"
 
 namespace sqr {
@@ -25,7 +26,9 @@ namespace sqr {
 namespace {
 
 constexpr int RB = 2;      // rays per bundle
-constexpr int TCAP = 384;  // runs listed per pass
+constexpr int TCAP = 256;  // runs listed per pass
+constexpr int RTH = 4;     // idle lanes that trigger a refill while others still walk
+constexpr int LU = 8;      // 32-entry batches whose loads the run listing issues together
 constexpr int QCAP = 32;   // pending flushes per warp
 constexpr int QW = 16;     // words per flush: key, 11 partials, sigma, W, ray slot, pad
 
@@ -145,10 +148,20 @@ __device__ __forceinline__ void drain_queue(float* __restrict__ gacc, const floa
     }
 }
 
+// Adds one pair's weighted partials to a run's sums (dL/dp_o = G sigma + w <gS, c>).
+__device__ __forceinline__ void accumulate(float acc[13], float po, const float pr[11], float G, float w, float sigma,
+                                           float cd) {
+    const float gf = -po * fmaf(G, sigma, w * cd);
+#pragma unroll
+    for (int i = 0; i < 11; ++i) acc[i] = fmaf(gf, pr[i], acc[i]);
+    acc[11] = fmaf(G, po, acc[11]);
+    acc[12] = fmaf(w, po, acc[12]);
+}
+
 // Fixed per-warp shared memory; the sample tables (RB * L entries) follow the
 // array of these in dynamic shared memory.
 struct alignas(16) WarpBwd {
-    int2 task[TCAP];  // listed runs: (primitive, ray slot << 16 | first sample)
+    int4 task[TCAP];  // listed runs: (primitive, ray slot / first / end sample, <gS, c>, 0)
     float queue[QCAP * QW];
     float gs[RB * 32];  // dL/dS of the bundle's rays, zero-padded
     int pre[32];        // inclusive prefix of list lengths over a chunk of samples
@@ -175,62 +188,97 @@ __device__ __forceinline__ Table table_at(unsigned char* base, int lmax) {
     return t;
 }
 
-// Fills ray slot q of the table (one warp, back to front in chunks of 32).
+// Back-to-front sweep of every ray (one warp per ray, chunks of 32 samples):
+// v_j = gD t_j + <gS, s_j> from the saved s_j, the carry
+// U_j = alpha_{j+1} v_{j+1} + (1 - alpha_{j+1}) U_{j+1} as a 32-lane suffix scan of
+// the affine maps U -> alpha v + (1 - alpha) U, then gw[r, j] = (dL/dalpha_j, w_j)
+// with dL/dalpha_j = T_j (v_j - U_j) (0 where the clamp was active), w_j = T_j alpha_j.
+template <int CP>
+__global__ void __launch_bounds__(256) k_bwd_sweep(Batch B) {
+    const int lane = threadIdx.x & 31;
+    const long long nwarp = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long gr = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gr < B.total; gr += nwarp) {
+        const int si = scene_of(B, gr);
+        const SceneDesc& S = B.d[si];
+        if (*S.status != SQ_OK) continue;
+        const long long r = gr - __ldg(B.off + si);
+        const int L = S.L, C = S.C;
+        const int Le = min(max(__ldg(S.save_n + r), 0), L);
+        const float gD = __ldg(S.grad_depth + r);
+        const float gsl = lane < C ? __ldg(S.grad_sem + r * C + lane) : 0.f;
+        const float* __restrict__ sS = S.save_S + r * C * L;
+        float carry = 0.f;  // U at the last sample of the chunk being processed
+        for (int jc = ((Le - 1) >> 5) << 5; Le > 0 && jc >= 0; jc -= 32) {
+            const int j = jc + lane;
+            const bool valid = j < Le;
+            float sa = 0.f, T = 0.f, tj = 0.f;
+            float sc[CP];
+#pragma unroll
+            for (int c = 0; c < CP; ++c) sc[c] = 0.f;
+            if (valid) {
+                sa = __ldg(S.save_A + r * L + j);
+                T = __ldg(S.save_T + r * L + j);
+                tj = __ldg(S.t + j);
+#pragma unroll
+                for (int c = 0; c < CP; ++c)
+                    if (c < C) sc[c] = __ldg(sS + (long long)c * L + j);
+            }
+            float dot = 0.f;
+#pragma unroll
+            for (int c = 0; c < CP; ++c) dot = fmaf(__shfl_sync(0xffffffffu, gsl, c), sc[c], dot);
+            const float v = valid ? fmaf(gD, tj, dot) : 0.f;
+            const float al = fabsf(sa);
+            // f_j(U) = al v + (1 - al) U; after the scan (a, b) is f_j o ... o f_{jc+31}
+            float a = al * v, b = 1.f - al;
+#pragma unroll
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const float a2 = __shfl_down_sync(0xffffffffu, a, o2);
+                const float b2 = __shfl_down_sync(0xffffffffu, b, o2);
+                if (lane + o2 < 32) {
+                    a = fmaf(b, a2, a);
+                    b *= b2;
+                }
+            }
+            float na = __shfl_down_sync(0xffffffffu, a, 1), nb = __shfl_down_sync(0xffffffffu, b, 1);
+            if (lane == 31) {
+                na = 0.f;
+                nb = 1.f;
+            }
+            const float U = fmaf(nb, carry, na);  // U_j
+            if (valid) S.gw[r * L + j] = make_float2(sa < 0.f ? 0.f : T * (v - U), T * al);
+            const float a0 = __shfl_sync(0xffffffffu, a, 0), b0 = __shfl_sync(0xffffffffu, b, 0);
+            carry = fmaf(b0, carry, a0);
+        }
+    }
+}
+
+// Fills ray slot q of the table (one warp, chunks of 32 samples): sample point,
+// voxel, its list and the sweep's (dL/dalpha_j, w_j).  Every load of a chunk is
+// independent of the others.
 __device__ __forceinline__ void build_table(const SceneDesc& S, long long r, int q, int Le, const Table& tb,
-                                            int lmax, const float* gs, int lane) {
+                                            int lmax, int lane) {
     float o[3], d[3];
     scene_ray(S, r, o, d);
-    const int L = S.L, C = S.C;
-    const float gD = __ldg(S.grad_depth + r);
-    const float* __restrict__ sS = S.save_S + r * C * L;
     const GridC g = S.g;
-    float carry = 0.f;  // U at the last sample of the chunk being processed
-    for (int jc = ((Le - 1) >> 5) << 5; Le > 0 && jc >= 0; jc -= 32) {
-        const int j = jc + lane;
-        const bool valid = j < Le;
-        float sa = 0.f, T = 0.f, v = 0.f, tj = 0.f;
-        if (valid) {
-            sa = __ldg(S.save_A + r * L + j);
-            T = __ldg(S.save_T + r * L + j);
-            tj = __ldg(S.t + j);
-            float dot = 0.f;
-#pragma unroll 4
-            for (int c = 0; c < C; ++c) dot = fmaf(gs[c], __ldg(sS + (long long)c * L + j), dot);
-            v = fmaf(gD, tj, dot);
-        }
-        const float al = fabsf(sa);
-        // f_j(U) = al v + (1 - al) U; after the scan (a, b) is f_j o ... o f_{jc+31}
-        float a = al * v, b = 1.f - al;
+    const float2* __restrict__ gw = S.gw + r * S.L;
+    for (int jc = 0; jc < Le; jc += 64) {
 #pragma unroll
-        for (int o2 = 1; o2 < 32; o2 <<= 1) {
-            const float a2 = __shfl_down_sync(0xffffffffu, a, o2);
-            const float b2 = __shfl_down_sync(0xffffffffu, b, o2);
-            if (lane + o2 < 32) {
-                a = fmaf(b, a2, a);
-                b *= b2;
+        for (int h = 0; h < 2; ++h) {
+            const int j = jc + 32 * h + lane;
+            if (j < Le) {
+                float x[3];
+                int vi[3];
+                const int vox = sample_voxel(g, o, d, __ldg(S.t + j), x, vi);
+                const float2 gwj = gw[j];
+                int2 nf = make_int2(0, 0);
+                if (vox >= 0) nf = make_int2(__ldg(S.v_n + vox), __ldg(S.v_f + vox));
+                const int at = q * lmax + j;
+                tb.xg[at] = make_float4(x[0], x[1], x[2], gwj.x);
+                tb.pv[at] = vox >= 0 ? make_int2(vi[0] | (vi[1] << 16), vi[2]) : make_int2(0, -1);
+                tb.nf[at] = nf;
+                tb.w[at] = gwj.y;
             }
         }
-        float na = __shfl_down_sync(0xffffffffu, a, 1), nb = __shfl_down_sync(0xffffffffu, b, 1);
-        if (lane == 31) {
-            na = 0.f;
-            nb = 1.f;
-        }
-        const float U = fmaf(nb, carry, na);  // U_j
-        if (valid) {
-            const float G = sa < 0.f ? 0.f : T * (v - U);
-            float x[3];
-            int vi[3];
-            const int vox = sample_voxel(g, o, d, tj, x, vi);
-            int2 nf = make_int2(0, 0);
-            if (vox >= 0) nf = make_int2(__ldg(S.v_n + vox), __ldg(S.v_f + vox));
-            const int at = q * lmax + j;
-            tb.xg[at] = make_float4(x[0], x[1], x[2], G);
-            tb.pv[at] = vox >= 0 ? make_int2(vi[0] | (vi[1] << 16), vi[2]) : make_int2(0, -1);
-            tb.nf[at] = nf;
-            tb.w[at] = T * al;
-        }
-        const float a0 = __shfl_sync(0xffffffffu, a, 0), b0 = __shfl_sync(0xffffffffu, b, 0);
-        carry = fmaf(b0, carry, a0);
     }
 }
 
@@ -270,7 +318,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
             if (lane == 0) sm.le[q] = q < nr ? min(max(__ldg(S.save_n + r0 + q), 0), S.L) : 0;
         }
         __syncwarp();
-        for (int q = 0; q < nr; ++q) build_table(S, r0 + q, q, sm.le[q], tb, lmax, sm.gs + q * 32, lane);
+        for (int q = 0; q < nr; ++q) build_table(S, r0 + q, q, sm.le[q], tb, lmax, lane);
         __syncwarp();
 
         int qn = 0;               // pending flushes
@@ -308,28 +356,40 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
                 sm.pre[lane] = incl;
                 __syncwarp();
                 bool full = false;
-                for (; ee < tot; ee += 32) {
-                    if (nt + 32 > TCAP) {
-                        full = true;
-                        break;
-                    }
-                    const int e = ee + lane;
-                    int l = 0;  // sample of entry e: number of prefixes <= e
+                // LU batches of 32 entries per round, their loads issued together
+                while (ee < tot && !full) {
+                    int kk[LU], jl[LU];
+                    bool has[LU];
 #pragma unroll
-                    for (int step = 16; step > 0; step >>= 1)
-                        if (sm.pre[l + step - 1] <= e) l += step;
-                    const int fl = __shfl_sync(0xffffffffu, fj, l);
-                    bool start = false;
-                    int k = 0;
-                    const int jl = ec * 32 + l;
-                    if (e < tot) {
-                        const int ex = l > 0 ? sm.pre[l - 1] : 0;
-                        k = __ldg(S.v_sq + fl + (e - ex));
-                        start = jl == 0 || !box_has(__ldg(S.boxes + k), tb.pv[eq * lmax + jl - 1]);
+                    for (int u = 0; u < LU; ++u) {
+                        const int e = ee + 32 * u + lane;
+                        int l = 0;  // sample of entry e: number of prefixes <= e
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1)
+                            if (sm.pre[l + step - 1] <= e) l += step;
+                        const int fl = __shfl_sync(0xffffffffu, fj, l);
+                        jl[u] = ec * 32 + l;
+                        has[u] = e < tot;
+                        kk[u] = 0;
+                        if (has[u]) kk[u] = __ldg(S.v_sq + fl + (e - (l > 0 ? sm.pre[l - 1] : 0)));
                     }
-                    const unsigned bm = __ballot_sync(0xffffffffu, start);
-                    if (start) sm.task[nt + __popc(bm & lt)] = make_int2(k, (eq << 16) | jl);
-                    nt += __popc(bm);
+                    int4 bx[LU];
+#pragma unroll
+                    for (int u = 0; u < LU; ++u) bx[u] = has[u] ? __ldg(S.boxes + kk[u]) : make_int4(1, 0, 1, 0);
+#pragma unroll
+                    for (int u = 0; u < LU; ++u) {
+                        if (nt + 32 > TCAP) {  // resume at batch u after the walk
+                            full = true;
+                            ee += 32 * u;
+                            break;
+                        }
+                        const bool start =
+                            has[u] && (jl[u] == 0 || !box_has(bx[u], tb.pv[eq * lmax + jl[u] - 1]));
+                        const unsigned bm = __ballot_sync(0xffffffffu, start);
+                        if (start) sm.task[nt + __popc(bm & lt)] = make_int4(kk[u], (eq << 16) | jl[u], 0, 0);
+                        nt += __popc(bm);
+                    }
+                    if (!full) ee += 32 * LU;
                 }
                 __syncwarp();
                 if (full) break;
@@ -337,11 +397,28 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
                 ee = 0;
             }
             __syncwarp();
-            // ---- walk the listed runs; idle lanes take the next run
+            // ---- per listed run, all lanes busy: its end (the samples in the
+            // primitive's box form one interval, so a binary search finds the
+            // last) and <gS, c_k> of its ray
+            for (int t = lane; t < nt; t += 32) {
+                const int4 tk = sm.task[t];
+                const int q = tk.y >> 16, j0 = tk.y & 0xffff;
+                const int4 box = __ldg(S.boxes + tk.x);
+                const int2* pv = tb.pv + q * lmax;
+                int lo = j0, hi = sm.le[q] - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (box_has(box, pv[mid])) lo = mid;
+                    else hi = mid - 1;
+                }
+                const float cd = logit_dot<CP>(S.lpad, tk.x, sm.gs + q * 32);
+                sm.task[t] = make_int4(tk.x, (q << 21) | ((lo + 1) << 10) | j0, __float_as_int(cd), 0);
+            }
+            __syncwarp();
+            // ---- walk the listed runs; idle lanes take the next runs together
             int next = 0;
             bool act = false;
-            int k = 0, rq = 0, jj = 0;
-            int4 box = make_int4(1, 0, 1, 0);
+            int k = 0, rq = 0, jj = 0, jend = 0;
             BwdPrim P;
             float cd = 0.f;
             float acc[13];
@@ -349,42 +426,40 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
             for (int i = 0; i < 13; ++i) acc[i] = 0.f;
             for (;;) {
                 const unsigned idle = __ballot_sync(0xffffffffu, !act);
-                if (idle != 0u && next < nt) {
+                const int nidle = __popc(idle);
+                if (next < nt && (nidle >= RTH || nidle == 32)) {
                     const int idx = next + __popc(idle & lt);
                     if (!act && idx < nt) {
-                        const int2 tk = sm.task[idx];
+                        const int4 tk = sm.task[idx];
                         k = tk.x;
-                        rq = tk.y >> 16;
-                        jj = tk.y & 0xffff;
+                        rq = tk.y >> 21;
+                        jend = (tk.y >> 10) & 2047;
+                        jj = tk.y & 1023;
+                        cd = __int_as_float(tk.z);
                         P = load_bwd(S.rec, S.aux, k);
-                        box = __ldg(S.boxes + k);
-                        cd = logit_dot<CP>(S.lpad, k, sm.gs + rq * 32);
 #pragma unroll
                         for (int i = 0; i < 13; ++i) acc[i] = 0.f;
                         act = true;
                     }
-                    next = min(next + __popc(idle), nt);
+                    next = min(next + nidle, nt);
                 }
                 if (!__any_sync(0xffffffffu, act)) break;
                 bool ends = false;
                 if (act) {
+                    // two samples of the run per step (two independent chains)
                     const int at = rq * lmax + jj;
-                    const float4 xg = tb.xg[at];
-                    const float w = tb.w[at], G = xg.w;
-                    if (G != 0.f || w != 0.f) {
-                        const float x[3] = {xg.x, xg.y, xg.z};
-                        float pr[11];
-                        const float po = occupancy_partials(P, x, pr);
-                        if (po != 0.f) {
-                            const float gf = -po * fmaf(G, P.f.sigma, w * cd);
-#pragma unroll
-                            for (int i = 0; i < 11; ++i) acc[i] = fmaf(gf, pr[i], acc[i]);
-                            acc[11] = fmaf(G, po, acc[11]);
-                            acc[12] = fmaf(w, po, acc[12]);
-                        }
-                    }
-                    ++jj;
-                    ends = jj >= sm.le[rq] || !box_has(box, tb.pv[at + 1]);
+                    const bool two = jj + 1 < jend;
+                    const float4 xg0 = tb.xg[at], xg1 = tb.xg[two ? at + 1 : at];
+                    const float w0 = tb.w[at], w1 = two ? tb.w[at + 1] : 0.f;
+                    const float G1 = two ? xg1.w : 0.f;
+                    const float x0[3] = {xg0.x, xg0.y, xg0.z}, x1[3] = {xg1.x, xg1.y, xg1.z};
+                    float pr0[11], pr1[11];
+                    const float po0 = occupancy_partials(P, x0, pr0);
+                    const float po1 = occupancy_partials(P, x1, pr1);
+                    if (po0 != 0.f) accumulate(acc, po0, pr0, xg0.w, w0, P.f.sigma, cd);
+                    if (two && po1 != 0.f) accumulate(acc, po1, pr1, G1, w1, P.f.sigma, cd);
+                    jj += two ? 2 : 1;
+                    ends = jj >= jend;
                 }
                 const unsigned dm = __ballot_sync(0xffffffffu, ends);
                 if (dm) {
@@ -466,8 +541,33 @@ sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream
             set_last_error("n_classes padding %d not supported", cp);
             return SQ_ERR_INVALID_ARG;
     }
+    const void* sw = nullptr;
+    switch (cp) {
+        case 4: sw = (const void*)k_bwd_sweep<4>; break;
+        case 8: sw = (const void*)k_bwd_sweep<8>; break;
+        case 12: sw = (const void*)k_bwd_sweep<12>; break;
+        case 16: sw = (const void*)k_bwd_sweep<16>; break;
+        case 20: sw = (const void*)k_bwd_sweep<20>; break;
+        case 24: sw = (const void*)k_bwd_sweep<24>; break;
+        case 28: sw = (const void*)k_bwd_sweep<28>; break;
+        case 32: sw = (const void*)k_bwd_sweep<32>; break;
+    }
+    {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sw, 256, 0);
+        if (e != cudaSuccess) return cuda_status(e, "k_bwd_sweep occupancy");
+        long long blocks = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+        const long long need = (B.total + 7) / 8;
+        if (blocks > need) blocks = need;
+        if (blocks < 1) blocks = 1;
+        Batch arg = B;
+        void* args[] = {&arg};
+        e = cudaLaunchKernel(sw, dim3((unsigned)blocks), dim3(256), args, 0, st);
+        if (e != cudaSuccess) return cuda_status(e, "k_bwd_sweep");
+    }
     // per warp: fixed part plus a sample table of RB * lmax entries
     const size_t per_warp = sizeof(WarpBwd) + table_stride(B.lmax);
+    cudaError_t e;
     const size_t kMaxSmem = 227 * 1024;
     while (warps > 1 && (size_t)warps * per_warp > kMaxSmem) --warps;
     const size_t smem = (size_t)warps * per_warp;
@@ -475,7 +575,7 @@ sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream
         set_last_error("backward: %d samples per ray need %zu bytes of shared memory", B.lmax, smem);
         return SQ_ERR_INVALID_ARG;
     }
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e, "k_backward shared memory");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem);

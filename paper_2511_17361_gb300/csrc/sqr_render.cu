@@ -120,9 +120,15 @@ SceneWs scene_ws(const sq_prims_t* p, size_t base) {
     return w;
 }
 
-size_t batch_ws_size(const sq_scene_t* sc, int n) {
+// The backward's per-sample (dL/dalpha_j, w_j) of every scene follow the scene
+// blocks, so a forward needs only the prefix.
+size_t gw_bytes(const sq_rays_t* r) { return align_up((size_t)r->n_cam * r->H * r->W * r->L * sizeof(float2), 256); }
+
+size_t batch_ws_size(const sq_scene_t* sc, int n, bool bwd) {
     size_t at = HDR_END;
     for (int i = 0; i < n; ++i) at = scene_ws(&sc[i].prims, at).end;
+    if (bwd)
+        for (int i = 0; i < n; ++i) at += gw_bytes(&sc[i].rays);
     return at;
 }
 
@@ -165,13 +171,25 @@ sq_status_t launch_pack(const sq_prims_t* prims, float4* rec, float4* aux, float
 
 size_t saved_size(const sq_rays_t* r, int n_classes) { return saved_bytes_of(r, n_classes); }
 
-size_t batched_workspace_size(const sq_scene_t* scenes, int n) { return batch_ws_size(scenes, n); }
+size_t batched_workspace_size(const sq_scene_t* scenes, int n) {
+    bool train = n > 0;
+    for (int i = 0; i < n; ++i) train = train && scenes[i].saved != nullptr;
+    return batch_ws_size(scenes, n, train);
+}
 
 size_t render_workspace_size(const sq_prims_t* p) {
     sq_scene_t s;
     memset(&s, 0, sizeof(s));
     s.prims = *p;
-    return batch_ws_size(&s, 1);
+    return batch_ws_size(&s, 1, false);
+}
+
+size_t render_bwd_workspace_size(const sq_prims_t* p, const sq_rays_t* r) {
+    sq_scene_t s;
+    memset(&s, 0, sizeof(s));
+    s.prims = *p;
+    s.rays = *r;
+    return batch_ws_size(&s, 1, true);
 }
 
 // Validates a batch for op, packs every scene, writes the descriptors and runs
@@ -182,7 +200,7 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
         set_last_error("batch of %d scenes, 1..%d supported", n, MAX_BATCH);
         return SQ_ERR_INVALID_ARG;
     }
-    const size_t need = batch_ws_size(sc, n);
+    const size_t need = batch_ws_size(sc, n, op == SQ_OP_BWD);
     if (ws == nullptr || ws_bytes < need) {
         set_last_error("render workspace of %zu bytes given, %zu needed", ws_bytes, need);
         return SQ_ERR_INVALID_ARG;
@@ -284,6 +302,11 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
     }
     P.off[n] = total;
     P.boff[n] = btotal;
+    if (op == SQ_OP_BWD)
+        for (int i = 0; i < n; ++i) {
+            P.s[i].gw = (float2*)(base + at);
+            at += gw_bytes(&sc[i].rays);
+        }
     SceneDesc* d = (SceneDesc*)(base + HDR_DESC);
     long long* off = (long long*)(base + HDR_OFF);
     long long* boff = (long long*)(base + HDR_BOFF);

@@ -38,6 +38,7 @@ struct SceneDesc {
     float* save_A;       // [R, L] saved alpha_j, negated where the clamp was active
     float* save_S;       // [R, C, L] saved semantic vector s_j of each sample (sample index fastest)
     int* save_n;         // [R] samples composited
+    float2* gw;          // [R, L] backward: (dL/dalpha_j, w_j) from the sweep
     const float* grad_depth;  // backward inputs
     const float* grad_sem;
     float* gacc;         // [N, GF] gradient accumulator (zeroed per backward)
