@@ -229,8 +229,8 @@ typedef struct {
 } sq_scene_t;
 
 /* Launch configuration: lanes (= samples marched together) per ray in the
- * forward (8 or 16), warps per CTA in the forward and backward (1..8).  The
- * defaults are {8, 8, 8}. */
+ * forward (4, 8 or 16), warps per CTA in the forward and backward (1..8).  The
+ * defaults are {4, 8, 8}. */
 typedef struct {
     int fwd_lanes_per_ray;
     int fwd_warps_per_cta;
@@ -250,7 +250,7 @@ sq_status_t sq_render_batched(int op, const sq_scene_t* scenes, int n_scenes, co
  * and, when every scene has saved state and cotangents, every backward one on
  * these scenes (reps timed launches each, CUDA events on the stream) and writes
  * the fastest to *best.  fwd_ms[4] / bwd_ms[2] (nullable) receive the mean
- * times of the candidates in the order {8,4},{8,8},{16,4},{16,8} and {4},{8}.
+ * times of the candidates in the order {4,4},{4,8},{8,4},{8,8} and {4},{8}.
  * Host-synchronous and overwrites the scenes' outputs; call it outside any
  * stream capture. */
 sq_status_t sq_autotune(const sq_scene_t* scenes, int n_scenes, void* workspace, size_t workspace_bytes, void* stream,

@@ -1,13 +1,17 @@
 // sqr_fwd.cu -- forward render (Sec. 3.3.2, Eq. 2, 4-6) on sm_103a.
 //
 // A warp marches 32/GS rays at a time, GS lanes per ray, one lane per sample.
-// Each lane walks its own sample's voxel list (Sec. 3.3.1), so the sums of Eq. 4
-// (alpha = sum p sigma, s = sum p c) stay in the lane's registers; compositing
+// Each lane sums its own sample's voxel list (Sec. 3.3.1), so the sums of Eq. 4
+// (alpha = sum p sigma, s = sum p c) stay in the lane's registers; the GS lanes
+// walk their lists together in ascending primitive order, so that a record that
+// several neighbouring samples need is loaded once for all of them; compositing
 // (Eq. 5-6) of a group's GS samples is a GS-lane product scan of (1 - alpha).
 // Rays of all scenes of the batch are handed out by one global counter, so a
 // lane group whose ray ends early takes the next ray, from whichever scene.
 // For the backward the forward saves, per composited sample, T_j, alpha_j (sign
 // marking the clamp) and s_j, and per ray the number of composited samples.
+#include <limits.h>
+
 #include "sqr_render.cuh"
 
 namespace sqr {
@@ -105,21 +109,37 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
         float sacc[CP];
 #pragma unroll
         for (int c = 0; c < CP; ++c) sacc[c] = 0.f;
-        const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
-        for (int e = 0; e < nmax; ++e) {
-            if (e < n) {
-                const int k = __ldg(v_sq + f + e);
-                const Prim p = load_prim(rec, k);
-                const float po = occupancy(p, x);
-                asum = fmaf(po, p.sigma, asum);
-                const float4* cr = lp4 + (size_t)k * (CP / 4);
+        // Merge-walk of the group's lists (each ascending in primitive id): every
+        // step takes the smallest pending id of the group, loads its record once
+        // for the group (one address, a broadcast) and adds it to the samples whose
+        // list holds it.  Each sample still sums its list in ascending id order.
+        int e = 0;
+        int head = n > 0 ? __ldg(v_sq + f) : INT_MAX;
+        int head2 = n > 1 ? __ldg(v_sq + f + 1) : INT_MAX;
+        for (;;) {
+            int kmin = head;
 #pragma unroll
-                for (int q = 0; q < CP / 4; ++q) {
-                    const float4 cv = __ldg(cr + q);
-                    sacc[4 * q + 0] = fmaf(po, cv.x, sacc[4 * q + 0]);
-                    sacc[4 * q + 1] = fmaf(po, cv.y, sacc[4 * q + 1]);
-                    sacc[4 * q + 2] = fmaf(po, cv.z, sacc[4 * q + 2]);
-                    sacc[4 * q + 3] = fmaf(po, cv.w, sacc[4 * q + 3]);
+            for (int o2 = GS / 2; o2 > 0; o2 >>= 1) kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o2, GS));
+            if (!__any_sync(0xffffffffu, kmin != INT_MAX)) break;
+            if (kmin != INT_MAX) {
+                const Prim p = load_prim(rec, kmin);
+                const float4* cr = lp4 + (size_t)kmin * (CP / 4);
+                float4 cv[CP / 4];
+#pragma unroll
+                for (int q = 0; q < CP / 4; ++q) cv[q] = __ldg(cr + q);
+                if (head == kmin) {
+                    const float po = occupancy(p, x);
+                    asum = fmaf(po, p.sigma, asum);
+#pragma unroll
+                    for (int q = 0; q < CP / 4; ++q) {
+                        sacc[4 * q + 0] = fmaf(po, cv[q].x, sacc[4 * q + 0]);
+                        sacc[4 * q + 1] = fmaf(po, cv[q].y, sacc[4 * q + 1]);
+                        sacc[4 * q + 2] = fmaf(po, cv[q].z, sacc[4 * q + 2]);
+                        sacc[4 * q + 3] = fmaf(po, cv[q].w, sacc[4 * q + 3]);
+                    }
+                    ++e;
+                    head = head2;
+                    head2 = e + 1 < n ? __ldg(v_sq + f + e + 1) : INT_MAX;
                 }
             }
         }
@@ -210,14 +230,15 @@ sq_status_t launch_cp_gs(const Batch& B, int warps, cudaStream_t st) {
 template <int CP>
 sq_status_t launch_cp(const Batch& B, const Tuning& tn, cudaStream_t st) {
     if (tn.fwd_lanes == 16) return launch_cp_gs<CP, 16>(B, tn.fwd_warps, st);
-    return launch_cp_gs<CP, 8>(B, tn.fwd_warps, st);
+    if (tn.fwd_lanes == 8) return launch_cp_gs<CP, 8>(B, tn.fwd_warps, st);
+    return launch_cp_gs<CP, 4>(B, tn.fwd_warps, st);
 }
 
 }  // namespace
 
 sq_status_t launch_forward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st) {
     if (B.total == 0) return SQ_OK;
-    if (tn.fwd_warps < 1 || tn.fwd_warps > MAX_WARPS || (tn.fwd_lanes != 8 && tn.fwd_lanes != 16)) {
+    if (tn.fwd_warps < 1 || tn.fwd_warps > MAX_WARPS || (tn.fwd_lanes != 4 && tn.fwd_lanes != 8 && tn.fwd_lanes != 16)) {
         set_last_error("forward tuning (lanes %d, warps %d) not supported", tn.fwd_lanes, tn.fwd_warps);
         return SQ_ERR_INVALID_ARG;
     }

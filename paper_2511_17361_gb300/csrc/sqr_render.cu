@@ -151,7 +151,7 @@ void saved_ptrs(const sq_rays_t* r, int C, void* saved, SceneDesc& D) {
     D.save_n = (int*)p;
 }
 
-Tuning default_tuning() { return Tuning{8, 8, 8}; }
+Tuning default_tuning() { return Tuning{4, 8, 8}; }
 
 }  // namespace
 
@@ -384,7 +384,7 @@ sq_status_t batched_api_impl(int op, const sq_scene_t* sc, int n, const sq_tunin
 // stream and keeps the fastest of each.  Host-synchronous.
 sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes, cudaStream_t st, sq_tuning_t* best,
                           float* fwd_ms, float* bwd_ms, int reps) {
-    const Tuning fcand[4] = {{8, 4, 8}, {8, 8, 8}, {16, 4, 8}, {16, 8, 8}};
+    const Tuning fcand[4] = {{4, 4, 8}, {4, 8, 8}, {8, 4, 8}, {8, 8, 8}};
     const int bcand[2] = {4, 8};
     if (reps < 1) reps = 1;
     cudaEvent_t e0, e1;

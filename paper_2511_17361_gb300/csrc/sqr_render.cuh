@@ -83,7 +83,7 @@ __device__ __forceinline__ void scene_ray(const SceneDesc& S, long long r, float
 
 // Launch configuration picked by the autotuner (or the defaults).
 struct Tuning {
-    int fwd_lanes;  // lanes (samples) per ray in the forward: 8 or 16
+    int fwd_lanes;  // lanes (samples) per ray in the forward: 4, 8 or 16
     int fwd_warps;  // warps per CTA, forward: 4 or 8
     int bwd_warps;  // warps per CTA, backward: 4 or 8
 };
