@@ -30,7 +30,7 @@ constexpr int TCAP = 256;  // runs listed per pass
 constexpr int RTH = 4;     // idle lanes that trigger a refill while others still walk
 constexpr int LU = 8;      // 32-entry batches whose loads the run listing issues together
 constexpr int QCAP = 32;   // pending flushes per warp
-constexpr int QW = 16;     // words per flush: key, 11 partials, sigma, W, ray slot, pad
+constexpr int QW = 16;     // words per flush: 11 partials, sigma, W, primitive, ray slot, pad
 
 struct BwdPrim {
     Prim f;
@@ -126,24 +126,37 @@ __device__ __forceinline__ float logit_dot(const float* __restrict__ lpad, int k
     return cd;
 }
 
-// Writes the warp's pending flushes into the accumulator of raw partial sums:
-// per entry, lane f adds field f (and f + 32).  Fields 0-11 are the summed
-// partials (gx 3, tau 3, u df/du 3, eps 2, sigma 1); fields 12.. the logit
-// gradients W gS_c of the entry's ray (gS of the bundle's rays in gsb).
+// Vector atomic add of four floats (16-byte aligned address).
+__device__ __forceinline__ void red_add4(float* addr, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Writes the warp's pending flushes into the accumulator of raw partial sums,
+// four entries per pass (two when n_classes > 20): lane (e, i) adds float4 i of
+// entry e's row.  A queue
+// entry holds the 12 summed partials (gx 3, tau 3, u df/du 3, eps 2, sigma 1), W,
+// the primitive and the ray slot; row fields 12.. are the logit gradients W gS_c
+// of that ray (gS of the bundle's rays in gsb, zero-padded to 32).
 __device__ __forceinline__ void drain_queue(float* __restrict__ gacc, const float* __restrict__ q, int qn, int lane,
                                             const float* __restrict__ gsb, int C) {
-    for (int e = 0; e < qn; ++e) {
-        const float* ent = q + e * QW;
-        const int k = __float_as_int(ent[0]);
-        const float* gs = gsb + __float_as_int(ent[14]) * 32;
-        float* row = gacc + (size_t)k * GF;
-        float v = 0.f;
-        if (lane < NRAW) v = ent[1 + lane];
-        else if (lane < NRAW + C) v = ent[1 + NRAW] * gs[lane - NRAW];
-        if (v != 0.f) red_add(row + lane, v);
-        if (lane + 32 < NRAW + C) {
-            const float v2 = ent[1 + NRAW] * gs[lane + 32 - NRAW];
-            if (v2 != 0.f) red_add(row + 32 + lane, v2);
+    const int sh = NRAW + C > 32 ? 4 : 3;  // log2 of the lanes per entry
+    const int sub = lane >> sh, i = lane & ((1 << sh) - 1);
+    const bool used = 4 * i < NRAW + C;
+    for (int e0 = 0; e0 < qn; e0 += 32 >> sh) {
+        const int e = e0 + sub;
+        if (e < qn && used) {
+            const float* ent = q + e * QW;
+            const int k = __float_as_int(ent[13]);
+            float4 v;
+            if (i < 3) {
+                v = *reinterpret_cast<const float4*>(ent + 4 * i);
+            } else {
+                const float W = ent[12];
+                const float4 g = *reinterpret_cast<const float4*>(gsb + __float_as_int(ent[14]) * 32 + 4 * i - NRAW);
+                v = make_float4(W * g.x, W * g.y, W * g.z, W * g.w);
+            }
+            red_add4(gacc + (size_t)k * GF + 4 * i, v);
         }
     }
 }
@@ -470,11 +483,11 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
                         qn = 0;
                     }
                     if (ends) {
-                        float* ent = sm.queue + (qn + __popc(dm & lt)) * QW;
-                        ent[0] = __int_as_float(k);
-#pragma unroll
-                        for (int i = 0; i < 13; ++i) ent[1 + i] = acc[i];
-                        ent[14] = __int_as_float(rq);
+                        float4* ent = reinterpret_cast<float4*>(sm.queue + (qn + __popc(dm & lt)) * QW);
+                        ent[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                        ent[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+                        ent[2] = make_float4(acc[8], acc[9], acc[10], acc[11]);
+                        ent[3] = make_float4(acc[12], __int_as_float(k), __int_as_float(rq), 0.f);
                         act = false;
                     }
                     qn += __popc(dm);
