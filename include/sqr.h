@@ -110,6 +110,13 @@ typedef struct {
     long long capacity;
     long long* p_total;
     int* status;
+    /* Optional (NULL = absent), no counterpart in the paper: [capacity] uint16,
+     * for every entry of v_sq the position of its voxel v against the primitive's
+     * voxel range (i0..i1, j0..j1, k0..k1) per axis a (bits 4a..4a+3):
+     * lo_a == v_a, lo_a == v_a - 1, hi_a == v_a, hi_a == v_a + 1.  Written by
+     * sq_build_index when non-NULL; sq_render_bwd uses it to find where a ray
+     * enters a primitive's range without reading the range (faster backward). */
+    unsigned short* v_flags;
 } sq_index_t;
 
 /* Rays and samples (Sec. 3.3.1): n_cam cameras of H x W pixels, L sample depths

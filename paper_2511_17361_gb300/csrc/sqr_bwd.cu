@@ -11,8 +11,9 @@
 // monotone in t and the primitive is listed in exactly the voxels of its box), so
 // every (ray, primitive) pair is one run of samples.  Per bundle the warp builds a
 // sample table in shared memory (point, voxel, list, dL/dalpha_j, w_j), lists the
-// runs that start at each sample (list entries whose box misses the previous
-// sample's voxel), finds each run's end by a binary search, and then every lane
+// runs that start at each sample (list entries whose voxel range misses the
+// previous sample's voxel, read from the index's range-boundary flags when it has
+// them), finds each run's end by a binary search, and then every lane
 // walks runs on its own: it holds the primitive's record in registers, evaluates
 // dp_o/d(params) at the run's samples (two per step), weights them by
 // dL/dp_o = G_j sigma + w_j <gS, c>, sums in registers and flushes once per run
@@ -101,11 +102,11 @@ __global__ void k_pack_boxes(const int* __restrict__ ranges, int n, int4* __rest
 
 
 // Packed inclusive box test; an empty box is stored as lo = 1, hi = 0.  pv holds
-// a sample's voxel as (ix | iy << 16, iz), iz = -1 outside the grid.
+// a sample's voxel as (ix | iy << 16, iz | extra << 16), pv.y = -1 outside the grid.
 __device__ __forceinline__ bool box_has(const int4 b, int2 pv) {
     if (pv.y < 0) return false;
     const unsigned bx = (unsigned)b.x, by = (unsigned)b.y, bz = (unsigned)b.z, px = (unsigned)pv.x;
-    const unsigned ix = px & 0xffffu, iy = px >> 16, iz = (unsigned)pv.y;
+    const unsigned ix = px & 0xffffu, iy = px >> 16, iz = (unsigned)pv.y & 0xffffu;
     return ix >= (bx & 0xffffu) && ix <= (bx >> 16) && iy >= (by & 0xffffu) && iy <= (by >> 16) &&
            iz >= (bz & 0xffffu) && iz <= (bz >> 16);
 }
@@ -174,7 +175,7 @@ __device__ __forceinline__ void accumulate(float acc[13], float po, const float 
 // Fixed per-warp shared memory; the sample tables (RB * L entries) follow the
 // array of these in dynamic shared memory.
 struct alignas(16) WarpBwd {
-    int4 task[TCAP];  // listed runs: (primitive, ray slot / first / end sample, <gS, c>, 0)
+    int4 task[TCAP];  // listed runs: (list entry, then primitive; ray slot / first / end sample; <gS, c>; 0)
     float queue[QCAP * QW];
     float gs[RB * 32];  // dL/dS of the bundle's rays, zero-padded
     int pre[32];        // inclusive prefix of list lengths over a chunk of samples
@@ -184,10 +185,18 @@ struct alignas(16) WarpBwd {
 // Sample table of one warp, structure of arrays over RB * lmax samples.
 struct Table {
     float4* xg;  // sample point, dL/dalpha_j
-    int2* pv;    // packed voxel
+    int2* pv;    // packed voxel (ix | iy << 16, iz | start mask << 16); (0, -1) outside
     int2* nf;    // V_n, V_f of the voxel (0 outside)
     float* w;    // w_j = T_j alpha_j
 };
+
+// Run-start test of a sample's list entries against the previous sample's voxel:
+// none start (same voxel, or no list), all start (first sample, or the previous
+// one outside the grid), test each entry's range, or a mask of range-boundary
+// flags (a step of at most two voxels per axis; entries start whose flags hit it).
+constexpr int MK_NONE = 0, MK_ALL = 0x1000, MK_BOX = 0x2000, MK_FLAGS = 0xfff;
+
+__device__ __forceinline__ int mask_of(int2 pv) { return pv.y < 0 ? MK_NONE : (int)((unsigned)pv.y >> 16); }
 
 __host__ __device__ inline size_t table_stride(int lmax) { return ((size_t)RB * lmax * 36 + 15) / 16 * 16; }
 
@@ -199,6 +208,24 @@ __device__ __forceinline__ Table table_at(unsigned char* base, int lmax) {
     t.nf = reinterpret_cast<int2*>(base + n * 24);
     t.w = reinterpret_cast<float*>(base + n * 32);
     return t;
+}
+
+// Start mask of a sample in voxel (ix, iy, iz) after one in voxel pv (packed).
+__device__ __forceinline__ int start_mask(int2 cur, int2 prev, bool has_flags) {
+    if (cur.y < 0) return MK_NONE;
+    if (prev.y < 0) return MK_ALL;
+    if (cur.x == prev.x && cur.y == prev.y) return MK_NONE;
+    if (!has_flags) return MK_BOX;
+    const int d[3] = {(cur.x & 0xffff) - (prev.x & 0xffff), (int)((unsigned)cur.x >> 16) - (int)((unsigned)prev.x >> 16),
+                      cur.y - prev.y};
+    int m = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] > 2 || d[a] < -2) return MK_BOX;
+        const int bits = d[a] == 1 ? 1 : d[a] == 2 ? 3 : d[a] == -1 ? 4 : d[a] == -2 ? 12 : 0;
+        m |= bits << (4 * a);
+    }
+    return m;
 }
 
 // Back-to-front sweep of every ray (one warp per ray, chunks of 32 samples):
@@ -266,31 +293,35 @@ __global__ void __launch_bounds__(256) k_bwd_sweep(Batch B) {
 }
 
 // Fills ray slot q of the table (one warp, chunks of 32 samples): sample point,
-// voxel, its list and the sweep's (dL/dalpha_j, w_j).  Every load of a chunk is
-// independent of the others.
+// voxel, its list, the run-start mask and the sweep's (dL/dalpha_j, w_j).
 __device__ __forceinline__ void build_table(const SceneDesc& S, long long r, int q, int Le, const Table& tb,
                                             int lmax, int lane) {
     float o[3], d[3];
     scene_ray(S, r, o, d);
     const GridC g = S.g;
+    const bool has_flags = S.v_flags != nullptr;
     const float2* __restrict__ gw = S.gw + r * S.L;
-    for (int jc = 0; jc < Le; jc += 64) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int j = jc + 32 * h + lane;
-            if (j < Le) {
-                float x[3];
-                int vi[3];
-                const int vox = sample_voxel(g, o, d, __ldg(S.t + j), x, vi);
-                const float2 gwj = gw[j];
-                int2 nf = make_int2(0, 0);
-                if (vox >= 0) nf = make_int2(__ldg(S.v_n + vox), __ldg(S.v_f + vox));
-                const int at = q * lmax + j;
-                tb.xg[at] = make_float4(x[0], x[1], x[2], gwj.x);
-                tb.pv[at] = vox >= 0 ? make_int2(vi[0] | (vi[1] << 16), vi[2]) : make_int2(0, -1);
-                tb.nf[at] = nf;
-                tb.w[at] = gwj.y;
-            }
+    int2 carry = make_int2(0, -1);  // voxel of the sample before the chunk (none yet)
+    for (int jc = 0; jc < Le; jc += 32) {
+        const int j = jc + lane;
+        float x[3] = {0.f, 0.f, 0.f};
+        int vi[3];
+        int vox = -1;
+        if (j < Le) vox = sample_voxel(g, o, d, __ldg(S.t + j), x, vi);
+        const int2 pv = vox >= 0 ? make_int2(vi[0] | (vi[1] << 16), vi[2]) : make_int2(0, -1);
+        int2 prev = make_int2(__shfl_up_sync(0xffffffffu, pv.x, 1), __shfl_up_sync(0xffffffffu, pv.y, 1));
+        if (lane == 0) prev = carry;
+        carry = make_int2(__shfl_sync(0xffffffffu, pv.x, 31), __shfl_sync(0xffffffffu, pv.y, 31));
+        if (j < Le) {
+            const float2 gwj = gw[j];
+            int2 nf = make_int2(0, 0);
+            if (vox >= 0) nf = make_int2(__ldg(S.v_n + vox), __ldg(S.v_f + vox));
+            const int at = q * lmax + j;
+            const int mk = nf.x > 0 ? start_mask(pv, prev, has_flags) : MK_NONE;
+            tb.xg[at] = make_float4(x[0], x[1], x[2], gwj.x);
+            tb.pv[at] = pv.y < 0 ? pv : make_int2(pv.x, pv.y | (mk << 16));
+            tb.nf[at] = nf;
+            tb.w[at] = gwj.y;
         }
     }
 }
@@ -334,11 +365,13 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
         for (int q = 0; q < nr; ++q) build_table(S, r0 + q, q, sm.le[q], tb, lmax, lane);
         __syncwarp();
 
-        int qn = 0;               // pending flushes
+        int qn = 0;                  // pending flushes
         int eq = 0, ec = 0, ee = 0;  // where the run listing resumes: ray slot, chunk, entry
         bool more = nr > 0;
         while (more) {
-            // ---- list run starts until the task list is full or every run is listed
+            // ---- list run starts until the task list is full or every run is listed:
+            // the list entries of a chunk of 32 samples are numbered consecutively
+            // and tested LU batches of 32 at a time
             int nt = 0;
             for (;;) {
                 if (eq >= nr) {
@@ -353,15 +386,13 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
                     continue;
                 }
                 const int j = ec * 32 + lane, at = eq * lmax + j;
-                int nj = 0, fj = 0;
+                int nj = 0, fj = 0, mj = MK_NONE;
                 if (j < Lq) {
-                    const int2 nf = tb.nf[at];
-                    nj = nf.x;
-                    fj = nf.y;
-                    // a sample in its predecessor's voxel starts no run
-                    if (j > 0 && nj > 0) {
-                        const int2 p0 = tb.pv[at - 1], p1 = tb.pv[at];
-                        if (p0.x == p1.x && p0.y == p1.y) nj = 0;
+                    mj = mask_of(tb.pv[at]);
+                    if (mj != MK_NONE) {
+                        const int2 nf = tb.nf[at];
+                        nj = nf.x;
+                        fj = nf.y;
                     }
                 }
                 const int incl = warp_incl_scan(nj, lane);
@@ -369,26 +400,34 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
                 sm.pre[lane] = incl;
                 __syncwarp();
                 bool full = false;
-                // LU batches of 32 entries per round, their loads issued together
                 while (ee < tot && !full) {
-                    int kk[LU], jl[LU];
-                    bool has[LU];
+                    int ent[LU], jl[LU], ml[LU];
+                    unsigned fv[LU];
+                    bool st[LU];
 #pragma unroll
                     for (int u = 0; u < LU; ++u) {
                         const int e = ee + 32 * u + lane;
+                        const bool valid = e < tot;
                         int l = 0;  // sample of entry e: number of prefixes <= e
 #pragma unroll
                         for (int step = 16; step > 0; step >>= 1)
                             if (sm.pre[l + step - 1] <= e) l += step;
+                        // every lane takes part in both shuffles; invalid lanes drop the results
                         const int fl = __shfl_sync(0xffffffffu, fj, l);
+                        const int ms = __shfl_sync(0xffffffffu, mj, l);
+                        ml[u] = valid ? ms : MK_NONE;
                         jl[u] = ec * 32 + l;
-                        has[u] = e < tot;
-                        kk[u] = 0;
-                        if (has[u]) kk[u] = __ldg(S.v_sq + fl + (e - (l > 0 ? sm.pre[l - 1] : 0)));
+                        ent[u] = valid ? fl + (e - (l > 0 ? sm.pre[l - 1] : 0)) : 0;
+                        fv[u] = (ml[u] & MK_FLAGS) ? __ldg(S.v_flags + ent[u]) : 0u;
                     }
-                    int4 bx[LU];
 #pragma unroll
-                    for (int u = 0; u < LU; ++u) bx[u] = has[u] ? __ldg(S.boxes + kk[u]) : make_int4(1, 0, 1, 0);
+                    for (int u = 0; u < LU; ++u) {
+                        st[u] = ml[u] == MK_ALL || (fv[u] & (unsigned)(ml[u] & MK_FLAGS)) != 0u;
+                        if (ml[u] == MK_BOX) {
+                            const int2 pl = tb.pv[eq * lmax + jl[u] - 1];
+                            st[u] = !box_has(__ldg(S.boxes + __ldg(S.v_sq + ent[u])), pl);
+                        }
+                    }
 #pragma unroll
                     for (int u = 0; u < LU; ++u) {
                         if (nt + 32 > TCAP) {  // resume at batch u after the walk
@@ -396,10 +435,8 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
                             ee += 32 * u;
                             break;
                         }
-                        const bool start =
-                            has[u] && (jl[u] == 0 || !box_has(bx[u], tb.pv[eq * lmax + jl[u] - 1]));
-                        const unsigned bm = __ballot_sync(0xffffffffu, start);
-                        if (start) sm.task[nt + __popc(bm & lt)] = make_int4(kk[u], (eq << 16) | jl[u], 0, 0);
+                        const unsigned bm = __ballot_sync(0xffffffffu, st[u]);
+                        if (st[u]) sm.task[nt + __popc(bm & lt)] = make_int4(ent[u], (eq << 16) | jl[u], 0, 0);
                         nt += __popc(bm);
                     }
                     if (!full) ee += 32 * LU;
@@ -416,7 +453,8 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
             for (int t = lane; t < nt; t += 32) {
                 const int4 tk = sm.task[t];
                 const int q = tk.y >> 16, j0 = tk.y & 0xffff;
-                const int4 box = __ldg(S.boxes + tk.x);
+                const int k = __ldg(S.v_sq + tk.x);
+                const int4 box = __ldg(S.boxes + k);
                 const int2* pv = tb.pv + q * lmax;
                 int lo = j0, hi = sm.le[q] - 1;
                 while (lo < hi) {
@@ -424,8 +462,8 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
                     if (box_has(box, pv[mid])) lo = mid;
                     else hi = mid - 1;
                 }
-                const float cd = logit_dot<CP>(S.lpad, tk.x, sm.gs + q * 32);
-                sm.task[t] = make_int4(tk.x, (q << 21) | ((lo + 1) << 10) | j0, __float_as_int(cd), 0);
+                const float cd = logit_dot<CP>(S.lpad, k, sm.gs + q * 32);
+                sm.task[t] = make_int4(k, (q << 21) | ((lo + 1) << 10) | j0, __float_as_int(cd), 0);
             }
             __syncwarp();
             // ---- walk the listed runs; idle lanes take the next runs together

@@ -295,18 +295,41 @@ __device__ void warp_bitonic(int n, int lane, Load ld, Store st) {
     }
 }
 
+// Range-boundary flags of primitive k listed in voxel (ix, iy, iz): per axis a,
+// bit 4a: lo == v, 4a+1: lo == v - 1, 4a+2: hi == v, 4a+3: hi == v + 1.
+__device__ __forceinline__ unsigned short entry_flags(const int* __restrict__ ranges, int k, int ix, int iy, int iz) {
+    const int* r = ranges + 6 * k;
+    const int v[3] = {ix, iy, iz};
+    unsigned f = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int lo = __ldg(r + 2 * a), hi = __ldg(r + 2 * a + 1);
+        f |= ((lo == v[a]) ? 1u : 0u) << (4 * a);
+        f |= ((lo == v[a] - 1) ? 2u : 0u) << (4 * a);
+        f |= ((hi == v[a]) ? 4u : 0u) << (4 * a);
+        f |= ((hi == v[a] + 1) ? 8u : 0u) << (4 * a);
+    }
+    return (unsigned short)f;
+}
+
+// Sorts every voxel's list ascending (one warp per voxel) and, when v_flags is
+// given, writes each entry's range-boundary flags.
 __global__ void __launch_bounds__(SORT_WARPS * 32) k_sort(const int* __restrict__ v_n, const int* __restrict__ v_f,
                                                           int* __restrict__ v_sq, long long nvox,
-                                                          const int* __restrict__ status) {
+                                                          const int* __restrict__ status,
+                                                          const int* __restrict__ ranges,
+                                                          unsigned short* __restrict__ v_flags, int ny, int nz) {
     __shared__ int sh[SORT_WARPS][SORT_SMEM];
     if (*status != SQ_OK) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long nwarps = (long long)gridDim.x * SORT_WARPS;
     for (long long v = (long long)blockIdx.x * SORT_WARPS + wid; v < nvox; v += nwarps) {
         const int n = v_n[v];
-        if (n <= 1) continue;
+        if (n < 1) continue;
         int* list = v_sq + v_f[v];
-        if (n <= 32) {
+        if (n == 1) {
+            // a single entry is sorted
+        } else if (n <= 32) {
             int x = lane < n ? list[lane] : 0x7fffffff;
 #pragma unroll
             for (int size = 2; size <= 32; size <<= 1) {
@@ -330,6 +353,12 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_sort(const int* __restrict_
         } else {
             volatile int* g = list;
             warp_bitonic(n, lane, [&](int i) { return g[i]; }, [&](int i, int val) { g[i] = val; });
+        }
+        if (v_flags) {
+            __syncwarp();
+            const int iz = (int)(v % nz), iy = (int)((v / nz) % ny), ix = (int)(v / ((long long)ny * nz));
+            unsigned short* fl = v_flags + v_f[v];
+            for (int i = lane; i < n; i += 32) fl[i] = entry_flags(ranges, list[i], ix, iy, iz);
         }
     }
 }
@@ -410,7 +439,8 @@ sq_status_t build_index_impl(const sq_prims_t* prims, const sq_grid_t* grid, con
         SQ_CHECK_LAUNCH("k_scatter");
         long long want = (nvox + SORT_WARPS - 1) / SORT_WARPS;
         int sblocks = (int)(want < 152 * 64 ? want : 152 * 64);
-        k_sort<<<sblocks, SORT_WARPS * 32, 0, st>>>(idx->v_n, idx->v_f, idx->v_sq, nvox, idx->status);
+        k_sort<<<sblocks, SORT_WARPS * 32, 0, st>>>(idx->v_n, idx->v_f, idx->v_sq, nvox, idx->status, idx->ranges,
+                                                    idx->v_flags, ny, nz);
         SQ_CHECK_LAUNCH("k_sort");
     }
     return SQ_OK;

@@ -23,6 +23,7 @@ struct SceneDesc {
     const int* v_n;
     const int* v_f;
     const int* v_sq;
+    const unsigned short* v_flags;  // nullable: per-entry range-boundary flags
     const int* status;
     GridC g;
     const float* K;

@@ -43,7 +43,7 @@ class SqIndexOpts(ctypes.Structure):
 
 class SqIndex(ctypes.Structure):
     _fields_ = [("v_n", _vp), ("v_f", _vp), ("v_sq", _vp), ("ranges", _vp), ("capacity", ctypes.c_longlong),
-                ("p_total", _vp), ("status", _vp)]
+                ("p_total", _vp), ("status", _vp), ("v_flags", _vp)]
 
 
 class SqRays(ctypes.Structure):
@@ -201,14 +201,16 @@ def workspace_size(op, prims=None, grid=None, rays=None) -> int:
 
 # ------------------------------------------------------------------ index
 class Index:
-    """Device buffers of the voxel -> superquadric index (V_n, V_f, V_sq, ranges)."""
+    """Device buffers of the voxel -> superquadric index (V_n, V_f, V_sq, ranges)
+    plus the per-entry range-boundary flags the backward uses."""
 
-    def __init__(self, grid: dict, n: int, capacity: int, device):
+    def __init__(self, grid: dict, n: int, capacity: int, device, flags: bool = True):
         nvox = int(grid["n"][0]) * int(grid["n"][1]) * int(grid["n"][2])
         self.grid = grid
         self.v_n = torch.empty(nvox, dtype=torch.int32, device=device)
         self.v_f = torch.empty(nvox, dtype=torch.int32, device=device)
         self.v_sq = torch.empty(max(int(capacity), 1), dtype=torch.int32, device=device)
+        self.v_flags = torch.empty(max(int(capacity), 1), dtype=torch.int16, device=device) if flags else None
         self.capacity = int(capacity)
         self.ranges = torch.empty((max(n, 1), 6), dtype=torch.int32, device=device)
         self.p_total = torch.zeros(1, dtype=torch.int64, device=device)
@@ -216,7 +218,7 @@ class Index:
 
     def struct(self) -> SqIndex:
         return SqIndex(_ptr(self.v_n), _ptr(self.v_f), _ptr(self.v_sq), _ptr(self.ranges), self.capacity,
-                       _ptr(self.p_total), _ptr(self.status))
+                       _ptr(self.p_total), _ptr(self.status), _ptr(self.v_flags))
 
     def P(self) -> int:
         return int(self.p_total.item())
@@ -228,16 +230,18 @@ class Index:
 
 
 def build_index(prims: dict, grid: dict, mode: int = SQ_INDEX_OBB, tau_cut: float = 0.01, nv: int = 5,
-                capacity: int | None = None, index: Index | None = None, sync: bool = True) -> Index:
+                capacity: int | None = None, index: Index | None = None, sync: bool = True,
+                flags: bool = True) -> Index:
     """Builds the index on the current stream.  With ``sync`` the host reads P and
-    re-runs once with a large enough V_sq when the capacity was too small."""
+    re-runs once with a large enough V_sq when the capacity was too small.
+    ``flags`` also writes the per-entry range-boundary flags the backward uses."""
     device = prims["means"].device
     n = prims["means"].shape[0]
     if index is None:
         if capacity is None:
             nvox = int(grid["n"][0]) * int(grid["n"][1]) * int(grid["n"][2])
             capacity = max(4 * nvox, 1024)
-        index = Index(grid, n, capacity, device)
+        index = Index(grid, n, capacity, device, flags)
     p, g = prims_struct(prims), grid_struct(grid)
     opts = SqIndexOpts(mode, tau_cut, nv)
     wsz = lib.sq_workspace_size(SQ_OP_INDEX, ctypes.byref(p), ctypes.byref(g), None)
@@ -248,7 +252,7 @@ def build_index(prims: dict, grid: dict, mode: int = SQ_INDEX_OBB, tau_cut: floa
     if sync:
         P = index.P()
         if P > index.capacity:
-            index = Index(grid, n, int(P * 1.25) + 1024, device)
+            index = Index(grid, n, int(P * 1.25) + 1024, device, index.v_flags is not None)
             return build_index(prims, grid, mode, tau_cut, nv, index=index, sync=True)
         index.check()
     return index

@@ -82,6 +82,45 @@ def test_index_empty_and_outside(sqr):
     assert ix0.P() == 0 and np.all(ix0.v_n.cpu().numpy() == 0)
 
 
+def _expected_flags(ix):
+    """Range-boundary flags of every index entry, from their definition: per axis
+    a, bit 4a: lo == v, 4a+1: lo == v - 1, 4a+2: hi == v, 4a+3: hi == v + 1, for
+    the entry's voxel v and its primitive's voxel range."""
+    ny, nz = int(ix.grid["n"][1]), int(ix.grid["n"][2])
+    got = np_index(ix)
+    vox = np.repeat(np.arange(len(got["v_n"]), dtype=np.int64), got["v_n"])
+    coords = (vox // (ny * nz), (vox // nz) % ny, vox % nz)
+    r = got["ranges"][got["v_sq"]]
+    f = np.zeros(got["P"], np.int64)
+    for a, c in enumerate(coords):
+        lo, hi = r[:, 2 * a].astype(np.int64), r[:, 2 * a + 1].astype(np.int64)
+        f |= ((lo == c) * 1 | (lo == c - 1) * 2 | (hi == c) * 4 | (hi == c + 1) * 8) << (4 * a)
+    return f
+
+
+@pytest.mark.parametrize("ci", [0, 2])
+def test_index_boundary_flags(sqr, ci):
+    """The optional per-entry flags equal their definition, bit for bit."""
+    cfg = synth.make_config(ci)
+    _, ix, _ = _index_pair(sqr, cfg)
+    P = ix.P()
+    got = ix.v_flags[:P].cpu().numpy().astype(np.int64) & 0xFFFF
+    assert np.array_equal(got, _expected_flags(ix))
+    assert np.count_nonzero(got) > 0
+
+
+def test_index_boundary_flags_long_lists(sqr):
+    rng = np.random.default_rng(7)
+    n = 1500
+    pr = prims_from(rng.uniform(0, 4, (n, 3)), rng.standard_normal((n, 4)), rng.uniform(0.2, 1.5, (n, 3)),
+                    rng.uniform(0.3, 1.8, (n, 2)), rng.uniform(0, 1, n), rng.standard_normal((n, 3)))
+    grid = synth.grid_spec(8, 6, 4, lo=(0, 0, 0), hi=(4, 3, 2))
+    _, ix, _ = _index_pair(sqr, {"prims": pr, "grid": grid})
+    got = ix.v_flags[:ix.P()].cpu().numpy().astype(np.int64) & 0xFFFF
+    assert np.array_equal(got, _expected_flags(ix))
+    assert np_index(ix)["v_n"].max() > 32
+
+
 def test_index_capacity_overflow_reported(sqr):
     """Too small a V_sq: status = SQ_ERR_CAPACITY and p_total = the needed size."""
     cfg = synth.make_config(0)
@@ -201,10 +240,10 @@ def test_forward_cube_index(sqr):
 
 
 # ----------------------------------------------------------------------- backward
-def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0, kappa=0.0):
+def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0, kappa=0.0, flags=True):
     prims_d, rays = scene_to_gpu(sqr, prims, rig, t, kappa, alpha_max)
     g = dev_grid(grid)
-    ix = sqr.build_index(prims_d, g)
+    ix = sqr.build_index(prims_d, g, flags=flags)
     R = rays.R
     gd_full = np.zeros(R, np.float32)
     gs_full = np.zeros((R, prims["logits"].shape[1]), np.float32)
@@ -231,6 +270,28 @@ def test_backward_small_scene_full(sqr, seed):
     got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs)
     for k in ref:
         check_grad(got[k], ref[k], k)
+
+
+@pytest.mark.parametrize("flags", [True, False])
+def test_backward_long_sample_steps(sqr, flags):
+    """Samples several voxels apart (run starts then come from a test of each list
+    entry's range, not from the boundary flags), with and without the index's
+    flags; and the default spacing without flags."""
+    pr, grid, rig, t = small_scene(9, n=10, H=8, W=10, L=10, gn=(64, 64, 16))
+    R = rig["H"] * rig["W"]
+    rng = np.random.default_rng(9)
+    gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, 5)).astype(np.float32)
+    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, flags=flags)
+    assert np.count_nonzero(ref["opacity"]) > 3
+    for k in ref:
+        check_grad(got[k], ref[k], k)
+    if not flags:
+        pr, grid, rig, t = small_scene(10, n=8, H=9, W=11, L=32)
+        R = rig["H"] * rig["W"]
+        gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, 5)).astype(np.float32)
+        got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, flags=False)
+        for k in ref:
+            check_grad(got[k], ref[k], k)
 
 
 def test_backward_clamp_active(sqr):
