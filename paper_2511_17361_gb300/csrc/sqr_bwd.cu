@@ -30,8 +30,11 @@ constexpr int RB = 2;      // rays per bundle
 constexpr int TCAP = 256;  // runs listed per pass
 constexpr int RTH = 4;     // idle lanes that trigger a refill while others still walk
 constexpr int LU = 8;      // 32-entry batches whose loads the run listing issues together
+constexpr int RU = 4;      // listed runs per lane whose loads the per-run pass issues together
 constexpr int QCAP = 32;   // pending flushes per warp
 constexpr int QW = 16;     // words per flush: 11 partials, sigma, W, primitive, ray slot, pad
+static_assert(QCAP >= 32, "one walker step can end a run in every lane");
+static_assert(TCAP >= 32 && TCAP % 32 == 0, "the listing appends up to 32 runs at a time");
 
 struct BwdPrim {
     Prim f;
@@ -450,20 +453,43 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
             // ---- per listed run, all lanes busy: its end (the samples in the
             // primitive's box form one interval, so a binary search finds the
             // last) and <gS, c_k> of its ray
-            for (int t = lane; t < nt; t += 32) {
-                const int4 tk = sm.task[t];
-                const int q = tk.y >> 16, j0 = tk.y & 0xffff;
-                const int k = __ldg(S.v_sq + tk.x);
-                const int4 box = __ldg(S.boxes + k);
-                const int2* pv = tb.pv + q * lmax;
-                int lo = j0, hi = sm.le[q] - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (box_has(box, pv[mid])) lo = mid;
-                    else hi = mid - 1;
+            for (int t0 = 0; t0 < nt; t0 += 32 * RU) {
+                // RU runs per lane, their loads in flight together
+                int k[RU], q[RU], j0[RU];
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int t = t0 + 32 * u + lane;
+                    k[u] = 0;
+                    q[u] = 0;
+                    j0[u] = 0;
+                    if (t < nt) {
+                        const int4 tk = sm.task[t];
+                        q[u] = tk.y >> 16;
+                        j0[u] = tk.y & 0xffff;
+                        k[u] = __ldg(S.v_sq + tk.x);
+                    }
                 }
-                const float cd = logit_dot<CP>(S.lpad, k, sm.gs + q * 32);
-                sm.task[t] = make_int4(k, (q << 21) | ((lo + 1) << 10) | j0, __float_as_int(cd), 0);
+                int4 box[RU];
+                float cd[RU];
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    box[u] = __ldg(S.boxes + k[u]);
+                    cd[u] = logit_dot<CP>(S.lpad, k[u], sm.gs + q[u] * 32);
+                }
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int t = t0 + 32 * u + lane;
+                    if (t < nt) {
+                        const int2* pv = tb.pv + q[u] * lmax;
+                        int lo = j0[u], hi = sm.le[q[u]] - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (box_has(box[u], pv[mid])) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        sm.task[t] = make_int4(k[u], (q[u] << 21) | ((lo + 1) << 10) | j0[u], __float_as_int(cd[u]), 0);
+                    }
+                }
             }
             __syncwarp();
             // ---- walk the listed runs; idle lanes take the next runs together

@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
         int e = 0;
         int head = n > 0 ? __ldg(v_sq + f) : INT_MAX;
         int head2 = n > 1 ? __ldg(v_sq + f + 1) : INT_MAX;
+        int head3 = n > 2 ? __ldg(v_sq + f + 2) : INT_MAX;  // list look-ahead of two
         for (;;) {
             int kmin = head;
 #pragma unroll
@@ -139,7 +140,8 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
                     }
                     ++e;
                     head = head2;
-                    head2 = e + 1 < n ? __ldg(v_sq + f + e + 1) : INT_MAX;
+                    head2 = head3;
+                    head3 = e + 2 < n ? __ldg(v_sq + f + e + 2) : INT_MAX;
                 }
             }
         }
