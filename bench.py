@@ -32,7 +32,6 @@ from paper_2511_17361_gb300 import synth  # noqa: E402
 
 WORKLOAD = 1
 MUFU_PER_PAIR = {"fwd": 9, "bwd": 13}  # SFU ops per (sample, primitive) pair in each kernel
-LAUNCHES_PER_STEP = 19                  # index 9, forward 3, loss 1, backward 6
 # DRAM traffic per launch from the committed ncu summaries, valid only while the
 # kernel source is unchanged (sha256 of the file holding it).
 NCU_TRAFFIC = {
@@ -233,11 +232,15 @@ def run_mine(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    sqr.profile_enable(True)  # CUDA events around every library kernel, on its stream
     for s in range(args.steps):
         flush.fill_(float(s))
         step(evs[s])
     torch.cuda.synchronize()
+    sqr.profile_enable(False)
     clocks = sampler.stop()
+    kernel_ms = {k: sqr.profile_query(k) for k in ("k_forward", "k_backward", "k_bwd_sweep")}
+    launches_timed, _, dropped = sqr.profile_query(None)
     phase = np.array([[evs[s][i].elapsed_time(evs[s][i + 1]) for i in range(4)] for s in range(args.steps)])
     step_ms = phase.sum(1)
     total_ms = max_over_ranks(float(step_ms.sum()), world, dev)
@@ -286,21 +289,24 @@ def run_mine(args):
     # ---- roofline of the dominant kernel (SFU-bound: MUFU ops per pair)
     mean_phase = phase.mean(0)
     names = ["index", "fwd", "loss", "bwd"]
-    dom = int(np.argmax(mean_phase))
     props = torch.cuda.get_device_properties(dev)
     sm_count = props.multi_processor_count
     peak_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = sm_count * 16 * peak_mhz * 1e6 / 1e9  # G MUFU ops / s
     roof = None
-    if names[dom] in MUFU_PER_PAIR:
-        achieved = Q * MUFU_PER_PAIR[names[dom]] / (mean_phase[dom] / 1e3) / 1e9
-        kname = "k_" + ("forward" if names[dom] == "fwd" else "backward")
+    # the dominant kernel: the longer of the two pair-evaluating kernels, its mean
+    # launch time from the events recorded around it over the timed steps
+    kname = max(("k_forward", "k_backward"), key=lambda k: kernel_ms[k][1])
+    n_launch, k_total_ms, _ = kernel_ms[kname]
+    if n_launch > 0:
+        k_mean_ms = k_total_ms / n_launch
+        achieved = Q * MUFU_PER_PAIR["fwd" if kname == "k_forward" else "bwd"] / (k_mean_ms / 1e3) / 1e9
         tr = NCU_TRAFFIC.get(kname)
         traffic = None
         if tr and tr["src_sha"] == _sha(os.path.join(ROOT, "paper_2511_17361_gb300", "csrc", tr["src"])):
             traffic = tr["bytes_per_launch"]
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GMUFUop/s",
-                "frac": achieved / peak, "traffic": traffic,
+                "frac": achieved / peak, "traffic": traffic, "kernel_ms_per_launch": k_mean_ms,
                 "peak_source": f"{sm_count} SMs x 16 SFU ops/clk x {peak_mhz:.0f} MHz (max SM clock seen)"}
     # algorithmic HBM bytes of the backward: cotangents in, parameters + index lists read, gradients out
     peaks = {}
@@ -309,9 +315,21 @@ def run_mine(args):
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    bwd_bytes = R * (1 + C) * 4 + prims["means"].shape[0] * (13 + C) * 4 * 2 + in_grid * 8 + Q * 4
-    hbm = {"bwd_algorithmic_GBps": bwd_bytes / (mean_phase[3] / 1e3) / 1e9,
-           "frac_of_measured_peak": bwd_bytes / (mean_phase[3] / 1e3) / 1e9 / hbm_peak, "peak_gbs": hbm_peak}
+    # the HBM-bound kernel of the step: the backward's back-to-front sweep reads the
+    # saved T_j, alpha_j, s_j of every composited sample (and t_j, gD, gS) and
+    # writes (dL/dalpha_j, w_j); the composited counts come from the saved state
+    # (its last block, int32 per ray, layout as sq_saved_size documents)
+    RL = R * L
+    a256 = lambda b: (b + 255) // 256 * 256
+    n_off = 2 * a256(RL * 4) + a256(RL * C * 4)
+    composited = int(saved[n_off:n_off + R * 4].view(torch.int32).sum().item())
+    sweep_bytes = composited * ((2 + C) * 4 + 4 + 8) + R * (1 + C) * 4 + R * 4
+    n_sw, sw_ms, _ = kernel_ms["k_bwd_sweep"]
+    hbm = None
+    if n_sw > 0:
+        gbps = sweep_bytes / (sw_ms / n_sw / 1e3) / 1e9
+        hbm = {"kernel": "k_bwd_sweep", "algorithmic_bytes": sweep_bytes, "achieved_GBps": gbps,
+               "frac": gbps / hbm_peak, "peak_gbs": hbm_peak, "composited_samples": composited}
 
     line = {"metric": "ray-samples/s (forward + backward), six-camera frame", "value": value,
             "unit": "ray-samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -322,7 +340,8 @@ def run_mine(args):
                 "in_grid_samples": in_grid, "l2": "flushed (256 MB write) between timed steps",
                 "parallelism": f"replicas x{world} (one frame per GPU)"},
             "phases_ms": {n: float(v) for n, v in zip(names, mean_phase)},
-            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "gpu_launches": launches_timed + dropped,
+            "kernel_ms_per_launch": {k: (v[1] / v[0] if v[0] else None) for k, v in kernel_ms.items()},
             "e2e": {"value": e2e_value, "unit": "ray-samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roof, "hbm": hbm, "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:

@@ -291,6 +291,20 @@ const char* sq_status_string(sq_status_t status);
 /* Human-readable text of the last SQ_ERR_* raised on the calling host thread. */
 const char* sq_last_error(void);
 
+/* Per-kernel timing, no counterpart in the paper.  While enabled, every kernel
+ * the library launches is bracketed by two CUDA events recorded on its stream
+ * (up to SQ_PROFILE_MAX_LAUNCHES launches; later ones are only counted as
+ * dropped).  Enabling clears the records.  Meant for benchmarks on one device;
+ * do not enable it while a stream is being captured into a graph. */
+#define SQ_PROFILE_MAX_LAUNCHES 8192
+sq_status_t sq_profile_enable(int on);
+
+/* Host-synchronous: waits for the recorded events and returns the number of
+ * recorded launches of kernel `name` (for example "k_backward"; NULL = every
+ * kernel) and their summed duration in milliseconds; *dropped (nullable) gets
+ * the number of launches that found the record pool full. */
+sq_status_t sq_profile_query(const char* name, long long* launches, double* total_ms, long long* dropped);
+
 #ifdef __cplusplus
 }
 #endif

@@ -305,9 +305,8 @@ sq_status_t sq_loss_ce_mse(const float* depth, const float* sem, const float* ta
     const float ws = lambda_s / (float)n_rays, wd = lambda_d / (float)n_rays;
     long long want = (n_rays + LOSS_THREADS - 1) / LOSS_THREADS;
     int blocks = (int)(want < 152LL * 16 ? want : 152LL * 16);
-    k_loss<<<blocks, LOSS_THREADS, 0, st>>>(depth, sem, target_depth, target_label, n_rays, n_classes, ws, wd, loss,
-                                            grad_depth, grad_sem);
-    SQ_CHECK_LAUNCH("k_loss");
+    SQ_LAUNCH("k_loss", st, k_loss<<<blocks, LOSS_THREADS, 0, st>>>(depth, sem, target_depth, target_label, n_rays, n_classes, ws, wd, loss,
+                                            grad_depth, grad_sem));
     return SQ_OK;
 }
 

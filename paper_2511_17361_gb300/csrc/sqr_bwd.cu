@@ -639,7 +639,9 @@ sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream
         if (blocks < 1) blocks = 1;
         Batch arg = B;
         void* args[] = {&arg};
+        prof_begin("k_bwd_sweep", st);
         e = cudaLaunchKernel(sw, dim3((unsigned)blocks), dim3(256), args, 0, st);
+        prof_end(st);
         if (e != cudaSuccess) return cuda_status(e, "k_bwd_sweep");
     }
     // per warp: fixed part plus a sample table of RB * lmax entries
@@ -663,7 +665,9 @@ sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream
     if (blocks < 1) blocks = 1;
     Batch arg = B;
     void* args[] = {&arg};
+    prof_begin("k_backward", st);
     e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(warps * 32), args, smem, st);
+    prof_end(st);
     if (e != cudaSuccess) return cuda_status(e, "k_backward");
     return SQ_OK;
 }
@@ -671,15 +675,13 @@ sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream
 sq_status_t launch_grad_out(const SceneDesc& S, float* gm, float* gq, float* gs, float* ge, float* go, float* gl,
                             cudaStream_t st) {
     if (S.n == 0) return SQ_OK;
-    k_grad_out<<<(S.n + 127) / 128, 128, 0, st>>>(S.gacc, S.aux, S.n, S.C, gm, gq, gs, ge, go, gl);
-    SQ_CHECK_LAUNCH("k_grad_out");
+    SQ_LAUNCH("k_grad_out", st, k_grad_out<<<(S.n + 127) / 128, 128, 0, st>>>(S.gacc, S.aux, S.n, S.C, gm, gq, gs, ge, go, gl));
     return SQ_OK;
 }
 
 sq_status_t launch_pack_boxes(const int* ranges, int n, int4* boxes, cudaStream_t st) {
     if (n == 0) return SQ_OK;
-    k_pack_boxes<<<(n + 127) / 128, 128, 0, st>>>(ranges, n, boxes);
-    SQ_CHECK_LAUNCH("k_pack_boxes");
+    SQ_LAUNCH("k_pack_boxes", st, k_pack_boxes<<<(n + 127) / 128, 128, 0, st>>>(ranges, n, boxes));
     return SQ_OK;
 }
 

@@ -23,6 +23,20 @@ sq_status_t cuda_status(cudaError_t e, const char* where);
         if (_e != cudaSuccess) return cuda_status(_e, where);  \
     } while (0)
 
+// Optional per-kernel timing (sq_profile_enable): events on the launching stream
+// around every launch of the library.
+void prof_begin(const char* name, cudaStream_t st);
+void prof_end(cudaStream_t st);
+
+// A <<<...>>> launch of kernel `name`, timed when profiling is on, then checked.
+#define SQ_LAUNCH(name, st, ...)       \
+    do {                               \
+        ::sqr::prof_begin(name, st);   \
+        __VA_ARGS__;                   \
+        ::sqr::prof_end(st);           \
+        SQ_CHECK_LAUNCH(name);         \
+    } while (0)
+
 // ---------------------------------------------------------------- grid
 struct GridC {
     int n[3];

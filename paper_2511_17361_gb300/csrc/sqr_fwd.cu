@@ -224,8 +224,7 @@ sq_status_t launch_cp_gs(const Batch& B, int warps, cudaStream_t st) {
     long long blocks = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    k_forward<CP, GS><<<(int)blocks, warps * 32, 0, st>>>(B);
-    SQ_CHECK_LAUNCH("k_forward");
+    SQ_LAUNCH("k_forward", st, k_forward<CP, GS><<<(int)blocks, warps * 32, 0, st>>>(B));
     return SQ_OK;
 }
 

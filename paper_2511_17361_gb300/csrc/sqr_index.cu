@@ -416,32 +416,23 @@ sq_status_t build_index_impl(const sq_prims_t* prims, const sq_grid_t* grid, con
     for (int i = 0; i < 3; ++i) { a.glo[i] = grid->lo[i]; a.gvs[i] = grid->vs[i]; }
 
     if (prims->n > 0) {
-        k_ranges<<<(prims->n + 127) / 128, 128, 0, st>>>(a, idx->ranges, diff);
-        SQ_CHECK_LAUNCH("k_ranges");
+        SQ_LAUNCH("k_ranges", st, k_ranges<<<(prims->n + 127) / 128, 128, 0, st>>>(a, idx->ranges, diff));
     }
     const int nxp = nx + 1, nyp = ny + 1, nzp = nz + 1;
-    k_prefix_z<<<(nxp * nyp + 255) / 256, 256, 0, st>>>(diff, nxp, nyp, nzp);
-    SQ_CHECK_LAUNCH("k_prefix_z");
-    k_prefix_y<<<(nxp * nzp + 255) / 256, 256, 0, st>>>(diff, nxp, nyp, nzp);
-    SQ_CHECK_LAUNCH("k_prefix_y");
-    k_prefix_x<<<(ny * nz + 255) / 256, 256, 0, st>>>(diff, idx->v_n, nx, ny, nz);
-    SQ_CHECK_LAUNCH("k_prefix_x");
-    k_scan_reduce<<<n_tiles, SCAN_THREADS, 0, st>>>(idx->v_n, nvox, tiles);
-    SQ_CHECK_LAUNCH("k_scan_reduce");
-    k_scan_tiles<<<1, SCAN_THREADS, 0, st>>>(tiles, n_tiles, idx->capacity, idx->p_total, idx->status);
-    SQ_CHECK_LAUNCH("k_scan_tiles");
-    k_scan_apply<<<n_tiles, SCAN_THREADS, 0, st>>>(idx->v_n, nvox, tiles, idx->v_f);
-    SQ_CHECK_LAUNCH("k_scan_apply");
+    SQ_LAUNCH("k_prefix_z", st, k_prefix_z<<<(nxp * nyp + 255) / 256, 256, 0, st>>>(diff, nxp, nyp, nzp));
+    SQ_LAUNCH("k_prefix_y", st, k_prefix_y<<<(nxp * nzp + 255) / 256, 256, 0, st>>>(diff, nxp, nyp, nzp));
+    SQ_LAUNCH("k_prefix_x", st, k_prefix_x<<<(ny * nz + 255) / 256, 256, 0, st>>>(diff, idx->v_n, nx, ny, nz));
+    SQ_LAUNCH("k_scan_reduce", st, k_scan_reduce<<<n_tiles, SCAN_THREADS, 0, st>>>(idx->v_n, nvox, tiles));
+    SQ_LAUNCH("k_scan_tiles", st, k_scan_tiles<<<1, SCAN_THREADS, 0, st>>>(tiles, n_tiles, idx->capacity, idx->p_total, idx->status));
+    SQ_LAUNCH("k_scan_apply", st, k_scan_apply<<<n_tiles, SCAN_THREADS, 0, st>>>(idx->v_n, nvox, tiles, idx->v_f));
     if (prims->n > 0) {
         int blocks = prims->n < 65535 ? prims->n : 65535;
-        k_scatter<<<blocks, 256, 0, st>>>(idx->ranges, prims->n, ny, nz, idx->v_f, cursor, idx->v_sq, idx->capacity,
-                                          idx->status);
-        SQ_CHECK_LAUNCH("k_scatter");
+        SQ_LAUNCH("k_scatter", st, k_scatter<<<blocks, 256, 0, st>>>(idx->ranges, prims->n, ny, nz, idx->v_f, cursor, idx->v_sq, idx->capacity,
+                                          idx->status));
         long long want = (nvox + SORT_WARPS - 1) / SORT_WARPS;
         int sblocks = (int)(want < 152 * 64 ? want : 152 * 64);
-        k_sort<<<sblocks, SORT_WARPS * 32, 0, st>>>(idx->v_n, idx->v_f, idx->v_sq, nvox, idx->status, idx->ranges,
-                                                    idx->v_flags, ny, nz);
-        SQ_CHECK_LAUNCH("k_sort");
+        SQ_LAUNCH("k_sort", st, k_sort<<<sblocks, SORT_WARPS * 32, 0, st>>>(idx->v_n, idx->v_f, idx->v_sq, nvox, idx->status, idx->ranges,
+                                                    idx->v_flags, ny, nz));
     }
     return SQ_OK;
 }

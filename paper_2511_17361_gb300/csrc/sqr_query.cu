@@ -104,8 +104,7 @@ static sq_status_t launch_query_cp(const QueryArgs& a, cudaStream_t st) {
     long long want = (a.nvox + Q_THREADS - 1) / Q_THREADS;
     int blocks = (int)(want < 152LL * 64 ? want : 152LL * 64);
     if (blocks < 1) blocks = 1;
-    k_query<CP><<<blocks, Q_THREADS, 0, st>>>(a);
-    SQ_CHECK_LAUNCH("k_query");
+    SQ_LAUNCH("k_query", st, k_query<CP><<<blocks, Q_THREADS, 0, st>>>(a));
     return SQ_OK;
 }
 

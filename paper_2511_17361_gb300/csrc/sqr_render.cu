@@ -164,8 +164,7 @@ int device_sm_count() {
 
 sq_status_t launch_pack(const sq_prims_t* prims, float4* rec, float4* aux, float* lpad, int cp, cudaStream_t st) {
     if (prims->n == 0) return SQ_OK;
-    k_pack<<<(prims->n + 127) / 128, 128, 0, st>>>(*prims, rec, aux, lpad, cp);
-    SQ_CHECK_LAUNCH("k_pack");
+    SQ_LAUNCH("k_pack", st, k_pack<<<(prims->n + 127) / 128, 128, 0, st>>>(*prims, rec, aux, lpad, cp));
     return SQ_OK;
 }
 
@@ -312,8 +311,7 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
     long long* off = (long long*)(base + HDR_OFF);
     long long* boff = (long long*)(base + HDR_BOFF);
     int* ctr = (int*)(base + HDR_CTR);
-    k_write_desc<<<1, 32, 0, st>>>(P, d, off, boff);
-    SQ_CHECK_LAUNCH("k_write_desc");
+    SQ_LAUNCH("k_write_desc", st, k_write_desc<<<1, 32, 0, st>>>(P, d, off, boff));
     cudaError_t e = cudaMemsetAsync(ctr, 0, 256, st);
     if (e != cudaSuccess) return cuda_status(e, "memset counter");
     Batch B{d, off, boff, n, total, ctr, lmax};
@@ -471,8 +469,7 @@ sq_status_t count_pairs_impl(const sq_index_t* idx, const sq_grid_t* grid, const
     if (S.R == 0) return SQ_OK;
     const long long want = (S.R * S.L + 255) / 256;
     const int blocks = (int)(want < 152LL * 16 ? want : 152LL * 16);
-    k_count_pairs<<<blocks, 256, 0, st>>>(S, reinterpret_cast<unsigned long long*>(out));
-    SQ_CHECK_LAUNCH("k_count_pairs");
+    SQ_LAUNCH("k_count_pairs", st, k_count_pairs<<<blocks, 256, 0, st>>>(S, reinterpret_cast<unsigned long long*>(out)));
     return SQ_OK;
 }
 

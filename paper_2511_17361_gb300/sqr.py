@@ -98,6 +98,10 @@ def _load():
     lib.sq_status_string.restype = ctypes.c_char_p
     lib.sq_status_string.argtypes = [ctypes.c_int]
     lib.sq_last_error.restype = ctypes.c_char_p
+    lib.sq_profile_enable.restype = ctypes.c_int
+    lib.sq_profile_enable.argtypes = [ctypes.c_int]
+    lib.sq_profile_query.restype = ctypes.c_int
+    lib.sq_profile_query.argtypes = [ctypes.c_char_p, P(ctypes.c_longlong), P(ctypes.c_double), P(ctypes.c_longlong)]
     return lib
 
 
@@ -348,6 +352,20 @@ def count_pairs(index: Index, grid: dict, rays: Rays):
            "sq_count_pairs")
     q, s = out.tolist()
     return int(q), int(s)
+
+
+def profile_enable(on: bool = True):
+    """Start (clearing earlier records) or stop timing every kernel launch of the library."""
+    _check(lib.sq_profile_enable(1 if on else 0), "sq_profile_enable")
+
+
+def profile_query(name: str | None = None):
+    """(launches, total ms, dropped) of the recorded launches of kernel ``name``
+    (None = every kernel); waits for the recorded events."""
+    n, ms, dropped = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_longlong()
+    _check(lib.sq_profile_query(None if name is None else name.encode(), ctypes.byref(n), ctypes.byref(ms),
+                                ctypes.byref(dropped)), "sq_profile_query")
+    return int(n.value), float(ms.value), int(dropped.value)
 
 
 class SQRender(torch.autograd.Function):
