@@ -31,6 +31,7 @@ constexpr int TCAP = 256;  // runs listed per pass
 constexpr int RTH = 4;     // idle lanes that trigger a refill while others still walk
 constexpr int LU = 8;      // 32-entry batches whose loads the run listing issues together
 constexpr int RU = 4;      // listed runs per lane whose loads the per-run pass issues together
+constexpr int NS = 2;      // samples of a run a lane evaluates per walker step
 constexpr int QCAP = 32;   // pending flushes per warp
 constexpr int QW = 16;     // words per flush: 11 partials, sigma, W, primitive, ray slot, pad
 static_assert(QCAP >= 32, "one walker step can end a run in every lane");
@@ -523,19 +524,27 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
                 if (!__any_sync(0xffffffffu, act)) break;
                 bool ends = false;
                 if (act) {
-                    // two samples of the run per step (two independent chains)
+                    // NS samples of the run per step (independent chains)
                     const int at = rq * lmax + jj;
-                    const bool two = jj + 1 < jend;
-                    const float4 xg0 = tb.xg[at], xg1 = tb.xg[two ? at + 1 : at];
-                    const float w0 = tb.w[at], w1 = two ? tb.w[at + 1] : 0.f;
-                    const float G1 = two ? xg1.w : 0.f;
-                    const float x0[3] = {xg0.x, xg0.y, xg0.z}, x1[3] = {xg1.x, xg1.y, xg1.z};
-                    float pr0[11], pr1[11];
-                    const float po0 = occupancy_partials(P, x0, pr0);
-                    const float po1 = occupancy_partials(P, x1, pr1);
-                    if (po0 != 0.f) accumulate(acc, po0, pr0, xg0.w, w0, P.f.sigma, cd);
-                    if (two && po1 != 0.f) accumulate(acc, po1, pr1, G1, w1, P.f.sigma, cd);
-                    jj += two ? 2 : 1;
+                    float po[NS], pr[NS][11];
+                    float4 xg[NS];
+                    float w[NS];
+#pragma unroll
+                    for (int i = 0; i < NS; ++i) {
+                        const bool in = jj + i < jend;
+                        xg[i] = tb.xg[in ? at + i : at];
+                        w[i] = in ? tb.w[at + i] : 0.f;
+                        if (!in) xg[i].w = 0.f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < NS; ++i) {
+                        const float x[3] = {xg[i].x, xg[i].y, xg[i].z};
+                        po[i] = occupancy_partials(P, x, pr[i]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < NS; ++i)
+                        if (jj + i < jend && po[i] != 0.f) accumulate(acc, po[i], pr[i], xg[i].w, w[i], P.f.sigma, cd);
+                    jj = min(jj + NS, jend);
                     ends = jj >= jend;
                 }
                 const unsigned dm = __ballot_sync(0xffffffffu, ends);
