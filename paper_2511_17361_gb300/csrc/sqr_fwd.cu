@@ -117,13 +117,19 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
         int head = n > 0 ? __ldg(v_sq + f) : INT_MAX;
         int head2 = n > 1 ? __ldg(v_sq + f + 1) : INT_MAX;
         int head3 = n > 2 ? __ldg(v_sq + f + 2) : INT_MAX;  // list look-ahead of two
-        for (;;) {
-            int kmin = head;
+        int kmin = head;
 #pragma unroll
-            for (int o2 = GS / 2; o2 > 0; o2 >>= 1) kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o2, GS));
-            if (!__any_sync(0xffffffffu, kmin != INT_MAX)) break;
+        for (int o2 = GS / 2; o2 > 0; o2 >>= 1) kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o2, GS));
+        Prim p;  // the group's record, loaded one step ahead
+        if (kmin != INT_MAX) p = load_prim(rec, kmin);
+        while (__any_sync(0xffffffffu, kmin != INT_MAX)) {
+            // the group's next id is known before this step's work: its record loads overlap the math
+            int knext = head == kmin ? head2 : head;
+#pragma unroll
+            for (int o2 = GS / 2; o2 > 0; o2 >>= 1) knext = min(knext, __shfl_xor_sync(0xffffffffu, knext, o2, GS));
+            Prim pn;
+            if (knext != INT_MAX) pn = load_prim(rec, knext);
             if (kmin != INT_MAX) {
-                const Prim p = load_prim(rec, kmin);
                 const float4* cr = lp4 + (size_t)kmin * (CP / 4);
                 float4 cv[CP / 4];
 #pragma unroll
@@ -144,6 +150,8 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
                     head3 = e + 2 < n ? __ldg(v_sq + f + e + 2) : INT_MAX;
                 }
             }
+            kmin = knext;
+            p = pn;
         }
         const float alpha = valid ? fminf(asum, S.alpha_max) : 0.f;
         float Tb;
