@@ -319,11 +319,11 @@ def run_mine(args):
     # saved T_j, alpha_j, s_j of every composited sample (and t_j, gD, gS) and
     # writes (dL/dalpha_j, w_j); the composited counts come from the saved state
     # (its last block, int32 per ray, layout as sq_saved_size documents)
-    RL = R * L
+    RL, CP = R * L, (C + 3) // 4 * 4
     a256 = lambda b: (b + 255) // 256 * 256
-    n_off = 2 * a256(RL * 4) + a256(RL * C * 4)
+    n_off = a256(RL * 8) + a256(RL * CP * 4)
     composited = int(saved[n_off:n_off + R * 4].view(torch.int32).sum().item())
-    sweep_bytes = composited * ((2 + C) * 4 + 4 + 8) + R * (1 + C) * 4 + R * 4
+    sweep_bytes = composited * ((2 + CP) * 4 + 4 + 8) + R * (1 + C) * 4 + R * 4
     n_sw, sw_ms, _ = kernel_ms["k_bwd_sweep"]
     hbm = None
     if n_sw > 0:

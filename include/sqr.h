@@ -149,11 +149,12 @@ sq_status_t sq_build_index(const sq_prims_t* prims, const sq_grid_t* grid, const
                            sq_index_t* index, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Bytes of the forward state that sq_render_fwd saves for sq_render_bwd, per
- * composited sample of every ray: T_j [R, L] FP32 (transmittance before the
- * sample), alpha_j [R, L] FP32 (negated where the alpha_max clamp was active),
- * s_j [R, n_classes, L] FP32 (Eq. 4, sample index fastest); then the per-ray
- * count of composited samples [R] int32.  Each block 256-byte aligned:
- * about R * L * (n_classes + 2) * 4 bytes.  0 on invalid rays or n_classes. */
+ * composited sample of every ray: (T_j, alpha_j) [R, L] FP32 pairs (the
+ * transmittance before the sample; alpha_j negated where the alpha_max clamp was
+ * active), s_j [R, L, CP] FP32 (Eq. 4; CP = n_classes rounded up to a multiple
+ * of 4, the padding zero); then the per-ray count of composited samples [R]
+ * int32.  Each block 256-byte aligned: about R * L * (CP + 2) * 4 bytes.
+ * 0 on invalid rays or n_classes. */
 size_t sq_saved_size(const sq_rays_t* rays, int n_classes);
 
 /* Sec. 3.3.2 forward pass (Eq. 2, 4-6).  Per ray r:

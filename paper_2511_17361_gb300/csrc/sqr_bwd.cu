@@ -250,26 +250,31 @@ __global__ void __launch_bounds__(256) k_bwd_sweep(Batch B) {
         const int Le = min(max(__ldg(S.save_n + r), 0), L);
         const float gD = __ldg(S.grad_depth + r);
         const float gsl = lane < C ? __ldg(S.grad_sem + r * C + lane) : 0.f;
-        const float* __restrict__ sS = S.save_S + r * C * L;
         float carry = 0.f;  // U at the last sample of the chunk being processed
         for (int jc = ((Le - 1) >> 5) << 5; Le > 0 && jc >= 0; jc -= 32) {
             const int j = jc + lane;
             const bool valid = j < Le;
             float sa = 0.f, T = 0.f, tj = 0.f;
-            float sc[CP];
+            float4 sc[CP / 4];
 #pragma unroll
-            for (int c = 0; c < CP; ++c) sc[c] = 0.f;
+            for (int q = 0; q < CP / 4; ++q) sc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (valid) {
-                sa = __ldg(S.save_A + r * L + j);
-                T = __ldg(S.save_T + r * L + j);
+                const float2 ta = __ldg(S.save_TA + r * L + j);
+                T = ta.x;
+                sa = ta.y;
                 tj = __ldg(S.t + j);
+                const float4* sv = S.save_S + (r * L + j) * (CP / 4);
 #pragma unroll
-                for (int c = 0; c < CP; ++c)
-                    if (c < C) sc[c] = __ldg(sS + (long long)c * L + j);
+                for (int q = 0; q < CP / 4; ++q) sc[q] = __ldg(sv + q);
             }
-            float dot = 0.f;
+            float dot = 0.f;  // <gS, s_j>; the padded classes of s_j are zero
 #pragma unroll
-            for (int c = 0; c < CP; ++c) dot = fmaf(__shfl_sync(0xffffffffu, gsl, c), sc[c], dot);
+            for (int q = 0; q < CP / 4; ++q) {
+                dot = fmaf(__shfl_sync(0xffffffffu, gsl, 4 * q + 0), sc[q].x, dot);
+                dot = fmaf(__shfl_sync(0xffffffffu, gsl, 4 * q + 1), sc[q].y, dot);
+                dot = fmaf(__shfl_sync(0xffffffffu, gsl, 4 * q + 2), sc[q].z, dot);
+                dot = fmaf(__shfl_sync(0xffffffffu, gsl, 4 * q + 3), sc[q].w, dot);
+            }
             const float v = valid ? fmaf(gD, tj, dot) : 0.f;
             const float al = fabsf(sa);
             // f_j(U) = al v + (1 - al) U; after the scan (a, b) is f_j o ... o f_{jc+31}

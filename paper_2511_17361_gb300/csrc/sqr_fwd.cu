@@ -159,14 +159,13 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
         bool stop;
         const float w = group_composite<GS>(alpha, s, gbase, S.kappa, T, Tb, valid, used, stop);
         if (valid) {
-            if (s < used && S.save_T) {
+            if (s < used && S.save_TA) {
                 const long long sj = r * L + j;
-                S.save_T[sj] = Tb;
-                S.save_A[sj] = asum > S.alpha_max ? -alpha : alpha;
-                float* sv = S.save_S + r * S.C * L + j;
+                S.save_TA[sj] = make_float2(Tb, asum > S.alpha_max ? -alpha : alpha);
+                float4* sv = S.save_S + sj * (CP / 4);
 #pragma unroll
-                for (int c = 0; c < CP; ++c)
-                    if (c < S.C) sv[(long long)c * L] = sacc[c];
+                for (int q = 0; q < CP / 4; ++q)
+                    sv[q] = make_float4(sacc[4 * q], sacc[4 * q + 1], sacc[4 * q + 2], sacc[4 * q + 3]);
             }
             Dp = fmaf(w, tj, Dp);
 #pragma unroll

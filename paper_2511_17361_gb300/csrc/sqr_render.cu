@@ -132,22 +132,21 @@ size_t batch_ws_size(const sq_scene_t* sc, int n, bool bwd) {
     return at;
 }
 
-// Saved forward state: T [R, L], signed alpha [R, L], s [R, C, L], then n [R].
+// Saved forward state: (T, signed alpha) [R, L] float2, s [R, L, CP] float
+// (CP = C rounded up to 4, zero-padded), then n [R] int32.
 size_t saved_bytes_of(const sq_rays_t* r, int C) {
     const size_t R = (size_t)r->n_cam * r->H * r->W, RL = R * (size_t)r->L;
-    return 2 * align_up(RL * sizeof(float), 256) + align_up(RL * (size_t)C * sizeof(float), 256) +
+    return align_up(RL * sizeof(float2), 256) + align_up(RL * (size_t)cpad(C) * sizeof(float), 256) +
            align_up(R * sizeof(int), 256);
 }
 
 void saved_ptrs(const sq_rays_t* r, int C, void* saved, SceneDesc& D) {
     const size_t R = (size_t)r->n_cam * r->H * r->W, RL = R * (size_t)r->L;
     char* p = (char*)saved;
-    D.save_T = (float*)p;
-    p += align_up(RL * sizeof(float), 256);
-    D.save_A = (float*)p;
-    p += align_up(RL * sizeof(float), 256);
-    D.save_S = (float*)p;
-    p += align_up(RL * (size_t)C * sizeof(float), 256);
+    D.save_TA = (float2*)p;
+    p += align_up(RL * sizeof(float2), 256);
+    D.save_S = (float4*)p;
+    p += align_up(RL * (size_t)cpad(C) * sizeof(float), 256);
     D.save_n = (int*)p;
 }
 

@@ -35,9 +35,8 @@ struct SceneDesc {
     float* depth;        // forward outputs
     float* sem;
     float* t_final;
-    float* save_T;       // [R, L] saved transmittance before each sample (nullable in inference)
-    float* save_A;       // [R, L] saved alpha_j, negated where the clamp was active
-    float* save_S;       // [R, C, L] saved semantic vector s_j of each sample (sample index fastest)
+    float2* save_TA;     // [R, L] saved (T_j before the sample, alpha_j negated where clamped); nullable
+    float4* save_S;      // [R, L, CP/4] saved semantic vector s_j of each sample, zero-padded to CP
     int* save_n;         // [R] samples composited
     float2* gw;          // [R, L] backward: (dL/dalpha_j, w_j) from the sweep
     const float* grad_depth;  // backward inputs
