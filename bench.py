@@ -35,8 +35,9 @@ MUFU_PER_PAIR = {"fwd": 9, "bwd": 13}  # SFU ops per (sample, primitive) pair in
 # DRAM traffic per launch from the committed ncu summaries, valid only while the
 # kernel source is unchanged (sha256 of the file holding it).
 NCU_TRAFFIC = {
-    "k_backward": {"src": "sqr_bwd.cu", "src_sha": "53b0e8338b23d8b7", "bytes_per_launch": 235353088},
-    "k_forward": {"src": "sqr_fwd.cu", "src_sha": "3473c5f9e9e13720", "bytes_per_launch": 160511232},
+    "k_backward": {"src": "sqr_bwd.cu", "src_sha": "c9aa43d605221735", "bytes_per_launch": 309531136},
+    "k_forward": {"src": "sqr_fwd.cu", "src_sha": "bbf4eba00091e5d5", "bytes_per_launch": 1716526336},
+    "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "c9aa43d605221735", "bytes_per_launch": 1938757120},
 }
 
 
@@ -328,8 +329,12 @@ def run_mine(args):
     hbm = None
     if n_sw > 0:
         gbps = sweep_bytes / (sw_ms / n_sw / 1e3) / 1e9
-        hbm = {"kernel": "k_bwd_sweep", "algorithmic_bytes": sweep_bytes, "achieved_GBps": gbps,
-               "frac": gbps / hbm_peak, "peak_gbs": hbm_peak, "composited_samples": composited}
+        trs = NCU_TRAFFIC["k_bwd_sweep"]
+        sw_traffic = trs["bytes_per_launch"] if trs["src_sha"] == _sha(
+            os.path.join(ROOT, "paper_2511_17361_gb300", "csrc", trs["src"])) else None
+        hbm = {"kernel": "k_bwd_sweep", "bound": "hbm", "algorithmic_bytes": sweep_bytes, "achieved_GBps": gbps,
+               "frac": gbps / hbm_peak, "peak_gbs": hbm_peak, "traffic": sw_traffic,
+               "composited_samples": composited}
 
     line = {"metric": "ray-samples/s (forward + backward), six-camera frame", "value": value,
             "unit": "ray-samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
