@@ -362,6 +362,68 @@ def run_mine(args):
 
 
 # ----------------------------------------------------------------------- batched workload
+def run_query(args):
+    """Supp. A.4 grid query of the 8192-superquadric scene at all 640,000 voxel
+    centres of the 200x200x16 grid (tau = 0.05): density, semantics and labels."""
+    import torch
+    from paper_2511_17361_gb300 import _build
+    _build.build()
+    from paper_2511_17361_gb300 import sqr
+    dev = torch.device("cuda", 0)
+    cfg = synth.make_config(4, seed=4)
+    prims = sqr.to_device(cfg["prims"], dev)
+    grid = {"n": cfg["grid"]["n"], "lo": [float(v) for v in cfg["grid"]["lo"]],
+            "vs": [float(v) for v in cfg["grid"]["vs"]]}
+    ix = sqr.build_index(prims, grid)
+    P = ix.P()
+    nvox = ix.v_n.numel()
+    C = cfg["prims"]["logits"].shape[1]
+    out = (torch.empty(nvox, device=dev), torch.empty((nvox, C), device=dev),
+           torch.empty(nvox, dtype=torch.uint8, device=dev))
+    for _ in range(max(3, args.warmup)):
+        sqr.query_grid(prims, ix, grid, 0.05, out=out)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    torch.cuda.synchronize()
+    sampler.start()
+    sqr.profile_enable(True)
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        ev[s][0].record()
+        sqr.query_grid(prims, ix, grid, 0.05, out=out)
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    sqr.profile_enable(False)
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    n_q, q_ms, _ = sqr.profile_query("k_query")
+    launches, _, dropped = sqr.profile_query(None)
+    k_ms = q_ms / max(n_q, 1)
+    props = torch.cuda.get_device_properties(dev)
+    peak_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * 16 * peak_mhz * 1e6 / 1e9
+    achieved = P * 9 / (k_ms / 1e3) / 1e9  # every voxel centre evaluates its whole list: P pairs, 9 MUFU each
+    out_bytes = nvox * (1 + C) * 4 + nvox
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
+    except Exception:
+        hbm_peak = 6800.0
+    line = {"metric": "voxel queries/s (density + semantics + label), 200x200x16 grid", "value": nvox / (ms / 1e3),
+            "unit": "voxels/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg["name"], "superquadrics": int(prims["means"].shape[0]), "voxels": nvox,
+                       "index_entries_P": P, "tau": 0.05, "l2": "flushed (256 MB write) between timed steps"},
+            "gpu_launches": launches + dropped, "kernel_ms_per_launch": {"k_query": k_ms},
+            "roofline": {"bound": "alu", "kernel": "k_query", "achieved": achieved, "peak": peak, "unit": "GMUFUop/s",
+                         "frac": achieved / peak, "traffic": None},
+            "hbm": {"kernel": "k_query", "bound": "hbm", "algorithmic_bytes": out_bytes + 4 * P + 8 * nvox,
+                    "achieved_GBps": (out_bytes + 4 * P + 8 * nvox) / (k_ms / 1e3) / 1e9,
+                    "frac": (out_bytes + 4 * P + 8 * nvox) / (k_ms / 1e3) / 1e9 / hbm_peak, "peak_gbs": hbm_peak},
+            "clocks": clocks}
+    print(json.dumps(line))
+
+
 def run_batch(args):
     """Twelve uneven scenes: per-scene launches vs one batched persistent launch per
     pass (autotuned), the whole step captured in a CUDA graph."""
@@ -457,8 +519,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["frame", "batch"], default="frame",
-                    help="frame: one six-camera frame (default); batch: 12 uneven scenes, batched vs per scene")
+    ap.add_argument("--workload", choices=["frame", "batch", "query"], default="frame",
+                    help="frame: one six-camera frame (default); batch: 12 uneven scenes, batched vs per scene; "
+                         "query: grid query of an 8192-superquadric scene at all 640,000 voxel centres")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
@@ -466,6 +529,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "query":
+        return run_query(args)
     return run_mine(args)
 
 

@@ -237,8 +237,10 @@ typedef struct {
 } sq_scene_t;
 
 /* Launch configuration: lanes (= samples marched together) per ray in the
- * forward (4, 8 or 16), warps per CTA in the forward and backward (1..8).  The
- * defaults are {4, 8, 8}. */
+ * forward (4, 8 or 16), warps per CTA in the forward (1..8) and backward (1..8,
+ * or 0: the count that keeps the most warps resident for the batch's largest L,
+ * whose sample tables set the backward's shared memory).  The defaults are
+ * {4, 8, 0}. */
 typedef struct {
     int fwd_lanes_per_ray;
     int fwd_warps_per_cta;
@@ -257,8 +259,9 @@ sq_status_t sq_render_batched(int op, const sq_scene_t* scenes, int n_scenes, co
 /* Autotuner: times every forward configuration (lanes per ray x warps per CTA)
  * and, when every scene has saved state and cotangents, every backward one on
  * these scenes (reps timed launches each, CUDA events on the stream) and writes
- * the fastest to *best.  fwd_ms[4] / bwd_ms[2] (nullable) receive the mean
- * times of the candidates in the order {4,4},{4,8},{8,4},{8,8} and {4},{8}.
+ * the fastest to *best.  fwd_ms[4] / bwd_ms[3] (nullable) receive the mean
+ * times of the candidates in the order {4,4},{4,8},{8,4},{8,8} and {0},{4},{8}
+ * (0 = automatic warps per CTA).
  * Host-synchronous and overwrites the scenes' outputs; call it outside any
  * stream capture. */
 sq_status_t sq_autotune(const sq_scene_t* scenes, int n_scenes, void* workspace, size_t workspace_bytes, void* stream,

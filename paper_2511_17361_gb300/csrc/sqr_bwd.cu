@@ -611,10 +611,42 @@ __global__ void k_grad_out(const float* __restrict__ gacc, const float4* __restr
 
 int bwd_rays_per_bundle() { return RB; }
 
+sq_status_t launch_sweep(const Batch& B, int cp, cudaStream_t st) {
+    if (B.total == 0) return SQ_OK;
+    const void* sw = nullptr;
+    switch (cp) {
+        case 4: sw = (const void*)k_bwd_sweep<4>; break;
+        case 8: sw = (const void*)k_bwd_sweep<8>; break;
+        case 12: sw = (const void*)k_bwd_sweep<12>; break;
+        case 16: sw = (const void*)k_bwd_sweep<16>; break;
+        case 20: sw = (const void*)k_bwd_sweep<20>; break;
+        case 24: sw = (const void*)k_bwd_sweep<24>; break;
+        case 28: sw = (const void*)k_bwd_sweep<28>; break;
+        case 32: sw = (const void*)k_bwd_sweep<32>; break;
+        default:
+            set_last_error("n_classes padding %d not supported", cp);
+            return SQ_ERR_INVALID_ARG;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sw, 256, 0);
+    if (e != cudaSuccess) return cuda_status(e, "k_bwd_sweep occupancy");
+    long long blocks = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    const long long need = (B.total + 7) / 8;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    Batch arg = B;
+    void* args[] = {&arg};
+    prof_begin("k_bwd_sweep", st);
+    e = cudaLaunchKernel(sw, dim3((unsigned)blocks), dim3(256), args, 0, st);
+    prof_end(st);
+    if (e != cudaSuccess) return cuda_status(e, "k_bwd_sweep");
+    return SQ_OK;
+}
+
 sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st) {
     if (B.total == 0) return SQ_OK;
-    int warps = tn.bwd_warps;
-    if (warps < 1 || warps > MAX_WARPS) {
+    int warps = tn.bwd_warps;  // 0: the count that keeps the most warps resident
+    if (warps < 0 || warps > MAX_WARPS) {
         set_last_error("backward tuning (warps %d) not supported", warps);
         return SQ_ERR_INVALID_ARG;
     }
@@ -632,47 +664,39 @@ sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream
             set_last_error("n_classes padding %d not supported", cp);
             return SQ_ERR_INVALID_ARG;
     }
-    const void* sw = nullptr;
-    switch (cp) {
-        case 4: sw = (const void*)k_bwd_sweep<4>; break;
-        case 8: sw = (const void*)k_bwd_sweep<8>; break;
-        case 12: sw = (const void*)k_bwd_sweep<12>; break;
-        case 16: sw = (const void*)k_bwd_sweep<16>; break;
-        case 20: sw = (const void*)k_bwd_sweep<20>; break;
-        case 24: sw = (const void*)k_bwd_sweep<24>; break;
-        case 28: sw = (const void*)k_bwd_sweep<28>; break;
-        case 32: sw = (const void*)k_bwd_sweep<32>; break;
-    }
-    {
-        int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sw, 256, 0);
-        if (e != cudaSuccess) return cuda_status(e, "k_bwd_sweep occupancy");
-        long long blocks = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
-        const long long need = (B.total + 7) / 8;
-        if (blocks > need) blocks = need;
-        if (blocks < 1) blocks = 1;
-        Batch arg = B;
-        void* args[] = {&arg};
-        prof_begin("k_bwd_sweep", st);
-        e = cudaLaunchKernel(sw, dim3((unsigned)blocks), dim3(256), args, 0, st);
-        prof_end(st);
-        if (e != cudaSuccess) return cuda_status(e, "k_bwd_sweep");
-    }
     // per warp: fixed part plus a sample table of RB * lmax entries
+    // shared memory per warp grows with the batch's largest L: the warps per CTA
+    // decide how many CTAs fit on an SM
     const size_t per_warp = sizeof(WarpBwd) + table_stride(B.lmax);
     cudaError_t e;
     const size_t kMaxSmem = 227 * 1024;
-    while (warps > 1 && (size_t)warps * per_warp > kMaxSmem) --warps;
-    const size_t smem = (size_t)warps * per_warp;
-    if (smem > kMaxSmem) {
-        set_last_error("backward: %d samples per ray need %zu bytes of shared memory", B.lmax, smem);
+    if (per_warp > kMaxSmem) {
+        set_last_error("backward: %d samples per ray need %zu bytes of shared memory per warp", B.lmax, per_warp);
         return SQ_ERR_INVALID_ARG;
     }
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
     if (e != cudaSuccess) return cuda_status(e, "k_backward shared memory");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem);
-    if (e != cudaSuccess) return cuda_status(e, "k_backward occupancy");
+    const int want = warps;
+    int per_sm = 0, best_resident = -1;
+    warps = 0;
+    for (int w = MAX_WARPS; w >= 1; w >>= 1) {
+        if ((want != 0 && w != want) || (size_t)w * per_warp > kMaxSmem) continue;
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, w * 32, (size_t)w * per_warp);
+        if (e != cudaSuccess) return cuda_status(e, "k_backward occupancy");
+        if (b * w > best_resident) {
+            best_resident = b * w;
+            per_sm = b;
+            warps = w;
+        }
+    }
+    if (warps == 0) {  // the requested count does not fit: the largest power of two that does
+        warps = 1;
+        while (warps * 2 <= MAX_WARPS && (size_t)(warps * 2) * per_warp <= kMaxSmem) warps *= 2;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, (size_t)warps * per_warp);
+        if (e != cudaSuccess) return cuda_status(e, "k_backward occupancy");
+    }
+    const size_t smem = (size_t)warps * per_warp;
     const long long need = (B.total / RB + B.n + warps - 1) / warps;
     long long blocks = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
     if (blocks > need) blocks = need;

@@ -50,13 +50,14 @@ __global__ void k_pack(sq_prims_t P, float4* __restrict__ rec, float4* __restric
 
 // Copies the by-value scene descriptors into device memory (one thread).
 __global__ void k_write_desc(BatchParams P, SceneDesc* __restrict__ d, long long* __restrict__ off,
-                             long long* __restrict__ boff) {
+                             long long* __restrict__ boff, long long* __restrict__ gboff) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (int i = 0; i < P.n; ++i) d[i] = P.s[i];
     for (int i = 0; i <= P.n; ++i) {
         off[i] = P.off[i];
         boff[i] = P.boff[i];
     }
+    for (int i = 0; i < 2 * MAX_BATCH; ++i) gboff[i] = P.gboff[i];
 }
 
 // ------------------------------------------------------------------ pair counter
@@ -104,7 +105,8 @@ struct SceneWs {
 constexpr size_t HDR_DESC = 0;
 constexpr size_t HDR_OFF = (MAX_BATCH * sizeof(SceneDesc) + 255) / 256 * 256;
 constexpr size_t HDR_BOFF = HDR_OFF + ((MAX_BATCH + 1) * sizeof(long long) + 255) / 256 * 256;
-constexpr size_t HDR_CTR = HDR_BOFF + ((MAX_BATCH + 1) * sizeof(long long) + 255) / 256 * 256;
+constexpr size_t HDR_GBOFF = HDR_BOFF + ((MAX_BATCH + 1) * sizeof(long long) + 255) / 256 * 256;
+constexpr size_t HDR_CTR = HDR_GBOFF + (2 * MAX_BATCH * sizeof(long long) + 255) / 256 * 256;
 constexpr size_t HDR_END = HDR_CTR + 256;
 
 SceneWs scene_ws(const sq_prims_t* p, size_t base) {
@@ -150,7 +152,7 @@ void saved_ptrs(const sq_rays_t* r, int C, void* saved, SceneDesc& D) {
     D.save_n = (int*)p;
 }
 
-Tuning default_tuning() { return Tuning{4, 8, 8}; }
+Tuning default_tuning() { return Tuning{4, 8, 0}; }
 
 }  // namespace
 
@@ -301,6 +303,18 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
     }
     P.off[n] = total;
     P.boff[n] = btotal;
+    // backward launch groups: consecutive scenes of equal L (the run walk sizes each
+    // warp's sample table by the launch's largest L); group g's bundle offsets sit at
+    // gboff[i0 + g ..], counted from its first scene i0
+    int gfirst[MAX_BATCH + 1], ng = 0;
+    for (int i0 = 0; i0 < n;) {
+        int i1 = i0 + 1;
+        while (i1 < n && sc[i1].rays.L == sc[i0].rays.L) ++i1;
+        for (int i = i0; i <= i1; ++i) P.gboff[i + ng] = P.boff[i] - P.boff[i0];
+        gfirst[ng++] = i0;
+        i0 = i1;
+    }
+    gfirst[ng] = n;
     if (op == SQ_OP_BWD)
         for (int i = 0; i < n; ++i) {
             P.s[i].gw = (float2*)(base + at);
@@ -309,14 +323,22 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
     SceneDesc* d = (SceneDesc*)(base + HDR_DESC);
     long long* off = (long long*)(base + HDR_OFF);
     long long* boff = (long long*)(base + HDR_BOFF);
+    long long* gboff = (long long*)(base + HDR_GBOFF);
     int* ctr = (int*)(base + HDR_CTR);
-    SQ_LAUNCH("k_write_desc", st, k_write_desc<<<1, 32, 0, st>>>(P, d, off, boff));
+    SQ_LAUNCH("k_write_desc", st, k_write_desc<<<1, 32, 0, st>>>(P, d, off, boff, gboff));
     cudaError_t e = cudaMemsetAsync(ctr, 0, 256, st);
     if (e != cudaSuccess) return cuda_status(e, "memset counter");
     Batch B{d, off, boff, n, total, ctr, lmax};
-    sq_status_t ls = (op == SQ_OP_FWD) ? launch_forward(B, cp, tn, st) : launch_backward(B, cp, tn, st);
+    sq_status_t ls = (op == SQ_OP_FWD) ? launch_forward(B, cp, tn, st) : launch_sweep(B, cp, st);
     if (ls != SQ_OK) return ls;
     if (op == SQ_OP_BWD) {
+        for (int g = 0; g < ng; ++g) {  // one run-walk launch per group, each with its own counter
+            const int i0 = gfirst[g], i1 = gfirst[g + 1];
+            const Batch Bg{d + i0, off + i0, gboff + i0 + g, i1 - i0, P.off[i1] - P.off[i0], ctr + 1 + g,
+                           sc[i0].rays.L};
+            ls = launch_backward(Bg, cp, tn, st);
+            if (ls != SQ_OK) return ls;
+        }
         for (int i = 0; i < n; ++i) {
             const sq_scene_t& s = sc[i];
             ls = launch_grad_out(P.s[i], s.g_means, s.g_quats, s.g_scales, s.g_eps, s.g_opacity, s.g_logits, st);
@@ -383,7 +405,7 @@ sq_status_t batched_api_impl(int op, const sq_scene_t* sc, int n, const sq_tunin
 sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes, cudaStream_t st, sq_tuning_t* best,
                           float* fwd_ms, float* bwd_ms, int reps) {
     const Tuning fcand[4] = {{4, 4, 8}, {4, 8, 8}, {8, 4, 8}, {8, 8, 8}};
-    const int bcand[2] = {4, 8};
+    const int bcand[3] = {0, 4, 8};  // 0: the most resident warps for the batch's L
     if (reps < 1) reps = 1;
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
@@ -419,7 +441,7 @@ sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes
     if (s == SQ_OK) s = batched_impl(SQ_OP_FWD, sc, n, tb, ws, ws_bytes, st);  // saved state for the backward
     bool do_bwd = s == SQ_OK;
     for (int i = 0; i < n && do_bwd; ++i) do_bwd = sc[i].saved != nullptr && sc[i].grad_depth && sc[i].grad_sem;
-    for (int c = 0; c < 2 && do_bwd && s == SQ_OK; ++c) {
+    for (int c = 0; c < 3 && do_bwd && s == SQ_OK; ++c) {
         Tuning t = tb;
         t.bwd_warps = bcand[c];
         s = batched_impl(SQ_OP_BWD, sc, n, t, ws, ws_bytes, st);

@@ -48,11 +48,14 @@ struct BatchParams {
     int n;
     long long off[MAX_BATCH + 1];   // ray offsets of the scenes in the concatenated ray range
     long long boff[MAX_BATCH + 1];  // offsets of the scenes' ray bundles (backward)
+    long long gboff[2 * MAX_BATCH];  // the same per launch group of the backward, from the group's first scene
     SceneDesc s[MAX_BATCH];
 };
 
 // What the render kernels receive: descriptors and offsets in device memory and
-// a zeroed work counter over the concatenated rays (or ray bundles).
+// a zeroed work counter over the concatenated rays (or ray bundles).  A backward
+// launch may cover a slice of the scenes: d then points at its first scene and
+// boff at bundle offsets counted from that scene.
 struct Batch {
     const SceneDesc* d;
     const long long* off;
@@ -85,12 +88,13 @@ __device__ __forceinline__ void scene_ray(const SceneDesc& S, long long r, float
 struct Tuning {
     int fwd_lanes;  // lanes (samples) per ray in the forward: 4, 8 or 16
     int fwd_warps;  // warps per CTA, forward: 4 or 8
-    int bwd_warps;  // warps per CTA, backward: 4 or 8
+    int bwd_warps;  // warps per CTA, backward: 1..8, or 0 for the count that keeps the most warps resident
 };
 
 int device_sm_count();
 int bwd_rays_per_bundle();
 sq_status_t launch_forward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st);
+sq_status_t launch_sweep(const Batch& B, int cp, cudaStream_t st);
 sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st);
 sq_status_t launch_grad_out(const SceneDesc& S, float* gm, float* gq, float* gs, float* ge, float* go, float* gl,
                             cudaStream_t st);

@@ -317,14 +317,18 @@ def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, gr
     return out
 
 
-def query_grid(prims: dict, index: Index, grid: dict, tau: float = 0.05, with_label: bool = True):
-    """Supp. A.4 voxelisation: density [V], sem [V, C], label [V] uint8 (C = free)."""
+def query_grid(prims: dict, index: Index, grid: dict, tau: float = 0.05, with_label: bool = True, out=None):
+    """Supp. A.4 voxelisation: density [V], sem [V, C], label [V] uint8 (C = free).
+    ``out`` = (density, sem, label or None) to write into."""
     device = prims["means"].device
     C = prims["logits"].shape[1]
     nvox = index.v_n.numel()
-    dens = torch.empty(nvox, device=device)
-    sem = torch.empty((nvox, C), device=device)
-    lab = torch.empty(nvox, dtype=torch.uint8, device=device) if with_label else None
+    if out is not None:
+        dens, sem, lab = out
+    else:
+        dens = torch.empty(nvox, device=device)
+        sem = torch.empty((nvox, C), device=device)
+        lab = torch.empty(nvox, dtype=torch.uint8, device=device) if with_label else None
     p, g, ix = prims_struct(prims), grid_struct(grid), index.struct()
     wsz = lib.sq_workspace_size(SQ_OP_QUERY, ctypes.byref(p), ctypes.byref(g), None)
     ws = _ws.get("query", wsz, device)
@@ -485,7 +489,7 @@ def autotune(scenes, reps: int = 3, use_cache: bool = True) -> dict:
     ws = _ws.get("batched", lib.sq_batched_workspace_size(arr, len(scenes)), device)
     best = SqTuning()
     fms = (ctypes.c_float * 4)()
-    bms = (ctypes.c_float * 2)()
+    bms = (ctypes.c_float * 3)()
     _check(lib.sq_autotune(arr, len(scenes), _ptr(ws), ws.numel(), _stream(), reps, ctypes.byref(best), fms, bms),
            "sq_autotune")
     out = {"fwd_lanes_per_ray": best.fwd_lanes_per_ray, "fwd_warps_per_cta": best.fwd_warps_per_cta,

@@ -88,7 +88,7 @@ def test_batched_scene_against_oracle(sqr):
             check_grad(sc.grads[k].cpu().numpy(), ref[k], k)
 
 
-@pytest.mark.parametrize("lanes,fw,bw", [(4, 4, 4), (8, 8, 8), (16, 4, 8), (4, 8, 4)])
+@pytest.mark.parametrize("lanes,fw,bw", [(4, 4, 4), (8, 8, 8), (16, 4, 2), (4, 8, 0)])
 def test_every_tuning_gives_the_same_render(sqr, lanes, fw, bw):
     scenes, _ = _scenes(sqr, seed=2)
     sqr.render_batched(sqr.SQ_OP_FWD, scenes)
@@ -109,7 +109,7 @@ def test_autotuner_picks_a_measured_candidate(sqr):
     scenes, _ = _scenes(sqr, seed=3)
     best = sqr.autotune(scenes, reps=2, use_cache=False)
     assert best["fwd_lanes_per_ray"] in (4, 8) and best["fwd_warps_per_cta"] in (4, 8)
-    assert best["bwd_warps_per_cta"] in (4, 8)
+    assert best["bwd_warps_per_cta"] in (0, 4, 8)
     assert all(ms > 0 for ms in best["fwd_ms"]) and all(ms > 0 for ms in best["bwd_ms"])
     cands = [(4, 4), (4, 8), (8, 4), (8, 8)]
     i = cands.index((best["fwd_lanes_per_ray"], best["fwd_warps_per_cta"]))
