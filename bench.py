@@ -425,14 +425,16 @@ def run_query(args):
 
 
 def run_batch(args):
-    """Twelve uneven scenes: per-scene launches vs one batched persistent launch per
-    pass (autotuned), the whole step captured in a CUDA graph."""
+    """Twelve uneven scenes (--workload batch) or the 13 frames of a temporal
+    horizon (--workload temporal): per-scene launches vs one batched persistent
+    launch per pass (autotuned), the whole step captured in a CUDA graph."""
     import torch
     from paper_2511_17361_gb300 import _build
     _build.build()
     from paper_2511_17361_gb300 import sqr
     dev = torch.device("cuda", 0)
-    cfgs = synth.make_batch_config(3)
+    temporal = args.workload == "temporal"
+    cfgs = synth.make_temporal_config() if temporal else synth.make_batch_config(3)
     scenes, targets = [], []
     for i, c in enumerate(cfgs):
         prims = sqr.to_device(c["prims"], dev)
@@ -496,10 +498,12 @@ def run_batch(args):
         batched_step()
     ms_graph = timed(graph.replay, args.steps)
     ms_batched = timed(batched_step, args.steps)
-    line = {"metric": "ray-samples/s (forward + backward), 12-scene uneven batch", "value": samples / (ms_graph / 1e3),
+    what = "13-frame temporal horizon (T = 6)" if temporal else "12-scene uneven batch"
+    line = {"metric": f"ray-samples/s (forward + backward), {what}", "value": samples / (ms_graph / 1e3),
             "unit": "ray-samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch12_uneven", "scenes": len(scenes), "ray_samples": samples,
+            "config": {"workload": "temporal13_ring6_N1600" if temporal else "batch12_uneven", "scenes": len(scenes),
+                       "ray_samples": samples,
                        "rays": [sc.rays.R for sc in scenes], "superquadrics": [int(sc.prims["means"].shape[0])
                                                                              for sc in scenes],
                        "samples_per_ray": [int(sc.rays.t.numel()) for sc in scenes], "tuning": tuning,
@@ -519,15 +523,16 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["frame", "batch", "query"], default="frame",
+    ap.add_argument("--workload", choices=["frame", "batch", "temporal", "query"], default="frame",
                     help="frame: one six-camera frame (default); batch: 12 uneven scenes, batched vs per scene; "
+                         "temporal: the 13 frames of a T = 6 horizon, batched vs per frame; "
                          "query: grid query of an 8192-superquadric scene at all 640,000 voxel centres")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch":
+    if args.workload in ("batch", "temporal"):
         return run_batch(args)
     if args.workload == "query":
         return run_query(args)

@@ -195,6 +195,32 @@ def make_config(idx: int, seed: int | None = None) -> dict:
     raise ValueError(f"unknown workload {idx}")
 
 
+def make_temporal_config(T: int = 6, n: int = 1600, seed: int = 6, H: int = 225, W: int = 400, f: float = 250.0,
+                         L: int = 100, ego_step: float = 0.5, speed: float = 0.4) -> list[dict]:
+    """Temporal horizon of Sec. 3.2: the 2T+1 frames t = -T..T of one superquadric
+    set (N = 1600, T = 6 as in the paper's training, Sec. 4.2) whose properties
+    are shared and whose means move by a per-frame offset v(t) = t * u_i (u_i per
+    primitive: 0 for the ground, N(0, speed^2) m per frame in x and y for objects),
+    each frame rendered by the six-camera rig moved by the ego motion t * ego_step m
+    along +x.  The grid stays centred on the current frame's ego pose."""
+    base = prims_driving(n, seed)
+    rng = np.random.default_rng(seed + 17)
+    ground = base["scales"][:, 2] <= 0.5
+    ground &= (base["eps"][:, 0] <= 0.3)
+    u = np.zeros((n, 3))
+    u[~ground, :2] = rng.normal(0.0, speed, (int((~ground).sum()), 2))
+    frames = []
+    for t in range(-T, T + 1):
+        pr = {k: v.copy() for k, v in base.items()}
+        pr["means"] = (base["means"].astype(np.float64) + t * u).astype(np.float32)
+        rig = rig_ring(H=H, W=W, f=f)
+        rig["cam2world"] = rig["cam2world"].copy()
+        rig["cam2world"][:, 0, 3] += np.float32(t * ego_step)
+        frames.append({"name": f"frame{t:+d}", "t_index": t, "prims": pr, "grid": grid_spec(200, 200, 16),
+                       "rig": rig, "t": sample_depths(L), "kappa": 0.0, "alpha_max": 1.0})
+    return frames
+
+
 def make_batch_config(seed: int = 3, n_scenes: int = 12) -> list[dict]:
     """Uneven batch: per scene N ~ U{1000..12000}, 1-6 ring cameras, 225x400 (f=250)
     or 450x800 (f=500) rays, L ~ U{64..128}, each with its own 200x200x16 grid."""

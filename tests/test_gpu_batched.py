@@ -160,3 +160,40 @@ def test_cuda_graph_replay_matches_eager(sqr):
         assert torch.equal(sc.depth, d) and torch.equal(sc.sem, s)
         for k in gr:
             check_grad(sc.grads[k].cpu().numpy(), gr[k].cpu().numpy(), k, rtol=2e-3)
+
+
+def test_temporal_horizon_batch(sqr):
+    """The 2T+1 frames of a temporal horizon (Sec. 3.2; T = 2 here, small images):
+    the batched launch equals per-frame calls, and the first and last frames
+    match the FP64 oracle."""
+    frames = synth.make_temporal_config(T=2, n=300, H=18, W=30, f=20.0, L=40)
+    assert len(frames) == 5
+    rng = np.random.default_rng(12)
+    scenes = []
+    for fr in frames:
+        prims_d = sqr.to_device(fr["prims"])
+        rays = sqr.Rays.from_rig(fr["rig"], fr["t"])
+        gd = dev_grid(fr["grid"])
+        sc = sqr.Scene(prims_d, sqr.build_index(prims_d, gd), gd, rays, training=True)
+        sc.grad_depth.copy_(torch.from_numpy(rng.standard_normal(rays.R).astype(np.float32)))
+        sc.grad_sem.copy_(torch.from_numpy(rng.standard_normal((rays.R, 18)).astype(np.float32)))
+        scenes.append(sc)
+    refs = [_per_scene(sqr, sc) for sc in scenes]
+    sqr.render_batched(sqr.SQ_OP_FWD, scenes)
+    sqr.render_batched(sqr.SQ_OP_BWD, scenes)
+    torch.cuda.synchronize()
+    for sc, (d, s, tf, g) in zip(scenes, refs):
+        assert torch.equal(sc.depth, d) and torch.equal(sc.sem, s)
+        for k in g:
+            check_grad(sc.grads[k].cpu().numpy(), g[k].cpu().numpy(), k, rtol=2e-3)
+    for i in (0, len(frames) - 1):
+        fr, sc = frames[i], scenes[i]
+        idx = np_index(sc.index)
+        D, S, T, _ = oracle.render_fwd(fr["prims"], fr["grid"], idx, fr["rig"], fr["t"])
+        check_depth(sc.depth.cpu().numpy(), D, 0.5)
+        check_sem(sc.sem.cpu().numpy(), S)
+        ref = oracle.render_bwd(fr["prims"], fr["grid"], idx, fr["rig"], fr["t"],
+                                sc.grad_depth.cpu().numpy().astype(np.float64),
+                                sc.grad_sem.cpu().numpy().astype(np.float64))
+        for k in ref:
+            check_grad(sc.grads[k].cpu().numpy(), ref[k], k)
