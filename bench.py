@@ -200,7 +200,8 @@ def run_mine(args):
     td = torch.from_numpy(td_np).to(dev)
     tl = torch.from_numpy(tl_np).to(dev)
 
-    ix = sqr.build_index(prims, grid)  # sizes V_sq (host sync once, before timing)
+    imode = {"obb": sqr.SQ_INDEX_OBB, "cube": sqr.SQ_INDEX_CUBE, "opacity": sqr.SQ_INDEX_OBB_OPACITY}[args.index]
+    ix = sqr.build_index(prims, grid, mode=imode)  # sizes V_sq (host sync once, before timing)
     P = ix.P()
     Q, in_grid = sqr.count_pairs(ix, grid, rays)
     depth = torch.empty(R, device=dev)
@@ -212,7 +213,7 @@ def run_mine(args):
 
     def step(ev=None):
         if ev: ev[0].record()
-        sqr.build_index(prims, grid, index=ix, sync=False)
+        sqr.build_index(prims, grid, mode=imode, index=ix, sync=False)
         if ev: ev[1].record()
         sqr.render_fwd(prims, ix, grid, rays, out=(depth, sem, tf), saved=saved)
         if ev: ev[2].record()
@@ -342,7 +343,9 @@ def run_mine(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg["name"], "rays": R, "samples_per_ray": L, "superquadrics": int(
                 prims["means"].shape[0]), "grid": list(grid["n"]), "index_entries_P": P, "pairs_Q": Q,
-                "in_grid_samples": in_grid, "l2": "flushed (256 MB write) between timed steps",
+                "in_grid_samples": in_grid, "index": {"obb": "OBB, tau_cut 0.01", "cube": "cube N_v = 5",
+                                                      "opacity": "opacity-aware OBB, tau_cut 0.01"}[args.index],
+                "l2": "flushed (256 MB write) between timed steps",
                 "parallelism": f"replicas x{world} (one frame per GPU)"},
             "phases_ms": {n: float(v) for n, v in zip(names, mean_phase)},
             "gpu_launches": launches_timed + dropped,
@@ -523,6 +526,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--index", choices=["obb", "cube", "opacity"], default="obb",
+                    help="voxel neighbourhood of the frame workload's index (default: OBB, tau_cut 0.01)")
     ap.add_argument("--workload", choices=["frame", "batch", "temporal", "query"], default="frame",
                     help="frame: one six-camera frame (default); batch: 12 uneven scenes, batched vs per scene; "
                          "temporal: the 13 frames of a T = 6 horizon, batched vs per frame; "

@@ -49,7 +49,7 @@ typedef enum {
     SQ_ERR_NUMERIC = 5      /* reserved: non-finite parameters detected */
 } sq_status_t;
 
-enum { SQ_INDEX_OBB = 0, SQ_INDEX_CUBE = 1 };
+enum { SQ_INDEX_OBB = 0, SQ_INDEX_CUBE = 1, SQ_INDEX_OBB_OPACITY = 2 };
 enum { SQ_OP_INDEX = 0, SQ_OP_FWD = 1, SQ_OP_BWD = 2, SQ_OP_QUERY = 3 };
 
 /* Limits of this build. */
@@ -85,7 +85,13 @@ typedef struct {
  *                 p_o >= tau_cut (local half-extents s_i * ln(1/tau_cut)^(eps1/2)),
  *                 mapped to an inclusive voxel range.  tau_cut in (0, 1).
  *  SQ_INDEX_CUBE: the voxel holding the centre +- nv voxels per axis (the
- *                 paper's cubic neighbourhood N_v = 5, Sec. 4.2).  nv >= 0. */
+ *                 paper's cubic neighbourhood N_v = 5, Sec. 4.2).  nv >= 0.
+ *  SQ_INDEX_OBB_OPACITY: the opacity-aware refinement the paper names as future
+ *                 work (Supp., limitations): as SQ_INDEX_OBB for the level set
+ *                 sigma_i p_o >= tau_cut, local half-extents
+ *                 s_i * (ln(sigma_i) - ln(tau_cut))^(eps1/2); a primitive with
+ *                 sigma_i <= tau_cut is listed nowhere.  It drops only pair terms
+ *                 whose sigma p_o is below tau_cut (their p_o c terms too). */
 typedef struct {
     int mode;
     float tau_cut;

@@ -94,14 +94,15 @@ def sq_p(x, m, q, s, e1, e2) -> float:
 
 # ----------------------------------------------------------------------- index
 def ranges(prims, grid, mode=0, tau_cut=0.01, nv=5):
-    """Per-primitive voxel box (i0,i1,j0,j1,k0,k1) and the near-tie count."""
+    """Per-primitive voxel box (i0,i1,j0,j1,k0,k1) and the near-tie count; mode 0
+    OBB, 1 cube, 2 opacity-aware OBB."""
     n = prims["means"].shape[0]
     out = np.zeros((n, 6), np.int32)
     gn, glo, gvs = _grid_args(grid)
     P = prims
     ties = _load().orc_ranges(ctypes.c_int(n), _p(_f32(P["means"])), _p(_f32(P["quats"])), _p(_f32(P["scales"])),
-                              _p(_f32(P["eps"])), _p(gn), _p(glo), _p(gvs), ctypes.c_int(mode),
-                              ctypes.c_float(tau_cut), ctypes.c_int(nv), _p(out))
+                              _p(_f32(P["eps"])), _p(_f32(P["opacity"])), _p(gn), _p(glo), _p(gvs),
+                              ctypes.c_int(mode), ctypes.c_float(tau_cut), ctypes.c_int(nv), _p(out))
     return out, int(ties)
 
 

@@ -247,17 +247,33 @@ static int near_integer(double u) { return fabs(u - floor(u + 0.5)) < 1e-9; }
  *     the world AABB of that oriented box has half-width sum_i |R_ji| h_i.
  *   mode 1 (cube): the voxel containing the centre +- nv voxels (the paper's
  *     cubic neighbourhood N_v).
+ *   mode 2 (opacity-aware OBB, the index refinement the paper names as future
+ *     work): as mode 0 for the level set sigma_k p_o >= tau_cut, i.e.
+ *     Kc_k = ln(sigma_k) - ln(tau_cut); a primitive with sigma_k <= tau_cut has
+ *     no voxels.
  * Returns the number of primitives whose box bounds fall within 1e-9 of a
  * voxel boundary (where a one-ulp difference could move the box). */
 long long orc_ranges(int n, const float* means, const float* quats, const float* scales, const float* eps,
-                     const int* gn, const float* glo, const float* gvs, int mode, float tau_cut, int nv, int* ranges) {
+                     const float* opacity, const int* gn, const float* glo, const float* gvs, int mode,
+                     float tau_cut, int nv, int* ranges) {
     long long ties = 0;
-    const double log_kc = log(-log((double)tau_cut));
+    const double log_kc0 = log(-log((double)tau_cut));
     for (int k = 0; k < n; ++k) {
         double q[4], qn[4], qnorm, R[9];
         for (int i = 0; i < 4; ++i) q[i] = quats[4 * k + i];
         quat_rotation(q, qn, &qnorm, R);
         double e1 = eps[2 * k + 0];
+        double log_kc = log_kc0;
+        if (mode == 2) {
+            if (!((double)opacity[k] > (double)tau_cut)) {
+                for (int j = 0; j < 3; ++j) {
+                    ranges[6 * k + 2 * j + 0] = 0;
+                    ranges[6 * k + 2 * j + 1] = -1;
+                }
+                continue;
+            }
+            log_kc = log(log((double)opacity[k]) - log((double)tau_cut));
+        }
         double ext = exp((0.5 * e1) * log_kc);
         double h[3];
         for (int i = 0; i < 3; ++i) h[i] = (double)scales[3 * k + i] * ext;
@@ -266,7 +282,7 @@ long long orc_ranges(int n, const float* means, const float* quats, const float*
             double m = means[3 * k + j];
             double lo = glo[j], vs = gvs[j];
             double ulo, uhi;
-            if (mode == 0) {
+            if (mode != 1) {
                 double hw = fabs(R[3 * j + 0]) * h[0] + fabs(R[3 * j + 1]) * h[1];
                 hw = hw + fabs(R[3 * j + 2]) * h[2];
                 ulo = ((m - hw) - lo) / vs;

@@ -218,7 +218,7 @@ sq_status_t sq_build_index(const sq_prims_t* prims, const sq_grid_t* grid, const
     if ((s = check_grid(grid)) != SQ_OK) return s;
     if ((s = check_index(index, grid, prims->n)) != SQ_OK) return s;
     if (!opts) { set_last_error("opts is NULL"); return SQ_ERR_INVALID_ARG; }
-    if (opts->mode == SQ_INDEX_OBB) {
+    if (opts->mode == SQ_INDEX_OBB || opts->mode == SQ_INDEX_OBB_OPACITY) {
         if (!(opts->tau_cut > 0.f && opts->tau_cut < 1.f)) {
             set_last_error("tau_cut = %g outside (0, 1)", (double)opts->tau_cut);
             return SQ_ERR_INVALID_ARG;

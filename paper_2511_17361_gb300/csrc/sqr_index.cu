@@ -31,10 +31,13 @@ struct RangeArgs {
     const float* quats;
     const float* scales;
     const float* eps;
+    const float* opacity;
     int n;
     int mode;
     int nv;
-    double log_kc;  // ln(ln(1/tau_cut)), computed on the host
+    double log_kc;   // ln(ln(1/tau_cut)), computed on the host
+    double tau;      // tau_cut (opacity-aware mode)
+    double log_tau;  // ln(tau_cut), computed on the host
     int gn[3];
     double glo[3];
     double gvs[3];
@@ -62,14 +65,28 @@ __device__ void prim_box(const RangeArgs& a, int k, int lo_i[3], int hi_i[3], bo
     R[7] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
     R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
     double e1 = a.eps[2 * k + 0];
-    double ext = exp(__dmul_rn(__dmul_rn(0.5, e1), a.log_kc));
+    double log_kc = a.log_kc;
+    if (a.mode == SQ_INDEX_OBB_OPACITY) {
+        // the level set sigma p_o >= tau_cut: Kc = ln(sigma) - ln(tau_cut); none if sigma <= tau_cut
+        const double sig = a.opacity[k];
+        if (!(sig > a.tau)) {
+            empty = true;
+            for (int j = 0; j < 3; ++j) {
+                lo_i[j] = 0;
+                hi_i[j] = -1;
+            }
+            return;
+        }
+        log_kc = log(__dsub_rn(log(sig), a.log_tau));
+    }
+    double ext = exp(__dmul_rn(__dmul_rn(0.5, e1), log_kc));
     double h[3];
     for (int i = 0; i < 3; ++i) h[i] = __dmul_rn((double)a.scales[3 * k + i], ext);
     empty = false;
     for (int j = 0; j < 3; ++j) {
         double m = a.means[3 * k + j];
         double ulo, uhi;
-        if (a.mode == SQ_INDEX_OBB) {
+        if (a.mode != SQ_INDEX_CUBE) {
             double hw = __dadd_rn(__dmul_rn(fabs(R[3 * j + 0]), h[0]), __dmul_rn(fabs(R[3 * j + 1]), h[1]));
             hw = __dadd_rn(hw, __dmul_rn(fabs(R[3 * j + 2]), h[2]));
             ulo = __ddiv_rn(__dsub_rn(__dsub_rn(m, hw), a.glo[j]), a.gvs[j]);
@@ -410,8 +427,11 @@ sq_status_t build_index_impl(const sq_prims_t* prims, const sq_grid_t* grid, con
 
     RangeArgs a;
     a.means = prims->means; a.quats = prims->quats; a.scales = prims->scales; a.eps = prims->eps;
+    a.opacity = prims->opacity;
     a.n = prims->n; a.mode = opts->mode; a.nv = opts->nv;
-    a.log_kc = (opts->mode == SQ_INDEX_OBB) ? log(-log((double)opts->tau_cut)) : 0.0;
+    a.log_kc = (opts->mode != SQ_INDEX_CUBE) ? log(-log((double)opts->tau_cut)) : 0.0;
+    a.tau = (double)opts->tau_cut;
+    a.log_tau = log((double)opts->tau_cut);
     a.gn[0] = nx; a.gn[1] = ny; a.gn[2] = nz;
     for (int i = 0; i < 3; ++i) { a.glo[i] = grid->lo[i]; a.gvs[i] = grid->vs[i]; }
 

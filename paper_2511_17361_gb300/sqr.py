@@ -21,7 +21,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libsqr.so")
 
 SQ_OK, SQ_ERR_INVALID_ARG, SQ_ERR_CAPACITY, SQ_ERR_CUDA, SQ_ERR_TIMEOUT, SQ_ERR_NUMERIC = range(6)
-SQ_INDEX_OBB, SQ_INDEX_CUBE = 0, 1
+SQ_INDEX_OBB, SQ_INDEX_CUBE, SQ_INDEX_OBB_OPACITY = 0, 1, 2
 SQ_OP_INDEX, SQ_OP_FWD, SQ_OP_BWD, SQ_OP_QUERY = 0, 1, 2, 3
 
 _vp = ctypes.c_void_p

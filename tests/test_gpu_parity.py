@@ -49,6 +49,16 @@ def test_index_bit_exact(sqr, ci):
     _assert_index_equal(ix, ref)
 
 
+@pytest.mark.parametrize("ci", [0, 1])
+def test_index_opacity_mode_bit_exact(sqr, ci):
+    """Opacity-aware OBB index (the paper's future-work refinement): identical to
+    the oracle's, and smaller than the plain OBB index."""
+    cfg = synth.make_config(ci)
+    _, ix, ref = _index_pair(sqr, cfg, mode=2)
+    _assert_index_equal(ix, ref)
+    assert ref["P"] < oracle.build_index(cfg["prims"], cfg["grid"])["P"]
+
+
 def test_index_cube_mode_bit_exact(sqr):
     cfg = synth.make_config(0)
     _, ix, ref = _index_pair(sqr, cfg, mode=1, nv=5)
@@ -240,10 +250,10 @@ def test_forward_cube_index(sqr):
 
 
 # ----------------------------------------------------------------------- backward
-def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0, kappa=0.0, flags=True):
+def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0, kappa=0.0, flags=True, mode=0):
     prims_d, rays = scene_to_gpu(sqr, prims, rig, t, kappa, alpha_max)
     g = dev_grid(grid)
-    ix = sqr.build_index(prims_d, g, flags=flags)
+    ix = sqr.build_index(prims_d, g, mode=mode, flags=flags)
     R = rays.R
     gd_full = np.zeros(R, np.float32)
     gs_full = np.zeros((R, prims["logits"].shape[1]), np.float32)
@@ -292,6 +302,22 @@ def test_backward_long_sample_steps(sqr, flags):
         got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, flags=False)
         for k in ref:
             check_grad(got[k], ref[k], k)
+
+
+def test_render_with_opacity_index(sqr):
+    """Forward and backward over the opacity-aware index, against the oracle
+    rendering the same index."""
+    cfg = synth.make_config(0)
+    d, s, tf, D, S, T, _ = _fwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], mode=2)
+    check_depth(d, D, 0.5)
+    check_sem(s, S)
+    pr, grid, rig, t = small_scene(13, n=10, H=9, W=11, L=32, sigma_max=0.6)
+    R = rig["H"] * rig["W"]
+    rng = np.random.default_rng(13)
+    gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, 5)).astype(np.float32)
+    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, mode=2)
+    for k in ref:
+        check_grad(got[k], ref[k], k)
 
 
 def test_backward_clamp_active(sqr):

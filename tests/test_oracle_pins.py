@@ -466,3 +466,64 @@ def test_grid_query_full_coverage_equals_brute_force():
     p = brute_p(pr, pc)
     np.testing.assert_allclose(dens, p @ pr["opacity"].astype(np.float64), rtol=1e-11, atol=1e-300)
     np.testing.assert_allclose(sem, p @ pr["logits"].astype(np.float64), rtol=1e-11, atol=1e-14)
+
+
+# ------------------------------------------------- opacity-aware index (mode 2)
+def test_opacity_mode_axis_aligned_box():
+    """Axis-aligned primitive: the box holds the level set sigma p_o >= tau, whose
+    local half-extents are s_i (ln(sigma/tau))^(eps1/2) (along a local axis
+    f = (|x_i|/s_i)^(2/eps1))."""
+    grid = synth.grid_spec(20, 20, 10, lo=(-10, -10, -5), hi=(10, 10, 5))
+    m, s, e1, sig, tau = np.array([0.3, -2.2, 1.1]), np.array([1.0, 2.0, 0.5]), 1.0, 0.5, 0.01
+    pr = prims_from([m], [[1, 0, 0, 0]], [s], [[e1, 1.0]], [sig], np.zeros((1, 2)))
+    rg, ties = oracle.ranges(pr, grid, 2, tau, 0)
+    h = s * np.log(sig / tau) ** (e1 / 2)
+    lo = np.floor((m - h - np.array([-10, -10, -5])) / 1.0).astype(int)
+    hi = np.floor((m + h - np.array([-10, -10, -5])) / 1.0).astype(int)
+    assert ties == 0
+    assert list(rg[0]) == [lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]] == [8, 12, 3, 11, 5, 7]
+
+
+def test_opacity_mode_drops_faint_and_matches_obb_at_full_opacity():
+    rng = np.random.default_rng(4)
+    n = 200
+    grid = synth.grid_spec(40, 40, 10, lo=(-20, -20, -2), hi=(20, 20, 8))
+    base = prims_from(rng.uniform(-15, 15, (n, 3)), rng.standard_normal((n, 4)), rng.uniform(0.2, 2.5, (n, 3)),
+                      rng.uniform(0.2, 1.8, (n, 2)), rng.uniform(0, 1, n), rng.standard_normal((n, 3)))
+    obb, _ = oracle.ranges(base, grid, 0, 0.01, 0)
+    opa, _ = oracle.ranges(base, grid, 2, 0.01, 0)
+    empty = (opa[:, 1] < opa[:, 0]) | (opa[:, 3] < opa[:, 2]) | (opa[:, 5] < opa[:, 4])
+    # sigma <= tau: listed nowhere
+    assert np.all(empty[base["opacity"] <= 0.01])
+    # otherwise contained in the OBB-mode box (sigma <= 1 shrinks the level set)
+    ok = ~empty
+    assert np.all(opa[ok, 0::2] >= obb[ok, 0::2]) and np.all(opa[ok, 1::2] <= obb[ok, 1::2])
+    assert np.any(opa[ok] != obb[ok])
+    # sigma = 1: ln(1) - ln(tau) = ln(1/tau) exactly, the same boxes as mode 0
+    full = dict(base)
+    full["opacity"] = np.ones(n, np.float32)
+    opa1, _ = oracle.ranges(full, grid, 2, 0.01, 0)
+    assert np.array_equal(opa1, obb)
+
+
+def test_opacity_mode_box_holds_level_set():
+    """Points of a rotated primitive with sigma p_o >= tau (brute force over a
+    lattice around it) all fall in its opacity-aware voxel box."""
+    grid = synth.grid_spec(40, 40, 40, lo=(-4, -4, -4), hi=(4, 4, 4))
+    rng = np.random.default_rng(9)
+    for _ in range(4):
+        m = rng.uniform(-0.5, 0.5, 3)
+        q = rng.standard_normal(4)
+        s = rng.uniform(0.3, 1.0, 3)
+        e = rng.uniform(0.3, 1.7, 2)
+        sig = rng.uniform(0.05, 1.0)
+        pr = prims_from([m], [q], [s], [e], [sig], np.zeros((1, 2)))
+        rg, _ = oracle.ranges(pr, grid, 2, 0.01, 0)
+        pts = m + rng.uniform(-3.9, 3.9, (4000, 3))
+        pts = pts[np.all(np.abs(pts) < 3.99, 1)]
+        inside = np.array([sig * oracle.sq_p(x, m, q, s, e[0], e[1]) >= 0.01 for x in pts])
+        vox = np.floor((pts + 4.0) / 0.2).astype(int)
+        in_box = ((vox[:, 0] >= rg[0, 0]) & (vox[:, 0] <= rg[0, 1]) & (vox[:, 1] >= rg[0, 2]) & (vox[:, 1] <= rg[0, 3])
+                  & (vox[:, 2] >= rg[0, 4]) & (vox[:, 2] <= rg[0, 5]))
+        assert inside.sum() > 0
+        assert np.all(in_box[inside])
