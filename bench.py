@@ -383,10 +383,15 @@ def run_query(args):
     C = cfg["prims"]["logits"].shape[1]
     out = (torch.empty(nvox, device=dev), torch.empty((nvox, C), device=dev),
            torch.empty(nvox, dtype=torch.uint8, device=dev))
+    rng = np.random.default_rng(4)
+    gd = torch.from_numpy(rng.standard_normal(nvox).astype(np.float32)).to(dev)
+    gsem = torch.from_numpy(rng.standard_normal((nvox, C)).astype(np.float32)).to(dev)
+    grads = {k: torch.empty_like(prims[k]) for k in sqr.PRIM_KEYS}
     for _ in range(max(3, args.warmup)):
         sqr.query_grid(prims, ix, grid, 0.05, out=out)
+        sqr.query_grid_bwd(prims, ix, grid, gd, gsem, out=grads)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     sampler = ClockSampler(0)
     torch.cuda.synchronize()
     sampler.start()
@@ -396,11 +401,16 @@ def run_query(args):
         ev[s][0].record()
         sqr.query_grid(prims, ix, grid, 0.05, out=out)
         ev[s][1].record()
+        sqr.query_grid_bwd(prims, ix, grid, gd, gsem, out=grads)
+        ev[s][2].record()
     torch.cuda.synchronize()
     sqr.profile_enable(False)
     clocks = sampler.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    ms_bwd = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
     n_q, q_ms, _ = sqr.profile_query("k_query")
+    n_qb, qb_ms, _ = sqr.profile_query("k_query_bwd")
+    kb_ms = qb_ms / max(n_qb, 1)
     launches, _, dropped = sqr.profile_query(None)
     k_ms = q_ms / max(n_q, 1)
     props = torch.cuda.get_device_properties(dev)
@@ -417,7 +427,11 @@ def run_query(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg["name"], "superquadrics": int(prims["means"].shape[0]), "voxels": nvox,
                        "index_entries_P": P, "tau": 0.05, "l2": "flushed (256 MB write) between timed steps"},
-            "gpu_launches": launches + dropped, "kernel_ms_per_launch": {"k_query": k_ms},
+            "gpu_launches": launches + dropped, "kernel_ms_per_launch": {"k_query": k_ms, "k_query_bwd": kb_ms},
+            "backward": {"ms_per_step": ms_bwd, "value": nvox / (ms_bwd / 1e3), "unit": "voxels/s",
+                         "roofline": {"bound": "alu", "kernel": "k_query_bwd",
+                                      "achieved": P * 13 / (kb_ms / 1e3) / 1e9, "peak": peak, "unit": "GMUFUop/s",
+                                      "frac": P * 13 / (kb_ms / 1e3) / 1e9 / peak}},
             "roofline": {"bound": "alu", "kernel": "k_query", "achieved": achieved, "peak": peak, "unit": "GMUFUop/s",
                          "frac": achieved / peak, "traffic": None},
             "hbm": {"kernel": "k_query", "bound": "hbm", "algorithmic_bytes": out_bytes + 4 * P + 8 * nvox,

@@ -281,6 +281,19 @@ sq_status_t sq_query_grid(const sq_prims_t* prims, const sq_index_t* index, cons
                           float* density, float* sem, unsigned char* label, void* workspace, size_t workspace_bytes,
                           void* stream);
 
+/* Backward of sq_query_grid (differentiable voxelisation, the next step the
+ * paper's NYUv2 voxel losses ask for; Supp. A.4): given dL/d density [nvox] and
+ * dL/d sem [nvox, n_classes] (device FP32, all voxels), overwrites g_means [n,3],
+ * g_quats [n,4] (raw quaternion), g_scales [n,3], g_eps [n,2], g_opacity [n],
+ * g_logits [n, n_classes] with dL/d(parameter), the index held fixed.  Per pair
+ * (voxel v, k in Q(v)): dL/dp_o = gd[v] sigma_k + <gs[v], c_k>.  Labels are not
+ * differentiable.  Workspace: sq_workspace_size(SQ_OP_QUERY, ...).  Runs no
+ * work (zero gradients) while the index status is non-zero. */
+sq_status_t sq_query_grid_bwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
+                              const float* grad_density, const float* grad_sem, float* g_means, float* g_quats,
+                              float* g_scales, float* g_eps, float* g_opacity, float* g_logits, void* workspace,
+                              size_t workspace_bytes, void* stream);
+
 /* Training loss of Supp. A.5 (Eq. 8) and its gradient w.r.t. the rendered maps:
  *   L = lambda_s * mean_r CE(softmax(sem[r]), label[r]) + lambda_d * mean_r (depth[r] - target[r])^2.
  * Writes loss (device scalar, overwritten), grad_depth [R], grad_sem [R, C].

@@ -173,6 +173,28 @@ def trace_ray(prims, grid, index, rig, t, ray, kappa=0.0, alpha_max=1.0):
     return {"alpha": alpha, "ssum": ssum, "T": T, "vox": vox, "xyz": xyz, "used": used}
 
 
+def query_grid_bwd(prims, grid, index, grad_density, grad_sem, voxel_ids=None):
+    """Gradient of sum(gd * density) + sum(gs * sem) of the grid query over the
+    listed voxels (None: all, gd/gs in voxel order) w.r.t. every parameter."""
+    P = prims
+    n, C = P["logits"].shape
+    gn, glo, gvs = _grid_args(grid)
+    nvox = int(np.prod(grid["n"]))
+    V = nvox if voxel_ids is None else len(voxel_ids)
+    ids = None if voxel_ids is None else np.ascontiguousarray(voxel_ids, np.int64)
+    v_sq = index["v_sq"] if index["v_sq"].size else np.zeros(1, np.int32)
+    keep = [_f32(P["means"]), _f32(P["quats"]), _f32(P["scales"]), _f32(P["eps"]), _f32(P["opacity"]),
+            _f32(P["logits"]), gn, glo, gvs, _i32(index["v_n"]), _i32(index["v_f"]), _i32(v_sq)]
+    gd = np.ascontiguousarray(grad_density, np.float64).reshape(V)
+    gs = np.ascontiguousarray(grad_sem, np.float64).reshape(V, C)
+    out = {"means": np.zeros((n, 3)), "quats": np.zeros((n, 4)), "scales": np.zeros((n, 3)), "eps": np.zeros((n, 2)),
+           "opacity": np.zeros(n), "logits": np.zeros((n, C))}
+    _load().orc_query_grid_bwd(ctypes.c_int(n), ctypes.c_int(C), *[_p(a) for a in keep], _p(ids),
+                               ctypes.c_longlong(V), _p(gd), _p(gs), _p(out["means"]), _p(out["quats"]),
+                               _p(out["scales"]), _p(out["eps"]), _p(out["opacity"]), _p(out["logits"]))
+    return out
+
+
 def ray_samples(K, c2w, u, v, t, grid):
     """FP32 sample positions and voxel ids (-1 outside) of pixel (u, v)."""
     gn, glo, gvs = _grid_args(grid)

@@ -681,6 +681,61 @@ int orc_query_grid(int n, int C, const float* means, const float* quats, const f
     return 0;
 }
 
+/* Gradient of sum_v gd[v] density[v] + sum_{v,c} gs[v,c] sem[v,c] over the listed
+ * voxels (voxel_ids NULL: every voxel; gd, gs indexed by position in that list)
+ * with respect to every primitive parameter, the index held fixed.  Per pair
+ * (voxel v, k in Q(v)): dL/dp_o = gd sigma_k + <gs, c_k>, so
+ * dL/dtheta += -p_o dL/dp_o df/dtheta, dL/dsigma_k += gd p_o and
+ * dL/dc_k += gs p_o.  Serial, outputs overwritten. */
+int orc_query_grid_bwd(int n, int C, const float* means, const float* quats, const float* scales, const float* eps,
+                       const float* opacity, const float* logits, const int* gn, const float* glo, const float* gvs,
+                       const int* v_n, const int* v_f, const int* v_sq, const long long* voxel_ids, long long n_sel,
+                       const double* gd, const double* gs, double* g_means, double* g_quats, double* g_scales,
+                       double* g_eps, double* g_opacity, double* g_logits) {
+    ogrid_t g = make_grid(gn, glo, gvs);
+    long long nvox = (long long)gn[0] * gn[1] * gn[2];
+    long long total = voxel_ids ? n_sel : nvox;
+    memset(g_means, 0, sizeof(double) * 3 * n);
+    memset(g_quats, 0, sizeof(double) * 4 * n);
+    memset(g_scales, 0, sizeof(double) * 3 * n);
+    memset(g_eps, 0, sizeof(double) * 2 * n);
+    memset(g_opacity, 0, sizeof(double) * n);
+    memset(g_logits, 0, sizeof(double) * (size_t)n * C);
+    for (long long i = 0; i < total; ++i) {
+        long long v = voxel_ids ? voxel_ids[i] : i;
+        int iz = (int)(v % gn[2]);
+        int iy = (int)((v / gn[2]) % gn[1]);
+        int ix = (int)(v / ((long long)gn[1] * gn[2]));
+        int id[3] = {ix, iy, iz};
+        double x[3];
+        for (int a = 0; a < 3; ++a) {
+            float c = (float)id[a] + 0.5f;
+            float cv = c * g.vs[a];
+            float xf = g.lo[a] + cv;
+            x[a] = xf;
+        }
+        const double* GS = gs + (size_t)i * C;
+        int beg = v_f[v], cnt = v_n[v];
+        for (int e = 0; e < cnt; ++e) {
+            int k = v_sq[beg + e];
+            oprim_t p = load_prim(k, C, means, quats, scales, eps, opacity, logits);
+            double gm[3], gq[4], gsc[3], ge[2];
+            double f = sq_f_grad(&p, x, gm, gq, gsc, ge);
+            double po = exp(-f);
+            double cd = 0.0;
+            for (int c = 0; c < C; ++c) cd += GS[c] * (double)p.c[c];
+            double gf = -po * (gd[i] * p.sigma + cd);
+            for (int a = 0; a < 3; ++a) g_means[3 * k + a] += gf * gm[a];
+            for (int a = 0; a < 4; ++a) g_quats[4 * k + a] += gf * gq[a];
+            for (int a = 0; a < 3; ++a) g_scales[3 * k + a] += gf * gsc[a];
+            for (int a = 0; a < 2; ++a) g_eps[2 * k + a] += gf * ge[a];
+            g_opacity[k] += gd[i] * po;
+            for (int c = 0; c < C; ++c) g_logits[(size_t)k * C + c] += GS[c] * po;
+        }
+    }
+    return 0;
+}
+
 /* FP32 sample positions and voxel ids of one ray (the discrete rule alone). */
 void orc_ray_samples(const float* K, const float* c2w, int u, int v, int L, const float* t, const int* gn,
                      const float* glo, const float* gvs, float* xyz, long long* vox) {

@@ -114,6 +114,8 @@ sq_status_t render_bwd_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_
                             size_t, const float*, const float*, float*, float*, float*, float*, float*, float*, void*,
                             size_t, cudaStream_t);
 size_t saved_size(const sq_rays_t* r, int n_classes);
+sq_status_t query_grid_bwd_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, const float*, const float*,
+                                float*, float*, float*, float*, float*, float*, void*, size_t, cudaStream_t);
 sq_status_t query_grid_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, float, float*, float*,
                             unsigned char*, void*, size_t, cudaStream_t);
 sq_status_t count_pairs_impl(const sq_index_t*, const sq_grid_t*, const sq_rays_t*, long long*, cudaStream_t);
@@ -288,6 +290,26 @@ sq_status_t sq_query_grid(const sq_prims_t* prims, const sq_index_t* index, cons
     if (!density || !sem) { set_last_error("sq_query_grid: output is NULL"); return SQ_ERR_INVALID_ARG; }
     if (label && prims->n_classes > 255) { set_last_error("labels need n_classes <= 255"); return SQ_ERR_INVALID_ARG; }
     return query_grid_impl(prims, index, grid, tau, density, sem, label, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+sq_status_t sq_query_grid_bwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
+                              const float* grad_density, const float* grad_sem, float* g_means, float* g_quats,
+                              float* g_scales, float* g_eps, float* g_opacity, float* g_logits, void* ws,
+                              size_t ws_bytes, void* stream) {
+    sq_status_t s;
+    if ((s = check_prims(prims)) != SQ_OK) return s;
+    if ((s = check_grid(grid)) != SQ_OK) return s;
+    if ((s = check_index(index, grid, prims->n)) != SQ_OK) return s;
+    if (!grad_density || !grad_sem) {
+        set_last_error("sq_query_grid_bwd: a cotangent is NULL");
+        return SQ_ERR_INVALID_ARG;
+    }
+    if (prims->n > 0 && (!g_means || !g_quats || !g_scales || !g_eps || !g_opacity || !g_logits)) {
+        set_last_error("sq_query_grid_bwd: a gradient output is NULL");
+        return SQ_ERR_INVALID_ARG;
+    }
+    return query_grid_bwd_impl(prims, index, grid, grad_density, grad_sem, g_means, g_quats, g_scales, g_eps,
+                               g_opacity, g_logits, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 sq_status_t sq_loss_ce_mse(const float* depth, const float* sem, const float* target_depth, const int* target_label,

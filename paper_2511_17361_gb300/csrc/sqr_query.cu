@@ -7,7 +7,15 @@
 // voxels with near-identical lists and the primitive gathers hit L1).  The
 // per-voxel semantic row is staged in shared memory so that the [nvox, C] output
 // is written with coalesced stores.
-#include "sqr_common.cuh"
+//
+// The backward (gradients of a loss on density and semantics) is primitive-major:
+// primitive k is listed in exactly the voxels of its range, so one warp walks
+// that range, sums dL/dp_o dp_o/dtheta over it in registers and writes the
+// primitive's row of raw sums once (no atomics); k_grad_out converts the rows.
+#include <string.h>
+
+#include "sqr_pair.cuh"
+#include "sqr_render.cuh"
 
 namespace sqr {
 
@@ -95,6 +103,105 @@ __global__ void __launch_bounds__(Q_THREADS) k_query(QueryArgs a) {
     }
 }
 
+constexpr int QB_THREADS = 256;
+
+struct QueryBwdArgs {
+    const float4* rec;
+    const float4* aux;
+    const float* lpad;
+    const int* ranges;
+    const int* status;
+    GridC g;
+    int n, C;
+    const float* grad_density;
+    const float* grad_sem;
+    float* gacc;  // [n, GF] raw sums, every row written
+    int* ctr;     // zeroed primitive counter
+};
+
+// One warp per primitive (drawn from a counter): over the voxels v of its range,
+// dL/dp_o = gd[v] sigma + <gs[v], c>; the row gets the 11 summed partials of f
+// weighted by -p_o dL/dp_o, sum gd p_o (opacity) and sum p_o gs[v, c] (logits).
+template <int CP>
+__global__ void __launch_bounds__(QB_THREADS) k_query_bwd(QueryBwdArgs a) {
+    const int lane = threadIdx.x & 31;
+    const bool ok = *a.status == SQ_OK;
+    const int ny = a.g.n[1], nz = a.g.n[2];
+    for (;;) {
+        int kk = 0;
+        if (lane == 0) kk = atomicAdd(a.ctr, 1);
+        const int k = __shfl_sync(0xffffffffu, kk, 0);
+        if (k >= a.n) break;
+        const int* r = a.ranges + 6 * k;
+        const int i0 = __ldg(r), i1 = __ldg(r + 1), j0 = __ldg(r + 2), j1 = __ldg(r + 3), k0 = __ldg(r + 4),
+                  k1 = __ldg(r + 5);
+        const int nxb = i1 - i0 + 1, nyb = j1 - j0 + 1, nzb = k1 - k0 + 1;
+        const long long nvb = (ok && nxb > 0 && nyb > 0 && nzb > 0) ? (long long)nxb * nyb * nzb : 0;
+        float acc[NRAW];
+        float accl[CP];
+#pragma unroll
+        for (int i = 0; i < NRAW; ++i) acc[i] = 0.f;
+#pragma unroll
+        for (int c = 0; c < CP; ++c) accl[c] = 0.f;
+        if (nvb > 0) {
+            const BwdPrim P = load_bwd(a.rec, a.aux, k);
+            float cl[CP];
+            const float4* cr = reinterpret_cast<const float4*>(a.lpad) + (size_t)k * (CP / 4);
+#pragma unroll
+            for (int q = 0; q < CP / 4; ++q) {
+                const float4 c4 = __ldg(cr + q);
+                cl[4 * q] = c4.x;
+                cl[4 * q + 1] = c4.y;
+                cl[4 * q + 2] = c4.z;
+                cl[4 * q + 3] = c4.w;
+            }
+            for (long long t = lane; t < nvb; t += 32) {
+                const int iz = k0 + (int)(t % nzb);
+                const long long rest = t / nzb;
+                const int iy = j0 + (int)(rest % nyb), ix = i0 + (int)(rest / nyb);
+                const long long v = ((long long)ix * ny + iy) * nz + iz;
+                const int id[3] = {ix, iy, iz};
+                float x[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    x[i] = __fadd_rn(a.g.lo[i], __fmul_rn(__fadd_rn(__int2float_rn(id[i]), 0.5f), a.g.vs[i]));
+                const float gd = __ldg(a.grad_density + v);
+                float gs[CP];
+                float cd = 0.f;
+#pragma unroll
+                for (int c = 0; c < CP; ++c) {
+                    gs[c] = c < a.C ? __ldg(a.grad_sem + v * a.C + c) : 0.f;
+                    cd = fmaf(gs[c], cl[c], cd);
+                }
+                float pr[11];
+                const float po = occupancy_partials(P, x, pr);
+                if (po != 0.f) {
+                    const float gf = -po * fmaf(gd, P.f.sigma, cd);
+#pragma unroll
+                    for (int i = 0; i < 11; ++i) acc[i] = fmaf(gf, pr[i], acc[i]);
+                    acc[11] = fmaf(gd, po, acc[11]);
+#pragma unroll
+                    for (int c = 0; c < CP; ++c) accl[c] = fmaf(po, gs[c], accl[c]);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int i = 0; i < NRAW; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+#pragma unroll
+            for (int c = 0; c < CP; ++c) accl[c] += __shfl_xor_sync(0xffffffffu, accl[c], o);
+        }
+        float* row = a.gacc + (size_t)k * GF;
+#pragma unroll
+        for (int i = 0; i < NRAW; ++i)
+            if (lane == i) row[i] = acc[i];
+#pragma unroll
+        for (int c = 0; c < CP; ++c)
+            if (lane == c && c < a.C) row[NRAW + c] = accl[c];
+    }
+}
+
 }  // namespace
 
 size_t render_workspace_size(const sq_prims_t* p);
@@ -148,6 +255,81 @@ sq_status_t query_grid_impl(const sq_prims_t* prims, const sq_index_t* idx, cons
         case 32: return launch_query_cp<32>(a, st);
         default: return SQ_ERR_INVALID_ARG;
     }
+}
+
+template <int CP>
+static sq_status_t launch_query_bwd_cp(const QueryBwdArgs& a, cudaStream_t st) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query_bwd<CP>, QB_THREADS, 0);
+    if (e != cudaSuccess) return cuda_status(e, "k_query_bwd occupancy");
+    long long blocks = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    const long long need = (a.n + QB_THREADS / 32 - 1) / (QB_THREADS / 32);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    SQ_LAUNCH("k_query_bwd", st, k_query_bwd<CP><<<(int)blocks, QB_THREADS, 0, st>>>(a));
+    return SQ_OK;
+}
+
+// Workspace of the query backward: records, backward extras, padded logits, the
+// accumulator rows and a counter (within render_workspace_size).
+sq_status_t query_grid_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, const sq_grid_t* grid,
+                                const float* grad_density, const float* grad_sem, float* g_means, float* g_quats,
+                                float* g_scales, float* g_eps, float* g_opacity, float* g_logits, void* ws,
+                                size_t ws_bytes, cudaStream_t st) {
+    const size_t need = render_workspace_size(prims);
+    if (ws == nullptr || ws_bytes < need) {
+        set_last_error("sq_query_grid_bwd: workspace of %zu bytes given, %zu needed", ws_bytes, need);
+        return SQ_ERR_INVALID_ARG;
+    }
+    const int n = prims->n, cp = cpad(prims->n_classes);
+    if (n == 0) return SQ_OK;
+    char* base = (char*)ws;
+    size_t at = 0;
+    float4* rec = (float4*)(base + at);
+    at = align_up(at + (size_t)n * REC4 * sizeof(float4), 256);
+    float4* aux = (float4*)(base + at);
+    at = align_up(at + (size_t)n * AUX4 * sizeof(float4), 256);
+    float* lpad = (float*)(base + at);
+    at = align_up(at + (size_t)n * cp * sizeof(float), 256);
+    float* gacc = (float*)(base + at);
+    at = align_up(at + (size_t)n * GF * sizeof(float), 256);
+    int* ctr = (int*)(base + at);
+    sq_status_t s = launch_pack(prims, rec, aux, lpad, cp, st);
+    if (s != SQ_OK) return s;
+    cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_status(e, "memset counter");
+    QueryBwdArgs a;
+    a.rec = rec;
+    a.aux = aux;
+    a.lpad = lpad;
+    a.ranges = idx->ranges;
+    a.status = idx->status;
+    a.g = make_grid(grid);
+    a.n = n;
+    a.C = prims->n_classes;
+    a.grad_density = grad_density;
+    a.grad_sem = grad_sem;
+    a.gacc = gacc;
+    a.ctr = ctr;
+    switch (cp) {
+        case 4: s = launch_query_bwd_cp<4>(a, st); break;
+        case 8: s = launch_query_bwd_cp<8>(a, st); break;
+        case 12: s = launch_query_bwd_cp<12>(a, st); break;
+        case 16: s = launch_query_bwd_cp<16>(a, st); break;
+        case 20: s = launch_query_bwd_cp<20>(a, st); break;
+        case 24: s = launch_query_bwd_cp<24>(a, st); break;
+        case 28: s = launch_query_bwd_cp<28>(a, st); break;
+        case 32: s = launch_query_bwd_cp<32>(a, st); break;
+        default: return SQ_ERR_INVALID_ARG;
+    }
+    if (s != SQ_OK) return s;
+    SceneDesc S;
+    memset(&S, 0, sizeof(S));
+    S.gacc = gacc;
+    S.aux = aux;
+    S.n = n;
+    S.C = prims->n_classes;
+    return launch_grad_out(S, g_means, g_quats, g_scales, g_eps, g_opacity, g_logits, st);
 }
 
 }  // namespace sqr

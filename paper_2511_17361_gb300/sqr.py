@@ -98,6 +98,9 @@ def _load():
     lib.sq_status_string.restype = ctypes.c_char_p
     lib.sq_status_string.argtypes = [ctypes.c_int]
     lib.sq_last_error.restype = ctypes.c_char_p
+    lib.sq_query_grid_bwd.restype = ctypes.c_int
+    lib.sq_query_grid_bwd.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                      _vp, ctypes.c_size_t, _vp]
     lib.sq_profile_enable.restype = ctypes.c_int
     lib.sq_profile_enable.argtypes = [ctypes.c_int]
     lib.sq_profile_query.restype = ctypes.c_int
@@ -335,6 +338,23 @@ def query_grid(prims: dict, index: Index, grid: dict, tau: float = 0.05, with_la
     _check(lib.sq_query_grid(ctypes.byref(p), ctypes.byref(ix), ctypes.byref(g), tau, _ptr(dens), _ptr(sem),
                              _ptr(lab), _ptr(ws), ws.numel(), _stream()), "sq_query_grid")
     return dens, sem, lab
+
+
+def query_grid_bwd(prims: dict, index: Index, grid: dict, grad_density, grad_sem, out=None) -> dict:
+    """Gradients of sum(gd * density) + sum(gs * sem) of the grid query w.r.t.
+    every parameter (index held fixed)."""
+    device = prims["means"].device
+    grad_density = _need_cuda_f32(grad_density.contiguous(), "grad_density")
+    grad_sem = _need_cuda_f32(grad_sem.contiguous(), "grad_sem")
+    if out is None:
+        out = {k: torch.empty_like(prims[k]) for k in PRIM_KEYS}
+    p, g, ix = prims_struct(prims), grid_struct(grid), index.struct()
+    wsz = lib.sq_workspace_size(SQ_OP_QUERY, ctypes.byref(p), ctypes.byref(g), None)
+    ws = _ws.get("query", wsz, device)
+    _check(lib.sq_query_grid_bwd(ctypes.byref(p), ctypes.byref(ix), ctypes.byref(g), _ptr(grad_density),
+                                 _ptr(grad_sem), *[_ptr(out[k]) for k in PRIM_KEYS], _ptr(ws), ws.numel(),
+                                 _stream()), "sq_query_grid_bwd")
+    return out
 
 
 def loss_ce_mse(depth, sem, target_depth, target_label, lambda_s=2.0, lambda_d=0.05, out=None):
