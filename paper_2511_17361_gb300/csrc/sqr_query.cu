@@ -9,9 +9,10 @@
 // is written with coalesced stores.
 //
 // The backward (gradients of a loss on density and semantics) is primitive-major:
-// primitive k is listed in exactly the voxels of its range, so one warp walks
-// that range, sums dL/dp_o dp_o/dtheta over it in registers and writes the
-// primitive's row of raw sums once (no atomics); k_grad_out converts the rows.
+// primitive k is listed in exactly the voxels of its range, so a warp walks one
+// of QB_SPLIT equal chunks of that range, sums dL/dp_o dp_o/dtheta over it in
+// registers and adds its sums to the primitive's row once (one coalesced atomic
+// add per chunk); k_grad_out converts the rows.
 #include <string.h>
 
 #include "sqr_pair.cuh"
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(Q_THREADS) k_query(QueryArgs a) {
 }
 
 constexpr int QB_THREADS = 256;
+constexpr int QB_SPLIT = 8;  // chunks per primitive range (ranges differ widely in size)
 
 struct QueryBwdArgs {
     const float4* rec;
@@ -115,35 +117,39 @@ struct QueryBwdArgs {
     int n, C;
     const float* grad_density;
     const float* grad_sem;
-    float* gacc;  // [n, GF] raw sums, every row written
-    int* ctr;     // zeroed primitive counter
+    float* gacc;  // [n, GF] raw sums, zeroed
+    int* ctr;     // zeroed work counter over (primitive, chunk)
 };
 
-// One warp per primitive (drawn from a counter): over the voxels v of its range,
-// dL/dp_o = gd[v] sigma + <gs[v], c>; the row gets the 11 summed partials of f
-// weighted by -p_o dL/dp_o, sum gd p_o (opacity) and sum p_o gs[v, c] (logits).
+// One warp per (primitive, chunk of its range), drawn from a counter: over the
+// voxels v of the chunk, dL/dp_o = gd[v] sigma + <gs[v], c>; the row gets the 11
+// summed partials of f weighted by -p_o dL/dp_o, sum gd p_o (opacity) and
+// sum p_o gs[v, c] (logits).
 template <int CP>
 __global__ void __launch_bounds__(QB_THREADS) k_query_bwd(QueryBwdArgs a) {
     const int lane = threadIdx.x & 31;
     const bool ok = *a.status == SQ_OK;
     const int ny = a.g.n[1], nz = a.g.n[2];
     for (;;) {
-        int kk = 0;
-        if (lane == 0) kk = atomicAdd(a.ctr, 1);
-        const int k = __shfl_sync(0xffffffffu, kk, 0);
-        if (k >= a.n) break;
+        int ww = 0;
+        if (lane == 0) ww = atomicAdd(a.ctr, 1);
+        const int w = __shfl_sync(0xffffffffu, ww, 0);
+        if (w >= a.n * QB_SPLIT) break;
+        const int k = w / QB_SPLIT, part = w - k * QB_SPLIT;
         const int* r = a.ranges + 6 * k;
         const int i0 = __ldg(r), i1 = __ldg(r + 1), j0 = __ldg(r + 2), j1 = __ldg(r + 3), k0 = __ldg(r + 4),
                   k1 = __ldg(r + 5);
         const int nxb = i1 - i0 + 1, nyb = j1 - j0 + 1, nzb = k1 - k0 + 1;
         const long long nvb = (ok && nxb > 0 && nyb > 0 && nzb > 0) ? (long long)nxb * nyb * nzb : 0;
+        const long long t_beg = nvb * part / QB_SPLIT, t_end = nvb * (part + 1) / QB_SPLIT;
+        if (t_beg >= t_end) continue;
         float acc[NRAW];
         float accl[CP];
 #pragma unroll
         for (int i = 0; i < NRAW; ++i) acc[i] = 0.f;
 #pragma unroll
         for (int c = 0; c < CP; ++c) accl[c] = 0.f;
-        if (nvb > 0) {
+        {
             const BwdPrim P = load_bwd(a.rec, a.aux, k);
             float cl[CP];
             const float4* cr = reinterpret_cast<const float4*>(a.lpad) + (size_t)k * (CP / 4);
@@ -155,7 +161,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_bwd(QueryBwdArgs a) {
                 cl[4 * q + 2] = c4.z;
                 cl[4 * q + 3] = c4.w;
             }
-            for (long long t = lane; t < nvb; t += 32) {
+            for (long long t = t_beg + lane; t < t_end; t += 32) {
                 const int iz = k0 + (int)(t % nzb);
                 const long long rest = t / nzb;
                 const int iy = j0 + (int)(rest % nyb), ix = i0 + (int)(rest / nyb);
@@ -193,12 +199,17 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_bwd(QueryBwdArgs a) {
             for (int c = 0; c < CP; ++c) accl[c] += __shfl_xor_sync(0xffffffffu, accl[c], o);
         }
         float* row = a.gacc + (size_t)k * GF;
+        float v0 = 0.f, v1 = 0.f;  // lane f adds field f and f + 32
 #pragma unroll
         for (int i = 0; i < NRAW; ++i)
-            if (lane == i) row[i] = acc[i];
+            if (lane == i) v0 = acc[i];
 #pragma unroll
-        for (int c = 0; c < CP; ++c)
-            if (lane == c && c < a.C) row[NRAW + c] = accl[c];
+        for (int c = 0; c < CP; ++c) {
+            if (lane == NRAW + c) v0 = accl[c];
+            if (lane + 32 == NRAW + c) v1 = accl[c];
+        }
+        if (lane < NRAW + a.C && v0 != 0.f) red_add(row + lane, v0);
+        if (lane + 32 < NRAW + a.C && v1 != 0.f) red_add(row + 32 + lane, v1);
     }
 }
 
@@ -263,7 +274,7 @@ static sq_status_t launch_query_bwd_cp(const QueryBwdArgs& a, cudaStream_t st) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query_bwd<CP>, QB_THREADS, 0);
     if (e != cudaSuccess) return cuda_status(e, "k_query_bwd occupancy");
     long long blocks = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
-    const long long need = (a.n + QB_THREADS / 32 - 1) / (QB_THREADS / 32);
+    const long long need = ((long long)a.n * QB_SPLIT + QB_THREADS / 32 - 1) / (QB_THREADS / 32);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     SQ_LAUNCH("k_query_bwd", st, k_query_bwd<CP><<<(int)blocks, QB_THREADS, 0, st>>>(a));
@@ -298,6 +309,8 @@ sq_status_t query_grid_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, 
     if (s != SQ_OK) return s;
     cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "memset counter");
+    e = cudaMemsetAsync(gacc, 0, (size_t)n * GF * sizeof(float), st);
+    if (e != cudaSuccess) return cuda_status(e, "memset accumulator");
     QueryBwdArgs a;
     a.rec = rec;
     a.aux = aux;
