@@ -467,6 +467,30 @@ def test_query_backward_sparse_large(sqr):
         check_grad(got[k].cpu().numpy(), ref[k], k)
 
 
+def test_kernel_timing_records_every_launch(sqr):
+    """sq_profile_*: while enabled, every launch of the library is recorded with a
+    positive duration on its stream; disabled, nothing is recorded."""
+    cfg = synth.make_config(0)
+    prims_d, rays = scene_to_gpu(sqr, cfg["prims"], cfg["rig"], cfg["t"])
+    g = dev_grid(cfg["grid"])
+    ix = sqr.build_index(prims_d, g)
+    sqr.profile_enable(True)
+    sqr.build_index(prims_d, g, index=ix, sync=False)  # 9 kernels
+    sqr.render_fwd(prims_d, ix, g, rays)  # pack, descriptors, forward
+    torch.cuda.synchronize()
+    sqr.profile_enable(False)
+    n_all, ms_all, dropped = sqr.profile_query(None)
+    n_fwd, ms_fwd, _ = sqr.profile_query("k_forward")
+    assert (n_all, dropped) == (12, 0) and n_fwd == 1
+    assert 0.0 < ms_fwd < ms_all
+    sqr.render_fwd(prims_d, ix, g, rays)
+    torch.cuda.synchronize()
+    assert sqr.profile_query(None)[0] == 12  # disabled: unchanged
+    sqr.profile_enable(True)
+    assert sqr.profile_query(None)[0] == 0  # enabling clears
+    sqr.profile_enable(False)
+
+
 # ----------------------------------------------------------------------- loss
 def test_loss_kernel_matches_torch(sqr):
     rng = np.random.default_rng(0)
