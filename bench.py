@@ -35,14 +35,23 @@ MUFU_PER_PAIR = {"fwd": 9, "bwd": 13}  # SFU ops per (sample, primitive) pair in
 # DRAM traffic per launch from the committed ncu summaries, valid only while the
 # kernel source is unchanged (sha256 of the file holding it).
 NCU_TRAFFIC = {
-    "k_backward": {"src": "sqr_bwd.cu", "src_sha": "c9aa43d605221735", "bytes_per_launch": 309531136},
-    "k_forward": {"src": "sqr_fwd.cu", "src_sha": "bbf4eba00091e5d5", "bytes_per_launch": 1716526336},
-    "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "c9aa43d605221735", "bytes_per_launch": 1938757120},
+    "k_backward": {"src": "sqr_bwd.cu", "src_sha": "b7f4511792737268", "bytes_per_launch": 309358336},
+    "k_forward": {"src": "sqr_fwd.cu", "src_sha": "bbf4eba00091e5d5", "bytes_per_launch": 1718119936},
+    "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "b7f4511792737268", "bytes_per_launch": 1938899200},
+    "k_query": {"src": "sqr_query.cu", "src_sha": "47dc05a1936a09f9", "bytes_per_launch": 176217856},
 }
 
 
 def _sha(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, None once the source changed."""
+    tr = NCU_TRAFFIC.get(kernel)
+    if tr and tr["src_sha"] == _sha(os.path.join(ROOT, "paper_2511_17361_gb300", "csrc", tr["src"])):
+        return tr["bytes_per_launch"]
+    return None
 
 
 def _env_rank():
@@ -433,7 +442,7 @@ def run_query(args):
                                       "achieved": P * 13 / (kb_ms / 1e3) / 1e9, "peak": peak, "unit": "GMUFUop/s",
                                       "frac": P * 13 / (kb_ms / 1e3) / 1e9 / peak}},
             "roofline": {"bound": "alu", "kernel": "k_query", "achieved": achieved, "peak": peak, "unit": "GMUFUop/s",
-                         "frac": achieved / peak, "traffic": None},
+                         "frac": achieved / peak, "traffic": _traffic("k_query")},
             "hbm": {"kernel": "k_query", "bound": "hbm", "algorithmic_bytes": out_bytes + 4 * P + 8 * nvox,
                     "achieved_GBps": (out_bytes + 4 * P + 8 * nvox) / (k_ms / 1e3) / 1e9,
                     "frac": (out_bytes + 4 * P + 8 * nvox) / (k_ms / 1e3) / 1e9 / hbm_peak, "peak_gbs": hbm_peak},
