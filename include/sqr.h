@@ -78,7 +78,12 @@ typedef struct {
     const float* logits;
     int n;         /* >= 0 */
     int n_classes; /* 1 .. SQ_MAX_CLASSES */
+    int sem_mode;  /* SQ_SEM_RAW: c_k as given (Eq. 4, the default); SQ_SEM_SOFTMAX:
+                      c_k replaced by softmax(c_k) over the classes of each primitive
+                      (g_logits are then w.r.t. the raw logits, through the softmax) */
 } sq_prims_t;
+
+enum { SQ_SEM_RAW = 0, SQ_SEM_SOFTMAX = 1 };
 
 /* How a primitive's voxel neighbourhood is chosen (Sec. 3.3.1).
  *  SQ_INDEX_OBB:  the world AABB of the oriented box that holds the level set

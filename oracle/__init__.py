@@ -65,6 +65,10 @@ def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
 
 
+def _f64(a):
+    return np.ascontiguousarray(a, np.float64)
+
+
 def _i32(a):
     return np.ascontiguousarray(a, dtype=np.int32)
 
@@ -121,13 +125,40 @@ def build_index(prims, grid, mode=0, tau_cut=0.01, nv=5) -> dict:
 
 
 # ----------------------------------------------------------------------- render
+def _softmax_rows(x):
+    x = np.asarray(x, np.float32).astype(np.float64)  # the parameters are FP32
+    e = np.exp(x - x.max(1, keepdims=True))
+    return e / e.sum(1, keepdims=True)
+
+
+def _semantic(prims, sem_mode):
+    """The prims as the renderer sees them, class vectors in FP64: the FP32 logits
+    (sem_mode 0, Eq. 4) or, with sem_mode 1 (per-primitive softmax), every
+    primitive's softmax over the classes of those logits."""
+    out = dict(prims)
+    if sem_mode == 0:
+        out["logits"] = np.asarray(prims["logits"], np.float32).astype(np.float64)
+    else:
+        assert sem_mode == 1, sem_mode
+        out["logits"] = _softmax_rows(prims["logits"])
+    return out
+
+
+def _logit_grad(prims, sem_mode, g):
+    """Logit gradient w.r.t. the raw logits: through s = softmax(c), s * (g - <g, s>)."""
+    if sem_mode == 0:
+        return g
+    s = _softmax_rows(prims["logits"])
+    return s * (g - (g * s).sum(1, keepdims=True))
+
+
 def _scene_args(prims, grid, index, rig, t):
     P = prims
     n, C = P["logits"].shape
     gn, glo, gvs = _grid_args(grid)
     v_sq = index["v_sq"] if index["v_sq"].size else np.zeros(1, np.int32)
     keep = [_f32(P["means"]), _f32(P["quats"]), _f32(P["scales"]), _f32(P["eps"]), _f32(P["opacity"]),
-            _f32(P["logits"]), gn, glo, gvs, _i32(index["v_n"]), _i32(index["v_f"]), _i32(v_sq),
+            _f64(P["logits"]), gn, glo, gvs, _i32(index["v_n"]), _i32(index["v_f"]), _i32(v_sq),
             _f32(rig["K"]), _f32(rig["cam2world"]), _f32(t)]
     args = [ctypes.c_int(n), ctypes.c_int(C)] + [_p(a) for a in keep[:12]] + [
         ctypes.c_int(rig["n_cam"]), ctypes.c_int(rig["H"]), ctypes.c_int(rig["W"]), _p(keep[12]), _p(keep[13]),
@@ -135,9 +166,9 @@ def _scene_args(prims, grid, index, rig, t):
     return args, keep, C
 
 
-def render_fwd(prims, grid, index, rig, t, kappa=0.0, alpha_max=1.0, ray_ids=None, threads=0):
+def render_fwd(prims, grid, index, rig, t, kappa=0.0, alpha_max=1.0, ray_ids=None, threads=0, sem_mode=0):
     """Eq. 4-6 per ray: returns depth [R], sem [R, C], t_final [R], n_used [R]."""
-    args, keep, C = _scene_args(prims, grid, index, rig, t)
+    args, keep, C = _scene_args(_semantic(prims, sem_mode), grid, index, rig, t)
     R = rig["n_cam"] * rig["H"] * rig["W"] if ray_ids is None else len(ray_ids)
     ids = None if ray_ids is None else np.ascontiguousarray(ray_ids, np.int64)
     depth = np.zeros(R); sem = np.zeros((R, C)); tf = np.zeros(R); nu = np.zeros(R, np.int32)
@@ -146,8 +177,11 @@ def render_fwd(prims, grid, index, rig, t, kappa=0.0, alpha_max=1.0, ray_ids=Non
     return depth, sem, tf, nu
 
 
-def render_bwd(prims, grid, index, rig, t, grad_depth, grad_sem, kappa=0.0, alpha_max=1.0, ray_ids=None, threads=0):
+def render_bwd(prims, grid, index, rig, t, grad_depth, grad_sem, kappa=0.0, alpha_max=1.0, ray_ids=None, threads=0,
+               sem_mode=0):
     """Gradient of sum(gD*D) + sum(gS*S) over the listed rays w.r.t. every parameter."""
+    raw = prims
+    prims = _semantic(prims, sem_mode)
     args, keep, C = _scene_args(prims, grid, index, rig, t)
     n = prims["means"].shape[0]
     R = rig["n_cam"] * rig["H"] * rig["W"] if ray_ids is None else len(ray_ids)
@@ -159,12 +193,13 @@ def render_bwd(prims, grid, index, rig, t, grad_depth, grad_sem, kappa=0.0, alph
     _load().orc_render_bwd(*args, ctypes.c_double(kappa), ctypes.c_double(alpha_max), _p(ids), ctypes.c_longlong(R),
                            _p(gd), _p(gs), _p(out["means"]), _p(out["quats"]), _p(out["scales"]), _p(out["eps"]),
                            _p(out["opacity"]), _p(out["logits"]), ctypes.c_int(threads))
+    out["logits"] = _logit_grad(raw, sem_mode, out["logits"])
     return out
 
 
-def trace_ray(prims, grid, index, rig, t, ray, kappa=0.0, alpha_max=1.0):
+def trace_ray(prims, grid, index, rig, t, ray, kappa=0.0, alpha_max=1.0, sem_mode=0):
     """Per-sample alpha, raw sum, T (length L+1), voxel ids and FP32 positions of one ray."""
-    args, keep, C = _scene_args(prims, grid, index, rig, t)
+    args, keep, C = _scene_args(_semantic(prims, sem_mode), grid, index, rig, t)
     L = len(t)
     alpha = np.zeros(L); ssum = np.zeros(L); T = np.zeros(L + 1); vox = np.zeros(L, np.int64)
     xyz = np.zeros((L, 3), np.float32)
@@ -173,10 +208,11 @@ def trace_ray(prims, grid, index, rig, t, ray, kappa=0.0, alpha_max=1.0):
     return {"alpha": alpha, "ssum": ssum, "T": T, "vox": vox, "xyz": xyz, "used": used}
 
 
-def query_grid_bwd(prims, grid, index, grad_density, grad_sem, voxel_ids=None):
+def query_grid_bwd(prims, grid, index, grad_density, grad_sem, voxel_ids=None, sem_mode=0):
     """Gradient of sum(gd * density) + sum(gs * sem) of the grid query over the
     listed voxels (None: all, gd/gs in voxel order) w.r.t. every parameter."""
-    P = prims
+    raw = prims
+    P = prims = _semantic(prims, sem_mode)
     n, C = P["logits"].shape
     gn, glo, gvs = _grid_args(grid)
     nvox = int(np.prod(grid["n"]))
@@ -184,7 +220,7 @@ def query_grid_bwd(prims, grid, index, grad_density, grad_sem, voxel_ids=None):
     ids = None if voxel_ids is None else np.ascontiguousarray(voxel_ids, np.int64)
     v_sq = index["v_sq"] if index["v_sq"].size else np.zeros(1, np.int32)
     keep = [_f32(P["means"]), _f32(P["quats"]), _f32(P["scales"]), _f32(P["eps"]), _f32(P["opacity"]),
-            _f32(P["logits"]), gn, glo, gvs, _i32(index["v_n"]), _i32(index["v_f"]), _i32(v_sq)]
+            _f64(P["logits"]), gn, glo, gvs, _i32(index["v_n"]), _i32(index["v_f"]), _i32(v_sq)]
     gd = np.ascontiguousarray(grad_density, np.float64).reshape(V)
     gs = np.ascontiguousarray(grad_sem, np.float64).reshape(V, C)
     out = {"means": np.zeros((n, 3)), "quats": np.zeros((n, 4)), "scales": np.zeros((n, 3)), "eps": np.zeros((n, 2)),
@@ -192,6 +228,7 @@ def query_grid_bwd(prims, grid, index, grad_density, grad_sem, voxel_ids=None):
     _load().orc_query_grid_bwd(ctypes.c_int(n), ctypes.c_int(C), *[_p(a) for a in keep], _p(ids),
                                ctypes.c_longlong(V), _p(gd), _p(gs), _p(out["means"]), _p(out["quats"]),
                                _p(out["scales"]), _p(out["eps"]), _p(out["opacity"]), _p(out["logits"]))
+    out["logits"] = _logit_grad(raw, sem_mode, out["logits"])
     return out
 
 
@@ -207,9 +244,9 @@ def ray_samples(K, c2w, u, v, t, grid):
     return xyz, vox
 
 
-def query_grid(prims, grid, index, tau=0.05, voxel_ids=None, threads=0):
+def query_grid(prims, grid, index, tau=0.05, voxel_ids=None, threads=0, sem_mode=0):
     """Supp. A.4 voxelisation: density [V], sem [V, C], label [V] (C = free)."""
-    P = prims
+    P = _semantic(prims, sem_mode)
     n, C = P["logits"].shape
     gn, glo, gvs = _grid_args(grid)
     nvox = int(np.prod(grid["n"]))
@@ -217,7 +254,7 @@ def query_grid(prims, grid, index, tau=0.05, voxel_ids=None, threads=0):
     ids = None if voxel_ids is None else np.ascontiguousarray(voxel_ids, np.int64)
     v_sq = index["v_sq"] if index["v_sq"].size else np.zeros(1, np.int32)
     keep = [_f32(P["means"]), _f32(P["quats"]), _f32(P["scales"]), _f32(P["eps"]), _f32(P["opacity"]),
-            _f32(P["logits"]), gn, glo, gvs, _i32(index["v_n"]), _i32(index["v_f"]), _i32(v_sq)]
+            _f64(P["logits"]), gn, glo, gvs, _i32(index["v_n"]), _i32(index["v_f"]), _i32(v_sq)]
     dens = np.zeros(V); sem = np.zeros((V, C)); lab = np.zeros(V, np.int32)
     _load().orc_query_grid(ctypes.c_int(n), ctypes.c_int(C), *[_p(a) for a in keep], ctypes.c_double(tau), _p(ids),
                            ctypes.c_longlong(V), _p(dens), _p(sem), _p(lab), ctypes.c_int(threads))

@@ -115,7 +115,7 @@ typedef struct {
     double s[3];
     double e1, e2;
     double sigma;
-    const float* c; /* C logits */
+    const double* c; /* C class values (FP64) */
 } oprim_t;
 
 /* Normalise q and form the Hamilton rotation matrix (local -> world). */
@@ -137,7 +137,7 @@ static void quat_rotation(const double q[4], double qn[4], double* qnorm, double
 }
 
 static oprim_t load_prim(int k, int C, const float* means, const float* quats, const float* scales,
-                         const float* eps, const float* opacity, const float* logits) {
+                         const float* eps, const float* opacity, const double* logits) {
     oprim_t p;
     for (int i = 0; i < 3; ++i) { p.m[i] = means[3 * k + i]; p.s[i] = scales[3 * k + i]; }
     for (int i = 0; i < 4; ++i) p.q[i] = quats[4 * k + i];
@@ -353,7 +353,8 @@ long long orc_index(int n, const int* ranges, const int* gn, int* v_n, int* v_f,
 
 typedef struct {
     int n, C;
-    const float *means, *quats, *scales, *eps, *opacity, *logits;
+    const float *means, *quats, *scales, *eps, *opacity;
+    const double* logits;
     ogrid_t g;
     const int *v_n, *v_f, *v_sq;
     int n_cam, H, W, L;
@@ -362,7 +363,7 @@ typedef struct {
 } oscene_t;
 
 static oscene_t make_scene(int n, int C, const float* means, const float* quats, const float* scales,
-                           const float* eps, const float* opacity, const float* logits, const int* gn,
+                           const float* eps, const float* opacity, const double* logits, const int* gn,
                            const float* glo, const float* gvs, const int* v_n, const int* v_f, const int* v_sq,
                            int n_cam, int H, int W, const float* K, const float* c2w, int L, const float* t,
                            double kappa, double alpha_max) {
@@ -463,7 +464,7 @@ static int set_threads(int n_threads) {
  * t_final = transmittance after the last composited sample, n_used = samples
  * composited. */
 int orc_render_fwd(int n, int C, const float* means, const float* quats, const float* scales, const float* eps,
-                   const float* opacity, const float* logits, const int* gn, const float* glo, const float* gvs,
+                   const float* opacity, const double* logits, const int* gn, const float* glo, const float* gvs,
                    const int* v_n, const int* v_f, const int* v_sq, int n_cam, int H, int W, const float* K,
                    const float* c2w, int L, const float* t, double kappa, double alpha_max, const long long* ray_ids,
                    long long n_rays, double* depth, double* sem, double* t_final, int* n_used, int n_threads) {
@@ -498,7 +499,7 @@ int orc_render_fwd(int n, int C, const float* means, const float* quats, const f
 /* Per-sample trace of one ray for tests: alpha, raw sum, T before each sample,
  * voxel id.  Returns samples composited. */
 int orc_trace_ray(int n, int C, const float* means, const float* quats, const float* scales, const float* eps,
-                  const float* opacity, const float* logits, const int* gn, const float* glo, const float* gvs,
+                  const float* opacity, const double* logits, const int* gn, const float* glo, const float* gvs,
                   const int* v_n, const int* v_f, const int* v_sq, int n_cam, int H, int W, const float* K,
                   const float* c2w, int L, const float* t, double kappa, double alpha_max, long long ray,
                   double* alpha, double* ssum, double* T, long long* vox, float* xyz) {
@@ -536,7 +537,7 @@ int orc_trace_ray(int n, int C, const float* means, const float* quats, const fl
  *                     and df/d(m, q, s, e) from sq_f_grad.
  * Gradient outputs are overwritten (not accumulated into). */
 int orc_render_bwd(int n, int C, const float* means, const float* quats, const float* scales, const float* eps,
-                   const float* opacity, const float* logits, const int* gn, const float* glo, const float* gvs,
+                   const float* opacity, const double* logits, const int* gn, const float* glo, const float* gvs,
                    const int* v_n, const int* v_f, const int* v_sq, int n_cam, int H, int W, const float* K,
                    const float* c2w, int L, const float* t, double kappa, double alpha_max, const long long* ray_ids,
                    long long n_rays, const double* grad_depth, const double* grad_sem, double* g_means,
@@ -636,7 +637,7 @@ int orc_render_bwd(int n, int C, const float* means, const float* quats, const f
  * label = argmax_c sem (lowest index on ties) if density >= tau, else C.
  * voxel_ids NULL means every voxel in id order. */
 int orc_query_grid(int n, int C, const float* means, const float* quats, const float* scales, const float* eps,
-                   const float* opacity, const float* logits, const int* gn, const float* glo, const float* gvs,
+                   const float* opacity, const double* logits, const int* gn, const float* glo, const float* gvs,
                    const int* v_n, const int* v_f, const int* v_sq, double tau, const long long* voxel_ids,
                    long long n_sel, double* density, double* sem, int* label, int n_threads) {
     ogrid_t g = make_grid(gn, glo, gvs);
@@ -688,7 +689,7 @@ int orc_query_grid(int n, int C, const float* means, const float* quats, const f
  * dL/dtheta += -p_o dL/dp_o df/dtheta, dL/dsigma_k += gd p_o and
  * dL/dc_k += gs p_o.  Serial, outputs overwritten. */
 int orc_query_grid_bwd(int n, int C, const float* means, const float* quats, const float* scales, const float* eps,
-                       const float* opacity, const float* logits, const int* gn, const float* glo, const float* gvs,
+                       const float* opacity, const double* logits, const int* gn, const float* glo, const float* gvs,
                        const int* v_n, const int* v_f, const int* v_sq, const long long* voxel_ids, long long n_sel,
                        const double* gd, const double* gs, double* g_means, double* g_quats, double* g_scales,
                        double* g_eps, double* g_opacity, double* g_logits) {

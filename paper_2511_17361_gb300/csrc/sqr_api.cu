@@ -46,6 +46,10 @@ sq_status_t check_prims(const sq_prims_t* p) {
         set_last_error("a primitive parameter pointer is NULL");
         return SQ_ERR_INVALID_ARG;
     }
+    if (p->sem_mode != SQ_SEM_RAW && p->sem_mode != SQ_SEM_SOFTMAX) {
+        set_last_error("prims.sem_mode = %d unknown", p->sem_mode);
+        return SQ_ERR_INVALID_ARG;
+    }
     return SQ_OK;
 }
 

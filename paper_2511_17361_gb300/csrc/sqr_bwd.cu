@@ -528,7 +528,8 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
 //   rotation mapped onto the tangent of the unit quaternion, then through q/|q|);
 //   dL/ds_j = -sum(u_j df/du_j) / s_j;  dL/deps, dL/dsigma as summed;
 //   dL/dc as accumulated.  One thread per primitive.
-__global__ void k_grad_out(const float* __restrict__ gacc, const float4* __restrict__ aux, int n, int C,
+__global__ void k_grad_out(const float* __restrict__ gacc, const float4* __restrict__ aux,
+                           const float* __restrict__ lpad, int cp, int sem_mode, int n, int C,
                            float* __restrict__ gm, float* __restrict__ gq, float* __restrict__ gs,
                            float* __restrict__ ge, float* __restrict__ go, float* __restrict__ gl) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -547,7 +548,15 @@ __global__ void k_grad_out(const float* __restrict__ gacc, const float4* __restr
     ge[2 * k + 0] = e[9];
     ge[2 * k + 1] = e[10];
     go[k] = e[11];
-    for (int c = 0; c < C; ++c) gl[(size_t)k * C + c] = e[NRAW + c];
+    if (sem_mode == SQ_SEM_SOFTMAX) {
+        // through s = softmax(c): dL/dc = s * (g - <g, s>), s as packed
+        const float* sm = lpad + (size_t)k * cp;
+        float gs_dot = 0.f;
+        for (int c = 0; c < C; ++c) gs_dot = fmaf(e[NRAW + c], sm[c], gs_dot);
+        for (int c = 0; c < C; ++c) gl[(size_t)k * C + c] = sm[c] * (e[NRAW + c] - gs_dot);
+    } else {
+        for (int c = 0; c < C; ++c) gl[(size_t)k * C + c] = e[NRAW + c];
+    }
 }
 
 
@@ -657,7 +666,7 @@ sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream
 sq_status_t launch_grad_out(const SceneDesc& S, float* gm, float* gq, float* gs, float* ge, float* go, float* gl,
                             cudaStream_t st) {
     if (S.n == 0) return SQ_OK;
-    SQ_LAUNCH("k_grad_out", st, k_grad_out<<<(S.n + 127) / 128, 128, 0, st>>>(S.gacc, S.aux, S.n, S.C, gm, gq, gs, ge, go, gl));
+    SQ_LAUNCH("k_grad_out", st, k_grad_out<<<(S.n + 127) / 128, 128, 0, st>>>(S.gacc, S.aux, S.lpad, S.cp, S.sem_mode, S.n, S.C, gm, gq, gs, ge, go, gl));
     return SQ_OK;
 }
 

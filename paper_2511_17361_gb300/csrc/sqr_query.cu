@@ -340,6 +340,9 @@ sq_status_t query_grid_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, 
     memset(&S, 0, sizeof(S));
     S.gacc = gacc;
     S.aux = aux;
+    S.lpad = lpad;
+    S.cp = cp;
+    S.sem_mode = prims->sem_mode;
     S.n = n;
     S.C = prims->n_classes;
     return launch_grad_out(S, g_means, g_quats, g_scales, g_eps, g_opacity, g_logits, st);

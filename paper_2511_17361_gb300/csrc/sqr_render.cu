@@ -45,7 +45,17 @@ __global__ void k_pack(sq_prims_t P, float4* __restrict__ rec, float4* __restric
         a[2] = make_float4(e1, e2, 1.f / e1, 1.f / e2);
     }
     const int C = P.n_classes;
-    for (int c = 0; c < cp; ++c) lpad[(size_t)k * cp + c] = c < C ? P.logits[(size_t)k * C + c] : 0.f;
+    const float* lg = P.logits + (size_t)k * C;
+    if (P.sem_mode == SQ_SEM_SOFTMAX) {  // per-primitive softmax of the logits
+        float mx = lg[0];
+        for (int c = 1; c < C; ++c) mx = fmaxf(mx, lg[c]);
+        float sum = 0.f;
+        for (int c = 0; c < C; ++c) sum += expf(lg[c] - mx);
+        const float inv = 1.0f / sum;
+        for (int c = 0; c < cp; ++c) lpad[(size_t)k * cp + c] = c < C ? expf(lg[c] - mx) * inv : 0.f;
+    } else {
+        for (int c = 0; c < cp; ++c) lpad[(size_t)k * cp + c] = c < C ? lg[c] : 0.f;
+    }
 }
 
 // Copies the by-value scene descriptors into device memory (one thread).
@@ -272,6 +282,8 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
         D.L = s.rays.L;
         D.C = C;
         D.n = s.prims.n;
+        D.sem_mode = s.prims.sem_mode;
+        D.cp = cp;
         D.R = R;
         D.kappa = s.rays.kappa;
         D.alpha_max = s.rays.alpha_max;

@@ -30,6 +30,8 @@ struct SceneDesc {
     const float* c2w;
     const float* t;
     int n_cam, H, W, L, C, n;
+    int sem_mode;        // SQ_SEM_*: the logit gradient goes through the softmax
+    int cp;              // C padded to a multiple of 4 (lpad row length)
     long long R;
     float kappa, alpha_max;
     float* depth;        // forward outputs

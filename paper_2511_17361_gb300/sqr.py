@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libsqr.so")
 
 SQ_OK, SQ_ERR_INVALID_ARG, SQ_ERR_CAPACITY, SQ_ERR_CUDA, SQ_ERR_TIMEOUT, SQ_ERR_NUMERIC = range(6)
 SQ_INDEX_OBB, SQ_INDEX_CUBE, SQ_INDEX_OBB_OPACITY = 0, 1, 2
+SQ_SEM_RAW, SQ_SEM_SOFTMAX = 0, 1
 SQ_OP_INDEX, SQ_OP_FWD, SQ_OP_BWD, SQ_OP_QUERY = 0, 1, 2, 3
 
 _vp = ctypes.c_void_p
@@ -34,7 +35,7 @@ class SqGrid(ctypes.Structure):
 
 class SqPrims(ctypes.Structure):
     _fields_ = [("means", _vp), ("quats", _vp), ("scales", _vp), ("eps", _vp), ("opacity", _vp), ("logits", _vp),
-                ("n", ctypes.c_int), ("n_classes", ctypes.c_int)]
+                ("n", ctypes.c_int), ("n_classes", ctypes.c_int), ("sem_mode", ctypes.c_int)]
 
 
 class SqIndexOpts(ctypes.Structure):
@@ -134,10 +135,12 @@ PRIM_KEYS = ("means", "quats", "scales", "eps", "opacity", "logits")
 
 
 def prims_struct(prims: dict) -> SqPrims:
+    """The parameter tensors (PRIM_KEYS) and, optionally, prims["sem_mode"]
+    (SQ_SEM_RAW by default, or SQ_SEM_SOFTMAX)."""
     for k in PRIM_KEYS:
         _need_cuda_f32(prims[k], k)
     n, C = prims["logits"].shape
-    return SqPrims(*[_ptr(prims[k]) for k in PRIM_KEYS], n, C)
+    return SqPrims(*[_ptr(prims[k]) for k in PRIM_KEYS], n, C, int(prims.get("sem_mode", SQ_SEM_RAW)))
 
 
 def grid_struct(grid: dict) -> SqGrid:

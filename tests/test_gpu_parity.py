@@ -467,6 +467,39 @@ def test_query_backward_sparse_large(sqr):
         check_grad(got[k].cpu().numpy(), ref[k], k)
 
 
+def test_softmax_sem_mode(sqr):
+    """Per-primitive softmax of the logits (sem_mode 1): render forward and
+    backward and the grid query and its backward against the oracle in the same
+    mode."""
+    pr, grid, rig, t = small_scene(40, n=8, H=9, W=11, L=32, C=6, sigma_max=0.6)
+    prims_d, rays = scene_to_gpu(sqr, pr, rig, t)
+    prims_d["sem_mode"] = sqr.SQ_SEM_SOFTMAX
+    g = dev_grid(grid)
+    ix = sqr.build_index(prims_d, g)
+    idx = np_index(ix)
+    d, s, _ = sqr.render_fwd(prims_d, ix, g, rays)
+    D, S, _, _ = oracle.render_fwd(pr, grid, idx, rig, t, sem_mode=1)
+    check_depth(d.cpu().numpy(), D, 0.5)
+    check_sem(s.cpu().numpy(), S)
+    R = rays.R
+    rng = np.random.default_rng(40)
+    gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, 6)).astype(np.float32)
+    got = sqr.render_bwd(prims_d, ix, g, rays, torch.from_numpy(gd).cuda(), torch.from_numpy(gs).cuda())
+    ref = oracle.render_bwd(pr, grid, idx, rig, t, gd.astype(np.float64), gs.astype(np.float64), sem_mode=1)
+    for k in ref:
+        check_grad(got[k].cpu().numpy(), ref[k], k)
+    assert np.allclose(got["logits"].cpu().numpy().sum(1), 0.0, atol=1e-5 * np.abs(ref["logits"]).max())
+    dens, sem, _ = sqr.query_grid(prims_d, ix, g, tau=0.05)
+    rd, rs, _ = oracle.query_grid(pr, grid, idx, tau=0.05, sem_mode=1)
+    assert np.max(np.abs(sem.cpu().numpy() - rs) / np.maximum(1.0, np.abs(rs))) < 5e-5
+    nvox = int(np.prod(grid["n"]))
+    qd, qs = rng.standard_normal(nvox).astype(np.float32), rng.standard_normal((nvox, 6)).astype(np.float32)
+    gq = sqr.query_grid_bwd(prims_d, ix, g, torch.from_numpy(qd).cuda(), torch.from_numpy(qs).cuda())
+    rq = oracle.query_grid_bwd(pr, grid, idx, qd.astype(np.float64), qs.astype(np.float64), sem_mode=1)
+    for k in rq:
+        check_grad(gq[k].cpu().numpy(), rq[k], k)
+
+
 def test_kernel_timing_records_every_launch(sqr):
     """sq_profile_*: while enabled, every launch of the library is recorded with a
     positive duration on its stream; disabled, nothing is recorded."""

@@ -568,3 +568,51 @@ def test_query_backward_voxel_subset_is_the_restriction():
     b = oracle.query_grid_bwd(pr, grid, idx, gd_full, gs_full)
     for k in a:
         np.testing.assert_allclose(a[k], b[k], rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------ per-primitive softmax
+def test_softmax_mode_backward_matches_central_differences():
+    """sem_mode 1 (c_k -> softmax(c_k)): the logit gradient through the softmax,
+    and the other parameters, against central differences of the FP64 render."""
+    pr, grid, rig, t = small_scene(30, n=4, H=5, W=6, L=20)
+    idx = oracle.build_index(pr, grid, 0, 1e-3, 5)
+    R = rig["H"] * rig["W"]
+    rng = np.random.default_rng(30)
+    gd, gs = rng.standard_normal(R), rng.standard_normal((R, pr["logits"].shape[1]))
+    g = oracle.render_bwd(pr, grid, idx, rig, t, gd, gs, sem_mode=1)
+
+    def loss(p2):
+        D, S, _, _ = oracle.render_fwd(p2, grid, idx, rig, t, sem_mode=1)
+        return float(np.dot(gd, D) + np.sum(gs * S))
+
+    h = 2.0 ** -13
+    for name in ["logits", "opacity", "means"]:
+        for i in range(pr[name].size):
+            fd = richardson_fd(loss, pr, name, i, h)
+            an = g[name].reshape(-1)[i]
+            assert an == pytest.approx(fd, rel=2e-5, abs=1e-6 * max(1.0, np.abs(g[name]).max())), (name, i, an, fd)
+
+
+def test_softmax_mode_invariances():
+    """A constant added to a primitive's logits changes nothing in softmax mode, so
+    every primitive's logit gradient sums to zero; with one class the semantic sum
+    is the plain occupancy sum (softmax of one logit is 1)."""
+    pr, grid, rig, t = small_scene(31, n=5)
+    idx = oracle.build_index(pr, grid, 0, 1e-3, 5)
+    R = rig["H"] * rig["W"]
+    rng = np.random.default_rng(31)
+    D0, S0, _, _ = oracle.render_fwd(pr, grid, idx, rig, t, sem_mode=1)
+    shifted = dict(pr)
+    shifted["logits"] = (pr["logits"] + rng.uniform(-3, 3, (pr["logits"].shape[0], 1))).astype(np.float32)
+    D1, S1, _, _ = oracle.render_fwd(shifted, grid, idx, rig, t, sem_mode=1)
+    np.testing.assert_allclose(S1, S0, rtol=1e-6, atol=1e-9)
+    np.testing.assert_array_equal(D1, D0)
+    g = oracle.render_bwd(pr, grid, idx, rig, t, rng.standard_normal(R), rng.standard_normal((R, 5)), sem_mode=1)
+    np.testing.assert_allclose(g["logits"].sum(1), 0.0, atol=1e-12 * max(1.0, np.abs(g["logits"]).max()))
+    one = dict(pr)
+    one["logits"] = rng.standard_normal((pr["logits"].shape[0], 1)).astype(np.float32)
+    _, S_soft, _, _ = oracle.render_fwd(one, grid, idx, rig, t, sem_mode=1)
+    ones = dict(pr)
+    ones["logits"] = np.ones((pr["logits"].shape[0], 1), np.float32)
+    _, S_ones, _, _ = oracle.render_fwd(ones, grid, idx, rig, t)
+    np.testing.assert_allclose(S_soft, S_ones, rtol=1e-12, atol=1e-15)
