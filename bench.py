@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 from paper_2511_17361_gb300 import synth  # noqa: E402
 
 WORKLOAD = 1
+BWD_ORDER = 0  # SQ_BWD_DEFAULT; --bwd-order
 MUFU_PER_PAIR = {"fwd": 9, "bwd": 13}  # SFU ops per (sample, primitive) pair in each kernel
 # DRAM traffic per launch from the committed ncu summaries, valid only while the
 # kernel source is unchanged (sha256 of the file holding it).
@@ -228,7 +229,7 @@ def run_mine(args):
         if ev: ev[2].record()
         _, gd, gs = sqr.loss_ce_mse(depth, sem, td, tl, out=loss_out)
         if ev: ev[3].record()
-        sqr.render_bwd(prims, ix, grid, rays, gd, gs, saved=saved, out=grads)
+        sqr.render_bwd(prims, ix, grid, rays, gd, gs, saved=saved, out=grads, order=BWD_ORDER)
         if ev: ev[4].record()
 
     for _ in range(max(3, args.warmup)):
@@ -250,7 +251,7 @@ def run_mine(args):
     torch.cuda.synchronize()
     sqr.profile_enable(False)
     clocks = sampler.stop()
-    kernel_ms = {k: sqr.profile_query(k) for k in ("k_forward", "k_backward", "k_bwd_sweep")}
+    kernel_ms = {k: sqr.profile_query(k) for k in ("k_forward", "k_backward", "k_pm_tiles", "k_bwd_sweep")}
     launches_timed, _, dropped = sqr.profile_query(None)
     phase = np.array([[evs[s][i].elapsed_time(evs[s][i + 1]) for i in range(4)] for s in range(args.steps)])
     step_ms = phase.sum(1)
@@ -307,7 +308,7 @@ def run_mine(args):
     roof = None
     # the dominant kernel: the longer of the two pair-evaluating kernels, its mean
     # launch time from the events recorded around it over the timed steps
-    kname = max(("k_forward", "k_backward"), key=lambda k: kernel_ms[k][1])
+    kname = max(("k_forward", "k_backward", "k_pm_tiles"), key=lambda k: kernel_ms[k][1])
     n_launch, k_total_ms, _ = kernel_ms[kname]
     if n_launch > 0:
         k_mean_ms = k_total_ms / n_launch
@@ -355,6 +356,7 @@ def run_mine(args):
                 "in_grid_samples": in_grid, "index": {"obb": "OBB, tau_cut 0.01", "cube": "cube N_v = 5",
                                                       "opacity": "opacity-aware OBB, tau_cut 0.01"}[args.index],
                 "l2": "flushed (256 MB write) between timed steps",
+                "backward_order": {0: "default", 1: "ray-major", 2: "primitive-major"}[BWD_ORDER],
                 "parallelism": f"replicas x{world} (one frame per GPU)"},
             "phases_ms": {n: float(v) for n, v in zip(names, mean_phase)},
             "gpu_launches": launches_timed + dropped,
@@ -551,6 +553,8 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--index", choices=["obb", "cube", "opacity"], default="obb",
                     help="voxel neighbourhood of the frame workload's index (default: OBB, tau_cut 0.01)")
+    ap.add_argument("--bwd-order", choices=["default", "ray", "primitive"], default="default",
+                    help="backward order (Sec. 3.3.3): ray-major run walk or primitive-major tiles")
     ap.add_argument("--workload", choices=["frame", "batch", "temporal", "query"], default="frame",
                     help="frame: one six-camera frame (default); batch: 12 uneven scenes, batched vs per scene; "
                          "temporal: the 13 frames of a T = 6 horizon, batched vs per frame; "
@@ -558,6 +562,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
+    global BWD_ORDER
+    BWD_ORDER = {"default": 0, "ray": 1, "primitive": 2}[args.bwd_order]
     if args.impl == "reference":
         return run_reference(args)
     if args.workload in ("batch", "temporal"):

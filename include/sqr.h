@@ -247,15 +247,30 @@ typedef struct {
     float* g_logits;
 } sq_scene_t;
 
+/* Order of the backward's gradient accumulation (Sec. 3.3.3).  Both first sweep
+ * every ray back to front (Process 1: dL/dalpha_j and w_j per sample).
+ *   SQ_BWD_RAY_MAJOR: a warp per pair of rays walks the rays' samples, one lane
+ *     per (ray, primitive) run, and flushes each run's partial sums to the
+ *     primitive with atomic adds (summation order varies between runs).
+ *   SQ_BWD_PRIMITIVE_MAJOR: the paper's grouping (Processes 2-3): each
+ *     primitive's interactions are generated from its voxel box (the pixels of
+ *     its projected rectangle, the exact sample interval of each pixel's ray in
+ *     the box), reduced per tile of candidate pixels by one CTA and summed over
+ *     the tiles in a fixed order: no atomics, bitwise reproducible gradients.
+ *   SQ_BWD_DEFAULT: the library's choice. */
+enum { SQ_BWD_DEFAULT = 0, SQ_BWD_RAY_MAJOR = 1, SQ_BWD_PRIMITIVE_MAJOR = 2 };
+
 /* Launch configuration: lanes (= samples marched together) per ray in the
- * forward (4, 8 or 16), warps per CTA in the forward (1..8) and backward (1..8,
- * or 0: the count that keeps the most warps resident for the batch's largest L,
- * whose sample tables set the backward's shared memory).  The defaults are
- * {4, 8, 0}. */
+ * forward (4, 8 or 16), warps per CTA in the forward (1..8) and in the
+ * ray-major backward (1..8, or 0: the count that keeps the most warps resident
+ * for the batch's largest L, whose sample tables set the backward's shared
+ * memory), and the backward order (SQ_BWD_*).  The defaults are {4, 8, 0,
+ * SQ_BWD_DEFAULT}. */
 typedef struct {
     int fwd_lanes_per_ray;
     int fwd_warps_per_cta;
     int bwd_warps_per_cta;
+    int bwd_order;
 } sq_tuning_t;
 
 /* Workspace bytes for sq_render_batched / sq_autotune on these scenes; when
@@ -270,9 +285,10 @@ sq_status_t sq_render_batched(int op, const sq_scene_t* scenes, int n_scenes, co
 /* Autotuner: times every forward configuration (lanes per ray x warps per CTA)
  * and, when every scene has saved state and cotangents, every backward one on
  * these scenes (reps timed launches each, CUDA events on the stream) and writes
- * the fastest to *best.  fwd_ms[4] / bwd_ms[3] (nullable) receive the mean
- * times of the candidates in the order {4,4},{4,8},{8,4},{8,8} and {0},{4},{8}
- * (0 = automatic warps per CTA).
+ * the fastest to *best.  fwd_ms[4] / bwd_ms[4] (nullable) receive the mean
+ * times of the candidates in the order {4,4},{4,8},{8,4},{8,8} (lanes, warps)
+ * and ray-major with {0},{4},{8} warps per CTA (0 = automatic), then
+ * primitive-major.
  * Host-synchronous and overwrites the scenes' outputs; call it outside any
  * stream capture. */
 sq_status_t sq_autotune(const sq_scene_t* scenes, int n_scenes, void* workspace, size_t workspace_bytes, void* stream,

@@ -110,16 +110,6 @@ __device__ __forceinline__ void drain_queue(float* __restrict__ gacc, const floa
     }
 }
 
-// Adds one pair's weighted partials to a run's sums (dL/dp_o = G sigma + w <gS, c>).
-__device__ __forceinline__ void accumulate(float acc[13], float po, const float pr[11], float G, float w, float sigma,
-                                           float cd) {
-    const float gf = -po * fmaf(G, sigma, w * cd);
-#pragma unroll
-    for (int i = 0; i < 11; ++i) acc[i] = fmaf(gf, pr[i], acc[i]);
-    acc[11] = fmaf(G, po, acc[11]);
-    acc[12] = fmaf(w, po, acc[12]);
-}
-
 // Fixed per-warp shared memory; the sample tables (RB * L entries) follow the
 // array of these in dynamic shared memory.
 struct alignas(16) WarpBwd {

@@ -1,0 +1,664 @@
+// sqr_bwd_pm.cu -- primitive-major render backward (Sec. 3.3.3, Processes 2-3).
+//
+// Process 1 (the back-to-front sweep that stores dL/dalpha_j and w_j per sample)
+// is shared with the ray-major path.  Here the (sample, superquadric)
+// interactions are grouped by primitive, as the paper's Process 2 does, but
+// without a sort: the samples whose voxel lies in primitive k's box form, on
+// every ray, one interval of consecutive samples (the voxel coordinates of a
+// ray's samples are monotone), so the interactions of k are generated directly
+// from its box:
+//   k_pm_rects  projects the box into every camera: a pixel rectangle that holds
+//               every pixel whose ray can meet the box (conservative, FP64);
+//   k_pm_scan   turns the rectangles' pixel counts into tiles (at most PM_MAXT per
+//               primitive) and numbers them, with each tile's primitive;
+//   k_pm_tiles  (Process 3) one block per tile: for each candidate pixel the exact
+//               sample interval of its ray inside the box (binary searches on the
+//               same FP32 sample/voxel rule the forward used), then the tile's
+//               pairs split evenly over the threads, each accumulating the
+//               partial derivatives of its pairs; a block reduction writes the
+//               tile's sums;
+//   k_pm_final  sums each primitive's tiles in tile order into its accumulator.
+// Every sum is taken in a fixed order, so the gradients are bitwise reproducible
+// (the ray-major path flushes with atomic adds).
+#include "sqr_pair.cuh"
+#include "sqr_render.cuh"
+
+namespace sqr {
+
+namespace {
+
+constexpr int PM_THREADS = 256;
+constexpr int PM_WARPS = PM_THREADS / 32;
+constexpr int PM_CPT = PM_CHUNK / PM_THREADS;  // candidates per thread and pass
+constexpr int PM_SMCAM = 16;                     // cameras whose rectangles a tile stages in shared memory
+constexpr int PM_NS = 2;                         // pairs of one run per walk step (4 and 8 measured slower)
+static_assert(PM_CHUNK % PM_THREADS == 0, "whole candidates per thread");
+static_assert((PM_CHUNK & (PM_CHUNK - 1)) == 0, "the slot search halves a power of two");
+
+__device__ __forceinline__ int scene_of_prim(const long long* __restrict__ poff, int nsc, int g) {
+    int lo = 0, hi = nsc;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(poff + mid) <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int tiles_of(int cnt) {
+    constexpr int per = PM_CHUNK * PM_TILE_CHUNKS;
+    return cnt <= 0 ? 0 : min(PM_MAXT, (cnt + per - 1) / per);
+}
+
+// Pixel rectangle (u0, v0, u1, v1), inclusive, of the pixels whose rays can meet
+// the world box [bl, bh] at a sample, for camera (K, c2w) of an H x W image;
+// (0, 0, -1, -1) when none can.  Samples lie at t >= t0 along rays through pixel
+// centres; in the camera frame (x_cam = R^-1 (x - o)) a sample of pixel (u, v)
+// is t (dx, dy, 1) / |(dx, dy, 1)| with dx = (u + 1/2 - cx) / fx, dy likewise,
+// so for t0 > 0 its depth is at least zc = t0 / max |(dx, dy, 1)|: the box is
+// clipped to the half-space z >= zc / 2 and the vertices of the clipped box
+// (corners in front, edge crossings of the plane) are projected.  Two pixels of
+// margin absorb rounding; degenerate cameras and boxes reaching behind a camera
+// whose rays start at t0 <= 0 get the whole image.
+__device__ int4 box_rect(const float* __restrict__ K, const float* __restrict__ c2w, int H, int W, const double bl[3],
+                         const double bh[3], double t0) {
+    const int4 none = make_int4(0, 0, -1, -1), all = make_int4(0, 0, W - 1, H - 1);
+    if (W <= 0 || H <= 0) return none;
+    const double fx = K[0], fy = K[1], cx = K[2], cy = K[3];
+    if (!(fabs(fx) > 0.0) || !(fabs(fy) > 0.0) || !isfinite(fx) || !isfinite(fy)) return all;
+    double R[3][3], o[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) R[i][j] = c2w[4 * i + j];
+        o[i] = c2w[4 * i + 3];
+    }
+    double A[3][3];  // adjugate: R^-1 = A / det
+    A[0][0] = R[1][1] * R[2][2] - R[1][2] * R[2][1];
+    A[0][1] = R[0][2] * R[2][1] - R[0][1] * R[2][2];
+    A[0][2] = R[0][1] * R[1][2] - R[0][2] * R[1][1];
+    A[1][0] = R[1][2] * R[2][0] - R[1][0] * R[2][2];
+    A[1][1] = R[0][0] * R[2][2] - R[0][2] * R[2][0];
+    A[1][2] = R[0][2] * R[1][0] - R[0][0] * R[1][2];
+    A[2][0] = R[1][0] * R[2][1] - R[1][1] * R[2][0];
+    A[2][1] = R[0][1] * R[2][0] - R[0][0] * R[2][1];
+    A[2][2] = R[0][0] * R[1][1] - R[0][1] * R[1][0];
+    const double det = R[0][0] * A[0][0] + R[0][1] * A[1][0] + R[0][2] * A[2][0];
+    if (!(fabs(det) > 0.0) || !isfinite(det)) return all;
+    double P[8][3];
+    for (int c = 0; c < 8; ++c) {
+        const double w[3] = {(c & 1) ? bh[0] : bl[0], (c & 2) ? bh[1] : bl[1], (c & 4) ? bh[2] : bl[2]};
+        for (int i = 0; i < 3; ++i)
+            P[c][i] = (A[i][0] * (w[0] - o[0]) + A[i][1] * (w[1] - o[1]) + A[i][2] * (w[2] - o[2])) / det;
+    }
+    double zc;
+    if (t0 > 0.0) {
+        const double mx = fmax(fabs(0.5 - cx), fabs(W - 0.5 - cx)) / fabs(fx);
+        const double my = fmax(fabs(0.5 - cy), fabs(H - 0.5 - cy)) / fabs(fy);
+        zc = 0.5 * t0 / sqrt(1.0 + mx * mx + my * my);
+    } else {
+        for (int c = 0; c < 8; ++c)
+            if (!(P[c][2] > 0.0)) return all;
+        zc = 0.0;
+    }
+    double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    bool any = false;
+    auto add = [&](double X, double Y, double Z) {
+        const double u = fx * X / Z + cx - 0.5, v = fy * Y / Z + cy - 0.5;
+        umin = fmin(umin, u);
+        umax = fmax(umax, u);
+        vmin = fmin(vmin, v);
+        vmax = fmax(vmax, v);
+        any = true;
+    };
+    for (int c = 0; c < 8; ++c)
+        if (P[c][2] >= zc && P[c][2] > 0.0) add(P[c][0], P[c][1], P[c][2]);
+    if (zc > 0.0)
+        for (int c = 0; c < 8; ++c)
+            for (int b = 1; b < 8; b <<= 1) {
+                if (c & b) continue;
+                const double za = P[c][2], zb = P[c | b][2];
+                if ((za < zc) == (zb < zc)) continue;
+                const double s = (zc - za) / (zb - za);
+                add(P[c][0] + s * (P[c | b][0] - P[c][0]), P[c][1] + s * (P[c | b][1] - P[c][1]), zc);
+            }
+    if (!any || !(umin <= umax) || !(vmin <= vmax)) return none;
+    const double u0 = fmax(floor(umin) - 2.0, 0.0), u1 = fmin(ceil(umax) + 2.0, W - 1.0);
+    const double v0 = fmax(floor(vmin) - 2.0, 0.0), v1 = fmin(ceil(vmax) + 2.0, H - 1.0);
+    if (!(u0 <= u1) || !(v0 <= v1)) return none;
+    return make_int4((int)u0, (int)v0, (int)u1, (int)v1);
+}
+
+// One warp per primitive of the batch, a lane per camera: the rectangle in
+// every camera and the number of candidate pixels.
+__global__ void k_pm_rects(Batch B, PmArgs A) {
+    const int g = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (g >= A.ntot) return;
+    const int s = scene_of_prim(A.poff, B.n, g);
+    const SceneDesc& S = B.d[s];
+    const int k = g - (int)__ldg(A.poff + s);
+    const int4 b = __ldg(S.boxes + k);
+    const int lo[3] = {b.x & 0xffff, b.y & 0xffff, b.z & 0xffff};
+    const int hi[3] = {(int)((unsigned)b.x >> 16), (int)((unsigned)b.y >> 16), (int)((unsigned)b.z >> 16)};
+    const bool ok = *S.status == SQ_OK && lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2];
+    double bl[3], bh[3];
+    for (int a = 0; a < 3; ++a) {
+        bl[a] = (double)S.g.lo[a] + (double)lo[a] * (double)S.g.vs[a];
+        bh[a] = (double)S.g.lo[a] + (double)(hi[a] + 1) * (double)S.g.vs[a];
+    }
+    const bool rays = S.n_cam > 0 && S.H > 0 && S.W > 0;  // t may be NULL without rays
+    const double t0 = rays ? (double)__ldg(S.t) : 0.0;
+    int4* rect = S.pm_rect + (size_t)k * S.n_cam;
+    long long total = 0;
+    for (int c = lane; c < (rays ? S.n_cam : 0); c += 32) {
+        const int4 rc = ok ? box_rect(S.K + 4 * c, S.c2w + 12 * c, S.H, S.W, bl, bh, t0) : make_int4(0, 0, -1, -1);
+        rect[c] = rc;
+        if (rc.z >= rc.x && rc.w >= rc.y) total += (long long)(rc.z - rc.x + 1) * (rc.w - rc.y + 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    if (lane == 0) A.cnt[g] = (int)total;  // at most the scene's ray count (< 2^31)
+}
+
+// Exclusive scan of the tile counts over all primitives (one block).
+__global__ void __launch_bounds__(1024) k_pm_scan(PmArgs A) {
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int per = (A.ntot + 1023) / 1024;
+    const int b = min(A.ntot, tid * per), e = min(A.ntot, b + per);
+    int sum = 0;
+    for (int i = b; i < e; ++i) sum += tiles_of(A.cnt[i]);
+    const int incl = warp_incl_scan(sum, lane);
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int w = wsum[lane];
+        const int wi = warp_incl_scan(w, lane);
+        wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    int run = wsum[wid] + incl - sum;
+    for (int i = b; i < e; ++i) {
+        A.toff[i] = run;
+        const int nt = tiles_of(A.cnt[i]);
+        for (int t = 0; t < nt; ++t) A.tprim[run + t] = i;
+        run += nt;
+    }
+    if (tid == 1023) A.toff[A.ntot] = run;
+}
+
+// Ray direction of every ray of the batch (pixel_ray) and its number of
+// composited samples (in .w), for the candidate pixels of the tiles: one thread
+// per ray.
+__global__ void k_pm_dirs(Batch B) {
+    const long long gr = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gr >= B.total) return;
+    const int s = scene_of(B, gr);
+    const SceneDesc& S = B.d[s];
+    const long long r = gr - __ldg(B.off + s);
+    float o[3], d[3];
+    scene_ray(S, r, o, d);
+    const int Le = min(max(__ldg(S.save_n + r), 0), S.L);
+    S.pm_dir[r] = make_float4(d[0], d[1], d[2], __int_as_float(Le));
+}
+
+// Scaled coordinate of sample j on one axis, rounded as sample_voxel rounds it,
+// tested against a threshold: (u_j < thr) != neg.
+__device__ __forceinline__ bool below(const float* ts, int j, float o, float d, float glo, float inv, float thr,
+                                      bool neg) {
+    const float x = __fadd_rn(o, __fmul_rn(ts[j], d));
+    const float u = __fmul_rn(__fsub_rn(x, glo), inv);
+    return (u < thr) != neg;
+}
+
+// Number of leading samples j of [0, Le) with below(j).  u_j is monotone in j (t
+// non-decreasing), so the predicate holds on a prefix: a binary search finds its
+// length.
+__device__ __noinline__ int lead_search(const float* ts, int Le, float o, float d, float glo, float inv, float thr,
+                                        bool neg) {
+    int n = 0;
+    for (int step = Le > 0 ? 1 << (31 - __clz(Le)) : 0; step > 0; step >>= 1)
+        if (n + step <= Le && below(ts, n + step - 1, o, d, glo, inv, thr, neg)) n += step;
+    return n;
+}
+
+// The same prefix length, starting from an estimate: the ray meets the plane
+// u = thr at t* = (lo + thr vs - o) / d (id: an approximate 1 / d), and with
+// evenly spaced samples about (t* - t_0) / dt samples lie before it.  The
+// estimate is moved to the exact boundary by testing the predicate itself (at
+// most a few steps each way, then the binary search), so the result never
+// depends on the estimate's rounding.
+__device__ __forceinline__ int lead(const float* ts, int Le, float o, float d, float id, float glo, float inv,
+                                    float vs, float thr, bool neg, float t0, float inv_dt) {
+    if (Le <= 0) return 0;
+    if (d == 0.f) return below(ts, 0, o, d, glo, inv, thr, neg) ? Le : 0;  // u_j constant
+    const float tstar = (fmaf(thr, vs, glo) - o) * id;
+    const float fe = ceilf((tstar - t0) * inv_dt);
+    int n = (int)fminf(fmaxf(fe, 0.f), (float)Le);
+    for (int k = 0; n > 0 && !below(ts, n - 1, o, d, glo, inv, thr, neg); ++k) {
+        if (k == 4) return lead_search(ts, Le, o, d, glo, inv, thr, neg);
+        --n;
+    }
+    for (int k = 0; n < Le && below(ts, n, o, d, glo, inv, thr, neg); ++k) {
+        if (k == 4) return lead_search(ts, Le, o, d, glo, inv, thr, neg);
+        ++n;
+    }
+    return n;
+}
+
+struct PmSmem {
+    float d[3][PM_CHUNK];        // ray direction of each candidate slot
+    float cd[PM_CHUNK];          // <dL/dS of the ray, c_k>
+    int r[PM_CHUNK];             // ray index in its scene
+    int jc[PM_CHUNK];            // first sample of the run | camera << 10
+    int pre[PM_CHUNK + 1];       // exclusive prefix of the run lengths (pairs)
+    float wsum[PM_CHUNK];        // sum over the run of w_j p_o
+    float ts[SQ_MAX_SAMPLES];    // sample distances of the tile's scene
+    int4 rc[PM_SMCAM];           // the primitive's rectangles (n_cam <= PM_SMCAM)
+    int rpre[PM_SMCAM + 1];      // exclusive prefix of their pixel counts
+    int head_slot[PM_THREADS];   // run a thread's slice starts inside (-1: none)
+    float head_val[PM_THREADS];  // that thread's part of the run's w p_o sum
+    float red[PM_WARPS][NRAW];
+    float cpart[PM_WARPS][32];
+    float lp[32];                // class vector of the tile's primitive (lpad row)
+    int wtot[PM_WARPS];
+    int tile;
+};
+static_assert(SQ_MAX_SAMPLES <= 1024, "first samples are packed in 10 bits");
+
+__device__ __forceinline__ void camera_origin(const SceneDesc& S, int cam, float o[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) o[a] = __ldg(S.c2w + 12 * cam + 4 * a + 3);
+}
+
+template <int CP>
+__global__ void __launch_bounds__(PM_THREADS, 2) k_pm_tiles(Batch B, PmArgs A) {
+    __shared__ PmSmem sh;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int ntiles = __ldg(A.toff + A.ntot);
+    for (;;) {
+        if (tid == 0) sh.tile = atomicAdd(A.ctr, 1);
+        __syncthreads();
+        const int tile = sh.tile;
+        if (tile >= ntiles) break;
+        const int g = __ldg(A.tprim + tile);
+        const int s = scene_of_prim(A.poff, B.n, g);
+        const SceneDesc& S = B.d[s];
+        const int k = g - (int)__ldg(A.poff + s);
+        const int it = tile - __ldg(A.toff + g), nt = __ldg(A.toff + g + 1) - __ldg(A.toff + g);
+        const long long nc = __ldg(A.cnt + g);
+        const int cbeg = (int)(nc * it / nt), cend = (int)(nc * (it + 1) / nt);
+        const int L = S.L, C = S.C, H = S.H, W = S.W, ncam = S.n_cam;
+        const BwdPrim P = load_bwd(S.rec, S.aux, k);
+        const int4 bx = __ldg(S.boxes + k);
+        const float blo[3] = {(float)(bx.x & 0xffff), (float)(bx.y & 0xffff), (float)(bx.z & 0xffff)};
+        const float bhi[3] = {(float)(((unsigned)bx.x >> 16) + 1u), (float)(((unsigned)bx.y >> 16) + 1u),
+                              (float)(((unsigned)bx.z >> 16) + 1u)};
+        const int4* __restrict__ rect = S.pm_rect + (size_t)k * ncam;
+        if (tid < CP) sh.lp[tid] = __ldg(S.lpad + (size_t)k * CP + tid);
+        for (int j = tid; j < L; j += PM_THREADS) sh.ts[j] = __ldg(S.t + j);
+        const bool rc_sm = ncam <= PM_SMCAM;
+        if (rc_sm && tid < 32) {  // rectangles and the prefix of their pixel counts
+            int area = 0;
+            if (tid < ncam) {
+                const int4 rc = __ldg(rect + tid);
+                const int w = rc.z - rc.x + 1, h = rc.w - rc.y + 1;
+                area = (w > 0 && h > 0) ? w * h : 0;
+                sh.rc[tid] = rc;
+            }
+            const int incl = warp_incl_scan(area, lane);
+            if (tid <= ncam) sh.rpre[tid] = incl - area;
+        }
+        float bwl[3], bwh[3];  // world extent of the box (for the slab test)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bwl[a] = fmaf(blo[a], S.g.vs[a], S.g.lo[a]);
+            bwh[a] = fmaf(bhi[a], S.g.vs[a], S.g.lo[a]);
+        }
+        const float t0 = __ldg(S.t), tl = __ldg(S.t + L - 1);
+        const float inv_dt = (L > 1 && tl > t0) ? (float)(L - 1) / (tl - t0) : 0.f;
+        float acc[13];
+#pragma unroll
+        for (int i = 0; i < 13; ++i) acc[i] = 0.f;
+        float cg = 0.f;  // class tid's gradient sum (threads tid < C)
+        __syncthreads();
+
+        for (int cb = cbeg; cb < cend; cb += PM_CHUNK) {
+            // ---- candidates -> runs: thread tid holds slots tid * PM_CPT + i, slot q
+            // being candidate cb + q.  Three stages over the thread's candidates, so
+            // that the loads of all of them are in flight together.
+            int rr[PM_CPT], cam[PM_CPT], Le[PM_CPT], j0s[PM_CPT], len[PM_CPT];
+            float4 dv[PM_CPT];
+#pragma unroll
+            for (int i = 0; i < PM_CPT; ++i) {  // pixel of the candidate
+                const int ci = cb + tid * PM_CPT + i;
+                rr[i] = -1;
+                cam[i] = 0;
+                if (ci >= cend) continue;
+                int c = 0, rem = ci;
+                int4 rc = make_int4(0, 0, -1, -1);
+                if (rc_sm) {
+                    while (c < ncam && sh.rpre[c + 1] <= ci) ++c;
+                    if (c >= ncam) continue;
+                    rc = sh.rc[c];
+                    rem = ci - sh.rpre[c];
+                } else {
+                    for (; c < ncam; ++c) {
+                        rc = __ldg(rect + c);
+                        const int w = rc.z - rc.x + 1, h = rc.w - rc.y + 1;
+                        const int area = (w > 0 && h > 0) ? w * h : 0;
+                        if (rem < area) break;
+                        rem -= area;
+                    }
+                    if (c >= ncam) continue;
+                }
+                const int w = rc.z - rc.x + 1;
+                rr[i] = (c * H + rc.y + rem / w) * W + rc.x + rem % w;
+                cam[i] = c;
+            }
+#pragma unroll
+            for (int i = 0; i < PM_CPT; ++i) {  // its ray direction and composited samples
+                dv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                Le[i] = 0;
+                if (rr[i] >= 0) {
+                    dv[i] = __ldg(S.pm_dir + rr[i]);
+                    Le[i] = __float_as_int(dv[i].w);
+                }
+            }
+            int tl_sum = 0;
+#pragma unroll
+            for (int i = 0; i < PM_CPT; ++i) {  // the run: samples of the ray inside the box
+                len[i] = 0;
+                j0s[i] = 0;
+                if (Le[i] == 0) continue;
+                const float d[3] = {dv[i].x, dv[i].y, dv[i].z};
+                float o[3];
+                camera_origin(S, cam[i], o);
+                // Slab test of the segment t in [t_0, t_last] against the box grown by
+                // dl, a bound (with a wide safety factor) on how far outside the box an
+                // FP32 sample can be and still pass the FP32 voxel test: a miss here
+                // means no composited sample of the ray lies in the box.
+                const float tlast = sh.ts[Le[i] - 1];
+                const float tm = fmaxf(fabsf(t0), fabsf(tlast));
+                float te = t0, tx = tlast, id[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float dl = 1e-5f * (fabsf(o[a]) + fabsf(S.g.lo[a]) + fabsf(bwl[a]) + fabsf(bwh[a]) +
+                                              tm * fabsf(d[a])) + 1e-6f;
+                    if (fabsf(d[a]) < 1e-20f) {  // the ray keeps this coordinate
+                        id[a] = 0.f;
+                        if (o[a] < bwl[a] - dl || o[a] > bwh[a] + dl) te = INFINITY;
+                    } else {
+                        id[a] = rcp(d[a]);
+                        const float t1 = (bwl[a] - dl - o[a]) * id[a], t2 = (bwh[a] + dl - o[a]) * id[a];
+                        const float lo_t = fminf(t1, t2), hi_t = fmaxf(t1, t2);
+                        te = fmaxf(te, lo_t - (1e-5f * fabsf(lo_t) + 1e-6f));
+                        tx = fminf(tx, hi_t + (1e-5f * fabsf(hi_t) + 1e-6f));
+                    }
+                }
+                if (!(te <= tx)) continue;
+                int j0 = 0, j1 = Le[i];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const bool neg = d[a] < 0.f;
+                    j0 = max(j0, lead(sh.ts, Le[i], o[a], d[a], id[a], S.g.lo[a], S.g.inv_vs[a], S.g.vs[a],
+                                      neg ? bhi[a] : blo[a], neg, t0, inv_dt));
+                }
+                if (j0 >= j1) continue;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const bool neg = d[a] < 0.f;
+                    j1 = min(j1, lead(sh.ts, Le[i], o[a], d[a], id[a], S.g.lo[a], S.g.inv_vs[a], S.g.vs[a],
+                                      neg ? blo[a] : bhi[a], neg, t0, inv_dt));
+                }
+                if (j1 <= j0) continue;
+                len[i] = j1 - j0;
+                j0s[i] = j0;
+                tl_sum += len[i];
+            }
+#pragma unroll
+            for (int i = 0; i < PM_CPT; ++i) {  // slot data of the non-empty runs, <dL/dS, c_k>
+                if (len[i] == 0) continue;
+                const int slot = tid * PM_CPT + i;
+                const float* gsr = S.grad_sem + (long long)rr[i] * C;
+                float gv[CP];
+#pragma unroll
+                for (int c = 0; c < CP; ++c) gv[c] = c < C ? __ldg(gsr + c) : 0.f;
+                float cdv = 0.f;
+#pragma unroll
+                for (int c = 0; c < CP; ++c) cdv = fmaf(gv[c], sh.lp[c], cdv);
+                sh.d[0][slot] = dv[i].x;
+                sh.d[1][slot] = dv[i].y;
+                sh.d[2][slot] = dv[i].z;
+                sh.r[slot] = rr[i];
+                sh.jc[slot] = j0s[i] | (cam[i] << 10);
+                sh.cd[slot] = cdv;
+            }
+            // ---- exclusive scan of the run lengths in slot order; list the non-empty slots
+            int npairs;
+            {
+                const int il = warp_incl_scan(tl_sum, lane);
+                if (lane == 31) sh.wtot[wid] = il;
+                __syncthreads();
+                int wl = 0, tl2 = 0;
+#pragma unroll
+                for (int w2 = 0; w2 < PM_WARPS; ++w2) {
+                    const int a = sh.wtot[w2];
+                    if (w2 < wid) wl += a;
+                    tl2 += a;
+                }
+                int pl = wl + il - tl_sum;
+#pragma unroll
+                for (int i = 0; i < PM_CPT; ++i) {
+                    sh.pre[tid * PM_CPT + i] = pl;
+                    pl += len[i];
+                }
+                npairs = tl2;
+                if (tid == 0) sh.pre[PM_CHUNK] = tl2;
+                sh.head_slot[tid] = -1;
+            }
+            __syncthreads();
+
+            // ---- walk: thread tid takes pairs [p, p1), the slices in thread order
+            // (empty slices only at the end).  Each step evaluates up to PM_NS pairs of
+            // one run; the next step's (dL/dalpha_j, w_j) loads are issued before
+            // this step's arithmetic (the gathers are latency-bound).
+            {
+                const int q = npairs / PM_THREADS, rm = npairs % PM_THREADS;
+                int p = tid * q + min(tid, rm);
+                const int p1 = p + q + (tid < rm ? 1 : 0);
+                if (p < p1) {
+                    int slot = 0;
+#pragma unroll
+                    for (int step = PM_CHUNK / 2; step > 0; step >>= 1)
+                        if (sh.pre[slot + step] <= p) slot += step;
+                    bool head = sh.pre[slot] < p;
+                    float o[3], d[3];
+                    int jcs = sh.jc[slot];
+                    camera_origin(S, jcs >> 10, o);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) d[a] = sh.d[a][slot];
+                    float cd = sh.cd[slot];
+                    const float2* gwr = S.gw + (long long)sh.r[slot] * L;
+                    int jj = (jcs & 1023) + (p - sh.pre[slot]);
+                    int rend = sh.pre[slot + 1];
+                    int se = min(rend, p1);
+                    int m = min(PM_NS, se - p);  // pairs of this step
+                    float2 gq[PM_NS];
+#pragma unroll
+                    for (int i = 0; i < PM_NS; ++i) gq[i] = i < m ? gwr[jj + i] : make_float2(0.f, 0.f);
+                    for (;;) {
+                        const int pn = p + m;
+                        // the next step: same run, or the next non-empty slot; its loads
+                        // are issued before this step's arithmetic
+                        const bool more = pn < p1;
+                        const bool sw = more && pn == rend;
+                        int slot_n = slot, jj_n = jj + m, rend_n = rend;
+                        const float2* gwr_n = gwr;
+                        if (sw) {
+                            do {
+                                ++slot_n;
+                            } while (sh.pre[slot_n + 1] == sh.pre[slot_n]);
+                            jj_n = sh.jc[slot_n] & 1023;
+                            rend_n = sh.pre[slot_n + 1];
+                            gwr_n = S.gw + (long long)sh.r[slot_n] * L;
+                        }
+                        const int se_n = min(rend_n, p1);
+                        const int m_n = more ? min(PM_NS, se_n - pn) : 0;
+                        float2 gq_n[PM_NS];
+#pragma unroll
+                        for (int i = 0; i < PM_NS; ++i)
+                            gq_n[i] = i < m_n ? gwr_n[jj_n + i] : make_float2(0.f, 0.f);
+                        // this step's pairs
+#pragma unroll
+                        for (int i = 0; i < PM_NS; ++i) {
+                            if (i < m) {
+                                const float tj = sh.ts[jj + i];
+                                float x[3], pr[11];
+#pragma unroll
+                                for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(tj, d[a]));
+                                const float po = occupancy_partials(P, x, pr);
+                                if (po != 0.f) accumulate(acc, po, pr, gq[i].x, gq[i].y, P.f.sigma, cd);
+                            }
+                        }
+                        if (pn == se) {  // the run's part in this slice is done
+                            if (head) {
+                                sh.head_slot[tid] = slot;
+                                sh.head_val[tid] = acc[12];
+                                head = false;
+                            } else {
+                                sh.wsum[slot] = acc[12];
+                            }
+                            acc[12] = 0.f;
+                        }
+                        if (!more) break;
+                        if (sw) {
+                            jcs = sh.jc[slot_n];
+                            camera_origin(S, jcs >> 10, o);
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) d[a] = sh.d[a][slot_n];
+                            cd = sh.cd[slot_n];
+                        }
+                        slot = slot_n;
+                        jj = jj_n;
+                        rend = rend_n;
+                        gwr = gwr_n;
+                        se = se_n;
+                        m = m_n;
+#pragma unroll
+                        for (int i = 0; i < PM_NS; ++i) gq[i] = gq_n[i];
+                        p = pn;
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- runs shared by several slices: the owner's part, then the others' in thread order
+            {
+                const int hs = sh.head_slot[tid];
+                if (hs >= 0 && (tid == 0 || sh.head_slot[tid - 1] != hs)) {
+                    float v = sh.wsum[hs];
+                    for (int t2 = tid; t2 < PM_THREADS && sh.head_slot[t2] == hs; ++t2) v += sh.head_val[t2];
+                    sh.wsum[hs] = v;
+                }
+            }
+            __syncthreads();
+            // ---- class gradient of the runs, sum over runs of (sum_j w_j p_o) dL/dS_ray:
+            // each thread over its own slots, then per class a butterfly within the
+            // warps and the warps in order
+            {
+                float cgp[CP];
+#pragma unroll
+                for (int c = 0; c < CP; ++c) cgp[c] = 0.f;
+#pragma unroll
+                for (int i = 0; i < PM_CPT; ++i) {
+                    const int slot = tid * PM_CPT + i;
+                    if (sh.pre[slot + 1] == sh.pre[slot]) continue;
+                    const float wv = sh.wsum[slot];
+                    const float* gsr = S.grad_sem + (long long)sh.r[slot] * C;
+#pragma unroll
+                    for (int c = 0; c < CP; ++c)
+                        if (c < C) cgp[c] = fmaf(wv, __ldg(gsr + c), cgp[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < CP; ++c) {
+                    const float v = warp_sum(cgp[c]);
+                    if (lane == 0) sh.cpart[wid][c] = v;
+                }
+                __syncthreads();
+                if (tid < C)
+#pragma unroll
+                    for (int w2 = 0; w2 < PM_WARPS; ++w2) cg += sh.cpart[w2][tid];
+                __syncthreads();
+            }
+        }
+        // ---- the tile's sums
+#pragma unroll
+        for (int i = 0; i < NRAW; ++i) {
+            const float v = warp_sum(acc[i]);
+            if (lane == 0) sh.red[wid][i] = v;
+        }
+        __syncthreads();
+        float* out = A.part + (size_t)tile * GF;
+        if (tid < NRAW) {
+            float v = 0.f;
+#pragma unroll
+            for (int w2 = 0; w2 < PM_WARPS; ++w2) v += sh.red[w2][tid];
+            out[tid] = v;
+        }
+        if (tid < C) out[NRAW + tid] = cg;
+        __syncthreads();
+    }
+}
+
+// Each primitive's accumulator row: its tiles' sums in tile order.
+__global__ void k_pm_final(Batch B, PmArgs A) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = (int)(idx / GF), i = (int)(idx % GF);
+    if (g >= A.ntot) return;
+    const int s = scene_of_prim(A.poff, B.n, g);
+    const SceneDesc& S = B.d[s];
+    if (i >= NRAW + S.C) return;
+    const int k = g - (int)__ldg(A.poff + s);
+    float v = 0.f;
+    for (int t = __ldg(A.toff + g); t < __ldg(A.toff + g + 1); ++t) v += A.part[(size_t)t * GF + i];
+    S.gacc[(size_t)k * GF + i] = v;
+}
+
+}  // namespace
+
+sq_status_t launch_backward_pm(const Batch& B, const PmArgs& A, int cp, cudaStream_t st) {
+    if (A.ntot == 0) return SQ_OK;
+    const void* fn = nullptr;
+    switch (cp) {
+        case 4: fn = (const void*)k_pm_tiles<4>; break;
+        case 8: fn = (const void*)k_pm_tiles<8>; break;
+        case 12: fn = (const void*)k_pm_tiles<12>; break;
+        case 16: fn = (const void*)k_pm_tiles<16>; break;
+        case 20: fn = (const void*)k_pm_tiles<20>; break;
+        case 24: fn = (const void*)k_pm_tiles<24>; break;
+        case 28: fn = (const void*)k_pm_tiles<28>; break;
+        case 32: fn = (const void*)k_pm_tiles<32>; break;
+        default:
+            set_last_error("n_classes padding %d not supported", cp);
+            return SQ_ERR_INVALID_ARG;
+    }
+    SQ_LAUNCH("k_pm_rects", st, k_pm_rects<<<(unsigned)(((long long)A.ntot * 32 + 127) / 128), 128, 0, st>>>(B, A));
+    if (B.total > 0) SQ_LAUNCH("k_pm_dirs", st, k_pm_dirs<<<(unsigned)((B.total + 255) / 256), 256, 0, st>>>(B));
+    SQ_LAUNCH("k_pm_scan", st, k_pm_scan<<<1, 1024, 0, st>>>(A));
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PM_THREADS, 0);
+    if (e != cudaSuccess) return cuda_status(e, "k_pm_tiles occupancy");
+    long long blocks = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    const long long most = (long long)A.ntot * PM_MAXT;
+    if (blocks > most) blocks = most;
+    Batch barg = B;
+    PmArgs aarg = A;
+    void* args[] = {&barg, &aarg};
+    prof_begin("k_pm_tiles", st);
+    e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(PM_THREADS), args, 0, st);
+    prof_end(st);
+    if (e != cudaSuccess) return cuda_status(e, "k_pm_tiles");
+    const long long nf = (long long)A.ntot * GF;
+    SQ_LAUNCH("k_pm_final", st, k_pm_final<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(B, A));
+    return SQ_OK;
+}
+
+}  // namespace sqr

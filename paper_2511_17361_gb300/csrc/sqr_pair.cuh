@@ -63,4 +63,15 @@ __device__ __forceinline__ float occupancy_partials(const BwdPrim& P, const floa
     return po;
 }
 
+// Adds one pair's weighted partials to running sums, with dL/dp_o = G sigma + w <gS, c>:
+//   acc[0..10] += -p_o dL/dp_o r[i],  acc[11] += G p_o,  acc[12] += w p_o.
+__device__ __forceinline__ void accumulate(float acc[13], float po, const float pr[11], float G, float w, float sigma,
+                                           float cd) {
+    const float gf = -po * fmaf(G, sigma, w * cd);
+#pragma unroll
+    for (int i = 0; i < 11; ++i) acc[i] = fmaf(gf, pr[i], acc[i]);
+    acc[11] = fmaf(G, po, acc[11]);
+    acc[12] = fmaf(w, po, acc[12]);
+}
+
 }  // namespace sqr

@@ -60,12 +60,16 @@ __global__ void k_pack(sq_prims_t P, float4* __restrict__ rec, float4* __restric
 
 // Copies the by-value scene descriptors into device memory (one thread).
 __global__ void k_write_desc(BatchParams P, SceneDesc* __restrict__ d, long long* __restrict__ off,
-                             long long* __restrict__ boff, long long* __restrict__ gboff) {
+                             long long* __restrict__ boff, long long* __restrict__ gboff,
+                             long long* __restrict__ poff) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (int i = 0; i < P.n; ++i) d[i] = P.s[i];
+    long long np = 0;
     for (int i = 0; i <= P.n; ++i) {
         off[i] = P.off[i];
         boff[i] = P.boff[i];
+        poff[i] = np;
+        if (i < P.n) np += P.s[i].n;
     }
     for (int i = 0; i < 2 * MAX_BATCH; ++i) gboff[i] = P.gboff[i];
 }
@@ -116,8 +120,10 @@ constexpr size_t HDR_DESC = 0;
 constexpr size_t HDR_OFF = (MAX_BATCH * sizeof(SceneDesc) + 255) / 256 * 256;
 constexpr size_t HDR_BOFF = HDR_OFF + ((MAX_BATCH + 1) * sizeof(long long) + 255) / 256 * 256;
 constexpr size_t HDR_GBOFF = HDR_BOFF + ((MAX_BATCH + 1) * sizeof(long long) + 255) / 256 * 256;
-constexpr size_t HDR_CTR = HDR_GBOFF + (2 * MAX_BATCH * sizeof(long long) + 255) / 256 * 256;
+constexpr size_t HDR_POFF = HDR_GBOFF + (2 * MAX_BATCH * sizeof(long long) + 255) / 256 * 256;
+constexpr size_t HDR_CTR = HDR_POFF + ((MAX_BATCH + 1) * sizeof(long long) + 255) / 256 * 256;
 constexpr size_t HDR_END = HDR_CTR + 256;
+constexpr int CTR_PM = 48;  // counter of the primitive-major tile walk (slots 0..MAX_BATCH serve the others)
 
 SceneWs scene_ws(const sq_prims_t* p, size_t base) {
     SceneWs w;
@@ -133,14 +139,46 @@ SceneWs scene_ws(const sq_prims_t* p, size_t base) {
 }
 
 // The backward's per-sample (dL/dalpha_j, w_j) of every scene follow the scene
-// blocks, so a forward needs only the prefix.
+// blocks, so a forward needs only the prefix; then the primitive-major
+// backward's blocks: per scene the box rectangles [n, n_cam], and over all
+// primitives the candidate counts, tile offsets and tile sums.
 size_t gw_bytes(const sq_rays_t* r) { return align_up((size_t)r->n_cam * r->H * r->W * r->L * sizeof(float2), 256); }
+
+size_t rect_bytes(const sq_scene_t* s) {
+    return align_up((size_t)(s->prims.n > 0 ? s->prims.n : 0) * (size_t)(s->rays.n_cam > 0 ? s->rays.n_cam : 0) *
+                        sizeof(int4),
+                    256);
+}
+
+size_t dir_bytes(const sq_rays_t* r) { return align_up((size_t)r->n_cam * r->H * r->W * sizeof(float4), 256); }
+
+struct PmWs {
+    size_t cnt, toff, tprim, part, end;
+};
+
+PmWs pm_ws(size_t at, long long ntot) {
+    PmWs w;
+    w.cnt = align_up(at, 256);
+    w.toff = align_up(w.cnt + (size_t)ntot * sizeof(int), 256);
+    w.tprim = align_up(w.toff + (size_t)(ntot + 1) * sizeof(int), 256);
+    w.part = align_up(w.tprim + (size_t)ntot * PM_MAXT * sizeof(int), 256);
+    w.end = align_up(w.part + (size_t)ntot * PM_MAXT * GF * sizeof(float), 256);
+    return w;
+}
 
 size_t batch_ws_size(const sq_scene_t* sc, int n, bool bwd) {
     size_t at = HDR_END;
     for (int i = 0; i < n; ++i) at = scene_ws(&sc[i].prims, at).end;
-    if (bwd)
-        for (int i = 0; i < n; ++i) at += gw_bytes(&sc[i].rays);
+    if (bwd) {
+        long long ntot = 0;
+        for (int i = 0; i < n; ++i) {
+            at += gw_bytes(&sc[i].rays);
+            at += rect_bytes(&sc[i]);
+            at += dir_bytes(&sc[i].rays);
+            ntot += sc[i].prims.n > 0 ? sc[i].prims.n : 0;
+        }
+        at = pm_ws(at, ntot).end;
+    }
     return at;
 }
 
@@ -162,7 +200,7 @@ void saved_ptrs(const sq_rays_t* r, int C, void* saved, SceneDesc& D) {
     D.save_n = (int*)p;
 }
 
-Tuning default_tuning() { return Tuning{4, 8, 0}; }
+Tuning default_tuning() { return Tuning{4, 8, 0, SQ_BWD_RAY_MAJOR}; }
 
 }  // namespace
 
@@ -327,29 +365,50 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
         i0 = i1;
     }
     gfirst[ng] = n;
-    if (op == SQ_OP_BWD)
+    long long ntot = 0;
+    PmWs pw{};
+    if (op == SQ_OP_BWD) {
         for (int i = 0; i < n; ++i) {
             P.s[i].gw = (float2*)(base + at);
             at += gw_bytes(&sc[i].rays);
+            P.s[i].pm_rect = (int4*)(base + at);
+            at += rect_bytes(&sc[i]);
+            P.s[i].pm_dir = (float4*)(base + at);
+            at += dir_bytes(&sc[i].rays);
+            ntot += sc[i].prims.n;
         }
+        if (ntot * PM_MAXT >= 2147483647LL) {
+            set_last_error("a backward batch holds at most %d primitives", (int)(2147483647LL / PM_MAXT));
+            return SQ_ERR_INVALID_ARG;
+        }
+        pw = pm_ws(at, ntot);
+    }
     SceneDesc* d = (SceneDesc*)(base + HDR_DESC);
     long long* off = (long long*)(base + HDR_OFF);
     long long* boff = (long long*)(base + HDR_BOFF);
     long long* gboff = (long long*)(base + HDR_GBOFF);
+    long long* poff = (long long*)(base + HDR_POFF);
     int* ctr = (int*)(base + HDR_CTR);
-    SQ_LAUNCH("k_write_desc", st, k_write_desc<<<1, 32, 0, st>>>(P, d, off, boff, gboff));
+    SQ_LAUNCH("k_write_desc", st, k_write_desc<<<1, 32, 0, st>>>(P, d, off, boff, gboff, poff));
     cudaError_t e = cudaMemsetAsync(ctr, 0, 256, st);
     if (e != cudaSuccess) return cuda_status(e, "memset counter");
     Batch B{d, off, boff, n, total, ctr, lmax};
     sq_status_t ls = (op == SQ_OP_FWD) ? launch_forward(B, cp, tn, st) : launch_sweep(B, cp, st);
     if (ls != SQ_OK) return ls;
     if (op == SQ_OP_BWD) {
-        for (int g = 0; g < ng; ++g) {  // one run-walk launch per group, each with its own counter
-            const int i0 = gfirst[g], i1 = gfirst[g + 1];
-            const Batch Bg{d + i0, off + i0, gboff + i0 + g, i1 - i0, P.off[i1] - P.off[i0], ctr + 1 + g,
-                           sc[i0].rays.L};
-            ls = launch_backward(Bg, cp, tn, st);
+        if (tn.bwd_order == SQ_BWD_PRIMITIVE_MAJOR) {
+            const PmArgs A{poff, (int)ntot, (int*)(base + pw.cnt), (int*)(base + pw.toff), (float*)(base + pw.part),
+                           (int*)(base + pw.tprim), ctr + CTR_PM};
+            ls = launch_backward_pm(B, A, cp, st);
             if (ls != SQ_OK) return ls;
+        } else {
+            for (int g = 0; g < ng; ++g) {  // one run-walk launch per group, each with its own counter
+                const int i0 = gfirst[g], i1 = gfirst[g + 1];
+                const Batch Bg{d + i0, off + i0, gboff + i0 + g, i1 - i0, P.off[i1] - P.off[i0], ctr + 1 + g,
+                               sc[i0].rays.L};
+                ls = launch_backward(Bg, cp, tn, st);
+                if (ls != SQ_OK) return ls;
+            }
         }
         for (int i = 0; i < n; ++i) {
             const sq_scene_t& s = sc[i];
@@ -407,6 +466,11 @@ sq_status_t batched_api_impl(int op, const sq_scene_t* sc, int n, const sq_tunin
         t.fwd_lanes = tuning->fwd_lanes_per_ray;
         t.fwd_warps = tuning->fwd_warps_per_cta;
         t.bwd_warps = tuning->bwd_warps_per_cta;
+        if (tuning->bwd_order != SQ_BWD_DEFAULT) t.bwd_order = tuning->bwd_order;
+    }
+    if (t.bwd_order != SQ_BWD_RAY_MAJOR && t.bwd_order != SQ_BWD_PRIMITIVE_MAJOR) {
+        set_last_error("backward order %d not supported", t.bwd_order);
+        return SQ_ERR_INVALID_ARG;
     }
     return batched_impl(op, sc, n, t, ws, ws_bytes, st);
 }
@@ -417,7 +481,10 @@ sq_status_t batched_api_impl(int op, const sq_scene_t* sc, int n, const sq_tunin
 sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes, cudaStream_t st, sq_tuning_t* best,
                           float* fwd_ms, float* bwd_ms, int reps) {
     const Tuning fcand[4] = {{4, 4, 8}, {4, 8, 8}, {8, 4, 8}, {8, 8, 8}};
-    const int bcand[3] = {0, 4, 8};  // 0: the most resident warps for the batch's L
+    // ray-major with 0 (the most resident warps for the batch's L), 4 or 8 warps per
+    // CTA, then primitive-major
+    const int bcand[4] = {0, 4, 8, 0};
+    const int bord[4] = {SQ_BWD_RAY_MAJOR, SQ_BWD_RAY_MAJOR, SQ_BWD_RAY_MAJOR, SQ_BWD_PRIMITIVE_MAJOR};
     if (reps < 1) reps = 1;
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
@@ -453,9 +520,10 @@ sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes
     if (s == SQ_OK) s = batched_impl(SQ_OP_FWD, sc, n, tb, ws, ws_bytes, st);  // saved state for the backward
     bool do_bwd = s == SQ_OK;
     for (int i = 0; i < n && do_bwd; ++i) do_bwd = sc[i].saved != nullptr && sc[i].grad_depth && sc[i].grad_sem;
-    for (int c = 0; c < 3 && do_bwd && s == SQ_OK; ++c) {
+    for (int c = 0; c < 4 && do_bwd && s == SQ_OK; ++c) {
         Tuning t = tb;
         t.bwd_warps = bcand[c];
+        t.bwd_order = bord[c];
         s = batched_impl(SQ_OP_BWD, sc, n, t, ws, ws_bytes, st);
         if (s != SQ_OK) break;
         cudaEventRecord(e0, st);
@@ -472,6 +540,7 @@ sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes
         if (ms < bestb) {
             bestb = ms;
             tb.bwd_warps = bcand[c];
+            tb.bwd_order = bord[c];
         }
     }
     cudaEventDestroy(e0);
@@ -480,6 +549,7 @@ sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes
     best->fwd_lanes_per_ray = tb.fwd_lanes;
     best->fwd_warps_per_cta = tb.fwd_warps;
     best->bwd_warps_per_cta = tb.bwd_warps;
+    best->bwd_order = tb.bwd_order;
     return SQ_OK;
 }
 

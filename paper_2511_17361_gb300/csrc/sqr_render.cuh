@@ -44,6 +44,8 @@ struct SceneDesc {
     const float* grad_depth;  // backward inputs
     const float* grad_sem;
     float* gacc;         // [N, GF] gradient accumulator (zeroed per backward)
+    int4* pm_rect;       // [N, n_cam] primitive-major backward: pixel rectangle (u0, v0, u1, v1) of each box
+    float4* pm_dir;      // [R] primitive-major backward: ray direction of each pixel, composited samples in .w
 };
 
 struct BatchParams {
@@ -90,7 +92,26 @@ __device__ __forceinline__ void scene_ray(const SceneDesc& S, long long r, float
 struct Tuning {
     int fwd_lanes;  // lanes (samples) per ray in the forward: 4, 8 or 16
     int fwd_warps;  // warps per CTA, forward: 4 or 8
-    int bwd_warps;  // warps per CTA, backward: 1..8, or 0 for the count that keeps the most warps resident
+    int bwd_warps;  // warps per CTA, ray-major backward: 1..8, or 0 for the count that keeps the most warps resident
+    int bwd_order;  // SQ_BWD_RAY_MAJOR or SQ_BWD_PRIMITIVE_MAJOR
+};
+
+// Primitive-major backward (Sec. 3.3.3, Processes 2-3): the primitives of all
+// scenes of a batch are numbered g = poff[scene] + k; each has cnt[g] candidate
+// pixels (its box's rectangles), cut into at most PM_MAXT tiles whose partial
+// sums land in part[tile, GF] and are reduced per primitive in tile order.
+constexpr int PM_MAXT = 64;         // tiles per primitive at most
+constexpr int PM_CHUNK = 1024;      // candidate pixels a tile block takes per pass
+constexpr int PM_TILE_CHUNKS = 4;   // passes per tile, unless the primitive would need more than PM_MAXT tiles
+
+struct PmArgs {
+    const long long* poff;  // [n_scenes + 1] primitive offsets of the scenes
+    int ntot;               // primitives of all scenes
+    int* cnt;               // [ntot] candidate pixels
+    int* toff;              // [ntot + 1] tile offsets (exclusive scan of the tile counts)
+    float* part;            // [ntot * PM_MAXT, GF] tile partial sums
+    int* tprim;             // [ntot * PM_MAXT] primitive of each tile
+    int* ctr;               // zeroed tile counter
 };
 
 int device_sm_count();
@@ -98,6 +119,7 @@ int bwd_rays_per_bundle();
 sq_status_t launch_forward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st);
 sq_status_t launch_sweep(const Batch& B, int cp, cudaStream_t st);
 sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream_t st);
+sq_status_t launch_backward_pm(const Batch& B, const PmArgs& A, int cp, cudaStream_t st);
 sq_status_t launch_grad_out(const SceneDesc& S, float* gm, float* gq, float* gs, float* ge, float* go, float* gl,
                             cudaStream_t st);
 sq_status_t launch_pack_boxes(const int* ranges, int n, int4* boxes, cudaStream_t st);

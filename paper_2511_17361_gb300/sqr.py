@@ -24,6 +24,7 @@ SQ_OK, SQ_ERR_INVALID_ARG, SQ_ERR_CAPACITY, SQ_ERR_CUDA, SQ_ERR_TIMEOUT, SQ_ERR_
 SQ_INDEX_OBB, SQ_INDEX_CUBE, SQ_INDEX_OBB_OPACITY = 0, 1, 2
 SQ_SEM_RAW, SQ_SEM_SOFTMAX = 0, 1
 SQ_OP_INDEX, SQ_OP_FWD, SQ_OP_BWD, SQ_OP_QUERY = 0, 1, 2, 3
+SQ_BWD_DEFAULT, SQ_BWD_RAY_MAJOR, SQ_BWD_PRIMITIVE_MAJOR = 0, 1, 2
 
 _vp = ctypes.c_void_p
 
@@ -61,7 +62,7 @@ class SqScene(ctypes.Structure):
 
 class SqTuning(ctypes.Structure):
     _fields_ = [("fwd_lanes_per_ray", ctypes.c_int), ("fwd_warps_per_cta", ctypes.c_int),
-                ("bwd_warps_per_cta", ctypes.c_int)]
+                ("bwd_warps_per_cta", ctypes.c_int), ("bwd_order", ctypes.c_int)]
 
 
 class SqrError(RuntimeError):
@@ -303,9 +304,12 @@ def new_saved(rays: Rays, n_classes: int, device="cuda"):
     return torch.empty(saved_size(rays, n_classes), dtype=torch.uint8, device=device)
 
 
-def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, grad_sem, saved=None, out=None) -> dict:
+def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, grad_sem, saved=None, out=None,
+               order: int = SQ_BWD_DEFAULT) -> dict:
     """Gradients of sum(gD * depth) + sum(gS * sem) w.r.t. every parameter.  ``saved``
-    comes from render_fwd on the same inputs; when None the forward is run here."""
+    comes from render_fwd on the same inputs; when None the forward is run here.
+    ``order`` (SQ_BWD_*) other than the default goes through sq_render_batched
+    with that backward order."""
     device = prims["means"].device
     grad_depth = _need_cuda_f32(grad_depth.contiguous(), "grad_depth")
     grad_sem = _need_cuda_f32(grad_sem.contiguous(), "grad_sem")
@@ -315,6 +319,19 @@ def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, gr
     if out is None:
         out = {k: torch.empty_like(prims[k]) for k in PRIM_KEYS}
     p, g, r, ix = prims_struct(prims), grid_struct(grid), rays.struct(), index.struct()
+    if order != SQ_BWD_DEFAULT:
+        sc = SqScene()
+        sc.prims, sc.index, sc.grid, sc.rays = p, ix, g, r
+        sc.saved, sc.saved_bytes = _ptr(saved), saved.numel() * saved.element_size()
+        sc.grad_depth, sc.grad_sem = _ptr(grad_depth), _ptr(grad_sem)
+        for k in PRIM_KEYS:
+            setattr(sc, "g_" + k, _ptr(out[k]))
+        arr = (SqScene * 1)(sc)
+        ws = _ws.get("bwd", lib.sq_batched_workspace_size(arr, 1), device)
+        tn = SqTuning(4, 8, 0, order)
+        _check(lib.sq_render_batched(SQ_OP_BWD, arr, 1, ctypes.byref(tn), _ptr(ws), ws.numel(), _stream()),
+               "sq_render_batched")
+        return out
     wsz = lib.sq_workspace_size(SQ_OP_BWD, ctypes.byref(p), ctypes.byref(g), ctypes.byref(r))
     ws = _ws.get("bwd", wsz, device)
     _check(lib.sq_render_bwd(ctypes.byref(p), ctypes.byref(ix), ctypes.byref(g), ctypes.byref(r), _ptr(saved),
@@ -480,7 +497,7 @@ def render_batched(op: int, scenes, tuning: dict | None = None):
     device = scenes[0].prims["means"].device
     ws = _ws.get("batched", lib.sq_batched_workspace_size(arr, len(scenes)), device)
     tn = None if tuning is None else SqTuning(tuning["fwd_lanes_per_ray"], tuning["fwd_warps_per_cta"],
-                                              tuning["bwd_warps_per_cta"])
+                                              tuning["bwd_warps_per_cta"], tuning.get("bwd_order", SQ_BWD_DEFAULT))
     _check(lib.sq_render_batched(op, arr, len(scenes), ctypes.byref(tn) if tn else None, _ptr(ws), ws.numel(),
                                  _stream()), "sq_render_batched")
 
@@ -512,11 +529,12 @@ def autotune(scenes, reps: int = 3, use_cache: bool = True) -> dict:
     ws = _ws.get("batched", lib.sq_batched_workspace_size(arr, len(scenes)), device)
     best = SqTuning()
     fms = (ctypes.c_float * 4)()
-    bms = (ctypes.c_float * 3)()
+    bms = (ctypes.c_float * 4)()
     _check(lib.sq_autotune(arr, len(scenes), _ptr(ws), ws.numel(), _stream(), reps, ctypes.byref(best), fms, bms),
            "sq_autotune")
     out = {"fwd_lanes_per_ray": best.fwd_lanes_per_ray, "fwd_warps_per_cta": best.fwd_warps_per_cta,
-           "bwd_warps_per_cta": best.bwd_warps_per_cta, "fwd_ms": list(fms), "bwd_ms": list(bms)}
+           "bwd_warps_per_cta": best.bwd_warps_per_cta, "bwd_order": best.bwd_order, "fwd_ms": list(fms),
+           "bwd_ms": list(bms)}
     if use_cache:
         cache[key] = out
         try:

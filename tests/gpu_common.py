@@ -55,14 +55,36 @@ def check_sem(s_gpu, s_ref, raw_tol=5e-5):
     assert rel.max() <= raw_tol, f"raw semantics off by {rel.max():.3g} (rel)"
 
 
-def check_grad(g_gpu, g_ref, name, rtol=1e-3):
-    """Per element |g - g_ref| <= rtol * max(|g_ref|, 1e-3 * max|g_ref| over the tensor)."""
+def check_grad(g_gpu, g_ref, name, rtol=1e-3, mag=None):
+    """Per element |g - g_ref| <= rtol * max(|g_ref|, 1e-3 * max|g_ref| over the tensor).
+    ``mag`` (optional, same shape): sum over rays of |per-ray gradient| from the
+    oracle.  An FP32 sum of terms whose magnitudes add up to mag carries a rounding
+    error of order 2^-24 * mag whatever the order of summation, so 16 * 2^-24 * mag
+    is added to the tolerance: this matters only where the rays' contributions
+    cancel (|g_ref| far below mag)."""
     g_gpu = np.asarray(g_gpu, np.float64)
     g_ref = np.asarray(g_ref, np.float64)
     scale = np.max(np.abs(g_ref)) if g_ref.size else 0.0
     tol = rtol * np.maximum(np.abs(g_ref), 1e-3 * scale)
+    if mag is not None:
+        tol = tol + 16.0 * 2.0 ** -24 * np.asarray(mag, np.float64)
     err = np.abs(g_gpu - g_ref)
     bad = err > tol + 1e-30
     assert not bad.any(), (f"{name}: {bad.sum()}/{bad.size} elements off; worst ratio "
                            f"{np.max(err / (tol + 1e-30)):.3g}; norm ratio "
                            f"{np.linalg.norm(g_gpu) / max(np.linalg.norm(g_ref), 1e-300):.6f}")
+
+
+def per_ray_magnitude(prims, grid, idx, rig, t, gd, gs, **kw):
+    """Sum over rays of |the oracle's gradient from that ray alone| per parameter
+    (the magnitude an FP32 sum over the rays' contributions rounds against)."""
+    out = None
+    for r in np.nonzero((np.asarray(gd) != 0) | np.any(np.asarray(gs) != 0, axis=1))[0]:
+        g = oracle.render_bwd(prims, grid, idx, rig, t, np.asarray(gd, np.float64)[[r]],
+                              np.asarray(gs, np.float64)[[r]], ray_ids=np.array([r]), **kw)
+        if out is None:
+            out = {k: np.abs(v) for k, v in g.items()}
+        else:
+            for k in out:
+                out[k] += np.abs(g[k])
+    return out

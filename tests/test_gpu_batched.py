@@ -114,6 +114,11 @@ def test_autotuner_picks_a_measured_candidate(sqr):
     cands = [(4, 4), (4, 8), (8, 4), (8, 8)]
     i = cands.index((best["fwd_lanes_per_ray"], best["fwd_warps_per_cta"]))
     assert best["fwd_ms"][i] == min(best["fwd_ms"])
+    assert len(best["bwd_ms"]) == 4 and best["bwd_order"] in (sqr.SQ_BWD_RAY_MAJOR, sqr.SQ_BWD_PRIMITIVE_MAJOR)
+    bc = [(sqr.SQ_BWD_RAY_MAJOR, 0), (sqr.SQ_BWD_RAY_MAJOR, 4), (sqr.SQ_BWD_RAY_MAJOR, 8),
+          (sqr.SQ_BWD_PRIMITIVE_MAJOR, 0)]
+    j = bc.index((best["bwd_order"], best["bwd_warps_per_cta"]))
+    assert best["bwd_ms"][j] == min(best["bwd_ms"])
 
 
 def test_cuda_graph_replay_matches_eager(sqr):

@@ -250,7 +250,14 @@ def test_forward_cube_index(sqr):
 
 
 # ----------------------------------------------------------------------- backward
-def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0, kappa=0.0, flags=True, mode=0):
+@pytest.fixture(params=["ray_major", "primitive_major"])
+def bwd_order(request, sqr):
+    """Both backward orders (Sec. 3.3.3): ray-major run walk, primitive-major tiles."""
+    return {"ray_major": sqr.SQ_BWD_RAY_MAJOR, "primitive_major": sqr.SQ_BWD_PRIMITIVE_MAJOR}[request.param]
+
+
+def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0, kappa=0.0, flags=True, mode=0,
+              order=0):
     prims_d, rays = scene_to_gpu(sqr, prims, rig, t, kappa, alpha_max)
     g = dev_grid(grid)
     ix = sqr.build_index(prims_d, g, mode=mode, flags=flags)
@@ -260,7 +267,8 @@ def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0, kap
     sel = np.arange(R) if ray_ids is None else np.asarray(ray_ids)
     gd_full[sel] = gd
     gs_full[sel] = gs
-    out = sqr.render_bwd(prims_d, ix, g, rays, torch.from_numpy(gd_full).cuda(), torch.from_numpy(gs_full).cuda())
+    out = sqr.render_bwd(prims_d, ix, g, rays, torch.from_numpy(gd_full).cuda(), torch.from_numpy(gs_full).cuda(),
+                         order=order)
     torch.cuda.synchronize()
     ref = oracle.render_bwd(prims, grid, np_index(ix), rig, t, gd_full[sel].astype(np.float64),
                             gs_full[sel].astype(np.float64), alpha_max=alpha_max, kappa=kappa,
@@ -269,7 +277,7 @@ def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0, kap
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_backward_small_scene_full(sqr, seed):
+def test_backward_small_scene_full(sqr, seed, bwd_order):
     """Every gradient of a small scene, for 5, 18 and 32 classes (the logit
     gradients of 32 classes span two 32-lane blocks of the accumulator)."""
     pr, grid, rig, t = small_scene(seed, n=8, H=9, W=11, L=32, C=[5, 18, 32][seed], sigma_max=0.6)
@@ -277,13 +285,13 @@ def test_backward_small_scene_full(sqr, seed):
     rng = np.random.default_rng(seed)
     gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, pr["logits"].shape[1])).astype(
         np.float32)
-    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs)
+    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, order=bwd_order)
     for k in ref:
         check_grad(got[k], ref[k], k)
 
 
 @pytest.mark.parametrize("flags", [True, False])
-def test_backward_long_sample_steps(sqr, flags):
+def test_backward_long_sample_steps(sqr, flags, bwd_order):
     """Samples several voxels apart (run starts then come from a test of each list
     entry's range, not from the boundary flags), with and without the index's
     flags; and the default spacing without flags."""
@@ -291,7 +299,7 @@ def test_backward_long_sample_steps(sqr, flags):
     R = rig["H"] * rig["W"]
     rng = np.random.default_rng(9)
     gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, 5)).astype(np.float32)
-    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, flags=flags)
+    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, flags=flags, order=bwd_order)
     assert np.count_nonzero(ref["opacity"]) > 3
     for k in ref:
         check_grad(got[k], ref[k], k)
@@ -299,12 +307,12 @@ def test_backward_long_sample_steps(sqr, flags):
         pr, grid, rig, t = small_scene(10, n=8, H=9, W=11, L=32)
         R = rig["H"] * rig["W"]
         gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, 5)).astype(np.float32)
-        got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, flags=False)
+        got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, flags=False, order=bwd_order)
         for k in ref:
             check_grad(got[k], ref[k], k)
 
 
-def test_render_with_opacity_index(sqr):
+def test_render_with_opacity_index(sqr, bwd_order):
     """Forward and backward over the opacity-aware index, against the oracle
     rendering the same index."""
     cfg = synth.make_config(0)
@@ -315,22 +323,22 @@ def test_render_with_opacity_index(sqr):
     R = rig["H"] * rig["W"]
     rng = np.random.default_rng(13)
     gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, 5)).astype(np.float32)
-    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, mode=2)
+    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, mode=2, order=bwd_order)
     for k in ref:
         check_grad(got[k], ref[k], k)
 
 
-def test_backward_clamp_active(sqr):
+def test_backward_clamp_active(sqr, bwd_order):
     pr, grid, rig, t = small_scene(6, n=12, sigma_max=2.5, s_range=(1.0, 2.5))
     R = rig["H"] * rig["W"]
     rng = np.random.default_rng(6)
     gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, 5)).astype(np.float32)
-    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs)
+    got, ref = _bwd_pair(sqr, pr, grid, rig, t, gd, gs, order=bwd_order)
     for k in ref:
         check_grad(got[k], ref[k], k)
 
 
-def test_backward_early_termination(sqr):
+def test_backward_early_termination(sqr, bwd_order):
     """kappa > 0: gradients flow only through the composited samples; cotangents on
     rays whose T stays clear of kappa (1e-4 relative) at every sample."""
     cfg = synth.make_config(0)
@@ -347,12 +355,13 @@ def test_backward_early_termination(sqr):
     rng = np.random.default_rng(8)
     gd = rng.standard_normal(len(safe)).astype(np.float32)
     gs = rng.standard_normal((len(safe), 18)).astype(np.float32)
-    got, ref = _bwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], gd, gs, ray_ids=safe, kappa=kappa)
+    got, ref = _bwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], gd, gs, ray_ids=safe, kappa=kappa,
+                         order=bwd_order)
     for k in ref:
         check_grad(got[k], ref[k], k)
 
 
-def test_backward_stress_crop(sqr):
+def test_backward_stress_crop(sqr, bwd_order):
     """16,384 clustered superquadrics, 32x32-ray crop of camera 0 (cotangents zero
     elsewhere): every parameter's gradient vs the FP64 oracle."""
     cfg = synth.make_config(2)
@@ -362,14 +371,15 @@ def test_backward_stress_crop(sqr):
     rng = np.random.default_rng(2)
     gd = rng.standard_normal(len(rays)).astype(np.float32)
     gs = rng.standard_normal((len(rays), 18)).astype(np.float32)
-    got, ref = _bwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], gd, gs, ray_ids=rays)
+    got, ref = _bwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], gd, gs, ray_ids=rays,
+                         order=bwd_order)
     touched = np.abs(ref["opacity"]) > 0
     assert touched.sum() > 100
     for k in ref:
         check_grad(got[k], ref[k], k)
 
 
-def test_backward_full_frame_sparse_cotangents(sqr):
+def test_backward_full_frame_sparse_cotangents(sqr, bwd_order):
     """540,000-ray frame, cotangents on 400 sampled rays only."""
     cfg = synth.make_config(1)
     R = synth.n_rays(cfg["rig"])
@@ -377,7 +387,8 @@ def test_backward_full_frame_sparse_cotangents(sqr):
     rays = np.unique(rng.integers(0, R, 400))
     gd = rng.standard_normal(len(rays)).astype(np.float32)
     gs = rng.standard_normal((len(rays), 18)).astype(np.float32)
-    got, ref = _bwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], gd, gs, ray_ids=rays)
+    got, ref = _bwd_pair(sqr, cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], gd, gs, ray_ids=rays,
+                         order=bwd_order)
     for k in ref:
         check_grad(got[k], ref[k], k)
 
