@@ -36,10 +36,11 @@ MUFU_PER_PAIR = {"fwd": 9, "bwd": 13}  # SFU ops per (sample, primitive) pair in
 # DRAM traffic per launch from the committed ncu summaries, valid only while the
 # kernel source is unchanged (sha256 of the file holding it).
 NCU_TRAFFIC = {
-    "k_backward": {"src": "sqr_bwd.cu", "src_sha": "b7f4511792737268", "bytes_per_launch": 309358336},
+    "k_backward": {"src": "sqr_bwd.cu", "src_sha": "34900eef8431e285", "bytes_per_launch": 310181888},
     "k_forward": {"src": "sqr_fwd.cu", "src_sha": "bbf4eba00091e5d5", "bytes_per_launch": 1718119936},
-    "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "b7f4511792737268", "bytes_per_launch": 1938899200},
-    "k_query": {"src": "sqr_query.cu", "src_sha": "47dc05a1936a09f9", "bytes_per_launch": 176217856},
+    "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "34900eef8431e285", "bytes_per_launch": 1938695008},
+    "k_pm_tiles": {"src": "sqr_bwd_pm.cu", "src_sha": "faea2da2f5f96db4", "bytes_per_launch": 7282913056},
+    "k_query": {"src": "sqr_query.cu", "src_sha": "87960f15eac3b56a", "bytes_per_launch": 176335872},
 }
 
 
@@ -394,13 +395,20 @@ def run_query(args):
     C = cfg["prims"]["logits"].shape[1]
     out = (torch.empty(nvox, device=dev), torch.empty((nvox, C), device=dev),
            torch.empty(nvox, dtype=torch.uint8, device=dev))
+    # synthetic voxel labels (0..C-1 occupied class, C free) for the voxel losses
     rng = np.random.default_rng(4)
-    gd = torch.from_numpy(rng.standard_normal(nvox).astype(np.float32)).to(dev)
-    gsem = torch.from_numpy(rng.standard_normal((nvox, C)).astype(np.float32)).to(dev)
+    vlab = torch.from_numpy(rng.integers(0, C + 1, nvox).astype(np.int32)).to(dev)
+    lout = (torch.empty(3, device=dev), torch.empty(2, dtype=torch.int32, device=dev),
+            torch.empty(nvox, device=dev), torch.empty((nvox, C), device=dev))
     grads = {k: torch.empty_like(prims[k]) for k in sqr.PRIM_KEYS}
+
+    def backward():  # voxel CE + BCE losses, then the query backward of their gradients
+        _, _, gd, gsem = sqr.loss_voxel(out[0], out[1], vlab, out=lout)
+        sqr.query_grid_bwd(prims, ix, grid, gd, gsem, out=grads)
+
     for _ in range(max(3, args.warmup)):
         sqr.query_grid(prims, ix, grid, 0.05, out=out)
-        sqr.query_grid_bwd(prims, ix, grid, gd, gsem, out=grads)
+        backward()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     sampler = ClockSampler(0)
@@ -412,7 +420,7 @@ def run_query(args):
         ev[s][0].record()
         sqr.query_grid(prims, ix, grid, 0.05, out=out)
         ev[s][1].record()
-        sqr.query_grid_bwd(prims, ix, grid, gd, gsem, out=grads)
+        backward()
         ev[s][2].record()
     torch.cuda.synchronize()
     sqr.profile_enable(False)
@@ -439,7 +447,8 @@ def run_query(args):
             "config": {"workload": cfg["name"], "superquadrics": int(prims["means"].shape[0]), "voxels": nvox,
                        "index_entries_P": P, "tau": 0.05, "l2": "flushed (256 MB write) between timed steps"},
             "gpu_launches": launches + dropped, "kernel_ms_per_launch": {"k_query": k_ms, "k_query_bwd": kb_ms},
-            "backward": {"ms_per_step": ms_bwd, "value": nvox / (ms_bwd / 1e3), "unit": "voxels/s",
+            "backward": {"what": "voxel CE + BCE losses (sq_loss_voxel) and the query backward of their gradients",
+                         "ms_per_step": ms_bwd, "value": nvox / (ms_bwd / 1e3), "unit": "voxels/s",
                          "roofline": {"bound": "alu", "kernel": "k_query_bwd",
                                       "achieved": P * 13 / (kb_ms / 1e3) / 1e9, "peak": peak, "unit": "GMUFUop/s",
                                       "frac": P * 13 / (kb_ms / 1e3) / 1e9 / peak}},

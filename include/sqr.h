@@ -323,6 +323,22 @@ sq_status_t sq_loss_ce_mse(const float* depth, const float* sem, const float* ta
                            long long n_rays, int n_classes, float lambda_s, float lambda_d, float* loss,
                            float* grad_depth, float* grad_sem, void* stream);
 
+/* Voxel losses of the grid query (Supp. A.4: cross-entropy on the semantic
+ * voxels, binary cross-entropy on the density voxels).  Labels y[v], int32:
+ * 0..C-1 an occupied voxel of that class, C a free voxel, -1 ignored.  With
+ * occupancy probability p = 1 - exp(-d) of the density d >= 0 (the chance that
+ * a ray through the voxel is absorbed, the compositing's alpha for density d):
+ *   L = lambda_s * mean_{y in [0,C)} CE(softmax(sem[v]), y[v])
+ *     + lambda_o * mean_{y in [0,C]} BCE(p[v], y[v] < C),
+ * where BCE(p, 0) = d and BCE(p, 1) = -log(1 - exp(-max(d, 1e-6))) (no gradient
+ * below the clamp).  Negative densities count as 0.  A mean over an empty set is
+ * 0.  Writes loss[0..2] = (L, semantic term, occupancy term), counts[0..1] =
+ * (occupied, labelled) voxels, grad_density [V], grad_sem [V, C] (all device,
+ * overwritten; counts also serves the normalisation). */
+sq_status_t sq_loss_voxel(const float* density, const float* sem, const int* label, long long n_voxels,
+                          int n_classes, float lambda_s, float lambda_o, float* loss, int* counts,
+                          float* grad_density, float* grad_sem, void* stream);
+
 /* Work counter for throughput and roofline reports: out[0] = Q, the number of
  * (sample, primitive) pairs the forward pass evaluates (sum over in-grid
  * samples of V_n of the sample's voxel, all L samples, no early termination),

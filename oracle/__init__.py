@@ -259,3 +259,45 @@ def query_grid(prims, grid, index, tau=0.05, voxel_ids=None, threads=0, sem_mode
     _load().orc_query_grid(ctypes.c_int(n), ctypes.c_int(C), *[_p(a) for a in keep], ctypes.c_double(tau), _p(ids),
                            ctypes.c_longlong(V), _p(dens), _p(sem), _p(lab), ctypes.c_int(threads))
     return dens, sem, lab
+
+
+def voxel_loss(density, sem, label, lambda_s=1.0, lambda_o=1.0, d_min=1e-6):
+    """Voxel losses of the grid query (Supp. A.4 / A.5: cross-entropy on the
+    semantic voxels, binary cross-entropy on the density voxels), in FP64.
+
+    Labels: 0..C-1 occupied voxel of that class, C free, -1 ignored.  The density
+    d = max(v_d, 0) enters the BCE through the occupancy probability
+    p = 1 - exp(-d); free voxels cost -log(1 - p) = d, occupied ones
+    -log(p) with d clamped below at d_min (zero gradient under the clamp).  The
+    CE is averaged over occupied voxels, the BCE over labelled ones.
+
+    Returns (total, semantic term, occupancy term, grad_density, grad_sem)."""
+    d_raw = np.asarray(density, np.float64)
+    s = np.asarray(sem, np.float64)
+    y = np.asarray(label, np.int64)
+    V, C = s.shape
+    occ = (y >= 0) & (y < C)
+    free = y == C
+    n_occ, n_lab = int(occ.sum()), int((occ | free).sum())
+    ws = lambda_s / n_occ if n_occ else 0.0
+    wo = lambda_o / n_lab if n_lab else 0.0
+    gs = np.zeros_like(s)
+    ce = 0.0
+    if n_occ:
+        so = s[occ]
+        mx = so.max(1, keepdims=True)
+        e = np.exp(so - mx)
+        z = e.sum(1, keepdims=True)
+        yo = y[occ]
+        ce = float(np.sum(mx[:, 0] + np.log(z[:, 0]) - so[np.arange(len(yo)), yo]))
+        g = e / z
+        g[np.arange(len(yo)), yo] -= 1.0
+        gs[occ] = ws * g
+    d = np.maximum(d_raw, 0.0)
+    gd = np.zeros_like(d)
+    bce = float(np.sum(d[free]))
+    gd[free] = np.where(d_raw[free] > 0.0, wo, 0.0)
+    dc = np.maximum(d[occ], d_min)
+    bce += float(np.sum(-np.log(-np.expm1(-dc))))
+    gd[occ] = np.where(d[occ] > d_min, -wo / np.expm1(np.maximum(d[occ], d_min)), 0.0)
+    return ws * ce + wo * bce, ws * ce, wo * bce, gd, gs

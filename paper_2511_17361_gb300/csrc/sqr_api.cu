@@ -178,6 +178,82 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float* __restrict__
         if (threadIdx.x == 0) atomicAdd(loss, v);
     }
 }
+// Voxel losses: counts of occupied / labelled voxels (first kernel), then the
+// losses and gradients normalised by them (second kernel).
+__global__ void __launch_bounds__(LOSS_THREADS) k_vloss_count(const int* __restrict__ lab, long long V, int C,
+                                                              int* __restrict__ counts) {
+    int no = 0, nl = 0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        const int y = lab[v];
+        no += (y >= 0 && y < C) ? 1 : 0;
+        nl += (y >= 0 && y <= C) ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        no += __shfl_xor_sync(0xffffffffu, no, o);
+        nl += __shfl_xor_sync(0xffffffffu, nl, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (no || nl)) {
+        atomicAdd(counts, no);
+        atomicAdd(counts + 1, nl);
+    }
+}
+
+__global__ void __launch_bounds__(LOSS_THREADS) k_vloss(const float* __restrict__ dens, const float* __restrict__ sem,
+                                                        const int* __restrict__ lab, long long V, int C, float ls,
+                                                        float lo, const int* __restrict__ counts,
+                                                        float* __restrict__ loss, float* __restrict__ gd,
+                                                        float* __restrict__ gs) {
+    __shared__ float red[2][LOSS_THREADS / 32];
+    const int no = counts[0], nl = counts[1];
+    const float ws = no > 0 ? ls / (float)no : 0.f, wo = nl > 0 ? lo / (float)nl : 0.f;
+    float pce = 0.f, pbce = 0.f;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        const int y = lab[v];
+        const float* s = sem + v * C;
+        float* g = gs + v * C;
+        if (y >= 0 && y < C) {  // cross-entropy of the class probabilities
+            float mx = s[0];
+            for (int c = 1; c < C; ++c) mx = fmaxf(mx, s[c]);
+            float z = 0.f;
+            for (int c = 0; c < C; ++c) z += expf(s[c] - mx);
+            pce += mx + logf(z) - s[y];
+            const float iz = 1.f / z;
+            for (int c = 0; c < C; ++c) g[c] = ws * (expf(s[c] - mx) * iz - (c == y ? 1.f : 0.f));
+        } else {
+            for (int c = 0; c < C; ++c) g[c] = 0.f;
+        }
+        const float d = fmaxf(dens[v], 0.f);
+        float gdv = 0.f;
+        if (y == C) {  // free: -log(1 - p) = d
+            pbce += d;
+            gdv = dens[v] > 0.f ? wo : 0.f;
+        } else if (y >= 0 && y < C) {  // occupied: -log p
+            const float dc = fmaxf(d, 1e-6f);
+            pbce += -logf(-expm1f(-dc));
+            gdv = d > 1e-6f ? -wo / expm1f(dc) : 0.f;
+        }
+        gd[v] = gdv;
+    }
+    pce = warp_sum(pce);
+    pbce = warp_sum(pbce);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = pce;
+        red[1][threadIdx.x >> 5] = pbce;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float a = threadIdx.x < (LOSS_THREADS / 32) ? red[0][threadIdx.x] : 0.f;
+        float b = threadIdx.x < (LOSS_THREADS / 32) ? red[1][threadIdx.x] : 0.f;
+        a = warp_sum(a) * ws;
+        b = warp_sum(b) * wo;
+        if (threadIdx.x == 0) {
+            atomicAdd(loss, a + b);
+            atomicAdd(loss + 1, a);
+            atomicAdd(loss + 2, b);
+        }
+    }
+}
 }  // namespace
 
 }  // namespace sqr
@@ -333,6 +409,28 @@ sq_status_t sq_loss_ce_mse(const float* depth, const float* sem, const float* ta
     int blocks = (int)(want < 152LL * 16 ? want : 152LL * 16);
     SQ_LAUNCH("k_loss", st, k_loss<<<blocks, LOSS_THREADS, 0, st>>>(depth, sem, target_depth, target_label, n_rays, n_classes, ws, wd, loss,
                                             grad_depth, grad_sem));
+    return SQ_OK;
+}
+
+sq_status_t sq_loss_voxel(const float* density, const float* sem, const int* label, long long n_voxels,
+                          int n_classes, float lambda_s, float lambda_o, float* loss, int* counts,
+                          float* grad_density, float* grad_sem, void* stream) {
+    if (n_voxels < 0 || n_classes < 1) { set_last_error("sq_loss_voxel: bad sizes"); return SQ_ERR_INVALID_ARG; }
+    if (!loss || !counts || (n_voxels > 0 && (!density || !sem || !label || !grad_density || !grad_sem))) {
+        set_last_error("sq_loss_voxel: NULL pointer");
+        return SQ_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(loss, 0, 3 * sizeof(float), st);
+    if (e != cudaSuccess) return cuda_status(e, "memset loss");
+    e = cudaMemsetAsync(counts, 0, 2 * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_status(e, "memset counts");
+    if (n_voxels == 0) return SQ_OK;
+    const long long want = (n_voxels + LOSS_THREADS - 1) / LOSS_THREADS;
+    const int blocks = (int)(want < 152LL * 16 ? want : 152LL * 16);
+    SQ_LAUNCH("k_vloss_count", st, k_vloss_count<<<blocks, LOSS_THREADS, 0, st>>>(label, n_voxels, n_classes, counts));
+    SQ_LAUNCH("k_vloss", st, k_vloss<<<blocks, LOSS_THREADS, 0, st>>>(density, sem, label, n_voxels, n_classes, lambda_s,
+                                                                     lambda_o, counts, loss, grad_density, grad_sem));
     return SQ_OK;
 }
 

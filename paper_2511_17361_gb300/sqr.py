@@ -88,13 +88,15 @@ def _load():
                                   ctypes.c_size_t, _vp]
     lib.sq_loss_ce_mse.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_float,
                                    ctypes.c_float, _vp, _vp, _vp, _vp]
+    lib.sq_loss_voxel.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                  _vp, _vp, _vp, _vp, _vp]
     lib.sq_count_pairs.argtypes = [P(SqIndex), P(SqGrid), P(SqRays), _vp, _vp]
     lib.sq_batched_workspace_size.restype = ctypes.c_size_t
     lib.sq_batched_workspace_size.argtypes = [P(SqScene), ctypes.c_int]
     lib.sq_render_batched.argtypes = [ctypes.c_int, P(SqScene), ctypes.c_int, P(SqTuning), _vp, ctypes.c_size_t, _vp]
     lib.sq_autotune.argtypes = [P(SqScene), ctypes.c_int, _vp, ctypes.c_size_t, _vp, ctypes.c_int, P(SqTuning),
                                 _vp, _vp]
-    for f in ("sq_build_index", "sq_render_fwd", "sq_render_bwd", "sq_query_grid", "sq_loss_ce_mse",
+    for f in ("sq_build_index", "sq_render_fwd", "sq_render_bwd", "sq_query_grid", "sq_loss_ce_mse", "sq_loss_voxel",
               "sq_count_pairs", "sq_render_batched", "sq_autotune"):
         getattr(lib, f).restype = ctypes.c_int
     lib.sq_status_string.restype = ctypes.c_char_p
@@ -386,6 +388,20 @@ def loss_ce_mse(depth, sem, target_depth, target_label, lambda_s=2.0, lambda_d=0
     _check(lib.sq_loss_ce_mse(_ptr(depth), _ptr(sem), _ptr(target_depth), _ptr(target_label), R, C, lambda_s,
                               lambda_d, _ptr(loss), _ptr(gd), _ptr(gs), _stream()), "sq_loss_ce_mse")
     return loss, gd, gs
+
+
+def loss_voxel(density, sem, label, lambda_s=1.0, lambda_o=1.0, out=None):
+    """Voxel losses of the grid query (CE on the semantic voxels, BCE on the
+    occupancy 1 - exp(-density)); labels int32, C = free, -1 = ignored.  Returns
+    (loss[3] = total, semantic, occupancy; counts[2]; grad_density; grad_sem)."""
+    V, C = sem.shape
+    if out is None:
+        out = (torch.empty(3, device=sem.device), torch.empty(2, dtype=torch.int32, device=sem.device),
+               torch.empty_like(density), torch.empty_like(sem))
+    loss, counts, gd, gs = out
+    _check(lib.sq_loss_voxel(_ptr(density), _ptr(sem), _ptr(label), V, C, lambda_s, lambda_o, _ptr(loss),
+                             _ptr(counts), _ptr(gd), _ptr(gs), _stream()), "sq_loss_voxel")
+    return loss, counts, gd, gs
 
 
 def count_pairs(index: Index, grid: dict, rays: Rays):

@@ -616,3 +616,45 @@ def test_softmax_mode_invariances():
     ones["logits"] = np.ones((pr["logits"].shape[0], 1), np.float32)
     _, S_ones, _, _ = oracle.render_fwd(ones, grid, idx, rig, t)
     np.testing.assert_allclose(S_soft, S_ones, rtol=1e-12, atol=1e-15)
+
+
+# ----------------------------------------------------------------------- voxel losses
+def test_voxel_loss_closed_forms():
+    """Uniform logits cost log C per occupied voxel; an occupied voxel of density
+    ln 2 (p = 1/2) costs ln 2; a free voxel costs its density; ignored voxels and
+    empty sets cost nothing."""
+    C = 6
+    s = np.zeros((4, C))
+    d = np.array([np.log(2.0), 0.7, 5.0, 0.3])
+    y = np.array([2, C, -1, -1])
+    tot, ce, bce, gd, gs = oracle.voxel_loss(d, s, y, lambda_s=1.0, lambda_o=1.0)
+    assert np.isclose(ce, np.log(C), rtol=1e-14)
+    assert np.isclose(bce, (np.log(2.0) + 0.7) / 2, rtol=1e-14)
+    assert np.isclose(tot, ce + bce, rtol=1e-14)
+    assert gd[2] == 0.0 and gd[3] == 0.0 and np.all(gs[1:] == 0.0)
+    assert np.isclose(gd[1], 0.5) and np.isclose(gd[0], -0.5 / (2.0 - 1.0))  # -w/(e^d - 1) at d = ln 2
+    tot, ce, bce, gd, gs = oracle.voxel_loss(d, s, np.full(4, -1))
+    assert tot == 0.0 and not gd.any() and not gs.any()
+
+
+def test_voxel_loss_matches_torch_library():
+    """Against torch's cross_entropy and binary_cross_entropy (FP64) on p = 1 -
+    exp(-d), gradients by autograd, densities away from the clamp."""
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    rng = np.random.default_rng(5)
+    V, C = 300, 7
+    d = rng.uniform(0.01, 4.0, V)
+    s = rng.standard_normal((V, C)) * 2
+    y = rng.integers(-1, C + 1, V)
+    tot, ce, bce, gd, gs = oracle.voxel_loss(d, s, y, lambda_s=2.0, lambda_o=0.5)
+    dt = torch.tensor(d, dtype=torch.float64, requires_grad=True)
+    st = torch.tensor(s, dtype=torch.float64, requires_grad=True)
+    yt = torch.tensor(y)
+    occ, lab = (yt >= 0) & (yt < C), (yt >= 0) & (yt <= C)
+    p = 1.0 - torch.exp(-dt)
+    ref = 2.0 * F.cross_entropy(st[occ], yt[occ]) + 0.5 * F.binary_cross_entropy(p[lab], (yt[lab] < C).double())
+    ref.backward()
+    assert np.isclose(tot, ref.item(), rtol=1e-12)
+    np.testing.assert_allclose(gd, dt.grad.numpy(), rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(gs, st.grad.numpy(), rtol=1e-10, atol=1e-14)
