@@ -209,7 +209,9 @@ sq_status_t sq_render_fwd_noalloc(const sq_prims_t* prims, const sq_index_t* ind
  * dL/dalpha_j = T_j (v_j - U_j) with v_j = gD t_j + <gS, s_j> and
  * U_j = alpha_{j+1} v_{j+1} + (1 - alpha_{j+1}) U_{j+1} needs no division by
  * (1 - alpha).  The index is treated as constant.  Where the alpha clamp is
- * active (sum > alpha_max) no gradient flows through that sample's alpha. */
+ * active (sum > alpha_max) no gradient flows through that sample's alpha.
+ * Accumulates in the default order (SQ_BWD_DEFAULT, below): primitive-major,
+ * bitwise reproducible; sq_render_batched takes the order as a tuning field. */
 sq_status_t sq_render_bwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
                           const sq_rays_t* rays, const void* saved, size_t saved_bytes, const float* grad_depth,
                           const float* grad_sem, float* g_means, float* g_quats, float* g_scales, float* g_eps,
@@ -257,7 +259,8 @@ typedef struct {
  *     its projected rectangle, the exact sample interval of each pixel's ray in
  *     the box), reduced per tile of candidate pixels by one CTA and summed over
  *     the tiles in a fixed order: no atomics, bitwise reproducible gradients.
- *   SQ_BWD_DEFAULT: the library's choice. */
+ *   SQ_BWD_DEFAULT: the library's choice, primitive-major (the faster of the two
+ *     on the six-camera frame; sq_autotune measures both on a given batch). */
 enum { SQ_BWD_DEFAULT = 0, SQ_BWD_RAY_MAJOR = 1, SQ_BWD_PRIMITIVE_MAJOR = 2 };
 
 /* Launch configuration: lanes (= samples marched together) per ray in the

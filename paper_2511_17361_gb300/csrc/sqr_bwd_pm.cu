@@ -8,7 +8,7 @@
 // ray's samples are monotone), so the interactions of k are generated directly
 // from its box:
 //   k_pm_rects  projects the box into every camera: a pixel rectangle that holds
-//               every pixel whose ray can meet the box (conservative, FP64);
+//               every pixel whose ray can meet the box (conservative);
 //   k_pm_scan   turns the rectangles' pixel counts into tiles (at most PM_MAXT per
 //               primitive) and numbers them, with each tile's primitive;
 //   k_pm_tiles  (Process 3) one block per tile: for each candidate pixel the exact
@@ -57,21 +57,22 @@ __device__ __forceinline__ int tiles_of(int cnt) {
 // is t (dx, dy, 1) / |(dx, dy, 1)| with dx = (u + 1/2 - cx) / fx, dy likewise,
 // so for t0 > 0 its depth is at least zc = t0 / max |(dx, dy, 1)|: the box is
 // clipped to the half-space z >= zc / 2 and the vertices of the clipped box
-// (corners in front, edge crossings of the plane) are projected.  Two pixels of
-// margin absorb rounding; degenerate cameras and boxes reaching behind a camera
-// whose rays start at t0 <= 0 get the whole image.
-__device__ int4 box_rect(const float* __restrict__ K, const float* __restrict__ c2w, int H, int W, const double bl[3],
-                         const double bh[3], double t0) {
+// (corners in front, edge crossings of the plane) are projected.  FP32: its
+// rounding is far below the two pixels of margin (the device's FP64 rate made
+// this kernel a fifth of a millisecond); degenerate cameras and boxes reaching
+// behind a camera whose rays start at t0 <= 0 get the whole image.
+__device__ int4 box_rect(const float* __restrict__ K, const float* __restrict__ c2w, int H, int W, const float bl[3],
+                         const float bh[3], float t0) {
     const int4 none = make_int4(0, 0, -1, -1), all = make_int4(0, 0, W - 1, H - 1);
     if (W <= 0 || H <= 0) return none;
-    const double fx = K[0], fy = K[1], cx = K[2], cy = K[3];
-    if (!(fabs(fx) > 0.0) || !(fabs(fy) > 0.0) || !isfinite(fx) || !isfinite(fy)) return all;
-    double R[3][3], o[3];
+    const float fx = K[0], fy = K[1], cx = K[2], cy = K[3];
+    if (!(fabsf(fx) > 0.f) || !(fabsf(fy) > 0.f) || !isfinite(fx) || !isfinite(fy)) return all;
+    float R[3][3], o[3];
     for (int i = 0; i < 3; ++i) {
         for (int j = 0; j < 3; ++j) R[i][j] = c2w[4 * i + j];
         o[i] = c2w[4 * i + 3];
     }
-    double A[3][3];  // adjugate: R^-1 = A / det
+    float A[3][3];  // adjugate: R^-1 = A / det
     A[0][0] = R[1][1] * R[2][2] - R[1][2] * R[2][1];
     A[0][1] = R[0][2] * R[2][1] - R[0][1] * R[2][2];
     A[0][2] = R[0][1] * R[1][2] - R[0][2] * R[1][1];
@@ -81,48 +82,50 @@ __device__ int4 box_rect(const float* __restrict__ K, const float* __restrict__ 
     A[2][0] = R[1][0] * R[2][1] - R[1][1] * R[2][0];
     A[2][1] = R[0][1] * R[2][0] - R[0][0] * R[2][1];
     A[2][2] = R[0][0] * R[1][1] - R[0][1] * R[1][0];
-    const double det = R[0][0] * A[0][0] + R[0][1] * A[1][0] + R[0][2] * A[2][0];
-    if (!(fabs(det) > 0.0) || !isfinite(det)) return all;
-    double P[8][3];
+    const float det = R[0][0] * A[0][0] + R[0][1] * A[1][0] + R[0][2] * A[2][0];
+    if (!(fabsf(det) > 0.f) || !isfinite(det)) return all;
+    const float idet = 1.f / det;
+    float P[8][3];
     for (int c = 0; c < 8; ++c) {
-        const double w[3] = {(c & 1) ? bh[0] : bl[0], (c & 2) ? bh[1] : bl[1], (c & 4) ? bh[2] : bl[2]};
+        const float w[3] = {(c & 1) ? bh[0] : bl[0], (c & 2) ? bh[1] : bl[1], (c & 4) ? bh[2] : bl[2]};
         for (int i = 0; i < 3; ++i)
-            P[c][i] = (A[i][0] * (w[0] - o[0]) + A[i][1] * (w[1] - o[1]) + A[i][2] * (w[2] - o[2])) / det;
+            P[c][i] = (A[i][0] * (w[0] - o[0]) + A[i][1] * (w[1] - o[1]) + A[i][2] * (w[2] - o[2])) * idet;
     }
-    double zc;
-    if (t0 > 0.0) {
-        const double mx = fmax(fabs(0.5 - cx), fabs(W - 0.5 - cx)) / fabs(fx);
-        const double my = fmax(fabs(0.5 - cy), fabs(H - 0.5 - cy)) / fabs(fy);
-        zc = 0.5 * t0 / sqrt(1.0 + mx * mx + my * my);
+    float zc;
+    if (t0 > 0.f) {
+        const float mx = fmaxf(fabsf(0.5f - cx), fabsf(W - 0.5f - cx)) / fabsf(fx);
+        const float my = fmaxf(fabsf(0.5f - cy), fabsf(H - 0.5f - cy)) / fabsf(fy);
+        zc = 0.5f * t0 / sqrtf(1.f + mx * mx + my * my);
     } else {
         for (int c = 0; c < 8; ++c)
-            if (!(P[c][2] > 0.0)) return all;
-        zc = 0.0;
+            if (!(P[c][2] > 0.f)) return all;
+        zc = 0.f;
     }
-    double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
     bool any = false;
-    auto add = [&](double X, double Y, double Z) {
-        const double u = fx * X / Z + cx - 0.5, v = fy * Y / Z + cy - 0.5;
-        umin = fmin(umin, u);
-        umax = fmax(umax, u);
-        vmin = fmin(vmin, v);
-        vmax = fmax(vmax, v);
+    auto add = [&](float X, float Y, float Z) {
+        const float iz = 1.f / Z;
+        const float u = fx * X * iz + cx - 0.5f, v = fy * Y * iz + cy - 0.5f;
+        umin = fminf(umin, u);
+        umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v);
+        vmax = fmaxf(vmax, v);
         any = true;
     };
     for (int c = 0; c < 8; ++c)
-        if (P[c][2] >= zc && P[c][2] > 0.0) add(P[c][0], P[c][1], P[c][2]);
-    if (zc > 0.0)
+        if (P[c][2] >= zc && P[c][2] > 0.f) add(P[c][0], P[c][1], P[c][2]);
+    if (zc > 0.f)
         for (int c = 0; c < 8; ++c)
             for (int b = 1; b < 8; b <<= 1) {
                 if (c & b) continue;
-                const double za = P[c][2], zb = P[c | b][2];
+                const float za = P[c][2], zb = P[c | b][2];
                 if ((za < zc) == (zb < zc)) continue;
-                const double s = (zc - za) / (zb - za);
+                const float s = (zc - za) / (zb - za);
                 add(P[c][0] + s * (P[c | b][0] - P[c][0]), P[c][1] + s * (P[c | b][1] - P[c][1]), zc);
             }
     if (!any || !(umin <= umax) || !(vmin <= vmax)) return none;
-    const double u0 = fmax(floor(umin) - 2.0, 0.0), u1 = fmin(ceil(umax) + 2.0, W - 1.0);
-    const double v0 = fmax(floor(vmin) - 2.0, 0.0), v1 = fmin(ceil(vmax) + 2.0, H - 1.0);
+    const float u0 = fmaxf(floorf(umin) - 2.f, 0.f), u1 = fminf(ceilf(umax) + 2.f, W - 1.f);
+    const float v0 = fmaxf(floorf(vmin) - 2.f, 0.f), v1 = fminf(ceilf(vmax) + 2.f, H - 1.f);
     if (!(u0 <= u1) || !(v0 <= v1)) return none;
     return make_int4((int)u0, (int)v0, (int)u1, (int)v1);
 }
@@ -139,13 +142,13 @@ __global__ void k_pm_rects(Batch B, PmArgs A) {
     const int lo[3] = {b.x & 0xffff, b.y & 0xffff, b.z & 0xffff};
     const int hi[3] = {(int)((unsigned)b.x >> 16), (int)((unsigned)b.y >> 16), (int)((unsigned)b.z >> 16)};
     const bool ok = *S.status == SQ_OK && lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2];
-    double bl[3], bh[3];
+    float bl[3], bh[3];
     for (int a = 0; a < 3; ++a) {
-        bl[a] = (double)S.g.lo[a] + (double)lo[a] * (double)S.g.vs[a];
-        bh[a] = (double)S.g.lo[a] + (double)(hi[a] + 1) * (double)S.g.vs[a];
+        bl[a] = S.g.lo[a] + (float)lo[a] * S.g.vs[a];
+        bh[a] = S.g.lo[a] + (float)(hi[a] + 1) * S.g.vs[a];
     }
     const bool rays = S.n_cam > 0 && S.H > 0 && S.W > 0;  // t may be NULL without rays
-    const double t0 = rays ? (double)__ldg(S.t) : 0.0;
+    const float t0 = rays ? __ldg(S.t) : 0.f;
     int4* rect = S.pm_rect + (size_t)k * S.n_cam;
     long long total = 0;
     for (int c = lane; c < (rays ? S.n_cam : 0); c += 32) {
@@ -270,7 +273,7 @@ __device__ __forceinline__ void camera_origin(const SceneDesc& S, int cam, float
 }
 
 template <int CP>
-__global__ void __launch_bounds__(PM_THREADS, 2) k_pm_tiles(Batch B, PmArgs A) {
+__global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
     __shared__ PmSmem sh;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ntiles = __ldg(A.toff + A.ntot);

@@ -200,7 +200,7 @@ void saved_ptrs(const sq_rays_t* r, int C, void* saved, SceneDesc& D) {
     D.save_n = (int*)p;
 }
 
-Tuning default_tuning() { return Tuning{4, 8, 0, SQ_BWD_RAY_MAJOR}; }
+Tuning default_tuning() { return Tuning{4, 8, 0, SQ_BWD_PRIMITIVE_MAJOR}; }
 
 }  // namespace
 

@@ -101,8 +101,8 @@ struct Tuning {
 // pixels (its box's rectangles), cut into at most PM_MAXT tiles whose partial
 // sums land in part[tile, GF] and are reduced per primitive in tile order.
 constexpr int PM_MAXT = 64;         // tiles per primitive at most
-constexpr int PM_CHUNK = 1024;      // candidate pixels a tile block takes per pass
-constexpr int PM_TILE_CHUNKS = 4;   // passes per tile, unless the primitive would need more than PM_MAXT tiles
+constexpr int PM_CHUNK = 512;       // candidate pixels a tile block takes per pass
+constexpr int PM_TILE_CHUNKS = 8;   // passes per tile, unless the primitive would need more than PM_MAXT tiles
 
 struct PmArgs {
     const long long* poff;  // [n_scenes + 1] primitive offsets of the scenes

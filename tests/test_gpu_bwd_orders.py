@@ -92,6 +92,24 @@ def test_multi_camera_ring(sqr):
         check_grad(got[k], ref[k], k, mag=mag[k])
 
 
+def test_many_cameras(sqr):
+    """18 cameras (more than a tile stages in shared memory: the rectangles are then
+    read from global memory), small images, primitives all around."""
+    pr = synth.prims_driving(200, 25)
+    grid = synth.grid_spec(50, 50, 8)
+    n_cam, H, W, f = 18, 5, 7, 3.0
+    K = np.ascontiguousarray([[f, f, W / 2.0, H / 2.0]] * n_cam, np.float32)
+    poses = [synth.camera_pose(np.deg2rad(20.0 * i), np.array([np.cos(np.deg2rad(20.0 * i)),
+                                                               np.sin(np.deg2rad(20.0 * i)), 1.6]))
+             for i in range(n_cam)]
+    rig = {"n_cam": n_cam, "H": H, "W": W, "K": K, "cam2world": np.ascontiguousarray(poses, np.float32)}
+    t = synth.sample_depths(40)
+    got, ref, mag = _oracle_case(sqr, pr, grid, rig, t, 25)
+    assert np.count_nonzero(ref["opacity"]) > 20
+    for k in ref:
+        check_grad(got[k], ref[k], k, mag=mag[k])
+
+
 def test_full_frame_reproducible_and_matches_ray_major(sqr):
     """540,000-ray frame with dense cotangents: two primitive-major runs agree bit
     for bit; against the ray-major backward (itself checked against the oracle)
