@@ -1,6 +1,7 @@
 // sqr_render.cuh -- internal interface between the render translation units:
 // per-scene descriptors (one or many scenes per launch), the packed-record
-// layout, and the kernel launchers implemented in sqr_fwd.cu and sqr_bwd.cu.
+// layout, and the kernel launchers implemented in sqr_fwd.cu, sqr_bwd.cu and
+// sqr_bwd_pm.cu.
 #pragma once
 
 #include "sqr_common.cuh"
