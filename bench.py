@@ -217,7 +217,8 @@ def run_mine(args):
     tl = torch.from_numpy(tl_np).to(dev)
 
     imode = {"obb": sqr.SQ_INDEX_OBB, "cube": sqr.SQ_INDEX_CUBE, "opacity": sqr.SQ_INDEX_OBB_OPACITY}[args.index]
-    ix = sqr.build_index(prims, grid, mode=imode)  # sizes V_sq (host sync once, before timing)
+    flags = BWD_ORDER == 1  # the range-boundary flags serve only the ray-major backward
+    ix = sqr.build_index(prims, grid, mode=imode, flags=flags)  # sizes V_sq (host sync once, before timing)
     P = ix.P()
     Q, in_grid = sqr.count_pairs(ix, grid, rays)
     depth = torch.empty(R, device=dev)
@@ -482,7 +483,7 @@ def run_batch(args):
         prims = sqr.to_device(c["prims"], dev)
         rays = sqr.Rays.from_rig(c["rig"], c["t"], device=dev)
         grid = {"n": c["grid"]["n"], "lo": [float(v) for v in c["grid"]["lo"]], "vs": [float(v) for v in c["grid"]["vs"]]}
-        ix = sqr.build_index(prims, grid)
+        ix = sqr.build_index(prims, grid, flags=True)  # the autotuner also times the ray-major order
         sc = sqr.Scene(prims, ix, grid, rays, training=True)
         td, tl = synth.loss_targets(rays.R, 300 + i)
         C = c["prims"]["logits"].shape[1]

@@ -215,9 +215,11 @@ def workspace_size(op, prims=None, grid=None, rays=None) -> int:
 # ------------------------------------------------------------------ index
 class Index:
     """Device buffers of the voxel -> superquadric index (V_n, V_f, V_sq, ranges)
-    plus the per-entry range-boundary flags the backward uses."""
+    and, with ``flags``, the per-entry range-boundary flags that the ray-major
+    backward uses to find where a ray enters a range (the primitive-major default
+    does not read them)."""
 
-    def __init__(self, grid: dict, n: int, capacity: int, device, flags: bool = True):
+    def __init__(self, grid: dict, n: int, capacity: int, device, flags: bool = False):
         nvox = int(grid["n"][0]) * int(grid["n"][1]) * int(grid["n"][2])
         self.grid = grid
         self.v_n = torch.empty(nvox, dtype=torch.int32, device=device)
@@ -244,10 +246,11 @@ class Index:
 
 def build_index(prims: dict, grid: dict, mode: int = SQ_INDEX_OBB, tau_cut: float = 0.01, nv: int = 5,
                 capacity: int | None = None, index: Index | None = None, sync: bool = True,
-                flags: bool = True) -> Index:
+                flags: bool = False) -> Index:
     """Builds the index on the current stream.  With ``sync`` the host reads P and
     re-runs once with a large enough V_sq when the capacity was too small.
-    ``flags`` also writes the per-entry range-boundary flags the backward uses."""
+    ``flags`` also writes the per-entry range-boundary flags (for the ray-major
+    backward order)."""
     device = prims["means"].device
     n = prims["means"].shape[0]
     if index is None:

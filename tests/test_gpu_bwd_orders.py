@@ -69,6 +69,17 @@ def test_camera_inside_boxes(sqr):
         check_grad(got[k], ref[k], k, mag=mag[k])
 
 
+def test_uneven_sample_spacing(sqr):
+    """Geometrically spaced samples: the interval ends' estimate (from even spacing)
+    is off by several samples, so the exact search takes over."""
+    pr, grid, rig, _ = small_scene(26, n=9, H=9, W=11, L=36)
+    t = (0.5 * 1.085 ** np.arange(36)).astype(np.float32)
+    got, ref, mag = _oracle_case(sqr, pr, grid, rig, t, 26)
+    assert np.count_nonzero(ref["opacity"]) >= 5
+    for k in ref:
+        check_grad(got[k], ref[k], k, mag=mag[k])
+
+
 def test_axis_aligned_ray(sqr):
     """A ray along a grid axis (two direction components exactly zero): the
     per-axis interval searches see constant coordinates."""

@@ -26,7 +26,7 @@ def sqr():
 
 def _index_pair(sqr, cfg, mode=0, tau=0.01, nv=5):
     prims_d = sqr.to_device(cfg["prims"])
-    ix = sqr.build_index(prims_d, dev_grid(cfg["grid"]), mode=mode, tau_cut=tau, nv=nv)
+    ix = sqr.build_index(prims_d, dev_grid(cfg["grid"]), mode=mode, tau_cut=tau, nv=nv, flags=True)
     ref = oracle.build_index(cfg["prims"], cfg["grid"], mode, tau, nv)
     return prims_d, ix, ref
 
