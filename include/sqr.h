@@ -148,7 +148,9 @@ typedef struct {
 /* Bytes of workspace an entry point needs (op = SQ_OP_*); rays may be NULL for
  * SQ_OP_INDEX, SQ_OP_FWD and SQ_OP_QUERY.  SQ_OP_BWD needs rays: besides the
  * per-primitive records it holds 8 bytes per sample of every ray (dL/dalpha_j
- * and w_j from the back-to-front sweep).  Returns 0 on invalid arguments. */
+ * and w_j from the back-to-front sweep), 16 bytes per ray and per primitive and
+ * camera, and up to 64 tile sums of 192 bytes per primitive (the primitive-major
+ * order).  Returns 0 on invalid arguments. */
 size_t sq_workspace_size(int op, const sq_prims_t* prims, const sq_grid_t* grid, const sq_rays_t* rays);
 
 /* Sec. 3.3.1 "Preliminary Construction": per-primitive voxel ranges, V_n by a
@@ -277,7 +279,8 @@ typedef struct {
 } sq_tuning_t;
 
 /* Workspace bytes for sq_render_batched / sq_autotune on these scenes; when
- * every scene has saved state it includes the backward's 8 bytes per sample. */
+ * every scene has saved state it includes the backward's buffers (as for
+ * SQ_OP_BWD in sq_workspace_size). */
 size_t sq_batched_workspace_size(const sq_scene_t* scenes, int n_scenes);
 
 /* op = SQ_OP_FWD or SQ_OP_BWD over n_scenes (1..SQ_MAX_BATCH) scenes; tuning
