@@ -19,30 +19,33 @@ __global__ void k_pack(sq_prims_t P, float4* __restrict__ rec, float4* __restric
                        int cp) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= P.n) return;
-    float w = P.quats[4 * k + 0], x = P.quats[4 * k + 1], y = P.quats[4 * k + 2], z = P.quats[4 * k + 3];
-    const float nq = sqrtf(w * w + x * x + y * y + z * z);
-    const float inq = 1.0f / nq;
+    // In FP64, each packed value rounded to FP32 once: the scaled coordinate
+    // u_j = M_j . (x - m) cancels near the planes u_j = 0 of the primitive's frame,
+    // where df/dx holds |u_j|^(2/eps - 1); an M carrying the roundings of an FP32
+    // construction cost the gradient there two decimal digits.
+    double w = P.quats[4 * k + 0], x = P.quats[4 * k + 1], y = P.quats[4 * k + 2], z = P.quats[4 * k + 3];
+    const double nq = sqrt(w * w + x * x + y * y + z * z);
+    const double inq = 1.0 / nq;
     w *= inq; x *= inq; y *= inq; z *= inq;
-    float R[3][3];
-    R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z); R[0][2] = 2.f * (x * z + w * y);
-    R[1][0] = 2.f * (x * y + w * z); R[1][1] = 1.f - 2.f * (x * x + z * z); R[1][2] = 2.f * (y * z - w * x);
-    R[2][0] = 2.f * (x * z - w * y); R[2][1] = 2.f * (y * z + w * x); R[2][2] = 1.f - 2.f * (x * x + y * y);
-    const float is[3] = {1.f / P.scales[3 * k + 0], 1.f / P.scales[3 * k + 1], 1.f / P.scales[3 * k + 2]};
-    const float e1 = P.eps[2 * k + 0], e2 = P.eps[2 * k + 1];
-    const float ea = 2.f / e2, eb = e2 / e1, ec = 2.f / e1;
+    double R[3][3];
+    R[0][0] = 1.0 - 2.0 * (y * y + z * z); R[0][1] = 2.0 * (x * y - w * z); R[0][2] = 2.0 * (x * z + w * y);
+    R[1][0] = 2.0 * (x * y + w * z); R[1][1] = 1.0 - 2.0 * (x * x + z * z); R[1][2] = 2.0 * (y * z - w * x);
+    R[2][0] = 2.0 * (x * z - w * y); R[2][1] = 2.0 * (y * z + w * x); R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+    const double is[3] = {1.0 / P.scales[3 * k + 0], 1.0 / P.scales[3 * k + 1], 1.0 / P.scales[3 * k + 2]};
+    const double e1 = P.eps[2 * k + 0], e2 = P.eps[2 * k + 1];
     float M[3][3];
     for (int j = 0; j < 3; ++j)
-        for (int i = 0; i < 3; ++i) M[j][i] = R[i][j] * is[j];
+        for (int i = 0; i < 3; ++i) M[j][i] = (float)(R[i][j] * is[j]);
     float4* r = rec + (size_t)k * REC4;
     r[0] = make_float4(P.means[3 * k + 0], P.means[3 * k + 1], P.means[3 * k + 2], P.opacity[k]);
-    r[1] = make_float4(M[0][0], M[0][1], M[0][2], ea);
-    r[2] = make_float4(M[1][0], M[1][1], M[1][2], eb);
-    r[3] = make_float4(M[2][0], M[2][1], M[2][2], ec);
+    r[1] = make_float4(M[0][0], M[0][1], M[0][2], (float)(2.0 / e2));
+    r[2] = make_float4(M[1][0], M[1][1], M[1][2], (float)(e2 / e1));
+    r[3] = make_float4(M[2][0], M[2][1], M[2][2], (float)(2.0 / e1));
     if (aux) {
         float4* a = aux + (size_t)k * AUX4;
-        a[0] = make_float4(w, x, y, z);
-        a[1] = make_float4(inq, is[0], is[1], is[2]);
-        a[2] = make_float4(e1, e2, 1.f / e1, 1.f / e2);
+        a[0] = make_float4((float)w, (float)x, (float)y, (float)z);
+        a[1] = make_float4((float)inq, (float)is[0], (float)is[1], (float)is[2]);
+        a[2] = make_float4((float)e1, (float)e2, (float)(1.0 / e1), (float)(1.0 / e2));
     }
     const int C = P.n_classes;
     const float* lg = P.logits + (size_t)k * C;

@@ -55,20 +55,19 @@ def check_sem(s_gpu, s_ref, raw_tol=5e-5):
     assert rel.max() <= raw_tol, f"raw semantics off by {rel.max():.3g} (rel)"
 
 
-def check_grad(g_gpu, g_ref, name, rtol=1e-3, mag=None, term_rel=0.0):
+def check_grad(g_gpu, g_ref, name, rtol=1e-3, mag=None):
     """Per element |g - g_ref| <= rtol * max(|g_ref|, 1e-3 * max|g_ref| over the tensor).
     ``mag`` (optional, same shape): sum over rays of |per-ray gradient| from the
     oracle.  An FP32 sum of terms whose magnitudes add up to mag carries a rounding
     error of order 2^-24 * mag whatever the order of summation, so 16 * 2^-24 * mag
     is added to the tolerance: this matters only where the rays' contributions
-    cancel (|g_ref| far below mag).  ``term_rel`` adds term_rel * mag for the FP32
-    evaluation error of each ray's own contribution (see the caller)."""
+    cancel (|g_ref| far below mag)."""
     g_gpu = np.asarray(g_gpu, np.float64)
     g_ref = np.asarray(g_ref, np.float64)
     scale = np.max(np.abs(g_ref)) if g_ref.size else 0.0
     tol = rtol * np.maximum(np.abs(g_ref), 1e-3 * scale)
     if mag is not None:
-        tol = tol + (16.0 * 2.0 ** -24 + term_rel) * np.asarray(mag, np.float64)
+        tol = tol + 16.0 * 2.0 ** -24 * np.asarray(mag, np.float64)
     err = np.abs(g_gpu - g_ref)
     bad = err > tol + 1e-30
     assert not bad.any(), (f"{name}: {bad.sum()}/{bad.size} elements off; worst ratio "
