@@ -147,28 +147,39 @@ __global__ void k_prefix_z(int* __restrict__ diff, int nxp, int nyp, int nzp) {
     }
 }
 
+// One warp per line along y (a line is long: 32 of its entries per step, a warp
+// scan and a carry).
 __global__ void k_prefix_y(int* __restrict__ diff, int nxp, int nyp, int nzp) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nxp * nzp) return;
-    int i = t / nzp, k = t - i * nzp;
+    const int lane = threadIdx.x & 31;
+    const long long line = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (line >= (long long)nxp * nzp) return;  // whole warps
+    const int i = (int)(line / nzp), k = (int)(line - (long long)i * nzp);
     int* base = diff + (size_t)i * nyp * nzp + k;
-    int s = 0;
-    for (int j = 0; j < nyp; ++j) {
-        s += base[(size_t)j * nzp];
-        base[(size_t)j * nzp] = s;
+    int carry = 0;
+    for (int j0 = 0; j0 < nyp; j0 += 32) {
+        const int j = j0 + lane;
+        int v = j < nyp ? base[(size_t)j * nzp] : 0;
+        v = warp_incl_scan(v, lane) + carry;
+        if (j < nyp) base[(size_t)j * nzp] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
     }
 }
 
-// Last axis, fused with the write of V_n (dropping the padding row of each axis).
+// Last axis, one warp per line, fused with the write of V_n (dropping the padding
+// row of each axis).
 __global__ void k_prefix_x(const int* __restrict__ diff, int* __restrict__ v_n, int nx, int ny, int nz) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ny * nz) return;
-    int j = t / nz, k = t - j * nz;
+    const int lane = threadIdx.x & 31;
+    const long long line = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (line >= (long long)ny * nz) return;  // whole warps
+    const int j = (int)(line / nz), k = (int)(line - (long long)j * nz);
     const int nzp = nz + 1, nyp = ny + 1;
-    int s = 0;
-    for (int i = 0; i < nx; ++i) {
-        s += diff[((size_t)i * nyp + j) * nzp + k];
-        v_n[((size_t)i * ny + j) * nz + k] = s;
+    int carry = 0;
+    for (int i0 = 0; i0 < nx; i0 += 32) {
+        const int i = i0 + lane;
+        int v = i < nx ? diff[((size_t)i * nyp + j) * nzp + k] : 0;
+        v = warp_incl_scan(v, lane) + carry;
+        if (i < nx) v_n[((size_t)i * ny + j) * nz + k] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
     }
 }
 
@@ -440,8 +451,8 @@ sq_status_t build_index_impl(const sq_prims_t* prims, const sq_grid_t* grid, con
     }
     const int nxp = nx + 1, nyp = ny + 1, nzp = nz + 1;
     SQ_LAUNCH("k_prefix_z", st, k_prefix_z<<<(nxp * nyp + 255) / 256, 256, 0, st>>>(diff, nxp, nyp, nzp));
-    SQ_LAUNCH("k_prefix_y", st, k_prefix_y<<<(nxp * nzp + 255) / 256, 256, 0, st>>>(diff, nxp, nyp, nzp));
-    SQ_LAUNCH("k_prefix_x", st, k_prefix_x<<<(ny * nz + 255) / 256, 256, 0, st>>>(diff, idx->v_n, nx, ny, nz));
+    SQ_LAUNCH("k_prefix_y", st, k_prefix_y<<<(unsigned)(((long long)nxp * nzp * 32 + 255) / 256), 256, 0, st>>>(diff, nxp, nyp, nzp));
+    SQ_LAUNCH("k_prefix_x", st, k_prefix_x<<<(unsigned)(((long long)ny * nz * 32 + 255) / 256), 256, 0, st>>>(diff, idx->v_n, nx, ny, nz));
     SQ_LAUNCH("k_scan_reduce", st, k_scan_reduce<<<n_tiles, SCAN_THREADS, 0, st>>>(idx->v_n, nvox, tiles));
     SQ_LAUNCH("k_scan_tiles", st, k_scan_tiles<<<1, SCAN_THREADS, 0, st>>>(tiles, n_tiles, idx->capacity, idx->p_total, idx->status));
     SQ_LAUNCH("k_scan_apply", st, k_scan_apply<<<n_tiles, SCAN_THREADS, 0, st>>>(idx->v_n, nvox, tiles, idx->v_f));
