@@ -39,7 +39,7 @@ NCU_TRAFFIC = {
     "k_backward": {"src": "sqr_bwd.cu", "src_sha": "34900eef8431e285", "bytes_per_launch": 310181888},
     "k_forward": {"src": "sqr_fwd.cu", "src_sha": "bbf4eba00091e5d5", "bytes_per_launch": 1718119936},
     "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "34900eef8431e285", "bytes_per_launch": 1938695008},
-    "k_pm_tiles": {"src": "sqr_bwd_pm.cu", "src_sha": "674d4c96393a20d9", "bytes_per_launch": 7529036072},
+    "k_pm_tiles": {"src": "sqr_bwd_pm.cu", "src_sha": "6befed5cd5f897b3", "bytes_per_launch": 7529036072},
     "k_query": {"src": "sqr_query.cu", "src_sha": "87960f15eac3b56a", "bytes_per_launch": 176335872},
 }
 

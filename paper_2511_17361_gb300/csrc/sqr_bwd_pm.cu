@@ -9,14 +9,16 @@
 // from its box:
 //   k_pm_rects  projects the box into every camera: a pixel rectangle that holds
 //               every pixel whose ray can meet the box (conservative);
+//   k_pm_dirs   the direction and composited sample count of every ray;
 //   k_pm_scan   turns the rectangles' pixel counts into tiles (at most PM_MAXT per
 //               primitive) and numbers them, with each tile's primitive;
-//   k_pm_tiles  (Process 3) one block per tile: for each candidate pixel the exact
-//               sample interval of its ray inside the box (binary searches on the
-//               same FP32 sample/voxel rule the forward used), then the tile's
-//               pairs split evenly over the threads, each accumulating the
-//               partial derivatives of its pairs; a block reduction writes the
-//               tile's sums;
+//   k_pm_tiles  (Process 3) persistent blocks (4 per SM) take tiles from a counter:
+//               for each candidate pixel a conservative slab test, then the exact
+//               sample interval of its ray inside the box (the same FP32
+//               sample/voxel rule the forward used, an estimate moved onto the
+//               exact boundary, a binary search as the fallback), then the pass's
+//               pairs split evenly over the threads, each accumulating the partial
+//               derivatives of its pairs; a block reduction writes the tile's sums;
 //   k_pm_final  sums each primitive's tiles in tile order into its accumulator.
 // Every sum is taken in a fixed order, so the gradients are bitwise reproducible
 // (the ray-major path flushes with atomic adds).
