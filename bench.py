@@ -363,7 +363,8 @@ def run_mine(args):
                 "in_grid_samples": in_grid, "index": {"obb": "OBB, tau_cut 0.01", "cube": "cube N_v = 5",
                                                       "opacity": "opacity-aware OBB, tau_cut 0.01"}[args.index],
                 "l2": "flushed (256 MB write) between timed steps",
-                "backward_order": {0: "default", 1: "ray-major", 2: "primitive-major"}[BWD_ORDER],
+                "backward_order": {0: "primitive-major (the default)", 1: "ray-major",
+                                   2: "primitive-major"}[BWD_ORDER],
                 "parallelism": f"replicas x{world} (one frame per GPU)"},
             "phases_ms": {n: float(v) for n, v in zip(names, mean_phase)},
             "gpu_launches": launches_timed + dropped,
