@@ -397,6 +397,46 @@ def test_backward_matches_central_differences(seed):
     assert checked == 5 * (3 + 4 + 3 + 2 + 1 + 5)
 
 
+def test_backward_matches_central_differences_on_stress_crop():
+    """The same check on the clustered 16,384-primitive scene (sharp and flat
+    shapes, eps down to 0.1), cotangents on every 8th ray of a 32x32 crop of camera
+    0 whose samples all stay clear of the alpha clamp: every parameter of the six
+    primitives with the largest opacity gradient."""
+    cfg = synth.make_config(2)
+    pr, grid, rig, t = cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"]
+    idx = oracle.build_index(pr, grid)
+    W = rig["W"]
+    crop = np.array([(96 + i) * W + (184 + j) for i in range(32) for j in range(32)])[::8]
+    safe = np.array([r for r in crop
+                     if np.all(np.abs(oracle.trace_ray(pr, grid, idx, rig, t, r)["ssum"] - 1.0) > 1e-2)])
+    assert len(safe) > 100
+    rng = np.random.default_rng(7)
+    gd, gs = rng.standard_normal(len(safe)), rng.standard_normal((len(safe), pr["logits"].shape[1]))
+    g = oracle.render_bwd(pr, grid, idx, rig, t, gd, gs, ray_ids=safe)
+
+    def loss(p2):
+        D, S, _, _ = oracle.render_fwd(p2, grid, idx, rig, t, ray_ids=safe)
+        return float(np.dot(gd, D) + np.sum(gs * S))
+
+    prims = np.argsort(-np.abs(g["opacity"]))[:6]
+    assert np.abs(g["opacity"][prims]).min() > 0
+    # a smaller step than on the tiny scenes: the sharper primitives' higher
+    # derivatives leave 4e-4 of truncation error at 2^-13 (one quaternion component
+    # of primitive 16208 goes -1.02938, -1.02353, -1.023938, -1.0239386 for steps
+    # 2^-11 .. 2^-17, the analytic value -1.0239386); x +- 2^-17 stays exact in FP32
+    # for |x| < 128, which holds for every parameter of this scene
+    h = 2.0 ** -17
+    sizes = {"means": 3, "quats": 4, "scales": 3, "eps": 2, "opacity": 1, "logits": pr["logits"].shape[1]}
+    for name, m in sizes.items():
+        scale = np.abs(g[name]).max()
+        for k in prims:
+            for c in range(m):
+                i = int(k) * m + c
+                fd = richardson_fd(loss, pr, name, i, h)
+                an = g[name].reshape(-1)[i]
+                assert an == pytest.approx(fd, rel=1e-5, abs=1e-7 * max(1.0, scale)), (name, int(k), c, an, fd)
+
+
 def test_quaternion_gradient_is_orthogonal_to_q():
     """p_o depends on q only through q/|q|, so q . dL/dq = 0."""
     pr, grid, rig, t = small_scene(4, n=6)
