@@ -463,6 +463,27 @@ def test_logit_gradient_closed_form_single_primitive():
     np.testing.assert_allclose(g["logits"][0], gs[0] * Wp, rtol=1e-12)
 
 
+def test_opacity_gradient_closed_form_single_primitive():
+    """One primitive, L = depth: with alpha_j = p_j sigma (unclamped) and
+    T_j = prod_{l<j} (1 - alpha_l), dD/dsigma = sum_j t_j (p_j T_j + alpha_j dT_j/dsigma)
+    with dT_j/dsigma = -T_j sum_{l<j} p_l / (1 - alpha_l) (forward-mode, written
+    from Eq. 5-6, not the reverse sweep the oracle uses)."""
+    pr = prims_from([(8.0, 0.3, 0)], [[0.9, 0.1, 0.3, -0.2]], [[1.5, 1.0, 2.0]], [[0.7, 1.3]], [0.6],
+                    [[0.2, -0.4, 1.0]])
+    grid = synth.grid_spec(21, 10, 10, lo=(-1, -5, -5), hi=(20, 5, 5))
+    t = synth.sample_depths(50, 0.5, 15.0)
+    idx = oracle.build_index(pr, grid, 1, 0.01, 100)
+    g = oracle.render_bwd(pr, grid, idx, axis_camera(), t, np.array([1.0]), np.zeros((1, 3)))
+    tr = oracle.trace_ray(pr, grid, idx, axis_camera(), t, 0)
+    sigma = float(np.float32(0.6))
+    alpha, T = tr["alpha"], tr["T"][:-1]
+    assert alpha.max() < 1.0 and np.count_nonzero(alpha) > 5
+    p = alpha / sigma
+    dT = -T * np.concatenate([[0.0], np.cumsum(p / (1.0 - alpha))[:-1]])
+    dD = np.sum(t.astype(np.float64) * (p * T + alpha * dT))
+    assert g["opacity"][0] == pytest.approx(dD, rel=1e-10)
+
+
 def test_clamped_samples_pass_no_alpha_gradient():
     """Where sum p sigma > alpha_max the alpha gradient is zero: a sigma change that
     keeps every sample clamped leaves the loss unchanged."""
