@@ -49,6 +49,13 @@ def test_index_bit_exact(sqr, ci):
     _assert_index_equal(ix, ref)
 
 
+def test_index_bit_exact_batch_and_horizon_scenes(sqr):
+    """The 12 scenes of the uneven batch and the 13 frames of the temporal horizon."""
+    for c in synth.make_batch_config(3) + synth.make_temporal_config():
+        _, ix, ref = _index_pair(sqr, c)
+        _assert_index_equal(ix, ref)
+
+
 @pytest.mark.parametrize("ci", [0, 1])
 def test_index_opacity_mode_bit_exact(sqr, ci):
     """Opacity-aware OBB index (the paper's future-work refinement): identical to
