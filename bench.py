@@ -207,6 +207,9 @@ def run_mine(args):
 
     dev = torch.device("cuda", local)
     cfg = synth.make_config(WORKLOAD, seed=1 + rank)
+    if args.cameras != 6:  # a smaller frame for profiler captures (the first k cameras of the ring)
+        cfg["rig"] = synth.rig_ring(n_cam=args.cameras)
+        cfg["name"] = cfg["name"].replace("ring6", f"ring{args.cameras}")
     grid = {"n": cfg["grid"]["n"], "lo": [float(v) for v in cfg["grid"]["lo"]],
             "vs": [float(v) for v in cfg["grid"]["vs"]]}
     prims = sqr.to_device(cfg["prims"], dev)
@@ -571,6 +574,8 @@ def main(argv=None):
                     help="voxel neighbourhood of the frame workload's index (default: OBB, tau_cut 0.01)")
     ap.add_argument("--bwd-order", choices=["default", "ray", "primitive"], default="default",
                     help="backward order (Sec. 3.3.3): ray-major run walk or primitive-major tiles")
+    ap.add_argument("--cameras", type=int, choices=range(1, 7), default=6,
+                    help="cameras of the frame workload's ring (default 6; fewer give a smaller case for ncu)")
     ap.add_argument("--workload", choices=["frame", "batch", "temporal", "query"], default="frame",
                     help="frame: one six-camera frame (default); batch: 12 uneven scenes, batched vs per scene; "
                          "temporal: the 13 frames of a T = 6 horizon, batched vs per frame; "

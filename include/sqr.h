@@ -149,8 +149,8 @@ typedef struct {
  * SQ_OP_INDEX, SQ_OP_FWD and SQ_OP_QUERY.  SQ_OP_BWD needs rays: besides the
  * per-primitive records it holds 8 bytes per sample of every ray (dL/dalpha_j
  * and w_j from the back-to-front sweep), 16 bytes per ray and per primitive and
- * camera, and up to 64 tile sums of 192 bytes per primitive (the primitive-major
- * order).  Returns 0 on invalid arguments. */
+ * camera, and up to 64 tile sums of 192 bytes and 64 queue entries per primitive
+ * (the primitive-major order).  Returns 0 on invalid arguments. */
 size_t sq_workspace_size(int op, const sq_prims_t* prims, const sq_grid_t* grid, const sq_rays_t* rays);
 
 /* Sec. 3.3.1 "Preliminary Construction": per-primitive voxel ranges, V_n by a
@@ -249,6 +249,13 @@ typedef struct {
     float* g_eps;
     float* g_opacity;
     float* g_logits;
+    /* Optional diagnostic output (NULL = not wanted), no counterpart in the paper:
+     * [prims.n] device int64.  An SQ_OP_BWD call in the primitive-major order
+     * overwrites it with the number of (sample, primitive) pairs it evaluated for
+     * each primitive: the samples j < (composited count of the ray) of every ray
+     * whose voxel lies in the primitive's voxel range.  The ray-major order and
+     * SQ_OP_FWD leave it untouched. */
+    long long* pair_visits;
 } sq_scene_t;
 
 /* Order of the backward's gradient accumulation (Sec. 3.3.3).  Both first sweep

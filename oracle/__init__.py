@@ -244,6 +244,18 @@ def ray_samples(K, c2w, u, v, t, grid):
     return xyz, vox
 
 
+def sample_voxels(rig, t, grid, threads=0):
+    """Voxel id (-1 outside) of every sample of every ray: int32 [R, L]."""
+    gn, glo, gvs = _grid_args(grid)
+    t = _f32(t)
+    R = rig["n_cam"] * rig["H"] * rig["W"]
+    vox = np.zeros((R, len(t)), np.int32)
+    _load().orc_sample_voxels(ctypes.c_int(rig["n_cam"]), ctypes.c_int(rig["H"]), ctypes.c_int(rig["W"]),
+                              _p(_f32(rig["K"])), _p(_f32(rig["cam2world"])), ctypes.c_int(len(t)), _p(t), _p(gn),
+                              _p(glo), _p(gvs), _p(vox), ctypes.c_int(threads))
+    return vox
+
+
 def query_grid(prims, grid, index, tau=0.05, voxel_ids=None, threads=0, sem_mode=0):
     """Supp. A.4 voxelisation: density [V], sem [V, C], label [V] (C = free)."""
     P = _semantic(prims, sem_mode)

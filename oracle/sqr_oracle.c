@@ -746,6 +746,25 @@ void orc_ray_samples(const float* K, const float* c2w, int u, int v, int L, cons
     for (int j = 0; j < L; ++j) vox[j] = sample_voxel(&g, o, d, t[j], xyz + 3 * j);
 }
 
+/* Voxel id (-1 outside the grid) of sample j of ray r at vox[r * L + j], for
+ * every ray of the rig (Sec. 3.3.1: the sample x = o + t_j d and the voxel
+ * floor((x - lo) / vs), by the FP32 rule of sample_voxel). */
+void orc_sample_voxels(int n_cam, int H, int W, const float* K, const float* c2w, int L, const float* t,
+                       const int* gn, const float* glo, const float* gvs, int* vox, int n_threads) {
+    ogrid_t g = make_grid(gn, glo, gvs);
+    long long R = (long long)n_cam * H * W;
+    int nt = set_threads(n_threads);
+#pragma omp parallel for num_threads(nt) schedule(static)
+    for (long long r = 0; r < R; ++r) {
+        int cam = (int)(r / ((long long)H * W));
+        long long pix = r - (long long)cam * H * W;
+        int v = (int)(pix / W), u = (int)(pix - (long long)v * W);
+        float o[3], d[3], x[3];
+        ray_of_pixel(K + 4 * cam, c2w + 12 * cam, u, v, o, d);
+        for (int j = 0; j < L; ++j) vox[r * L + j] = (int)sample_voxel(&g, o, d, t[j], x);
+    }
+}
+
 int orc_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

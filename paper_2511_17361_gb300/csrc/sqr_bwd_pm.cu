@@ -34,6 +34,7 @@ constexpr int PM_WARPS = PM_THREADS / 32;
 constexpr int PM_CPT = PM_CHUNK / PM_THREADS;  // candidates per thread and pass
 constexpr int PM_SMCAM = 16;                     // cameras whose rectangles a tile stages in shared memory
 constexpr int PM_NS = 2;                         // pairs of one run per walk step (4 and 8 measured slower)
+constexpr int PM_CSUB = 4;                       // runs a warp reads gS rows of at once in the class stage
 static_assert(PM_CHUNK % PM_THREADS == 0, "whole candidates per thread");
 static_assert((PM_CHUNK & (PM_CHUNK - 1)) == 0, "the slot search halves a power of two");
 
@@ -132,8 +133,27 @@ __device__ int4 box_rect(const float* __restrict__ K, const float* __restrict__ 
     return make_int4((int)u0, (int)v0, (int)u1, (int)v1);
 }
 
+// Morton cell of the centre of the voxel box [lo, hi]: per axis the centre voxel
+// scaled to pm_cell_bits(axis) bits, the bits interleaved (x lowest).
+__device__ __forceinline__ int morton_cell(const int lo[3], const int hi[3], const int n[3]) {
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const long long mid = ((long long)lo[a] + hi[a]) >> 1;
+        c[a] = (int)min((long long)(1 << pm_cell_bits(a)) - 1, (mid << pm_cell_bits(a)) / max(n[a], 1));
+    }
+    int key = 0, bit = 0;
+    for (int b = 0; b < 5; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (b < pm_cell_bits(a)) key |= ((c[a] >> b) & 1) << bit++;
+    return key;
+}
+static_assert(pm_cell_bits(0) + pm_cell_bits(1) + pm_cell_bits(2) == 12 && PM_CELLS == 4096, "cell key width");
+static_assert(NRAW + SQ_MAX_CLASSES <= PM_VISIT_SLOT, "the visit count needs a free slot of the tile row");
+
 // One warp per primitive of the batch, a lane per camera: the rectangle in
-// every camera and the number of candidate pixels.
+// every camera, the number of candidate pixels and the box's Morton cell.
 __global__ void k_pm_rects(Batch B, PmArgs A) {
     const int g = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (g >= A.ntot) return;
@@ -160,7 +180,10 @@ __global__ void k_pm_rects(Batch B, PmArgs A) {
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-    if (lane == 0) A.cnt[g] = (int)total;  // at most the scene's ray count (< 2^31)
+    if (lane == 0) {
+        A.cnt[g] = (int)total;  // at most the scene's ray count (< 2^31)
+        A.key[g] = ok ? morton_cell(lo, hi, S.g.n) : 0;
+    }
 }
 
 // Exclusive scan of the tile counts over all primitives (one block).
@@ -188,6 +211,54 @@ __global__ void __launch_bounds__(1024) k_pm_scan(PmArgs A) {
         run += nt;
     }
     if (tid == 1023) A.toff[A.ntot] = run;
+    __syncthreads();
+
+    // The queue: per scene, the primitives' tiles bucketed by Morton cell (a
+    // counting sort in shared memory); within a cell the order the shared-memory
+    // atomics give, which moves only the schedule, never a sum.
+    __shared__ int hist[PM_CELLS];
+    int qbase = 0;
+    for (int s = 0; s < A.nscene; ++s) {
+        const int p0 = (int)A.poff[s], p1 = (int)A.poff[s + 1];
+        for (int c = tid; c < PM_CELLS; c += 1024) hist[c] = 0;
+        __syncthreads();
+        for (int i = p0 + tid; i < p1; i += 1024) {
+            const int nt = A.toff[i + 1] - A.toff[i];
+            if (nt > 0) atomicAdd(&hist[A.key[i]], nt);
+        }
+        __syncthreads();
+        constexpr int PER = PM_CELLS / 1024;
+        int loc[PER], lsum = 0;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            loc[i] = hist[tid * PER + i];
+            lsum += loc[i];
+        }
+        const int li = warp_incl_scan(lsum, lane);
+        if (lane == 31) wsum[wid] = li;
+        __syncthreads();
+        if (wid == 0) {
+            const int w = wsum[lane];
+            wsum[lane] = warp_incl_scan(w, lane) - w;
+        }
+        __syncthreads();
+        int at = qbase + wsum[wid] + li - lsum;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            hist[tid * PER + i] = at;
+            at += loc[i];
+        }
+        const int scene_tiles = A.toff[p1] - A.toff[p0];
+        __syncthreads();
+        for (int i = p0 + tid; i < p1; i += 1024) {
+            const int t0 = A.toff[i], nt = A.toff[i + 1] - t0;
+            if (nt <= 0) continue;
+            const int q = atomicAdd(&hist[A.key[i]], nt);
+            for (int t = 0; t < nt; ++t) A.qtile[q + t] = t0 + t;
+        }
+        qbase += scene_tiles;
+        __syncthreads();
+    }
 }
 
 // Ray direction of every ray of the batch (pixel_ray) and its number of
@@ -203,6 +274,25 @@ __global__ void k_pm_dirs(Batch B) {
     scene_ray(S, r, o, d);
     const int Le = min(max(__ldg(S.save_n + r), 0), S.L);
     S.pm_dir[r] = make_float4(d[0], d[1], d[2], __int_as_float(Le));
+}
+
+// grad_sem of every ray of the batch copied to rows of CP classes (zero padding),
+// so that a tile reads a ray's row with CP / 4 aligned vector loads: one thread
+// per (ray, group of four classes).
+__global__ void k_pm_gs(Batch B) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cp4 = B.d[0].cp >> 2;  // the scenes of a batch share n_classes
+    const long long gr = i / cp4;
+    if (gr >= B.total) return;
+    const int q = (int)(i - gr * cp4);
+    const int s = scene_of(B, gr);
+    const SceneDesc& S = B.d[s];
+    const long long r = gr - __ldg(B.off + s);
+    const float* row = S.grad_sem + r * S.C;
+    float v[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = 4 * q + c < S.C ? __ldg(row + 4 * q + c) : 0.f;
+    S.pm_gs[r * cp4 + q] = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // Scaled coordinate of sample j on one axis, rounded as sample_voxel rounds it,
@@ -262,9 +352,11 @@ struct PmSmem {
     int head_slot[PM_THREADS];   // run a thread's slice starts inside (-1: none)
     float head_val[PM_THREADS];  // that thread's part of the run's w p_o sum
     float red[PM_WARPS][NRAW];
-    float cpart[PM_WARPS][32];
+    float4 cacc[PM_WARPS][PM_CSUB][8];  // class gradient partials: per warp and slot lane group, classes 4q..4q+3
+    int nz[PM_CHUNK];            // the pass's non-empty slots, in slot order
     float lp[32];                // class vector of the tile's primitive (lpad row)
     int wtot[PM_WARPS];
+    int ztot[PM_WARPS];
     int tile;
 };
 static_assert(SQ_MAX_SAMPLES <= 1024, "first samples are packed in 10 bits");
@@ -280,10 +372,13 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ntiles = __ldg(A.toff + A.ntot);
     for (;;) {
-        if (tid == 0) sh.tile = atomicAdd(A.ctr, 1);
+        if (tid == 0) {
+            const int q = atomicAdd(A.ctr, 1);
+            sh.tile = q < ntiles ? __ldg(A.qtile + q) : -1;
+        }
         __syncthreads();
         const int tile = sh.tile;
-        if (tile >= ntiles) break;
+        if (tile < 0) break;
         const int g = __ldg(A.tprim + tile);
         const int s = scene_of_prim(A.poff, B.n, g);
         const SceneDesc& S = B.d[s];
@@ -323,7 +418,9 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
         float acc[13];
 #pragma unroll
         for (int i = 0; i < 13; ++i) acc[i] = 0.f;
-        float cg = 0.f;  // class tid's gradient sum (threads tid < C)
+        int tpairs = 0;  // pairs of the tile (the same value in every thread)
+        for (int i = tid; i < PM_WARPS * PM_CSUB * 8; i += PM_THREADS)
+            (&sh.cacc[0][0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
 
         for (int cb = cbeg; cb < cend; cb += PM_CHUNK) {
@@ -423,13 +520,18 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
             for (int i = 0; i < PM_CPT; ++i) {  // slot data of the non-empty runs, <dL/dS, c_k>
                 if (len[i] == 0) continue;
                 const int slot = tid * PM_CPT + i;
-                const float* gsr = S.grad_sem + (long long)rr[i] * C;
-                float gv[CP];
+                const float4* gsr = S.pm_gs + (long long)rr[i] * (CP / 4);
+                float4 gv[CP / 4];
 #pragma unroll
-                for (int c = 0; c < CP; ++c) gv[c] = c < C ? __ldg(gsr + c) : 0.f;
+                for (int q = 0; q < CP / 4; ++q) gv[q] = __ldg(gsr + q);
                 float cdv = 0.f;
 #pragma unroll
-                for (int c = 0; c < CP; ++c) cdv = fmaf(gv[c], sh.lp[c], cdv);
+                for (int q = 0; q < CP / 4; ++q) {
+                    cdv = fmaf(gv[q].x, sh.lp[4 * q + 0], cdv);
+                    cdv = fmaf(gv[q].y, sh.lp[4 * q + 1], cdv);
+                    cdv = fmaf(gv[q].z, sh.lp[4 * q + 2], cdv);
+                    cdv = fmaf(gv[q].w, sh.lp[4 * q + 3], cdv);
+                }
                 sh.d[0][slot] = dv[i].x;
                 sh.d[1][slot] = dv[i].y;
                 sh.d[2][slot] = dv[i].z;
@@ -438,25 +540,39 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
                 sh.cd[slot] = cdv;
             }
             // ---- exclusive scan of the run lengths in slot order; list the non-empty slots
-            int npairs;
+            int npairs, nnz;
             {
+                int nzt = 0;
+#pragma unroll
+                for (int i = 0; i < PM_CPT; ++i) nzt += len[i] > 0 ? 1 : 0;
                 const int il = warp_incl_scan(tl_sum, lane);
-                if (lane == 31) sh.wtot[wid] = il;
+                const int zl = warp_incl_scan(nzt, lane);
+                if (lane == 31) {
+                    sh.wtot[wid] = il;
+                    sh.ztot[wid] = zl;
+                }
                 __syncthreads();
-                int wl = 0, tl2 = 0;
+                int wl = 0, tl2 = 0, zw = 0;
+                nnz = 0;
 #pragma unroll
                 for (int w2 = 0; w2 < PM_WARPS; ++w2) {
-                    const int a = sh.wtot[w2];
-                    if (w2 < wid) wl += a;
+                    const int a = sh.wtot[w2], z = sh.ztot[w2];
+                    if (w2 < wid) {
+                        wl += a;
+                        zw += z;
+                    }
                     tl2 += a;
+                    nnz += z;
                 }
-                int pl = wl + il - tl_sum;
+                int pl = wl + il - tl_sum, zp = zw + zl - nzt;
 #pragma unroll
                 for (int i = 0; i < PM_CPT; ++i) {
                     sh.pre[tid * PM_CPT + i] = pl;
                     pl += len[i];
+                    if (len[i] > 0) sh.nz[zp++] = tid * PM_CPT + i;
                 }
                 npairs = tl2;
+                tpairs += tl2;
                 if (tid == 0) sh.pre[PM_CHUNK] = tl2;
                 sh.head_slot[tid] = -1;
             }
@@ -566,31 +682,25 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
             }
             __syncthreads();
             // ---- class gradient of the runs, sum over runs of (sum_j w_j p_o) dL/dS_ray:
-            // each thread over its own slots, then per class a butterfly within the
-            // warps and the warps in order
+            // the non-empty runs in list order, PM_CSUB per warp at a time; lane
+            // (sub, q) reads classes 4q..4q+3 of run sub's padded gS row and keeps
+            // their partial sums in its warp's accumulator row (fixed order)
             {
-                float cgp[CP];
-#pragma unroll
-                for (int c = 0; c < CP; ++c) cgp[c] = 0.f;
-#pragma unroll
-                for (int i = 0; i < PM_CPT; ++i) {
-                    const int slot = tid * PM_CPT + i;
-                    if (sh.pre[slot + 1] == sh.pre[slot]) continue;
-                    const float wv = sh.wsum[slot];
-                    const float* gsr = S.grad_sem + (long long)sh.r[slot] * C;
-#pragma unroll
-                    for (int c = 0; c < CP; ++c)
-                        if (c < C) cgp[c] = fmaf(wv, __ldg(gsr + c), cgp[c]);
+                const int sub = lane >> 3, q = lane & 7;
+                if (q < CP / 4) {
+                    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int e = wid * PM_CSUB + sub; e < nnz; e += PM_WARPS * PM_CSUB) {
+                        const int slot = sh.nz[e];
+                        const float wv = sh.wsum[slot];
+                        const float4 g4 = __ldg(S.pm_gs + (long long)sh.r[slot] * (CP / 4) + q);
+                        a.x = fmaf(wv, g4.x, a.x);
+                        a.y = fmaf(wv, g4.y, a.y);
+                        a.z = fmaf(wv, g4.z, a.z);
+                        a.w = fmaf(wv, g4.w, a.w);
+                    }
+                    float4& c4 = sh.cacc[wid][sub][q];
+                    c4 = make_float4(c4.x + a.x, c4.y + a.y, c4.z + a.z, c4.w + a.w);
                 }
-#pragma unroll
-                for (int c = 0; c < CP; ++c) {
-                    const float v = warp_sum(cgp[c]);
-                    if (lane == 0) sh.cpart[wid][c] = v;
-                }
-                __syncthreads();
-                if (tid < C)
-#pragma unroll
-                    for (int w2 = 0; w2 < PM_WARPS; ++w2) cg += sh.cpart[w2][tid];
                 __syncthreads();
             }
         }
@@ -608,7 +718,14 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
             for (int w2 = 0; w2 < PM_WARPS; ++w2) v += sh.red[w2][tid];
             out[tid] = v;
         }
-        if (tid < C) out[NRAW + tid] = cg;
+        if (tid < C) {  // the warps' and lane groups' class partials in a fixed order
+            float cg = 0.f;
+            for (int w2 = 0; w2 < PM_WARPS; ++w2)
+#pragma unroll
+                for (int s2 = 0; s2 < PM_CSUB; ++s2) cg += (&sh.cacc[w2][s2][0].x)[tid];
+            out[NRAW + tid] = cg;
+        }
+        if (tid == 0) out[PM_VISIT_SLOT] = __int_as_float(tpairs);
         __syncthreads();
     }
 }
@@ -620,8 +737,17 @@ __global__ void k_pm_final(Batch B, PmArgs A) {
     if (g >= A.ntot) return;
     const int s = scene_of_prim(A.poff, B.n, g);
     const SceneDesc& S = B.d[s];
-    if (i >= NRAW + S.C) return;
     const int k = g - (int)__ldg(A.poff + s);
+    if (i == PM_VISIT_SLOT) {  // pairs the tiles of the primitive evaluated
+        if (S.pair_visits) {
+            long long nv = 0;
+            for (int t = __ldg(A.toff + g); t < __ldg(A.toff + g + 1); ++t)
+                nv += __float_as_int(A.part[(size_t)t * GF + i]);
+            S.pair_visits[k] = nv;
+        }
+        return;
+    }
+    if (i >= NRAW + S.C) return;
     float v = 0.f;
     for (int t = __ldg(A.toff + g); t < __ldg(A.toff + g + 1); ++t) v += A.part[(size_t)t * GF + i];
     S.gacc[(size_t)k * GF + i] = v;
@@ -646,7 +772,11 @@ sq_status_t launch_backward_pm(const Batch& B, const PmArgs& A, int cp, cudaStre
             return SQ_ERR_INVALID_ARG;
     }
     SQ_LAUNCH("k_pm_rects", st, k_pm_rects<<<(unsigned)(((long long)A.ntot * 32 + 127) / 128), 128, 0, st>>>(B, A));
-    if (B.total > 0) SQ_LAUNCH("k_pm_dirs", st, k_pm_dirs<<<(unsigned)((B.total + 255) / 256), 256, 0, st>>>(B));
+    if (B.total > 0) {
+        SQ_LAUNCH("k_pm_dirs", st, k_pm_dirs<<<(unsigned)((B.total + 255) / 256), 256, 0, st>>>(B));
+        const long long ng = B.total * (cp / 4);
+        SQ_LAUNCH("k_pm_gs", st, k_pm_gs<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(B));
+    }
     SQ_LAUNCH("k_pm_scan", st, k_pm_scan<<<1, 1024, 0, st>>>(A));
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PM_THREADS, 0);

@@ -155,8 +155,12 @@ size_t rect_bytes(const sq_scene_t* s) {
 
 size_t dir_bytes(const sq_rays_t* r) { return align_up((size_t)r->n_cam * r->H * r->W * sizeof(float4), 256); }
 
+size_t gs_bytes(const sq_rays_t* r, int C) {
+    return align_up((size_t)r->n_cam * r->H * r->W * (size_t)cpad(C) * sizeof(float), 256);
+}
+
 struct PmWs {
-    size_t cnt, toff, tprim, part, end;
+    size_t cnt, toff, tprim, part, key, qtile, end;
 };
 
 PmWs pm_ws(size_t at, long long ntot) {
@@ -165,7 +169,9 @@ PmWs pm_ws(size_t at, long long ntot) {
     w.toff = align_up(w.cnt + (size_t)ntot * sizeof(int), 256);
     w.tprim = align_up(w.toff + (size_t)(ntot + 1) * sizeof(int), 256);
     w.part = align_up(w.tprim + (size_t)ntot * PM_MAXT * sizeof(int), 256);
-    w.end = align_up(w.part + (size_t)ntot * PM_MAXT * GF * sizeof(float), 256);
+    w.key = align_up(w.part + (size_t)ntot * PM_MAXT * GF * sizeof(float), 256);
+    w.qtile = align_up(w.key + (size_t)ntot * sizeof(int), 256);
+    w.end = align_up(w.qtile + (size_t)ntot * PM_MAXT * sizeof(int), 256);
     return w;
 }
 
@@ -178,6 +184,7 @@ size_t batch_ws_size(const sq_scene_t* sc, int n, bool bwd) {
             at += gw_bytes(&sc[i].rays);
             at += rect_bytes(&sc[i]);
             at += dir_bytes(&sc[i].rays);
+            at += gs_bytes(&sc[i].rays, sc[i].prims.n_classes);
             ntot += sc[i].prims.n > 0 ? sc[i].prims.n : 0;
         }
         at = pm_ws(at, ntot).end;
@@ -334,6 +341,7 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
         if (s.saved) saved_ptrs(&s.rays, C, s.saved, D);
         D.grad_depth = s.grad_depth;
         D.grad_sem = s.grad_sem;
+        D.pair_visits = s.pair_visits;
         D.gacc = (float*)(base + w.gacc);
         P.off[i] = total;
         P.boff[i] = btotal;
@@ -378,6 +386,8 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
             at += rect_bytes(&sc[i]);
             P.s[i].pm_dir = (float4*)(base + at);
             at += dir_bytes(&sc[i].rays);
+            P.s[i].pm_gs = (float4*)(base + at);
+            at += gs_bytes(&sc[i].rays, C);
             ntot += sc[i].prims.n;
         }
         if (ntot * PM_MAXT >= 2147483647LL) {
@@ -400,8 +410,16 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
     if (ls != SQ_OK) return ls;
     if (op == SQ_OP_BWD) {
         if (tn.bwd_order == SQ_BWD_PRIMITIVE_MAJOR) {
-            const PmArgs A{poff, (int)ntot, (int*)(base + pw.cnt), (int*)(base + pw.toff), (float*)(base + pw.part),
-                           (int*)(base + pw.tprim), ctr + CTR_PM};
+            const PmArgs A{poff,
+                           n,
+                           (int)ntot,
+                           (int*)(base + pw.cnt),
+                           (int*)(base + pw.toff),
+                           (float*)(base + pw.part),
+                           (int*)(base + pw.tprim),
+                           ctr + CTR_PM,
+                           (int*)(base + pw.key),
+                           (int*)(base + pw.qtile)};
             ls = launch_backward_pm(B, A, cp, st);
             if (ls != SQ_OK) return ls;
         } else {

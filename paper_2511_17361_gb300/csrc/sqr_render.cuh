@@ -47,6 +47,8 @@ struct SceneDesc {
     float* gacc;         // [N, GF] gradient accumulator (zeroed per backward)
     int4* pm_rect;       // [N, n_cam] primitive-major backward: pixel rectangle (u0, v0, u1, v1) of each box
     float4* pm_dir;      // [R] primitive-major backward: ray direction of each pixel, composited samples in .w
+    long long* pair_visits;  // [N] nullable: (sample, primitive) pairs the primitive-major backward evaluated
+    float4* pm_gs;       // [R, CP/4] primitive-major backward: grad_sem rows zero-padded to CP classes
 };
 
 struct BatchParams {
@@ -105,14 +107,27 @@ constexpr int PM_MAXT = 64;         // tiles per primitive at most
 constexpr int PM_CHUNK = 512;       // candidate pixels a tile block takes per pass
 constexpr int PM_TILE_CHUNKS = 8;   // passes per tile, unless the primitive would need more than PM_MAXT tiles
 
+// The tiles are taken in a spatial order (queue position -> tile in qtile): the
+// primitives' box centres sorted into PM_CELLS Morton cells per scene, so that the
+// blocks resident at one time work on neighbouring primitives, whose runs lie on
+// the same rays and samples and share their (dL/dalpha_j, w_j) lines in L2.  The
+// order decides only which block sums a tile when; every tile's sum, and the
+// tile-ordered sum per primitive, is the same whatever the order.
+__host__ __device__ constexpr int pm_cell_bits(int a) { return a == 2 ? 2 : 5; }  // Morton cells per axis: 32 x 32 x 4
+constexpr int PM_CELLS = 1 << 12;
+constexpr int PM_VISIT_SLOT = GF - 1;  // tile row slot holding the tile's pair count (int bits); unused by sums
+
 struct PmArgs {
     const long long* poff;  // [n_scenes + 1] primitive offsets of the scenes
+    int nscene;             // scenes of the batch
     int ntot;               // primitives of all scenes
     int* cnt;               // [ntot] candidate pixels
     int* toff;              // [ntot + 1] tile offsets (exclusive scan of the tile counts)
     float* part;            // [ntot * PM_MAXT, GF] tile partial sums
     int* tprim;             // [ntot * PM_MAXT] primitive of each tile
     int* ctr;               // zeroed tile counter
+    int* key;               // [ntot] Morton cell of each primitive's box centre
+    int* qtile;             // [ntot * PM_MAXT] tile at each queue position
 };
 
 int device_sm_count();

@@ -57,7 +57,7 @@ class SqScene(ctypes.Structure):
     _fields_ = [("prims", SqPrims), ("index", SqIndex), ("grid", SqGrid), ("rays", SqRays), ("depth", _vp),
                 ("sem", _vp), ("t_final", _vp), ("saved", _vp), ("saved_bytes", ctypes.c_size_t), ("grad_depth", _vp),
                 ("grad_sem", _vp), ("g_means", _vp), ("g_quats", _vp), ("g_scales", _vp), ("g_eps", _vp),
-                ("g_opacity", _vp), ("g_logits", _vp)]
+                ("g_opacity", _vp), ("g_logits", _vp), ("pair_visits", _vp)]
 
 
 class SqTuning(ctypes.Structure):
@@ -309,12 +309,22 @@ def new_saved(rays: Rays, n_classes: int, device="cuda"):
     return torch.empty(saved_size(rays, n_classes), dtype=torch.uint8, device=device)
 
 
+def saved_counts(saved, rays: Rays, n_classes: int):
+    """The per-ray composited sample counts [R] int32 held at the end of a saved
+    forward state (layout as sq_saved_size documents)."""
+    R, L, cp = rays.R, rays.t.numel(), (int(n_classes) + 3) // 4 * 4
+    a256 = lambda b: (b + 255) // 256 * 256
+    off = a256(R * L * 8) + a256(R * L * cp * 4)
+    return saved[off:off + R * 4].view(torch.int32)
+
+
 def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, grad_sem, saved=None, out=None,
-               order: int = SQ_BWD_DEFAULT) -> dict:
+               order: int = SQ_BWD_DEFAULT, pair_visits=None) -> dict:
     """Gradients of sum(gD * depth) + sum(gS * sem) w.r.t. every parameter.  ``saved``
     comes from render_fwd on the same inputs; when None the forward is run here.
     ``order`` (SQ_BWD_*) other than the default goes through sq_render_batched
-    with that backward order."""
+    with that backward order, and so does a ``pair_visits`` int64 tensor [n], which
+    receives the pairs the primitive-major order evaluated per primitive."""
     device = prims["means"].device
     grad_depth = _need_cuda_f32(grad_depth.contiguous(), "grad_depth")
     grad_sem = _need_cuda_f32(grad_sem.contiguous(), "grad_sem")
@@ -324,13 +334,18 @@ def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, gr
     if out is None:
         out = {k: torch.empty_like(prims[k]) for k in PRIM_KEYS}
     p, g, r, ix = prims_struct(prims), grid_struct(grid), rays.struct(), index.struct()
-    if order != SQ_BWD_DEFAULT:
+    if order != SQ_BWD_DEFAULT or pair_visits is not None:
         sc = SqScene()
         sc.prims, sc.index, sc.grid, sc.rays = p, ix, g, r
         sc.saved, sc.saved_bytes = _ptr(saved), saved.numel() * saved.element_size()
         sc.grad_depth, sc.grad_sem = _ptr(grad_depth), _ptr(grad_sem)
         for k in PRIM_KEYS:
             setattr(sc, "g_" + k, _ptr(out[k]))
+        if pair_visits is not None:
+            if not (pair_visits.is_cuda and pair_visits.dtype == torch.int64 and pair_visits.is_contiguous()
+                    and pair_visits.numel() == prims["means"].shape[0]):
+                raise SqrError("pair_visits must be a contiguous int64 CUDA tensor with one entry per primitive")
+            sc.pair_visits = _ptr(pair_visits)
         arr = (SqScene * 1)(sc)
         ws = _ws.get("bwd", lib.sq_batched_workspace_size(arr, 1), device)
         tn = SqTuning(4, 8, 0, order)

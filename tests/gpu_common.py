@@ -31,6 +31,28 @@ def np_index(ix):
             "ranges": ix.ranges.cpu().numpy(), "P": P}
 
 
+def assert_index_equal(ix, ref, no_ties=True):
+    """The GPU index equals the oracle's bit for bit (P, ranges, V_n, V_f, V_sq);
+    with no_ties the seeded scene also has no voxel-boundary near-tie."""
+    got = np_index(ix)
+    if no_ties:
+        assert ref["ties"] == 0, "seeded workload has a voxel-boundary near-tie"
+    assert got["P"] == ref["P"]
+    assert np.array_equal(got["ranges"][:len(ref["ranges"])], ref["ranges"])
+    assert np.array_equal(got["v_n"], ref["v_n"])
+    assert np.array_equal(got["v_f"], ref["v_f"])
+    assert np.array_equal(got["v_sq"], ref["v_sq"])
+
+
+def oracle_index(ix, prims, grid, mode=0, tau=0.01, nv=5):
+    """The oracle's own index of the scene, after checking that the GPU's index ix
+    (built with the same options) equals it bit for bit: the oracle then renders
+    over lists it built itself, never over the GPU's."""
+    ref = oracle.build_index(prims, grid, mode, tau, nv)
+    assert_index_equal(ix, ref, no_ties=False)
+    return ref
+
+
 def softmax(x):
     x = np.asarray(x, np.float64)
     e = np.exp(x - x.max(-1, keepdims=True))

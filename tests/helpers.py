@@ -125,3 +125,18 @@ def richardson_fd(loss, prims, name, i, h):
         return (vals[0] - vals[1]) / (2 * hh)
 
     return (4 * cd(h / 2) - cd(h)) / 3
+
+
+def box_sums(counts, ranges):
+    """Per primitive, the sum of counts [nx, ny, nz] over its inclusive voxel range
+    (i0, i1, j0, j1, k0, k1); 0 for an empty range.  A summed-volume table in int64."""
+    sat = np.zeros(tuple(n + 1 for n in counts.shape), np.int64)
+    sat[1:, 1:, 1:] = counts.astype(np.int64).cumsum(0).cumsum(1).cumsum(2)
+    r = ranges.astype(np.int64)
+    i0, i1, j0, j1, k0, k1 = (r[:, c] for c in range(6))
+    empty = (i1 < i0) | (j1 < j0) | (k1 < k0)
+    i0, j0, k0 = [np.where(empty, 0, a) for a in (i0, j0, k0)]
+    i1, j1, k1 = [np.where(empty, -1, a) + 1 for a in (i1, j1, k1)]
+    tot = (sat[i1, j1, k1] - sat[i0, j1, k1] - sat[i1, j0, k1] - sat[i1, j1, k0] + sat[i0, j0, k1] + sat[i0, j1, k0]
+           + sat[i1, j0, k0] - sat[i0, j0, k0])
+    return np.where(empty, 0, tot)

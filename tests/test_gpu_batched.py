@@ -11,7 +11,7 @@ import torch
 
 import oracle
 from paper_2511_17361_gb300 import synth
-from tests.gpu_common import check_depth, check_grad, check_sem, dev_grid, lib, np_index, per_ray_magnitude
+from tests.gpu_common import check_depth, check_grad, check_sem, dev_grid, lib, oracle_index, per_ray_magnitude
 from tests.helpers import small_scene
 
 pytestmark = pytest.mark.gpu
@@ -78,7 +78,7 @@ def test_batched_scene_against_oracle(sqr):
     sqr.render_batched(sqr.SQ_OP_BWD, scenes)
     torch.cuda.synchronize()
     for sc, (pr, g, rig, t) in zip(scenes, host):
-        idx = np_index(sc.index)
+        idx = oracle_index(sc.index, pr, g)
         D, S, T, _ = oracle.render_fwd(pr, g, idx, rig, t)
         check_depth(sc.depth.cpu().numpy(), D, 0.5)
         check_sem(sc.sem.cpu().numpy(), S)
@@ -193,7 +193,7 @@ def test_temporal_horizon_batch(sqr):
             check_grad(sc.grads[k].cpu().numpy(), g[k].cpu().numpy(), k, rtol=2e-3)
     for i in (0, len(frames) - 1):
         fr, sc = frames[i], scenes[i]
-        idx = np_index(sc.index)
+        idx = oracle_index(sc.index, fr["prims"], fr["grid"])
         D, S, T, _ = oracle.render_fwd(fr["prims"], fr["grid"], idx, fr["rig"], fr["t"])
         check_depth(sc.depth.cpu().numpy(), D, 0.5)
         check_sem(sc.sem.cpu().numpy(), S)
@@ -232,7 +232,7 @@ def _batch_sampled_parity(sqr, cfgs, n_rays=24, seed=0):
     sqr.render_batched(sqr.SQ_OP_BWD, batch)
     torch.cuda.synchronize()
     for sc, c, ids, gd, gs in scenes:
-        idx = np_index(sc.index)
+        idx = oracle_index(sc.index, c["prims"], c["grid"])
         D, S, _, _ = oracle.render_fwd(c["prims"], c["grid"], idx, c["rig"], c["t"], ray_ids=ids)
         check_depth(sc.depth.cpu().numpy()[ids], D, float(c["t"][0]))
         check_sem(sc.sem.cpu().numpy()[ids], S)

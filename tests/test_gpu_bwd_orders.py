@@ -9,7 +9,7 @@ import torch
 
 import oracle
 from paper_2511_17361_gb300 import synth
-from tests.gpu_common import check_grad, dev_grid, lib, np_index, per_ray_magnitude, scene_to_gpu
+from tests.gpu_common import check_grad, dev_grid, lib, oracle_index, per_ray_magnitude, scene_to_gpu
 from tests.helpers import axis_camera, small_scene
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +39,7 @@ def _oracle_case(sqr, pr, grid, rig, t, seed):
     gd, gs = rng.standard_normal(R).astype(np.float32), rng.standard_normal((R, C)).astype(np.float32)
     got = _grads(sqr, prims_d, ix, g, rays, torch.from_numpy(gd).cuda(), torch.from_numpy(gs).cuda(),
                  sqr.SQ_BWD_PRIMITIVE_MAJOR)
-    idx = np_index(ix)
+    idx = oracle_index(ix, pr, grid)
     ref = oracle.render_bwd(pr, grid, idx, rig, t, gd.astype(np.float64), gs.astype(np.float64))
     mag = per_ray_magnitude(pr, grid, idx, rig, t, gd, gs)
     return got, ref, mag

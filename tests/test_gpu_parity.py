@@ -10,7 +10,8 @@ import torch
 
 import oracle
 from paper_2511_17361_gb300 import synth
-from tests.gpu_common import check_depth, check_grad, check_sem, dev_grid, lib, np_index, scene_to_gpu
+from tests.gpu_common import (assert_index_equal, check_depth, check_grad, check_sem, dev_grid, lib, np_index,
+                              oracle_index, scene_to_gpu)
 from tests.helpers import prims_from, small_scene
 
 pytestmark = pytest.mark.gpu
@@ -32,13 +33,7 @@ def _index_pair(sqr, cfg, mode=0, tau=0.01, nv=5):
 
 
 def _assert_index_equal(ix, ref):
-    got = np_index(ix)
-    assert ref["ties"] == 0, "seeded workload has a voxel-boundary near-tie"
-    assert got["P"] == ref["P"]
-    assert np.array_equal(got["ranges"][:len(ref["ranges"])], ref["ranges"])
-    assert np.array_equal(got["v_n"], ref["v_n"])
-    assert np.array_equal(got["v_f"], ref["v_f"])
-    assert np.array_equal(got["v_sq"], ref["v_sq"])
+    assert_index_equal(ix, ref)
 
 
 # ----------------------------------------------------------------------- index
@@ -168,7 +163,7 @@ def _fwd_pair(sqr, prims, grid, rig, t, kappa=0.0, alpha_max=1.0, ray_ids=None, 
     ix = sqr.build_index(prims_d, g, mode=mode, tau_cut=tau, nv=nv)
     depth, sem, tf = sqr.render_fwd(prims_d, ix, g, rays)
     torch.cuda.synchronize()
-    ref_ix = np_index(ix)
+    ref_ix = oracle_index(ix, prims, grid, mode, tau, nv)
     D, S, T, NU = oracle.render_fwd(prims, grid, ref_ix, rig, t, kappa, alpha_max, ray_ids=ray_ids)
     sel = slice(None) if ray_ids is None else np.asarray(ray_ids)
     return depth.cpu().numpy()[sel], sem.cpu().numpy()[sel], tf.cpu().numpy()[sel], D, S, T, NU
@@ -277,7 +272,7 @@ def _bwd_pair(sqr, prims, grid, rig, t, gd, gs, ray_ids=None, alpha_max=1.0, kap
     out = sqr.render_bwd(prims_d, ix, g, rays, torch.from_numpy(gd_full).cuda(), torch.from_numpy(gs_full).cuda(),
                          order=order)
     torch.cuda.synchronize()
-    ref = oracle.render_bwd(prims, grid, np_index(ix), rig, t, gd_full[sel].astype(np.float64),
+    ref = oracle.render_bwd(prims, grid, oracle_index(ix, prims, grid, mode), rig, t, gd_full[sel].astype(np.float64),
                             gs_full[sel].astype(np.float64), alpha_max=alpha_max, kappa=kappa,
                             ray_ids=None if ray_ids is None else sel)
     return {k: v.cpu().numpy() for k, v in out.items()}, ref
@@ -429,7 +424,7 @@ def test_query_grid_full(sqr):
     ix = sqr.build_index(prims_d, g)
     dens, sem, lab = sqr.query_grid(prims_d, ix, g, tau=0.05)
     torch.cuda.synchronize()
-    rd, rs, rl = oracle.query_grid(cfg["prims"], cfg["grid"], np_index(ix), tau=0.05)
+    rd, rs, rl = oracle.query_grid(cfg["prims"], cfg["grid"], oracle_index(ix, cfg["prims"], cfg["grid"]), tau=0.05)
     dens, sem, lab = dens.cpu().numpy(), sem.cpu().numpy(), lab.cpu().numpy()
     assert np.max(np.abs(dens - rd) / np.maximum(1.0, rd)) < 5e-5
     assert np.max(np.abs(sem - rs) / np.maximum(1.0, np.abs(rs))) < 5e-5
@@ -456,7 +451,8 @@ def test_query_backward_full(sqr):
     gs = rng.standard_normal((nvox, 18)).astype(np.float32)
     got = sqr.query_grid_bwd(prims_d, ix, g, torch.from_numpy(gd).cuda(), torch.from_numpy(gs).cuda())
     torch.cuda.synchronize()
-    ref = oracle.query_grid_bwd(cfg["prims"], cfg["grid"], np_index(ix), gd.astype(np.float64),
+    ref = oracle.query_grid_bwd(cfg["prims"], cfg["grid"], oracle_index(ix, cfg["prims"], cfg["grid"]),
+                                gd.astype(np.float64),
                                 gs.astype(np.float64))
     assert np.count_nonzero(ref["opacity"]) > 100
     for k in ref:
@@ -478,7 +474,8 @@ def test_query_backward_sparse_large(sqr):
     gd_full[sel], gs_full[sel] = gd, gs
     got = sqr.query_grid_bwd(prims_d, ix, g, torch.from_numpy(gd_full).cuda(), torch.from_numpy(gs_full).cuda())
     torch.cuda.synchronize()
-    ref = oracle.query_grid_bwd(cfg["prims"], cfg["grid"], np_index(ix), gd.astype(np.float64),
+    ref = oracle.query_grid_bwd(cfg["prims"], cfg["grid"], oracle_index(ix, cfg["prims"], cfg["grid"]),
+                                gd.astype(np.float64),
                                 gs.astype(np.float64), voxel_ids=sel)
     assert np.count_nonzero(ref["opacity"]) > 50
     for k in ref:
@@ -494,7 +491,7 @@ def test_softmax_sem_mode(sqr):
     prims_d["sem_mode"] = sqr.SQ_SEM_SOFTMAX
     g = dev_grid(grid)
     ix = sqr.build_index(prims_d, g)
-    idx = np_index(ix)
+    idx = oracle_index(ix, pr, grid)
     d, s, _ = sqr.render_fwd(prims_d, ix, g, rays)
     D, S, _, _ = oracle.render_fwd(pr, grid, idx, rig, t, sem_mode=1)
     check_depth(d.cpu().numpy(), D, 0.5)

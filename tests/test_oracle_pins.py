@@ -11,7 +11,7 @@ from scipy.spatial.transform import Rotation
 
 import oracle
 from paper_2511_17361_gb300 import synth
-from tests.helpers import axis_camera, brute_p, brute_render, prims_from, richardson_fd, small_scene
+from tests.helpers import _fp32_samples, axis_camera, brute_p, brute_render, prims_from, richardson_fd, small_scene
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -239,6 +239,25 @@ def test_axis_ray_samples_closed_form():
             assert vox[j] == (ix * 50 + 25) * 8 + int(np.floor((np.float32(1.6) + 1.0) / 0.8))
 
 
+def test_sample_voxels_of_every_ray_match_numpy_fp32():
+    """The oracle's voxel of every sample of every ray of workload 0 equals a numpy
+    FP32 restatement of the rule (pixel-centre ray, x = o + t d, floor((x - lo) * (1/vs)),
+    -1 outside), element by element."""
+    cfg = synth.make_config(0)
+    grid, rig, t = cfg["grid"], cfg["rig"], cfg["t"]
+    vox = oracle.sample_voxels(rig, t, grid)
+    x = _fp32_samples(rig, t)
+    inv = (np.float32(1.0) / np.asarray(grid["vs"], np.float32)).astype(np.float32)
+    u = ((x - np.asarray(grid["lo"], np.float32)) * inv).astype(np.float32)
+    n = np.asarray(grid["n"])
+    inside = np.all((u >= 0) & (u < n.astype(np.float32)), axis=-1)
+    i = np.floor(u).astype(np.int64)
+    ref = np.where(inside, (i[..., 0] * n[1] + i[..., 1]) * n[2] + i[..., 2], -1)
+    assert vox.shape == ref.shape
+    assert np.array_equal(vox, ref)
+    assert 0 < inside.sum() < inside.size
+
+
 # --------------------------------------------------------------------- forward
 def _recurrence(alpha, t, c):
     T, D, S = 1.0, 0.0, np.zeros_like(c[0])
@@ -275,6 +294,52 @@ def test_sphere_ray_closed_form(b, sigma, n_sph):
     assert T[0] == pytest.approx(T0, rel=1e-12, abs=1e-300)
     if n_sph == 2:
         assert np.any(p @ pr["opacity"] > 1.0)  # the clamp was exercised
+
+
+def _recurrence_kappa(alpha, t, c, kappa):
+    """The 1-D recurrence cut after the first sample j whose T_{j+1} < kappa."""
+    T, D, S = 1.0, 0.0, np.zeros_like(c[0])
+    for j in range(len(t)):
+        w = T * alpha[j]
+        D += w * t[j]
+        S = S + w * c[j]
+        T *= 1 - alpha[j]
+        if T < kappa:
+            return D, S, T, j + 1
+    return D, S, T, len(t)
+
+
+@pytest.mark.parametrize("kappa", [1e-2, 0.3])
+@pytest.mark.parametrize("b,sigma,n_sph", [(0.0, 0.7, 1), (0.3, 0.9, 2)])
+def test_sphere_ray_closed_form_early_termination(kappa, b, sigma, n_sph):
+    """Early termination (Tab. 4b): the sphere ray of the closed form above with
+    kappa > 0 stops after the first sample whose following transmittance is below
+    kappa.  D, S, T_final and the composited count match the truncated 1-D
+    recurrence to 1e-12, and stopping one sample earlier or later (testing T_j, or
+    testing before compositing j) would move D by that sample's w_j t_j."""
+    r = 1.5
+    centres = [(8.0, b, 0.0), (8.5, -b, 0.2)][:n_sph]
+    logits = np.array([[0.3, -1.2, 2.0], [1.0, 0.5, -0.5]])[:n_sph]
+    pr = prims_from(centres, [[1, 0, 0, 0], [0.6, 0.0, 0.8, 0.0]][:n_sph], [[r, r, r]] * n_sph, [[1, 1]] * n_sph,
+                    [sigma] * n_sph, logits)
+    grid = synth.grid_spec(21, 10, 10, lo=(-1, -5, -5), hi=(20, 5, 5))
+    t = synth.sample_depths(40, 0.5, 15.0)
+    idx = oracle.build_index(pr, grid, 1, 0.01, 100)
+    D, S, T, nu = oracle.render_fwd(pr, grid, idx, axis_camera(), t, kappa=kappa)
+    tt = t.astype(np.float64)
+    p = np.stack([np.exp(-(((tt - c[0]) ** 2) + c[1] ** 2 + c[2] ** 2) / r ** 2) for c in np.asarray(pr["means"],
+                                                                                                     np.float64)], 1)
+    alpha = np.minimum(p @ pr["opacity"].astype(np.float64), 1.0)
+    sem = p @ pr["logits"].astype(np.float64)
+    D0, S0, T0, n0 = _recurrence_kappa(alpha, tt, sem, kappa)
+    assert 1 < n0 < len(t)  # the ray really stops early, after at least one weighted sample
+    assert nu[0] == n0
+    assert D[0] == pytest.approx(D0, rel=1e-12)
+    np.testing.assert_allclose(S[0], S0, rtol=1e-12, atol=1e-14)
+    assert T[0] == pytest.approx(T0, rel=1e-12, abs=1e-300)
+    # the neighbouring stop rules give visibly different depths
+    w = np.cumprod(np.concatenate([[1.0], 1 - alpha]))[:-1] * alpha
+    assert abs(w[n0 - 1] * tt[n0 - 1]) > 1e-6 * abs(D0)
 
 
 def test_box_like_superquadric_entry_depth():
@@ -435,6 +500,42 @@ def test_backward_matches_central_differences_on_stress_crop():
                 fd = richardson_fd(loss, pr, name, i, h)
                 an = g[name].reshape(-1)[i]
                 assert an == pytest.approx(fd, rel=1e-5, abs=1e-7 * max(1.0, scale)), (name, int(k), c, an, fd)
+
+
+def test_backward_with_early_termination_matches_central_differences():
+    """kappa > 0: the analytic gradient through the truncated composite (Tab. 4b)
+    against central differences, on rays whose transmittance stays clear of kappa
+    (at least 2% relative at every sample), so that a step of 2^-13 moves no ray's
+    stopping sample."""
+    kappa = 0.4
+    pr, grid, rig, t = small_scene(4, n=6, H=5, W=6, L=20, sigma_max=0.6)
+    idx = oracle.build_index(pr, grid, 0, 1e-3, 5)
+    R = rig["H"] * rig["W"]
+    _, _, _, nu = oracle.render_fwd(pr, grid, idx, rig, t, kappa=kappa)
+    safe = []
+    for ray in range(R):
+        tr = oracle.trace_ray(pr, grid, idx, rig, t, ray, kappa=kappa)
+        Tn = tr["T"][1:tr["used"] + 1]
+        if np.all(np.abs(Tn - kappa) > 0.02 * kappa) and np.all(np.abs(tr["ssum"] - 1.0) > 1e-2):
+            safe.append(ray)
+    safe = np.array(safe)
+    assert np.any(nu[safe] < len(t)), "no checked ray stops early"
+    assert len(safe) > R // 3
+    rng = np.random.default_rng(11)
+    gd, gs = rng.standard_normal(len(safe)), rng.standard_normal((len(safe), pr["logits"].shape[1]))
+    g = oracle.render_bwd(pr, grid, idx, rig, t, gd, gs, kappa=kappa, ray_ids=safe)
+
+    def loss(p2):
+        D, S, _, _ = oracle.render_fwd(p2, grid, idx, rig, t, kappa=kappa, ray_ids=safe)
+        return float(np.dot(gd, D) + np.sum(gs * S))
+
+    h = 2.0 ** -13
+    for name in ["means", "quats", "scales", "eps", "opacity", "logits"]:
+        scale = np.abs(g[name]).max()
+        for i in range(pr[name].size):
+            fd = richardson_fd(loss, pr, name, i, h)
+            an = g[name].reshape(-1)[i]
+            assert an == pytest.approx(fd, rel=1e-5, abs=1e-7 * max(1.0, scale)), (name, i, an, fd)
 
 
 def test_quaternion_gradient_is_orthogonal_to_q():

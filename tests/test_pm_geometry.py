@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_2511_17361_gb300 import synth
-from tests.helpers import small_scene
+from tests.helpers import box_sums, small_scene
 
 f32 = np.float32
 
@@ -163,3 +163,24 @@ def test_full_frame_primitives_never_miss_a_run():
     """Every ray of the six-camera frame for its first 12 primitives."""
     cfg = synth.make_config(1)
     assert _check(cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], kmax=12) > 10000
+
+
+def test_box_sums_equal_brute_force():
+    """The summed-volume box sums used by the pair-visit check equal direct sums
+    over every inclusive range, empty ranges giving 0."""
+    rng = np.random.default_rng(3)
+    counts = rng.integers(0, 50, (7, 5, 4))
+    ranges = []
+    for _ in range(200):
+        r = []
+        for n in counts.shape:
+            a, b = sorted(rng.integers(0, n, 2))
+            r += [a, b]
+        ranges.append(r)
+    ranges += [[0, -1, 0, -1, 0, -1], [3, 2, 0, 4, 0, 3], [0, 6, 0, 4, 0, 3]]
+    ranges = np.array(ranges, np.int32)
+    got = box_sums(counts, ranges)
+    for r, g in zip(ranges, got):
+        want = counts[r[0]:r[1] + 1, r[2]:r[3] + 1, r[4]:r[5] + 1].sum() if r[1] >= r[0] and r[3] >= r[2] and \
+            r[5] >= r[4] else 0
+        assert g == want
