@@ -20,8 +20,9 @@
  *    Calls are asynchronous on that stream and never synchronise the host.
  *  - Argument errors are detected on the host before any launch and return
  *    SQ_ERR_INVALID_ARG; launch failures return SQ_ERR_CUDA.  Data-dependent
- *    errors (index capacity overflow) are written to the device status word
- *    sq_index_t.status, read by the caller after the stream completes.
+ *    errors (index capacity overflow, parameters outside their domain) are
+ *    written to the device status word sq_index_t.status, read by the caller
+ *    after the stream completes.
  *  - Quaternions are (w, x, y, z), a Hamilton local-to-world rotation; the
  *    canonical-frame point is x_S = R(q/|q|)^T (x - m) (Eq. 2).
  *  - Cameras are OpenCV pinholes: K[cam] = (fx, fy, cx, cy); cam2world[cam] is
@@ -46,7 +47,7 @@ typedef enum {
     SQ_ERR_CAPACITY = 2,    /* index entries exceed sq_index_t.capacity (device status only) */
     SQ_ERR_CUDA = 3,        /* a CUDA launch or runtime call failed */
     SQ_ERR_TIMEOUT = 4,     /* reserved: a bounded device wait gave up */
-    SQ_ERR_NUMERIC = 5      /* reserved: non-finite parameters detected */
+    SQ_ERR_NUMERIC = 5      /* a superquadric parameter outside its domain (device status only) */
 } sq_status_t;
 
 enum { SQ_INDEX_OBB = 0, SQ_INDEX_CUBE = 1, SQ_INDEX_OBB_OPACITY = 2 };
@@ -110,8 +111,13 @@ typedef struct {
  *   v_sq   [capacity] int32  primitive ids, each voxel's list ascending, no duplicates
  *   ranges [n,6] int32  per primitive (i0,i1,j0,j1,k0,k1) inclusive; empty = (0,-1,0,-1,0,-1)
  *   p_total  device int64 scalar: total entries P (written even on overflow)
- *   status   device int32 scalar: SQ_OK or SQ_ERR_CAPACITY after sq_build_index;
- *            render and query kernels do no work while it is non-zero.
+ *   status   device int32 scalar after sq_build_index: SQ_OK; SQ_ERR_CAPACITY;
+ *            or SQ_ERR_NUMERIC when a parameter of some primitive lies outside
+ *            the domain sq_prims_t states (a NaN or infinity anywhere, a
+ *            zero-length quaternion, a scale <= 0, eps outside (0, 2]), which
+ *            takes precedence.  While it is non-zero v_sq is not written and the
+ *            render and query kernels do no work (forward outputs stay as they
+ *            were, gradients come out zero).
  * P must stay below 2^31. */
 typedef struct {
     int* v_n;
@@ -196,9 +202,13 @@ sq_status_t sq_render_fwd(const sq_prims_t* prims, const sq_index_t* index, cons
  * every device that loads the library until exit).  Limits: prims->n at most
  * SQ_NOALLOC_MAX_PRIMS (otherwise SQ_ERR_INVALID_ARG, no work done).  The first
  * call on each device looks up the buffer's device address; make that first
- * call before any stream capture.  All calls share the buffer, so calls that
- * overlap on the GPU race; order them (one stream, or events).  Allocates
- * nothing: no cudaMalloc, no cudaFree, no allocating library call. */
+ * call before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset on a device, do not call this entry point on
+ * that device again.  All calls share the buffer, so calls that overlap on the
+ * GPU race; order them (one stream, or events).  Allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library call -- unless kernel timing
+ * is switched on (sq_profile_enable), which creates CUDA events as it records
+ * launches; leave it off where nothing may be allocated. */
 #define SQ_NOALLOC_MAX_PRIMS 16384
 sq_status_t sq_render_fwd_noalloc(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
                                   const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* stream);

@@ -269,7 +269,7 @@ const char* sq_status_string(sq_status_t s) {
         case SQ_ERR_CAPACITY: return "SQ_ERR_CAPACITY: index entries exceed the v_sq capacity";
         case SQ_ERR_CUDA: return "SQ_ERR_CUDA: CUDA error";
         case SQ_ERR_TIMEOUT: return "SQ_ERR_TIMEOUT: bounded device wait expired";
-        case SQ_ERR_NUMERIC: return "SQ_ERR_NUMERIC: non-finite input";
+        case SQ_ERR_NUMERIC: return "SQ_ERR_NUMERIC: a superquadric parameter outside its domain";
     }
     return "unknown status";
 }

@@ -520,10 +520,18 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
 //   dL/dc as accumulated.  One thread per primitive.
 __global__ void k_grad_out(const float* __restrict__ gacc, const float4* __restrict__ aux,
                            const float* __restrict__ lpad, int cp, int sem_mode, int n, int C,
-                           float* __restrict__ gm, float* __restrict__ gq, float* __restrict__ gs,
-                           float* __restrict__ ge, float* __restrict__ go, float* __restrict__ gl) {
+                           const int* __restrict__ status, float* __restrict__ gm, float* __restrict__ gq,
+                           float* __restrict__ gs, float* __restrict__ ge, float* __restrict__ go,
+                           float* __restrict__ gl) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
+    if (*status != SQ_OK) {  // no work was done: zero gradients (the packed records may hold NaN)
+        for (int i = 0; i < 3; ++i) gm[3 * k + i] = gs[3 * k + i] = 0.f;
+        for (int i = 0; i < 4; ++i) gq[4 * k + i] = 0.f;
+        ge[2 * k + 0] = ge[2 * k + 1] = go[k] = 0.f;
+        for (int c = 0; c < C; ++c) gl[(size_t)k * C + c] = 0.f;
+        return;
+    }
     const float* e = gacc + (size_t)k * GF;
     const float4 a0 = aux[(size_t)k * AUX4], a1 = aux[(size_t)k * AUX4 + 1];
     const float w = a0.x, v[3] = {a0.y, a0.z, a0.w}, inq = a1.x, is[3] = {a1.y, a1.z, a1.w};
@@ -656,7 +664,7 @@ sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream
 sq_status_t launch_grad_out(const SceneDesc& S, float* gm, float* gq, float* gs, float* ge, float* go, float* gl,
                             cudaStream_t st) {
     if (S.n == 0) return SQ_OK;
-    SQ_LAUNCH("k_grad_out", st, k_grad_out<<<(S.n + 127) / 128, 128, 0, st>>>(S.gacc, S.aux, S.lpad, S.cp, S.sem_mode, S.n, S.C, gm, gq, gs, ge, go, gl));
+    SQ_LAUNCH("k_grad_out", st, k_grad_out<<<(S.n + 127) / 128, 128, 0, st>>>(S.gacc, S.aux, S.lpad, S.cp, S.sem_mode, S.n, S.C, S.status, gm, gq, gs, ge, go, gl));
     return SQ_OK;
 }
 

@@ -2,9 +2,10 @@
 // Construction"): V_n (count per voxel), V_f (offset per voxel) and V_sq
 // (primitive ids per voxel, ascending), built on the GPU without any host sync.
 //
-//   1. k_ranges     one thread per primitive: its inclusive voxel box, in FP64 with
-//                   explicitly rounded operations (bit-reproducible), and the 8
-//                   signed corner updates of a 3-D difference array;
+//   1. k_ranges     one thread per primitive: the check of its parameters' domain
+//                   (SQ_ERR_NUMERIC in the status word), its inclusive voxel box, in
+//                   FP64 with explicitly rounded operations (bit-reproducible), and
+//                   the 8 signed corner updates of a 3-D difference array;
 //   2. k_prefix_*   three axis-wise prefix sums turn the difference array into V_n;
 //   3. k_scan_*     exclusive scan of V_n -> V_f and the total P (+ capacity check);
 //   4. k_scatter    one CTA per primitive writes its id into every voxel of its box
@@ -32,6 +33,9 @@ struct RangeArgs {
     const float* scales;
     const float* eps;
     const float* opacity;
+    const float* logits;
+    int C;
+    int* status;
     int n;
     int mode;
     int nv;
@@ -113,9 +117,33 @@ __device__ void prim_box(const RangeArgs& a, int k, int lo_i[3], int hi_i[3], bo
     }
 }
 
+// The parameter domain of one superquadric (sq_prims_t): every value finite, a
+// quaternion of non-zero length, scales > 0, eps1 and eps2 in (0, 2].
+__device__ bool params_in_domain(const RangeArgs& a, int k) {
+    bool ok = true;
+    float q2 = 0.f;
+    for (int i = 0; i < 3; ++i) {
+        const float m = a.means[3 * k + i], s = a.scales[3 * k + i];
+        ok = ok && isfinite(m) && isfinite(s) && s > 0.f;
+    }
+    for (int i = 0; i < 4; ++i) {
+        const float q = a.quats[4 * k + i];
+        ok = ok && isfinite(q);
+        q2 = fmaxf(q2, fabsf(q));
+    }
+    for (int i = 0; i < 2; ++i) {
+        const float e = a.eps[2 * k + i];
+        ok = ok && e > 0.f && e <= 2.f;  // false for NaN
+    }
+    ok = ok && q2 > 0.f && isfinite(a.opacity[k]);
+    for (int c = 0; c < a.C; ++c) ok = ok && isfinite(a.logits[(size_t)k * a.C + c]);
+    return ok;
+}
+
 __global__ void k_ranges(RangeArgs a, int* __restrict__ ranges, int* __restrict__ diff) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.n) return;
+    if (!params_in_domain(a, k)) atomicMax(a.status, (int)SQ_ERR_NUMERIC);
     int lo[3], hi[3];
     bool empty;
     prim_box(a, k, lo, hi, empty);
@@ -240,7 +268,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(long long* __restri
     }
     if (threadIdx.x == 0) {
         *p_total = carry;
-        if (carry > capacity || carry >= 2147483647LL) *status = SQ_ERR_CAPACITY;
+        // SQ_ERR_NUMERIC (set by k_ranges) outranks the capacity error
+        if (carry > capacity || carry >= 2147483647LL) atomicMax(status, (int)SQ_ERR_CAPACITY);
     }
 }
 
@@ -439,6 +468,9 @@ sq_status_t build_index_impl(const sq_prims_t* prims, const sq_grid_t* grid, con
     RangeArgs a;
     a.means = prims->means; a.quats = prims->quats; a.scales = prims->scales; a.eps = prims->eps;
     a.opacity = prims->opacity;
+    a.logits = prims->logits;
+    a.C = prims->n_classes;
+    a.status = idx->status;
     a.n = prims->n; a.mode = opts->mode; a.nv = opts->nv;
     a.log_kc = (opts->mode != SQ_INDEX_CUBE) ? log(-log((double)opts->tau_cut)) : 0.0;
     a.tau = (double)opts->tau_cut;

@@ -345,6 +345,7 @@ sq_status_t query_grid_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, 
     S.sem_mode = prims->sem_mode;
     S.n = n;
     S.C = prims->n_classes;
+    S.status = idx->status;
     return launch_grad_out(S, g_means, g_quats, g_scales, g_eps, g_opacity, g_logits, st);
 }
 

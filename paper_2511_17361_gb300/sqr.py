@@ -240,8 +240,10 @@ class Index:
 
     def check(self):
         s = int(self.status.item())
-        if s != SQ_OK:
+        if s == SQ_ERR_CAPACITY:
             raise SqrError(f"index: {lib.sq_status_string(s).decode()} (needed {self.P()}, have {self.capacity})")
+        if s != SQ_OK:
+            raise SqrError(f"index: {lib.sq_status_string(s).decode()}")
 
 
 def build_index(prims: dict, grid: dict, mode: int = SQ_INDEX_OBB, tau_cut: float = 0.01, nv: int = 5,

@@ -156,6 +156,50 @@ def test_index_capacity_overflow_reported(sqr):
     _assert_index_equal(ix2, ref)
 
 
+@pytest.mark.parametrize("field,index,value", [("scales", (7, 1), float("nan")), ("scales", (3, 0), 0.0),
+                                               ("eps", (5, 0), 2.5), ("eps", (9, 1), -0.1),
+                                               ("quats", (2, slice(None)), 0.0), ("means", (4, 2), float("inf")),
+                                               ("opacity", (11,), float("nan")), ("logits", (6, 17), float("-inf"))])
+def test_index_numeric_status(sqr, field, index, value):
+    """A parameter outside its domain (set on the host): the index build reports
+    SQ_ERR_NUMERIC (over a capacity overflow too), the forward leaves its outputs
+    untouched, the backward and the query backward return zero gradients, and the
+    grid query writes nothing."""
+    cfg = synth.make_config(0)
+    pr = {k: v.copy() for k, v in cfg["prims"].items()}
+    pr[field][index] = value
+    prims_d = sqr.to_device(pr)
+    g = dev_grid(cfg["grid"])
+    for cap in (None, 1000):
+        ix = sqr.build_index(prims_d, g, capacity=cap, sync=False)
+        torch.cuda.synchronize()
+        assert int(ix.status.item()) == sqr.SQ_ERR_NUMERIC
+    with pytest.raises(sqr.SqrError, match="NUMERIC"):
+        sqr.build_index(prims_d, g)
+    rays = sqr.Rays.from_rig(cfg["rig"], cfg["t"])
+    depth = torch.full((rays.R,), -7.0, device="cuda")
+    sem = torch.full((rays.R, 18), 3.0, device="cuda")
+    tf = torch.full((rays.R,), 5.0, device="cuda")
+    saved = sqr.new_saved(rays, 18)
+    sqr.render_fwd(prims_d, ix, g, rays, out=(depth, sem, tf), saved=saved)
+    torch.cuda.synchronize()
+    assert torch.all(depth == -7.0) and torch.all(sem == 3.0) and torch.all(tf == 5.0)
+    gd, gs = torch.ones(rays.R, device="cuda"), torch.ones((rays.R, 18), device="cuda")
+    for order in (sqr.SQ_BWD_DEFAULT, sqr.SQ_BWD_RAY_MAJOR):
+        grads = {k: torch.full_like(prims_d[k], 9.0) for k in sqr.PRIM_KEYS}
+        sqr.render_bwd(prims_d, ix, g, rays, gd, gs, saved=saved, out=grads, order=order)
+        torch.cuda.synchronize()
+        assert all(torch.all(v == 0.0) for v in grads.values())
+    nvox = ix.v_n.numel()
+    dens = torch.full((nvox,), -1.0, device="cuda")
+    qs = torch.full((nvox, 18), -1.0, device="cuda")
+    sqr.query_grid(prims_d, ix, g, out=(dens, qs, None))
+    qg = sqr.query_grid_bwd(prims_d, ix, g, torch.ones(nvox, device="cuda"), torch.ones((nvox, 18), device="cuda"))
+    torch.cuda.synchronize()
+    assert torch.all(dens == -1.0) and torch.all(qs == -1.0)
+    assert all(torch.all(v == 0.0) for v in qg.values())
+
+
 # ----------------------------------------------------------------------- forward
 def _fwd_pair(sqr, prims, grid, rig, t, kappa=0.0, alpha_max=1.0, ray_ids=None, mode=0, tau=0.01, nv=5):
     prims_d, rays = scene_to_gpu(sqr, prims, rig, t, kappa, alpha_max)
