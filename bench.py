@@ -32,7 +32,16 @@ from paper_2511_17361_gb300 import synth  # noqa: E402
 
 WORKLOAD = 1
 BWD_ORDER = 0  # SQ_BWD_DEFAULT; --bwd-order
-MUFU_PER_PAIR = {"fwd": 9, "bwd": 13}  # SFU ops per (sample, primitive) pair in each kernel
+# SFU instructions per (sample, primitive) pair: the forward's occupancy takes 4 lg2
+# and 5 ex2, the backward's partial derivatives add 4 rcp
+MUFU_MIX = {"fwd": {"ex2": 5, "lg2": 4, "rcp": 0}, "bwd": {"ex2": 5, "lg2": 4, "rcp": 4}}
+MUFU_PER_PAIR = {k: sum(v.values()) for k, v in MUFU_MIX.items()}
+
+
+def mix_peak(sfu, mix):
+    """The SFU rate for a kernel's instruction mix: every instruction of the mix
+    issued at its own measured rate, G instructions / s."""
+    return sum(mix.values()) / sum(n / sfu[op] for op, n in mix.items() if n)
 # DRAM traffic per launch from the committed ncu summaries, valid only while the
 # kernel source is unchanged (sha256 of the file holding it).
 NCU_TRAFFIC = {
@@ -126,36 +135,71 @@ def _oracle_sample(cfg, n_rays, seed=0):
     return np.sort(rng.choice(R, size=min(n_rays, R), replace=False))
 
 
-def oracle_step_time(cfg, index_np, ray_ids, targets):
-    """One oracle fwd + loss-gradient + bwd pass over ray_ids (seconds, threads used)."""
+def oracle_step_time(cfg, index_np, ray_ids, targets, threads=0):
+    """One oracle fwd + loss-gradient + bwd pass over ray_ids (seconds, threads used;
+    threads = 0: all host cores)."""
     import oracle
     t0 = time.perf_counter()
-    D, S, _, _ = oracle.render_fwd(cfg["prims"], cfg["grid"], index_np, cfg["rig"], cfg["t"], ray_ids=ray_ids)
+    D, S, _, _ = oracle.render_fwd(cfg["prims"], cfg["grid"], index_np, cfg["rig"], cfg["t"], ray_ids=ray_ids,
+                                   threads=threads)
     td, tl = targets
     R = len(ray_ids)
     e = np.exp(S - S.max(1, keepdims=True))
     gs = 2.0 / R * (e / e.sum(1, keepdims=True) - np.eye(S.shape[1])[tl[ray_ids]])
     gd = 0.05 / R * 2 * (D - td[ray_ids])
-    oracle.render_bwd(cfg["prims"], cfg["grid"], index_np, cfg["rig"], cfg["t"], gd, gs, ray_ids=ray_ids)
-    return time.perf_counter() - t0, oracle.max_threads()
+    oracle.render_bwd(cfg["prims"], cfg["grid"], index_np, cfg["rig"], cfg["t"], gd, gs, ray_ids=ray_ids,
+                      threads=threads)
+    return time.perf_counter() - t0, (threads if threads > 0 else oracle.max_threads())
 
 
-def cpu_baseline(cfg, index_np, targets, budget_s=12.0):
+def cpu_baseline(cfg, index_np, targets, budget_s=12.0, threads=0):
     """The FP64 oracle on a bounded random ray sample of the same frame."""
-    probe = _oracle_sample(cfg, 600, seed=1)
-    t_probe, threads = oracle_step_time(cfg, index_np, probe, targets)
+    probe = _oracle_sample(cfg, 600 if threads != 1 else 60, seed=1)
+    t_probe, used = oracle_step_time(cfg, index_np, probe, targets, threads)
     total = synth.n_rays(cfg["rig"])
-    n = int(min(total, max(600, 600 * budget_s / max(t_probe, 1e-3))))
+    n = int(min(total, max(len(probe), len(probe) * budget_s / max(t_probe, 1e-3))))
     ids = _oracle_sample(cfg, n, seed=2)
-    t, threads = oracle_step_time(cfg, index_np, ids, targets)
+    t, used = oracle_step_time(cfg, index_np, ids, targets, threads)
     if t < 0.6 * budget_s and n < total:  # the small probe overstates the cost per ray: size again from this run
         n = int(min(total, n * budget_s / max(t, 1e-3)))
         ids = _oracle_sample(cfg, n, seed=2)
-        t, threads = oracle_step_time(cfg, index_np, ids, targets)
+        t, used = oracle_step_time(cfg, index_np, ids, targets, threads)
     L = len(cfg["t"])
-    return {"value": n * L / t, "unit": "ray-samples/s", "cores": threads, "kind": "oracle",
+    return {"value": n * L / t, "unit": "ray-samples/s", "cores": used, "kind": "oracle",
             "sample": f"{n} random rays of the {cfg['name']} frame (index built by the oracle), "
                       f"forward + loss gradient + backward, FP64, {t:.1f} s"}
+
+
+def cpu_extra_legs():
+    """The other oracle timings on the host cores: the stress frame's 32x32-ray crop
+    of camera 0 (forward + backward of seeded cotangents) and the grid query of
+    the 8192-superquadric scene at all 640,000 voxel centres."""
+    import oracle
+    out = {}
+    cfg = synth.make_config(2)
+    idx = oracle.build_index(cfg["prims"], cfg["grid"])
+    W = cfg["rig"]["W"]
+    crop = np.array([(96 + i) * W + (184 + j) for i in range(32) for j in range(32)], np.int64)
+    gd, gs = synth.cotangents(len(crop), 2)
+    t0 = time.perf_counter()
+    oracle.render_fwd(cfg["prims"], cfg["grid"], idx, cfg["rig"], cfg["t"], ray_ids=crop)
+    oracle.render_bwd(cfg["prims"], cfg["grid"], idx, cfg["rig"], cfg["t"], gd.astype(np.float64),
+                      gs.astype(np.float64), ray_ids=crop)
+    t = time.perf_counter() - t0
+    L = len(cfg["t"])
+    out["stress_crop"] = {"value": len(crop) * L / t, "unit": "ray-samples/s", "cores": oracle.max_threads(),
+                          "kind": "oracle", "sample": f"the 32x32-ray crop of camera 0 of {cfg['name']} (1024 rays), "
+                                                      f"forward + backward, FP64, {t:.2f} s"}
+    cfg = synth.make_config(4, seed=4)
+    idx = oracle.build_index(cfg["prims"], cfg["grid"])
+    t0 = time.perf_counter()
+    oracle.query_grid(cfg["prims"], cfg["grid"], idx, tau=0.05)
+    t = time.perf_counter() - t0
+    nvox = int(np.prod(cfg["grid"]["n"]))
+    out["query"] = {"value": nvox / t, "unit": "voxels/s", "cores": oracle.max_threads(), "kind": "oracle",
+                    "sample": f"all {nvox} voxel centres of {cfg['name']} (density, semantics, label), "
+                              f"FP64, {t:.2f} s"}
+    return out
 
 
 def run_reference(args):
@@ -308,53 +352,61 @@ def run_mine(args):
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     e2e_value = job_throughput(R * L * args.steps, world, e2e_ms)
 
-    # ---- roofline of the dominant kernel (SFU-bound: MUFU ops per pair)
+    # ---- pairs evaluated: the backward's own per-primitive count of the pairs of
+    # composited samples (one extra call, outside the timed region); the forward
+    # evaluates the same pairs plus those of at most a chunk of samples past a ray's stop
+    visits = torch.zeros(int(prims["means"].shape[0]), dtype=torch.int64, device=dev)
+    sqr.render_bwd(prims, ix, grid, rays, loss_out[1], loss_out[2], saved=saved, out=grads,
+                   order=sqr.SQ_BWD_PRIMITIVE_MAJOR, pair_visits=visits)
+    q_eval = int(visits.sum().item())
+    peak_mem = int(torch.cuda.max_memory_allocated(dev))
+    saved_bytes = int(saved.numel())
+
+    # ---- roofline of the pair kernels (SFU-bound: MUFU ops per pair) against the
+    # measured SFU rate; frac_survey is the survey's count (every in-grid sample's
+    # pairs Q, 9 MUFU each) against the nominal 16 MUFU/clk/SM at the top clock
     mean_phase = phase.mean(0)
     names = ["index", "fwd", "loss", "bwd"]
     props = torch.cuda.get_device_properties(dev)
     sm_count = props.multi_processor_count
     peak_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak = sm_count * 16 * peak_mhz * 1e6 / 1e9  # G MUFU ops / s
-    roof = None
-    # the dominant kernel: the longer of the two pair-evaluating kernels, its mean
-    # launch time from the events recorded around it over the timed steps
-    kname = max(("k_forward", "k_backward", "k_pm_tiles"), key=lambda k: kernel_ms[k][1])
-    n_launch, k_total_ms, _ = kernel_ms[kname]
-    if n_launch > 0:
+    nominal = sm_count * 16 * peak_mhz * 1e6 / 1e9  # G MUFU ops / s
+    sfu = {op: sqr.measure_sfu(op) / 1e9 for op in ("ex2", "lg2", "rcp")}
+    pair_kernels = {}
+    for kname in ("k_forward", "k_backward", "k_pm_tiles"):
+        n_launch, k_total_ms, _ = kernel_ms[kname]
+        if n_launch == 0:
+            continue
         k_mean_ms = k_total_ms / n_launch
-        achieved = Q * MUFU_PER_PAIR["fwd" if kname == "k_forward" else "bwd"] / (k_mean_ms / 1e3) / 1e9
-        tr = NCU_TRAFFIC.get(kname)
-        traffic = None
-        if tr and tr["src_sha"] == _sha(os.path.join(ROOT, "paper_2511_17361_gb300", "csrc", tr["src"])):
-            traffic = tr["bytes_per_launch"]
-        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GMUFUop/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel_ms_per_launch": k_mean_ms,
-                "peak_source": f"{sm_count} SMs x 16 SFU ops/clk x {peak_mhz:.0f} MHz (max SM clock seen)"}
-    # algorithmic HBM bytes of the backward: cotangents in, parameters + index lists read, gradients out
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        kind = "fwd" if kname == "k_forward" else "bwd"
+        mufu, peak = MUFU_PER_PAIR[kind], mix_peak(sfu, MUFU_MIX[kind])
+        achieved = q_eval * mufu / (k_mean_ms / 1e3) / 1e9
+        pair_kernels[kname] = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                               "unit": "GMUFUop/s", "frac": achieved / peak, "frac_evaluated": achieved / peak,
+                               "frac_survey": Q * 9 / (k_mean_ms / 1e3) / 1e9 / nominal,
+                               "mufu_per_pair": mufu, "pairs_evaluated": q_eval, "pairs_Q": Q,
+                               "traffic": _traffic(kname), "kernel_ms_per_launch": k_mean_ms}
+    # the dominant kernel: the longer of the pair-evaluating kernels
+    kdom = max(pair_kernels, key=lambda k: pair_kernels[k]["kernel_ms_per_launch"]) if pair_kernels else None
+    roof = dict(pair_kernels[kdom]) if kdom else None
+    if roof:
+        roof["peak_source"] = (f"measured SFU rates (sq_measure_sfu: ex2/lg2/rcp {sfu['ex2']:.0f}/{sfu['lg2']:.0f}/"
+                               f"{sfu['rcp']:.0f} G/s), combined for the kernel's mix of "
+                               f"{roof['mufu_per_pair']} per pair; frac_survey: nominal {sm_count} SMs x 16/clk x "
+                               f"{peak_mhz:.0f} MHz = {nominal:.0f} G/s")
+    hbm_peak = _hbm_peak()
     # the HBM-bound kernel of the step: the backward's back-to-front sweep reads the
     # saved T_j, alpha_j, s_j of every composited sample (and t_j, gD, gS) and
     # writes (dL/dalpha_j, w_j); the composited counts come from the saved state
-    # (its last block, int32 per ray, layout as sq_saved_size documents)
-    RL, CP = R * L, (C + 3) // 4 * 4
-    a256 = lambda b: (b + 255) // 256 * 256
-    n_off = a256(RL * 8) + a256(RL * CP * 4)
-    composited = int(saved[n_off:n_off + R * 4].view(torch.int32).sum().item())
+    CP = (C + 3) // 4 * 4
+    composited = int(sqr.saved_counts(saved, rays, C).sum().item())
     sweep_bytes = composited * ((2 + CP) * 4 + 4 + 8) + R * (1 + C) * 4 + R * 4
     n_sw, sw_ms, _ = kernel_ms["k_bwd_sweep"]
     hbm = None
     if n_sw > 0:
         gbps = sweep_bytes / (sw_ms / n_sw / 1e3) / 1e9
-        trs = NCU_TRAFFIC["k_bwd_sweep"]
-        sw_traffic = trs["bytes_per_launch"] if trs["src_sha"] == _sha(
-            os.path.join(ROOT, "paper_2511_17361_gb300", "csrc", trs["src"])) else None
         hbm = {"kernel": "k_bwd_sweep", "bound": "hbm", "algorithmic_bytes": sweep_bytes, "achieved_GBps": gbps,
-               "frac": gbps / hbm_peak, "peak_gbs": hbm_peak, "traffic": sw_traffic,
+               "frac": gbps / hbm_peak, "peak_gbs": hbm_peak, "traffic": _traffic("k_bwd_sweep"),
                "composited_samples": composited}
 
     line = {"metric": "ray-samples/s (forward + backward), six-camera frame", "value": value,
@@ -363,8 +415,9 @@ def run_mine(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg["name"], "rays": R, "samples_per_ray": L, "superquadrics": int(
                 prims["means"].shape[0]), "grid": list(grid["n"]), "index_entries_P": P, "pairs_Q": Q,
-                "in_grid_samples": in_grid, "index": {"obb": "OBB, tau_cut 0.01", "cube": "cube N_v = 5",
-                                                      "opacity": "opacity-aware OBB, tau_cut 0.01"}[args.index],
+                "pairs_evaluated": q_eval, "in_grid_samples": in_grid, "composited_samples": composited,
+                "index": {"obb": "OBB, tau_cut 0.01", "cube": "cube N_v = 5",
+                          "opacity": "opacity-aware OBB, tau_cut 0.01"}[args.index],
                 "l2": "flushed (256 MB write) between timed steps",
                 "backward_order": {0: "primitive-major (the default)", 1: "ray-major",
                                    2: "primitive-major"}[BWD_ORDER],
@@ -373,12 +426,34 @@ def run_mine(args):
             "gpu_launches": launches_timed + dropped,
             "kernel_ms_per_launch": {k: (v[1] / v[0] if v[0] else None) for k, v in kernel_ms.items()},
             "e2e": {"value": e2e_value, "unit": "ray-samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "roofline": roof, "hbm": hbm, "clocks": clocks}
+            "roofline": roof, "pair_kernels": pair_kernels, "sfu_measured_Gops": sfu, "hbm": hbm,
+            "memory": {"peak_mem_bytes": peak_mem, "saved_state_bytes": saved_bytes,
+                       "what": "torch.cuda.max_memory_allocated over the timed and end-to-end steps: inputs, "
+                               "index, saved forward state, outputs, gradients and the library's workspaces "
+                               "(all caller-owned torch tensors)"},
+            "clocks": clocks}
+    extras = world == 1 and not args.no_extras and args.cameras == 6 and args.index == "obb" and BWD_ORDER == 0
+    if extras:
+        # the other workloads, each a few seconds, after the frame's buffers are freed
+        del saved, grads, loss_out, depth, sem, tf, flush, host_in, host_out
+        torch.cuda.empty_cache()
+        xs = max(3, min(args.steps, 5))
+        line["stress_ab"] = stress_result(sqr, dev, xs, 2)
+        torch.cuda.empty_cache()
+        line["batched"] = batch_result(sqr, dev, "batch", xs, 2)
+        torch.cuda.empty_cache()
+        line["temporal"] = batch_result(sqr, dev, "temporal", xs, 2)
+        torch.cuda.empty_cache()
+        line["query"] = query_result(sqr, dev, max(5, args.steps), 3, sfu=sfu)
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        idx_np = {"v_n": ix.v_n.cpu().numpy(), "v_f": ix.v_f.cpu().numpy(), "v_sq": ix.v_sq[:P].cpu().numpy()}
+        idx_np = oracle.build_index(cfg["prims"], cfg["grid"])
         line["cpu_baseline"] = cpu_baseline(cfg, idx_np, (td_np, tl_np), budget_s=args.cpu_budget)
+        if extras:
+            line["cpu_baseline"]["one_core"] = cpu_baseline(cfg, idx_np, (td_np, tl_np),
+                                                            budget_s=max(3.0, args.cpu_budget / 3), threads=1)
+            line["cpu_baseline"].update(cpu_extra_legs())
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -386,15 +461,24 @@ def run_mine(args):
     return 0
 
 
-# ----------------------------------------------------------------------- batched workload
-def run_query(args):
-    """Supp. A.4 grid query of the 8192-superquadric scene at all 640,000 voxel
-    centres of the 200x200x16 grid (tau = 0.05): density, semantics and labels."""
+# ----------------------------------------------------------------------- other workloads
+def _hbm_peak():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
+    except Exception:
+        return 6800.0
+
+
+def _flush_buffer(dev):
     import torch
-    from paper_2511_17361_gb300 import _build
-    _build.build()
-    from paper_2511_17361_gb300 import sqr
-    dev = torch.device("cuda", 0)
+    return torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+
+def query_result(sqr, dev, steps, warmup, sfu=None):
+    """Supp. A.4 grid query of the 8192-superquadric scene at all 640,000 voxel
+    centres of the 200x200x16 grid (tau = 0.05): density, semantics and labels;
+    then the voxel losses and the query backward."""
+    import torch
     cfg = synth.make_config(4, seed=4)
     prims = sqr.to_device(cfg["prims"], dev)
     grid = {"n": cfg["grid"]["n"], "lo": [float(v) for v in cfg["grid"]["lo"]],
@@ -416,16 +500,14 @@ def run_query(args):
         _, _, gd, gsem = sqr.loss_voxel(out[0], out[1], vlab, out=lout)
         sqr.query_grid_bwd(prims, ix, grid, gd, gsem, out=grads)
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         sqr.query_grid(prims, ix, grid, 0.05, out=out)
         backward()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    sampler = ClockSampler(0)
+    flush = _flush_buffer(dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
     torch.cuda.synchronize()
-    sampler.start()
     sqr.profile_enable(True)
-    for s in range(args.steps):
+    for s in range(steps):
         flush.fill_(float(s))
         ev[s][0].record()
         sqr.query_grid(prims, ix, grid, 0.05, out=out)
@@ -434,53 +516,62 @@ def run_query(args):
         ev[s][2].record()
     torch.cuda.synchronize()
     sqr.profile_enable(False)
-    clocks = sampler.stop()
-    ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
-    ms_bwd = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
+    ms = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
+    ms_bwd = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
     n_q, q_ms, _ = sqr.profile_query("k_query")
     n_qb, qb_ms, _ = sqr.profile_query("k_query_bwd")
-    kb_ms = qb_ms / max(n_qb, 1)
     launches, _, dropped = sqr.profile_query(None)
-    k_ms = q_ms / max(n_q, 1)
-    props = torch.cuda.get_device_properties(dev)
-    peak_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * 16 * peak_mhz * 1e6 / 1e9
-    achieved = P * 9 / (k_ms / 1e3) / 1e9  # every voxel centre evaluates its whole list: P pairs, 9 MUFU each
+    k_ms, kb_ms = q_ms / max(n_q, 1), qb_ms / max(n_qb, 1)
+    if sfu is None:
+        sfu = {op: sqr.measure_sfu(op) / 1e9 for op in ("ex2", "lg2", "rcp")}
+    peak_f, peak_b = mix_peak(sfu, MUFU_MIX["fwd"]), mix_peak(sfu, MUFU_MIX["bwd"])
+    # every voxel centre evaluates its whole list: P pairs, 9 MUFU each (13 in the backward)
+    achieved, achieved_b = P * 9 / (k_ms / 1e3) / 1e9, P * 13 / (kb_ms / 1e3) / 1e9
     out_bytes = nvox * (1 + C) * 4 + nvox
-    try:
-        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
-    except Exception:
-        hbm_peak = 6800.0
-    line = {"metric": "voxel queries/s (density + semantics + label), 200x200x16 grid", "value": nvox / (ms / 1e3),
-            "unit": "voxels/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    hbm_bytes = out_bytes + 4 * P + 8 * nvox
+    return {"metric": "voxel queries/s (density + semantics + label), 200x200x16 grid",
+            "value": nvox / (ms / 1e3), "unit": "voxels/s", "ms_per_step": ms, "steps": steps,
             "config": {"workload": cfg["name"], "superquadrics": int(prims["means"].shape[0]), "voxels": nvox,
                        "index_entries_P": P, "tau": 0.05, "l2": "flushed (256 MB write) between timed steps"},
             "gpu_launches": launches + dropped, "kernel_ms_per_launch": {"k_query": k_ms, "k_query_bwd": kb_ms},
             "backward": {"what": "voxel CE + BCE losses (sq_loss_voxel) and the query backward of their gradients",
                          "ms_per_step": ms_bwd, "value": nvox / (ms_bwd / 1e3), "unit": "voxels/s",
-                         "roofline": {"bound": "alu", "kernel": "k_query_bwd",
-                                      "achieved": P * 13 / (kb_ms / 1e3) / 1e9, "peak": peak, "unit": "GMUFUop/s",
-                                      "frac": P * 13 / (kb_ms / 1e3) / 1e9 / peak}},
-            "roofline": {"bound": "alu", "kernel": "k_query", "achieved": achieved, "peak": peak, "unit": "GMUFUop/s",
-                         "frac": achieved / peak, "traffic": _traffic("k_query")},
-            "hbm": {"kernel": "k_query", "bound": "hbm", "algorithmic_bytes": out_bytes + 4 * P + 8 * nvox,
-                    "achieved_GBps": (out_bytes + 4 * P + 8 * nvox) / (k_ms / 1e3) / 1e9,
-                    "frac": (out_bytes + 4 * P + 8 * nvox) / (k_ms / 1e3) / 1e9 / hbm_peak, "peak_gbs": hbm_peak},
-            "clocks": clocks}
-    print(json.dumps(line))
+                         "roofline": {"bound": "alu", "kernel": "k_query_bwd", "achieved": achieved_b,
+                                      "peak": peak_b, "unit": "GMUFUop/s", "frac": achieved_b / peak_b}},
+            "roofline": {"bound": "alu", "kernel": "k_query", "achieved": achieved, "peak": peak_f,
+                         "unit": "GMUFUop/s", "frac": achieved / peak_f, "traffic": _traffic("k_query")},
+            "sfu_measured_Gops": sfu,
+            "hbm": {"kernel": "k_query", "bound": "hbm", "algorithmic_bytes": hbm_bytes,
+                    "achieved_GBps": hbm_bytes / (k_ms / 1e3) / 1e9,
+                    "frac": hbm_bytes / (k_ms / 1e3) / 1e9 / _hbm_peak(), "peak_gbs": _hbm_peak()}}
 
 
-def run_batch(args):
-    """Twelve uneven scenes (--workload batch) or the 13 frames of a temporal
-    horizon (--workload temporal): per-scene launches vs one batched persistent
-    launch per pass (autotuned), the whole step captured in a CUDA graph."""
+def run_query(args):
     import torch
     from paper_2511_17361_gb300 import _build
     _build.build()
     from paper_2511_17361_gb300 import sqr
     dev = torch.device("cuda", 0)
-    temporal = args.workload == "temporal"
+    sampler = ClockSampler(0)
+    sampler.start()
+    r = query_result(sqr, dev, args.steps, args.warmup)
+    clocks = sampler.stop()
+    line = {"metric": r.pop("metric"), "value": r.pop("value"), "unit": r.pop("unit"), "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    r.pop("steps")
+    line.update(r)
+    line["clocks"] = clocks
+    print(json.dumps(line))
+    return 0
+
+
+def batch_result(sqr, dev, kind, steps, warmup):
+    """Twelve uneven scenes (kind "batch") or the 13 frames of a temporal horizon
+    (kind "temporal"): per-scene launches vs one batched persistent launch per
+    pass (autotuned), eager and captured in a CUDA graph."""
+    import torch
+    temporal = kind == "temporal"
     cfgs = synth.make_temporal_config() if temporal else synth.make_batch_config(3)
     scenes, targets = [], []
     for i, c in enumerate(cfgs):
@@ -519,8 +610,9 @@ def run_batch(args):
         loss_all()
         sqr.render_batched(sqr.SQ_OP_BWD, scenes, tuning)
 
-    def timed(fn, steps):
-        flush = torch.empty(64 * 1024 * 1024, device=dev)
+    flush = _flush_buffer(dev)
+
+    def timed(fn):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize()
         for s in range(steps):
@@ -531,10 +623,10 @@ def run_batch(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in ev) / steps
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         per_scene_step()
         batched_step()
-    ms_per_scene = timed(per_scene_step, args.steps)
+    ms_per_scene = timed(per_scene_step)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
@@ -543,12 +635,11 @@ def run_batch(args):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         batched_step()
-    ms_graph = timed(graph.replay, args.steps)
-    ms_batched = timed(batched_step, args.steps)
+    ms_graph = timed(graph.replay)
+    ms_batched = timed(batched_step)
     what = "13-frame temporal horizon (T = 6)" if temporal else "12-scene uneven batch"
-    line = {"metric": f"ray-samples/s (forward + backward), {what}", "value": samples / (ms_graph / 1e3),
-            "unit": "ray-samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    return {"metric": f"ray-samples/s (forward + backward), {what}", "value": samples / (ms_graph / 1e3),
+            "unit": "ray-samples/s", "ms_per_step": ms_graph, "steps": steps,
             "config": {"workload": "temporal13_ring6_N1600" if temporal else "batch12_uneven", "scenes": len(scenes),
                        "ray_samples": samples,
                        "rays": [sc.rays.R for sc in scenes], "superquadrics": [int(sc.prims["means"].shape[0])
@@ -557,9 +648,78 @@ def run_batch(args):
                        "l2": "flushed (256 MB write) between timed steps"},
             "per_scene_launches": {"ms_per_step": ms_per_scene, "value": samples / (ms_per_scene / 1e3)},
             "batched_eager": {"ms_per_step": ms_batched, "value": samples / (ms_batched / 1e3)},
-            "batched_graph": {"ms_per_step": ms_graph, "value": samples / (ms_graph / 1e3)}}
+            "batched_graph": {"ms_per_step": ms_graph, "value": samples / (ms_graph / 1e3)},
+            "graph_over_per_scene": ms_per_scene / ms_graph}
+
+
+def run_batch(args):
+    import torch
+    from paper_2511_17361_gb300 import _build
+    _build.build()
+    from paper_2511_17361_gb300 import sqr
+    dev = torch.device("cuda", 0)
+    r = batch_result(sqr, dev, args.workload, args.steps, args.warmup)
+    line = {"metric": r.pop("metric"), "value": r.pop("value"), "unit": r.pop("unit"), "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    r.pop("steps")
+    line.update(r)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def stress_result(sqr, dev, steps, warmup):
+    """The backward stress frame (16,384 clustered superquadrics, six 225x400
+    cameras, L = 100): index + forward, then the backward in each order (the
+    ray-major run walk and the primitive-major tiles of Processes 2-3)."""
+    import torch
+    cfg = synth.make_config(2)
+    grid = {"n": cfg["grid"]["n"], "lo": [float(v) for v in cfg["grid"]["lo"]],
+            "vs": [float(v) for v in cfg["grid"]["vs"]]}
+    prims = sqr.to_device(cfg["prims"], dev)
+    rays = sqr.Rays.from_rig(cfg["rig"], cfg["t"], device=dev)
+    R, L, C = rays.R, len(cfg["t"]), cfg["prims"]["logits"].shape[1]
+    ix = sqr.build_index(prims, grid, flags=True)  # the ray-major order reads the range-boundary flags
+    Q, _ = sqr.count_pairs(ix, grid, rays)
+    saved = sqr.new_saved(rays, C, dev)
+    depth, sem, _ = sqr.render_fwd(prims, ix, grid, rays, saved=saved)
+    td, tl = synth.loss_targets(R, 2)
+    _, gd, gs = sqr.loss_ce_mse(depth, sem, torch.from_numpy(td).to(dev), torch.from_numpy(tl).to(dev))
+    grads = {k: torch.empty_like(prims[k]) for k in sqr.PRIM_KEYS}
+    visits = torch.zeros(prims["means"].shape[0], dtype=torch.int64, device=dev)
+    sqr.render_bwd(prims, ix, grid, rays, gd, gs, saved=saved, out=grads, order=sqr.SQ_BWD_PRIMITIVE_MAJOR,
+                   pair_visits=visits)
+    flush = _flush_buffer(dev)
+    res = {"config": {"workload": cfg["name"], "rays": R, "samples_per_ray": L,
+                      "superquadrics": int(prims["means"].shape[0]), "index_entries_P": ix.P(), "pairs_Q": Q,
+                      "pairs_evaluated": int(visits.sum().item()), "max_list": int(ix.v_n.max().item())}}
+
+    def timed(fn, kern):
+        for _ in range(warmup):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        sqr.profile_enable(True)
+        for s in range(steps):
+            flush.fill_(float(s))
+            ev[s][0].record()
+            fn()
+            ev[s][1].record()
+        torch.cuda.synchronize()
+        sqr.profile_enable(False)
+        n, kms, _ = sqr.profile_query(kern) if kern else (0, 0.0, 0)
+        return sum(a.elapsed_time(b) for a, b in ev) / steps, (kms / n if n else None)
+
+    ms_fwd, kf = timed(lambda: (sqr.build_index(prims, grid, index=ix, sync=False, flags=True),
+                                sqr.render_fwd(prims, ix, grid, rays, saved=saved)), "k_forward")
+    res["index_fwd_ms"], res["k_forward_ms"] = ms_fwd, kf
+    for name, order, kern in (("ray_major", sqr.SQ_BWD_RAY_MAJOR, "k_backward"),
+                              ("primitive_major", sqr.SQ_BWD_PRIMITIVE_MAJOR, "k_pm_tiles")):
+        ms, km = timed(lambda: sqr.render_bwd(prims, ix, grid, rays, gd, gs, saved=saved, out=grads, order=order),
+                       kern)
+        res[name] = {"bwd_ms": ms, f"{kern}_ms": km, "ray_samples_per_s": R * L / ((ms + ms_fwd) / 1e3)}
+    res["primitive_over_ray_major"] = res["ray_major"]["bwd_ms"] / res["primitive_major"]["bwd_ms"]
+    return res
 
 
 def main(argv=None):
@@ -569,6 +729,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the frame workload (skip the stress A/B, batch, horizon and query keys)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--index", choices=["obb", "cube", "opacity"], default="obb",
                     help="voxel neighbourhood of the frame workload's index (default: OBB, tau_cut 0.01)")

@@ -388,6 +388,17 @@ sq_status_t sq_profile_enable(int on);
  * the number of launches that found the record pool full. */
 sq_status_t sq_profile_query(const char* name, long long* launches, double* total_ms, long long* dropped);
 
+/* Measured throughput of the special-function unit, no counterpart in the
+ * paper: the renderer's pair kernels are bound by its exp2 / log2 / reciprocal
+ * instructions (9 per pair in the forward, 13 in the backward), and a roofline
+ * should divide by the rate this device reaches rather than a nominal count per
+ * clock.  op: 0 = ex2.approx, 1 = lg2.approx, 2 = rcp.approx.  Runs a few
+ * milliseconds of independent chains of that instruction on every SM (the
+ * fastest of three timed launches, CUDA events on `stream`, host-synchronous)
+ * and writes the instructions per second (all lanes) to *ops_per_s.  Creates
+ * two CUDA events; allocates no device memory. */
+sq_status_t sq_measure_sfu(int op, double* ops_per_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

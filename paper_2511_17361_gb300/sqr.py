@@ -105,6 +105,8 @@ def _load():
     lib.sq_query_grid_bwd.restype = ctypes.c_int
     lib.sq_query_grid_bwd.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                       _vp, ctypes.c_size_t, _vp]
+    lib.sq_measure_sfu.restype = ctypes.c_int
+    lib.sq_measure_sfu.argtypes = [ctypes.c_int, P(ctypes.c_double), _vp]
     lib.sq_profile_enable.restype = ctypes.c_int
     lib.sq_profile_enable.argtypes = [ctypes.c_int]
     lib.sq_profile_query.restype = ctypes.c_int
@@ -432,6 +434,14 @@ def count_pairs(index: Index, grid: dict, rays: Rays):
            "sq_count_pairs")
     q, s = out.tolist()
     return int(q), int(s)
+
+
+def measure_sfu(op: str) -> float:
+    """Measured SFU instructions per second on the current device for op in
+    ("ex2", "lg2", "rcp") (host-synchronous, a few milliseconds)."""
+    v = ctypes.c_double()
+    _check(lib.sq_measure_sfu({"ex2": 0, "lg2": 1, "rcp": 2}[op], ctypes.byref(v), _stream()), "sq_measure_sfu")
+    return float(v.value)
 
 
 def profile_enable(on: bool = True):
