@@ -255,7 +255,7 @@ def test_forward_heavy_voxels(sqr):
     t = synth.sample_depths(30, 0.5, 9.5)
     d, s, tf, D, S, T, _ = _fwd_pair(sqr, pr, grid, rig, t)
     check_depth(d, D, 0.5)
-    check_sem(s, S, raw_tol=2e-4)
+    check_sem(s, S)
 
 
 def test_forward_early_termination(sqr):
