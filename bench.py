@@ -286,6 +286,14 @@ def run_mine(args):
         sqr.render_bwd(prims, ix, grid, rays, gd, gs, saved=saved, out=grads, order=BWD_ORDER)
         if ev: ev[4].record()
 
+    step()
+    # the saved state sized to the pages this frame's forward needs (+2%), the
+    # buffer for every sample of every ray released before the memory peak is taken
+    pages_needed, _ = sqr.saved_header(saved)
+    saved_all_bytes = int(saved.numel())
+    saved = sqr.new_saved(rays, C, dev, pages=pages_needed + pages_needed // 50 + 16)
+    torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats(dev)
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -361,6 +369,8 @@ def run_mine(args):
     q_eval = int(visits.sum().item())
     peak_mem = int(torch.cuda.max_memory_allocated(dev))
     saved_bytes = int(saved.numel())
+    pages_after, save_status = sqr.saved_header(saved)
+    assert save_status == sqr.SQ_OK and pages_after == pages_needed, "saved-state pages changed between steps"
 
     # ---- roofline of the pair kernels (SFU-bound: MUFU ops per pair) against the
     # measured SFU rate; frac_survey is the survey's count (every in-grid sample's
@@ -428,8 +438,10 @@ def run_mine(args):
             "e2e": {"value": e2e_value, "unit": "ray-samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roof, "pair_kernels": pair_kernels, "sfu_measured_Gops": sfu, "hbm": hbm,
             "memory": {"peak_mem_bytes": peak_mem, "saved_state_bytes": saved_bytes,
+                       "saved_state_pages": pages_needed, "saved_state_bytes_every_sample": saved_all_bytes,
                        "what": "torch.cuda.max_memory_allocated over the timed and end-to-end steps: inputs, "
-                               "index, saved forward state, outputs, gradients and the library's workspaces "
+                               "index, saved forward state (sized to the pages of composited samples the "
+                               "forward needed, +2%), outputs, gradients and the library's workspaces "
                                "(all caller-owned torch tensors)"},
             "clocks": clocks}
     extras = world == 1 and not args.no_extras and args.cameras == 6 and args.index == "obb" and BWD_ORDER == 0
@@ -602,6 +614,8 @@ def batch_result(sqr, dev, kind, steps, warmup):
             sqr.render_bwd(sc.prims, sc.index, sc.grid, sc.rays, out[1], out[2], saved=sc.saved, out=sc.grads)
 
     tuning = sqr.autotune(scenes, reps=2)
+    saved_bytes = sum(sc.fit_saved() for sc in scenes)  # to the pages the tuned forward needed, +5%
+    torch.cuda.empty_cache()
 
     def batched_step():
         for sc in scenes:
@@ -649,7 +663,7 @@ def batch_result(sqr, dev, kind, steps, warmup):
             "per_scene_launches": {"ms_per_step": ms_per_scene, "value": samples / (ms_per_scene / 1e3)},
             "batched_eager": {"ms_per_step": ms_batched, "value": samples / (ms_batched / 1e3)},
             "batched_graph": {"ms_per_step": ms_graph, "value": samples / (ms_graph / 1e3)},
-            "graph_over_per_scene": ms_per_scene / ms_graph}
+            "graph_over_per_scene": ms_per_scene / ms_graph, "saved_state_bytes": saved_bytes}
 
 
 def run_batch(args):

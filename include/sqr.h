@@ -167,14 +167,27 @@ size_t sq_workspace_size(int op, const sq_prims_t* prims, const sq_grid_t* grid,
 sq_status_t sq_build_index(const sq_prims_t* prims, const sq_grid_t* grid, const sq_index_opts_t* opts,
                            sq_index_t* index, void* workspace, size_t workspace_bytes, void* stream);
 
-/* Bytes of the forward state that sq_render_fwd saves for sq_render_bwd, per
- * composited sample of every ray: (T_j, alpha_j) [R, L] FP32 pairs (the
- * transmittance before the sample; alpha_j negated where the alpha_max clamp was
- * active), s_j [R, L, CP] FP32 (Eq. 4; CP = n_classes rounded up to a multiple
- * of 4, the padding zero); then the per-ray count of composited samples [R]
- * int32.  Each block 256-byte aligned: about R * L * (CP + 2) * 4 bytes.
- * 0 on invalid rays or n_classes. */
+/* The forward state that sq_render_fwd saves for sq_render_bwd.  Only the
+ * samples a ray composites (up to its early stop) take memory: they are saved in
+ * pages of SQ_SAVE_PAGE consecutive samples of one ray, handed out as the rays
+ * advance, per sample (T_j, alpha_j) as FP32 (the transmittance before the
+ * sample; alpha_j negated where the alpha_max clamp was active) and s_j as CP FP32
+ * (Eq. 4; CP = n_classes rounded up to a multiple of 4, the padding zero).
+ * Layout of the caller's buffer (each block 256-byte aligned): a 256-byte header
+ * -- int64 at byte 0: the pages the last forward needed (written even when they
+ * did not fit), int32 at byte 8: SQ_OK or SQ_ERR_CAPACITY --; the page of every
+ * SQ_SAVE_PAGE samples of every ray [R, ceil(L / SQ_SAVE_PAGE)] int32; the
+ * per-ray count of composited samples [R] int32; then as many pages as the
+ * buffer holds.  When the pages run out the forward still writes its outputs,
+ * sets SQ_ERR_CAPACITY and the header's page count, and a backward from that
+ * state does no work (zero gradients): size the buffer again from the count
+ * (sq_saved_size_pages) and rerun the forward.
+ * sq_saved_size: the bytes for every sample of every ray (always enough).
+ * sq_saved_size_pages: the bytes for a buffer of `pages` pages.
+ * 0 on invalid rays, n_classes or pages. */
+#define SQ_SAVE_PAGE 8
 size_t sq_saved_size(const sq_rays_t* rays, int n_classes);
+size_t sq_saved_size_pages(const sq_rays_t* rays, int n_classes, long long pages);
 
 /* Sec. 3.3.2 forward pass (Eq. 2, 4-6).  Per ray r:
  *   depth[r]   = sum_j w_j t_j,                  w_j = T_j alpha_j, T_j = prod_{l<j} (1 - alpha_l)
@@ -186,8 +199,9 @@ size_t sq_saved_size(const sq_rays_t* rays, int n_classes);
  * t must be non-decreasing (the paper's uniform samples are): a ray that has
  * left the grid is not followed further.
  * Outputs: depth [R], sem [R, n_classes], t_final [R]; R = n_cam*H*W.
- * saved (nullable, sq_saved_size bytes, caller-owned device memory) receives the
- * state the backward pass needs; pass NULL for inference. */
+ * saved (nullable, caller-owned device memory of saved_bytes, at least
+ * sq_saved_size_pages(rays, C, 1)) receives the state the backward pass needs
+ * (see sq_saved_size); pass NULL for inference. */
 sq_status_t sq_render_fwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,
                           const sq_rays_t* rays, float* depth, float* sem, float* t_final, void* saved,
                           size_t saved_bytes, void* workspace, size_t workspace_bytes, void* stream);

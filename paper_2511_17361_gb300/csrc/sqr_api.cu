@@ -118,6 +118,7 @@ sq_status_t render_bwd_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_
                             size_t, const float*, const float*, float*, float*, float*, float*, float*, float*, void*,
                             size_t, cudaStream_t);
 size_t saved_size(const sq_rays_t* r, int n_classes);
+size_t saved_size_pages(const sq_rays_t* r, int n_classes, long long pages);
 sq_status_t query_grid_bwd_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, const float*, const float*,
                                 float*, float*, float*, float*, float*, float*, void*, size_t, cudaStream_t);
 sq_status_t query_grid_impl(const sq_prims_t*, const sq_index_t*, const sq_grid_t*, float, float*, float*,
@@ -321,6 +322,15 @@ size_t sq_saved_size(const sq_rays_t* rays, int n_classes) {
         return 0;
     }
     return saved_size(rays, n_classes);
+}
+
+size_t sq_saved_size_pages(const sq_rays_t* rays, int n_classes, long long pages) {
+    if (check_rays(rays) != SQ_OK) return 0;
+    if (n_classes < 1 || n_classes > SQ_MAX_CLASSES || pages < 1) {
+        set_last_error("n_classes = %d outside 1..%d or pages = %lld < 1", n_classes, SQ_MAX_CLASSES, pages);
+        return 0;
+    }
+    return saved_size_pages(rays, n_classes, pages);
 }
 
 sq_status_t sq_render_fwd(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid,

@@ -178,26 +178,35 @@ __global__ void __launch_bounds__(256) k_bwd_sweep(Batch B) {
     for (long long gr = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gr < B.total; gr += nwarp) {
         const int si = scene_of(B, gr);
         const SceneDesc& S = B.d[si];
-        if (*S.status != SQ_OK) continue;
+        if (*S.status != SQ_OK || *S.save_status != SQ_OK) continue;
         const long long r = gr - __ldg(B.off + si);
         const int L = S.L, C = S.C;
         const int Le = min(max(__ldg(S.save_n + r), 0), L);
         const float gD = __ldg(S.grad_depth + r);
         const float gsl = lane < C ? __ldg(S.grad_sem + r * C + lane) : 0.f;
         float carry = 0.f;  // U at the last sample of the chunk being processed
-        for (int jc = ((Le - 1) >> 5) << 5; Le > 0 && jc >= 0; jc -= 32) {
+        // the ray's page table: up to 32 entries held one per lane (read together
+        // with the ray's counts), longer tables read per chunk
+        const int* __restrict__ prow = S.save_page + r * S.save_np;
+        const bool reg_table = S.save_np <= 32;
+        const int pent = reg_table && lane < S.save_np ? __ldg(prow + lane) : -1;
+        for (int jc = Le > 0 ? ((Le - 1) >> 5) << 5 : 0; Le > 0 && jc >= 0; jc -= 32) {
             const int j = jc + lane;
             const bool valid = j < Le;
+            const int pidx = j / SAVE_PS;
+            int pg = __shfl_sync(0xffffffffu, pent, pidx & 31);
+            if (!reg_table) pg = valid ? __ldg(prow + pidx) : -1;
             float sa = 0.f, T = 0.f, tj = 0.f;
             float4 sc[CP / 4];
 #pragma unroll
             for (int q = 0; q < CP / 4; ++q) sc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (valid) {
-                const float2 ta = __ldg(S.save_TA + r * L + j);
+            if (valid && pg >= 0) {
+                const long long sj = (long long)pg * SAVE_PS + (j % SAVE_PS);
+                const float2 ta = __ldg(S.save_TA + sj);
                 T = ta.x;
                 sa = ta.y;
                 tj = __ldg(S.t + j);
-                const float4* sv = S.save_S + (r * L + j) * (CP / 4);
+                const float4* sv = S.save_S + sj * (CP / 4);
 #pragma unroll
                 for (int q = 0; q < CP / 4; ++q) sc[q] = __ldg(sv + q);
             }
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
             si = lo;
         }
         const SceneDesc& S = B.d[si];
-        if (*S.status != SQ_OK) continue;
+        if (*S.status != SQ_OK || *S.save_status != SQ_OK) continue;
         const long long r0 = (gb - __ldg(B.boff + si)) * RB;
         const int nr = (int)min((long long)RB, S.R - r0);
         const int C = S.C;
@@ -520,12 +529,13 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
 //   dL/dc as accumulated.  One thread per primitive.
 __global__ void k_grad_out(const float* __restrict__ gacc, const float4* __restrict__ aux,
                            const float* __restrict__ lpad, int cp, int sem_mode, int n, int C,
-                           const int* __restrict__ status, float* __restrict__ gm, float* __restrict__ gq,
-                           float* __restrict__ gs, float* __restrict__ ge, float* __restrict__ go,
-                           float* __restrict__ gl) {
+                           const int* __restrict__ status, const int* __restrict__ save_status,
+                           float* __restrict__ gm, float* __restrict__ gq, float* __restrict__ gs,
+                           float* __restrict__ ge, float* __restrict__ go, float* __restrict__ gl) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    if (*status != SQ_OK) {  // no work was done: zero gradients (the packed records may hold NaN)
+    if (*status != SQ_OK || (save_status && *save_status != SQ_OK)) {
+        // no work was done: zero gradients (the packed records may hold NaN)
         for (int i = 0; i < 3; ++i) gm[3 * k + i] = gs[3 * k + i] = 0.f;
         for (int i = 0; i < 4; ++i) gq[4 * k + i] = 0.f;
         ge[2 * k + 0] = ge[2 * k + 1] = go[k] = 0.f;
@@ -664,7 +674,7 @@ sq_status_t launch_backward(const Batch& B, int cp, const Tuning& tn, cudaStream
 sq_status_t launch_grad_out(const SceneDesc& S, float* gm, float* gq, float* gs, float* ge, float* go, float* gl,
                             cudaStream_t st) {
     if (S.n == 0) return SQ_OK;
-    SQ_LAUNCH("k_grad_out", st, k_grad_out<<<(S.n + 127) / 128, 128, 0, st>>>(S.gacc, S.aux, S.lpad, S.cp, S.sem_mode, S.n, S.C, S.status, gm, gq, gs, ge, go, gl));
+    SQ_LAUNCH("k_grad_out", st, k_grad_out<<<(S.n + 127) / 128, 128, 0, st>>>(S.gacc, S.aux, S.lpad, S.cp, S.sem_mode, S.n, S.C, S.status, S.save_status, gm, gq, gs, ge, go, gl));
     return SQ_OK;
 }
 

@@ -163,7 +163,8 @@ __global__ void k_pm_rects(Batch B, PmArgs A) {
     const int4 b = __ldg(S.boxes + k);
     const int lo[3] = {b.x & 0xffff, b.y & 0xffff, b.z & 0xffff};
     const int hi[3] = {(int)((unsigned)b.x >> 16), (int)((unsigned)b.y >> 16), (int)((unsigned)b.z >> 16)};
-    const bool ok = *S.status == SQ_OK && lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2];
+    const bool ok = *S.status == SQ_OK && *S.save_status == SQ_OK && lo[0] <= hi[0] && lo[1] <= hi[1] &&
+                    lo[2] <= hi[2];
     float bl[3], bh[3];
     for (int a = 0; a < 3; ++a) {
         bl[a] = S.g.lo[a] + (float)lo[a] * S.g.vs[a];

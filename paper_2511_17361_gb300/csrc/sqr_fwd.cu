@@ -9,7 +9,9 @@
 // Rays of all scenes of the batch are handed out by one global counter, so a
 // lane group whose ray ends early takes the next ray, from whichever scene.
 // For the backward the forward saves, per composited sample, T_j, alpha_j (sign
-// marking the clamp) and s_j, and per ray the number of composited samples.
+// marking the clamp) and s_j, in pages of SAVE_PS samples handed out as rays
+// advance (only composited chunks take memory), and per ray the number of
+// composited samples.
 #include <limits.h>
 
 #include "sqr_render.cuh"
@@ -58,6 +60,7 @@ __device__ __forceinline__ float group_composite(float alpha, int s, int gbase, 
 
 template <int CP, int GS>
 __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
+    static_assert(GS % SAVE_PS == 0 || SAVE_PS % GS == 0, "chunks and pages of the saved state nest");
     const int lane = threadIdx.x & 31;
     const int s = lane & (GS - 1), gbase = lane & ~(GS - 1);
     const unsigned gmask = (GS == 32) ? 0xffffffffu : ((1u << GS) - 1u);
@@ -78,6 +81,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
     if (live) scene_ray(B.d[si], r, o, d);
     float T = 1.f, Dp = 0.f;
     int j0 = 0, used_total = 0;
+    int last_pg = -1;  // the ray's most recent page of saved state (the same in the lane group)
     bool seen_inside = false;
     float acc[CP];
 #pragma unroll
@@ -92,6 +96,24 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
         const int* __restrict__ v_sq = S.v_sq;
         const int j = j0 + s;
         const bool valid = live && j < L;
+        // Pages of the saved state for this chunk: the counter update is issued here
+        // and its result read after the list walk, which hides its latency.  In a
+        // launch over one scene the groups' requests (0, 1 or 2 pages each) are
+        // combined into one update per warp by ballots; over several scenes each
+        // group asks its own buffer's counter.
+        const int fp = (j0 + SAVE_PS - 1) / SAVE_PS;  // the pages that start in this chunk: fp .. fp + cntg - 1
+        const int cntg = (live && S.save_TA != nullptr) ? max(0, (min(j0 + GS, L) - 1) / SAVE_PS - fp + 1) : 0;
+        const int cnt = s == 0 ? cntg : 0;
+        static_assert(GS <= 2 * SAVE_PS, "at most two pages per chunk");
+        const unsigned b1 = __ballot_sync(0xffffffffu, cnt >= 1), b2 = __ballot_sync(0xffffffffu, cnt >= 2);
+        const unsigned lt = (1u << lane) - 1u;
+        const int before = __popc(b1 & lt) + __popc(b2 & lt);  // pages of the lower groups
+        unsigned long long pbase = 0;
+        if (B.n == 1) {
+            if (lane == 0 && b1 != 0u) pbase = atomicAdd(S.save_ctr, (unsigned long long)(__popc(b1) + __popc(b2)));
+        } else if (cnt > 0) {
+            pbase = atomicAdd(S.save_ctr, (unsigned long long)cnt);
+        }
         float x[3] = {0.f, 0.f, 0.f};
         int vox = -1;
         float tj = 0.f;
@@ -158,9 +180,29 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
         int used;
         bool stop;
         const float w = group_composite<GS>(alpha, s, gbase, S.kappa, T, Tb, valid, used, stop);
+        // the chunk's pages: the group's first page, a page table entry per page; a
+        // group past the buffer's capacity marks the overflow and saves nothing (its
+        // rays' backward then does no work)
+        int pg;
+        {
+            const unsigned long long wb = __shfl_sync(0xffffffffu, pbase, 0);
+            int first = -1;
+            if (cnt > 0) {
+                const long long f = B.n == 1 ? (long long)wb + before : (long long)pbase;
+                const bool fits = f + cnt <= S.save_cap;
+                if (!fits) atomicExch(S.save_status, (int)SQ_ERR_CAPACITY);
+                for (int i = 0; i < cnt; ++i) S.save_page[r * S.save_np + fp + i] = fits ? (int)(f + i) : -1;
+                first = fits ? (int)f : -1;
+            }
+            first = __shfl_sync(0xffffffffu, first, gbase);
+            // a sample in a page begun by an earlier chunk goes to the ray's last page
+            const int pi = j / SAVE_PS;
+            pg = pi >= fp ? (first >= 0 ? first + (pi - fp) : -1) : last_pg;
+            if (cntg > 0) last_pg = first >= 0 ? first + cntg - 1 : -1;
+        }
         if (valid) {
-            if (s < used && S.save_TA) {
-                const long long sj = r * L + j;
+            if (s < used && pg >= 0) {
+                const long long sj = (long long)pg * SAVE_PS + (j % SAVE_PS);
                 S.save_TA[sj] = make_float2(Tb, asum > S.alpha_max ? -alpha : alpha);
                 float4* sv = S.save_S + sj * (CP / 4);
 #pragma unroll
@@ -213,6 +255,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
                 Dp = 0.f;
                 j0 = 0;
                 used_total = 0;
+                last_pg = -1;
                 seen_inside = false;
 #pragma unroll
                 for (int c = 0; c < CP; ++c) acc[c] = 0.f;

@@ -192,22 +192,56 @@ size_t batch_ws_size(const sq_scene_t* sc, int n, bool bwd) {
     return at;
 }
 
-// Saved forward state: (T, signed alpha) [R, L] float2, s [R, L, CP] float
-// (CP = C rounded up to 4, zero-padded), then n [R] int32.
-size_t saved_bytes_of(const sq_rays_t* r, int C) {
-    const size_t R = (size_t)r->n_cam * r->H * r->W, RL = R * (size_t)r->L;
-    return align_up(RL * sizeof(float2), 256) + align_up(RL * (size_t)cpad(C) * sizeof(float), 256) +
-           align_up(R * sizeof(int), 256);
+// Saved forward state (sq_saved_size): a 256-byte header (int64 pages needed,
+// int32 status), the page of every SAVE_PS samples of every ray [R, ceil(L /
+// SAVE_PS)] int32, the composited count [R] int32, then cap pages of SAVE_PS
+// samples: (T, signed alpha) float2 each, and s [CP] float each (CP = C rounded
+// up to 4, zero-padded).  Each block 256-byte aligned.
+constexpr size_t SAVE_HDR = 256;
+
+size_t saved_fixed_bytes(const sq_rays_t* r) {
+    const size_t R = (size_t)r->n_cam * r->H * r->W, np = ((size_t)r->L + SAVE_PS - 1) / SAVE_PS;
+    return SAVE_HDR + align_up(R * np * sizeof(int), 256) + align_up(R * sizeof(int), 256);
 }
 
-void saved_ptrs(const sq_rays_t* r, int C, void* saved, SceneDesc& D) {
-    const size_t R = (size_t)r->n_cam * r->H * r->W, RL = R * (size_t)r->L;
+size_t saved_bytes_pages(const sq_rays_t* r, int C, long long pages) {
+    const size_t ns = (size_t)(pages > 0 ? pages : 0) * SAVE_PS;
+    return saved_fixed_bytes(r) + align_up(ns * sizeof(float2), 256) + align_up(ns * (size_t)cpad(C) * sizeof(float), 256);
+}
+
+// Pages that every sample of every ray needs at most.
+long long saved_pages_max(const sq_rays_t* r) {
+    return (long long)r->n_cam * r->H * r->W * (((long long)r->L + SAVE_PS - 1) / SAVE_PS);
+}
+
+size_t saved_bytes_of(const sq_rays_t* r, int C) { return saved_bytes_pages(r, C, saved_pages_max(r)); }
+
+// Pages a buffer of `bytes` holds (0 if it cannot hold the fixed blocks).
+long long saved_cap_of(const sq_rays_t* r, int C, size_t bytes) {
+    const size_t fixed = saved_fixed_bytes(r);
+    if (bytes <= fixed) return 0;
+    const size_t per = SAVE_PS * (sizeof(float2) + (size_t)cpad(C) * sizeof(float));
+    long long cap = (long long)((bytes - fixed) / per);  // the two blocks' alignment takes at most 510 bytes
+    while (cap > 0 && saved_bytes_pages(r, C, cap) > bytes) --cap;
+    return cap;
+}
+
+void saved_ptrs(const sq_rays_t* r, int C, void* saved, size_t bytes, SceneDesc& D) {
+    const size_t R = (size_t)r->n_cam * r->H * r->W, np = ((size_t)r->L + SAVE_PS - 1) / SAVE_PS;
+    const long long cap = saved_cap_of(r, C, bytes);
     char* p = (char*)saved;
-    D.save_TA = (float2*)p;
-    p += align_up(RL * sizeof(float2), 256);
-    D.save_S = (float4*)p;
-    p += align_up(RL * (size_t)cpad(C) * sizeof(float), 256);
+    D.save_ctr = (unsigned long long*)p;
+    D.save_status = (int*)(p + 8);
+    p += SAVE_HDR;
+    D.save_page = (int*)p;
+    p += align_up(R * np * sizeof(int), 256);
     D.save_n = (int*)p;
+    p += align_up(R * sizeof(int), 256);
+    D.save_TA = (float2*)p;
+    p += align_up((size_t)cap * SAVE_PS * sizeof(float2), 256);
+    D.save_S = (float4*)p;
+    D.save_cap = cap;
+    D.save_np = (int)np;
 }
 
 Tuning default_tuning() { return Tuning{4, 8, 0, SQ_BWD_PRIMITIVE_MAJOR}; }
@@ -228,6 +262,10 @@ sq_status_t launch_pack(const sq_prims_t* prims, float4* rec, float4* aux, float
 }
 
 size_t saved_size(const sq_rays_t* r, int n_classes) { return saved_bytes_of(r, n_classes); }
+
+size_t saved_size_pages(const sq_rays_t* r, int n_classes, long long pages) {
+    return saved_bytes_pages(r, n_classes, pages);
+}
 
 size_t batched_workspace_size(const sq_scene_t* scenes, int n) {
     bool train = n > 0;
@@ -283,14 +321,14 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
             set_last_error("scene %d: depth/sem output is NULL", i);
             return SQ_ERR_INVALID_ARG;
         }
-        const size_t sneed = saved_bytes_of(&s.rays, C);
+        const size_t sneed = saved_bytes_pages(&s.rays, C, 1);  // the fixed blocks and one page
         if (op == SQ_OP_FWD && s.saved && s.saved_bytes < sneed) {
-            set_last_error("scene %d: saved state of %zu bytes given, %zu needed", i, s.saved_bytes, sneed);
+            set_last_error("scene %d: saved state of %zu bytes given, at least %zu needed", i, s.saved_bytes, sneed);
             return SQ_ERR_INVALID_ARG;
         }
         if (op == SQ_OP_BWD) {
             if (!s.saved || s.saved_bytes < sneed) {
-                set_last_error("scene %d: backward needs the saved forward state (%zu bytes given, %zu needed)", i,
+                set_last_error("scene %d: backward needs the saved forward state (%zu bytes given, at least %zu)", i,
                                s.saved_bytes, sneed);
                 return SQ_ERR_INVALID_ARG;
             }
@@ -338,7 +376,13 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
         D.depth = s.depth;
         D.sem = s.sem;
         D.t_final = s.t_final;
-        if (s.saved) saved_ptrs(&s.rays, C, s.saved, D);
+        if (s.saved) {
+            saved_ptrs(&s.rays, C, s.saved, s.saved_bytes, D);
+            if (op == SQ_OP_FWD) {  // page counter and status start at zero
+                cudaError_t e = cudaMemsetAsync(s.saved, 0, 16, st);
+                if (e != cudaSuccess) return cuda_status(e, "memset saved header");
+            }
+        }
         D.grad_depth = s.grad_depth;
         D.grad_sem = s.grad_sem;
         D.pair_visits = s.pair_visits;

@@ -9,6 +9,7 @@
 namespace sqr {
 
 constexpr int MAX_BATCH = 32;  // scenes per launch (= SQ_MAX_BATCH)
+constexpr int SAVE_PS = SQ_SAVE_PAGE;  // samples per page of the saved forward state
 constexpr int GF = 48;         // floats per primitive in the gradient accumulator (12 partials + up to 32 classes)
 constexpr int NRAW = 12;       // summed partials: gx 3, tau 3, u df/du 3, eps 2, sigma 1
 constexpr int MAX_WARPS = 8;   // warps per CTA accepted by the render kernels
@@ -38,9 +39,16 @@ struct SceneDesc {
     float* depth;        // forward outputs
     float* sem;
     float* t_final;
-    float2* save_TA;     // [R, L] saved (T_j before the sample, alpha_j negated where clamped); nullable
-    float4* save_S;      // [R, L, CP/4] saved semantic vector s_j of each sample, zero-padded to CP
+    // Saved forward state, in pages of SAVE_PS consecutive samples of one ray handed
+    // out on demand, so that only the composited samples take memory:
+    float2* save_TA;     // [cap * SAVE_PS] (T_j before the sample, alpha_j negated where clamped); nullable
+    float4* save_S;      // [cap * SAVE_PS, CP/4] semantic vector s_j of each sample, zero-padded to CP
     int* save_n;         // [R] samples composited
+    int* save_page;      // [R, save_np] page of samples SAVE_PS*i .. SAVE_PS*i+SAVE_PS-1 of each ray
+    unsigned long long* save_ctr;  // pages handed out (the pages the forward needed, even past cap)
+    int* save_status;    // SQ_OK, or SQ_ERR_CAPACITY once a page request found no room
+    long long save_cap;  // pages the buffer holds
+    int save_np;         // pages per ray, ceil(L / SAVE_PS)
     float2* gw;          // [R, L] backward: (dL/dalpha_j, w_j) from the sweep
     const float* grad_depth;  // backward inputs
     const float* grad_sem;

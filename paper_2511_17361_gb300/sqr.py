@@ -80,6 +80,8 @@ def _load():
     lib.sq_build_index.argtypes = [P(SqPrims), P(SqGrid), P(SqIndexOpts), P(SqIndex), _vp, ctypes.c_size_t, _vp]
     lib.sq_saved_size.restype = ctypes.c_size_t
     lib.sq_saved_size.argtypes = [P(SqRays), ctypes.c_int]
+    lib.sq_saved_size_pages.restype = ctypes.c_size_t
+    lib.sq_saved_size_pages.argtypes = [P(SqRays), ctypes.c_int, ctypes.c_longlong]
     lib.sq_render_fwd.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), P(SqRays), _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                   _vp, ctypes.c_size_t, _vp]
     lib.sq_render_bwd.argtypes = [P(SqPrims), P(SqIndex), P(SqGrid), P(SqRays), _vp, ctypes.c_size_t, _vp, _vp, _vp,
@@ -279,11 +281,18 @@ def build_index(prims: dict, grid: dict, mode: int = SQ_INDEX_OBB, tau_cut: floa
 
 
 # ------------------------------------------------------------------ render
-def saved_size(rays: Rays, n_classes: int) -> int:
-    """Bytes of forward state the backward pass needs (T_j, alpha_j and s_j per
-    sample, samples per ray)."""
+SQ_SAVE_PAGE = 8
+
+
+def saved_size(rays: Rays, n_classes: int, pages: int | None = None) -> int:
+    """Bytes of the forward state the backward pass needs: T_j, alpha_j and s_j of
+    the composited samples, in pages of SQ_SAVE_PAGE samples.  ``pages`` None: room
+    for every sample of every ray (always enough); else room for that many pages."""
     r = rays.struct()
-    n = int(lib.sq_saved_size(ctypes.byref(r), int(n_classes)))
+    if pages is None:
+        n = int(lib.sq_saved_size(ctypes.byref(r), int(n_classes)))
+    else:
+        n = int(lib.sq_saved_size_pages(ctypes.byref(r), int(n_classes), max(int(pages), 1)))
     if n == 0 and rays.R > 0:
         raise ValueError(f"sq_saved_size: {lib.sq_last_error().decode()}")
     return n
@@ -309,16 +318,26 @@ def render_fwd(prims: dict, index: Index, grid: dict, rays: Rays, out=None, save
     return depth, sem, tf
 
 
-def new_saved(rays: Rays, n_classes: int, device="cuda"):
-    return torch.empty(saved_size(rays, n_classes), dtype=torch.uint8, device=device)
+def new_saved(rays: Rays, n_classes: int, device="cuda", pages: int | None = None):
+    """A saved-state buffer: room for every sample (pages None) or for ``pages``
+    pages (after a forward, saved_header gives the pages it needed)."""
+    return torch.empty(saved_size(rays, n_classes, pages), dtype=torch.uint8, device=device)
+
+
+def saved_header(saved):
+    """(pages the last forward needed, status SQ_OK or SQ_ERR_CAPACITY); waits
+    for the stream."""
+    h = saved[:16].cpu()
+    return int(h[:8].view(torch.int64).item()), int(h[8:12].view(torch.int32).item())
 
 
 def saved_counts(saved, rays: Rays, n_classes: int):
-    """The per-ray composited sample counts [R] int32 held at the end of a saved
-    forward state (layout as sq_saved_size documents)."""
-    R, L, cp = rays.R, rays.t.numel(), (int(n_classes) + 3) // 4 * 4
+    """The per-ray composited sample counts [R] int32 of a saved forward state
+    (its third block, layout as sq_saved_size documents)."""
+    R, L = rays.R, rays.t.numel()
+    npr = (L + SQ_SAVE_PAGE - 1) // SQ_SAVE_PAGE
     a256 = lambda b: (b + 255) // 256 * 256
-    off = a256(R * L * 8) + a256(R * L * cp * 4)
+    off = 256 + a256(R * npr * 4)
     return saved[off:off + R * 4].view(torch.int32)
 
 
@@ -458,29 +477,44 @@ def profile_query(name: str | None = None):
     return int(n.value), float(ms.value), int(dropped.value)
 
 
+# Pages of saved state to reserve per (rays, samples, classes): learnt from the
+# forwards so far (the first forward of a shape reserves every sample).
+_SAVED_PAGES: dict = {}
+
+
 class SQRender(torch.autograd.Function):
     """(means, quats, scales, eps, opacity, logits) -> (depth [R], sem [R, C]).
 
     The index and rays are constants of the call; the backward runs
-    sq_render_bwd with the incoming cotangents."""
+    sq_render_bwd with the incoming cotangents.  The saved state is sized from
+    the pages earlier forwards of the same shape needed (plus 5%); the backward
+    reads the page count (one wait for the stream), remembers it, and if the
+    pages ran out re-runs the forward into a large enough buffer first."""
 
     @staticmethod
     def forward(ctx, means, quats, scales, eps, opacity, logits, index: Index, grid: dict, rays: Rays):
         prims = dict(zip(PRIM_KEYS, (t.contiguous() for t in (means, quats, scales, eps, opacity, logits))))
-        saved = new_saved(rays, logits.shape[1], means.device)
+        key = (rays.R, rays.t.numel(), logits.shape[1])
+        saved = new_saved(rays, logits.shape[1], means.device, _SAVED_PAGES.get(key))
         depth, sem, _ = render_fwd(prims, index, grid, rays, saved=saved)
         ctx.save_for_backward(*[prims[k] for k in PRIM_KEYS], saved)
-        ctx.index, ctx.grid, ctx.rays = index, grid, rays
+        ctx.index, ctx.grid, ctx.rays, ctx.key = index, grid, rays, key
         return depth, sem
 
     @staticmethod
     def backward(ctx, g_depth, g_sem):
         prims = dict(zip(PRIM_KEYS, ctx.saved_tensors[:6]))
         saved = ctx.saved_tensors[6]
+        C = prims["logits"].shape[1]
         if g_depth is None:
             g_depth = torch.zeros(ctx.rays.R, device=prims["means"].device)
         if g_sem is None:
-            g_sem = torch.zeros((ctx.rays.R, prims["logits"].shape[1]), device=prims["means"].device)
+            g_sem = torch.zeros((ctx.rays.R, C), device=prims["means"].device)
+        needed, status = saved_header(saved)
+        _SAVED_PAGES[ctx.key] = max(_SAVED_PAGES.get(ctx.key, 0), needed + needed // 20 + 16)
+        if status != SQ_OK:  # the pages ran out: the forward again into a buffer that holds them
+            saved = new_saved(ctx.rays, C, prims["means"].device, _SAVED_PAGES[ctx.key])
+            render_fwd(prims, ctx.index, ctx.grid, ctx.rays, saved=saved)
         g = render_bwd(prims, ctx.index, ctx.grid, ctx.rays, g_depth, g_sem, saved=saved)
         return (g["means"], g["quats"], g["scales"], g["eps"], g["opacity"], g["logits"], None, None, None)
 
@@ -508,9 +542,17 @@ class Scene:
         self.sem = torch.empty((R, C), device=device)
         self.t_final = torch.empty(R, device=device)
         self.saved = new_saved(rays, C, device) if training else None
+        self.C = C
         self.grad_depth = torch.zeros(R, device=device) if training else None
         self.grad_sem = torch.zeros((R, C), device=device) if training else None
         self.grads = {k: torch.empty_like(prims[k]) for k in PRIM_KEYS} if training else None
+
+    def fit_saved(self, slack: float = 0.05):
+        """Shrinks the saved-state buffer to the pages the last forward needed plus
+        ``slack`` (waits for the stream); returns its bytes."""
+        needed, _ = saved_header(self.saved)
+        self.saved = new_saved(self.rays, self.C, self.saved.device, int(needed * (1 + slack)) + 16)
+        return self.saved.numel()
 
     def struct(self) -> SqScene:
         sc = SqScene()

@@ -59,3 +59,19 @@ def test_oracle_is_not_imported_by_the_product_package():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src and "sqr_oracle" not in src, f
+
+
+def test_saved_state_sizes_without_gpu():
+    """sq_saved_size is the paged size of every sample's page; sizes grow with the
+    page count; invalid page counts give 0 (host arithmetic only)."""
+    from paper_2511_17361_gb300 import sqr
+    dummy = (ctypes.c_float * 16)()
+    p = ctypes.cast(dummy, ctypes.c_void_p)
+    for (nc, H, W, L, C) in [(1, 1, 1, 40, 5), (6, 225, 400, 100, 18), (2, 3, 5, 7, 32)]:
+        r = sqr.SqRays(nc, H, W, p, p, p, L, 0.0, 1.0)
+        pages = nc * H * W * ((L + sqr.SQ_SAVE_PAGE - 1) // sqr.SQ_SAVE_PAGE)
+        full = sqr.lib.sq_saved_size(ctypes.byref(r), C)
+        assert full == sqr.lib.sq_saved_size_pages(ctypes.byref(r), C, pages)
+        sizes = [sqr.lib.sq_saved_size_pages(ctypes.byref(r), C, q) for q in (1, 2, pages // 2 + 1, pages)]
+        assert all(a <= b for a, b in zip(sizes, sizes[1:])) and sizes[0] > 0
+        assert sqr.lib.sq_saved_size_pages(ctypes.byref(r), C, 0) == 0
