@@ -152,7 +152,9 @@ typedef struct {
 } sq_rays_t;
 
 /* Bytes of workspace an entry point needs (op = SQ_OP_*); rays may be NULL for
- * SQ_OP_INDEX, SQ_OP_FWD and SQ_OP_QUERY.  SQ_OP_BWD needs rays: besides the
+ * SQ_OP_INDEX, SQ_OP_FWD and SQ_OP_QUERY.  SQ_OP_QUERY needs the grid (the query
+ * backward keeps the cotangent row of every voxel, padded to a multiple of 4
+ * classes).  SQ_OP_BWD needs rays: besides the
  * per-primitive records it holds 8 bytes per sample of every ray (dL/dalpha_j
  * and w_j from the back-to-front sweep), 16 bytes per ray and per primitive and
  * camera, and up to 64 tile sums of 192 bytes and 64 queue entries per primitive

@@ -109,6 +109,7 @@ sq_status_t check_rays(const sq_rays_t* r) {
 
 size_t index_workspace_size(const sq_grid_t* g);
 size_t render_workspace_size(const sq_prims_t* p);
+size_t query_workspace_size(const sq_prims_t* p, const sq_grid_t* g);
 size_t render_bwd_workspace_size(const sq_prims_t* p, const sq_rays_t* r);
 sq_status_t build_index_impl(const sq_prims_t*, const sq_grid_t*, const sq_index_opts_t*, sq_index_t*, void*, size_t,
                              cudaStream_t);
@@ -283,9 +284,11 @@ size_t sq_workspace_size(int op, const sq_prims_t* prims, const sq_grid_t* grid,
             if (check_grid(grid) != SQ_OK) return 0;
             return index_workspace_size(grid);
         case SQ_OP_FWD:
-        case SQ_OP_QUERY:
             if (check_prims(prims) != SQ_OK) return 0;
             return render_workspace_size(prims);
+        case SQ_OP_QUERY:
+            if (check_prims(prims) != SQ_OK || check_grid(grid) != SQ_OK) return 0;
+            return query_workspace_size(prims, grid);
         case SQ_OP_BWD:
             if (check_prims(prims) != SQ_OK || check_rays(rays) != SQ_OK) return 0;
             return render_bwd_workspace_size(prims, rays);

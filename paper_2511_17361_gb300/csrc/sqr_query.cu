@@ -3,16 +3,18 @@
 // sum s = sum p_o c_k; label = argmax_c s (lowest index on ties) when density >= tau,
 // otherwise "free" (= C).
 //
-// One thread per voxel (voxel ids are z-fastest, so a warp covers neighbouring
-// voxels with near-identical lists and the primitive gathers hit L1).  The
-// per-voxel semantic row is staged in shared memory so that the [nvox, C] output
-// is written with coalesced stores.
+// One lane per voxel; groups of Q_GROUP lanes (voxel ids are z-fastest, so the
+// group's voxels are neighbours with near-identical lists) walk their lists
+// together so that each record is loaded once per group.  The per-voxel semantic
+// row is staged in shared memory so that the [nvox, C] output is written with
+// coalesced stores.
 //
 // The backward (gradients of a loss on density and semantics) is primitive-major:
 // primitive k is listed in exactly the voxels of its range, so a warp walks one
 // of QB_SPLIT equal chunks of that range, sums dL/dp_o dp_o/dtheta over it in
 // registers and adds its sums to the primitive's row once (one coalesced atomic
 // add per chunk); k_grad_out converts the rows.
+#include <limits.h>
 #include <string.h>
 
 #include "sqr_pair.cuh"
@@ -23,6 +25,7 @@ namespace sqr {
 namespace {
 
 constexpr int Q_THREADS = 128;
+constexpr int Q_GROUP = 16;  // voxels (lanes) that walk their lists together (4 and 8 measured 2% slower)
 
 struct QueryArgs {
     const float4* rec;
@@ -40,7 +43,20 @@ struct QueryArgs {
     unsigned char* label;
 };
 
-template <int CP>
+// Smallest id over a lane group of GQ lanes.
+template <int GQ>
+__device__ __forceinline__ int group_min(int k) {
+#pragma unroll
+    for (int o = GQ / 2; o > 0; o >>= 1) k = min(k, __shfl_xor_sync(0xffffffffu, k, o, GQ));
+    return k;
+}
+
+// A group of GQ lanes (GQ consecutive voxels, z-fastest: neighbours whose lists
+// are nearly the same) walks the union of its sorted lists in ascending id: each
+// step loads one record and class row for the whole group (the next step's record
+// one step ahead) and the lanes whose list holds the id add its term.  Every voxel
+// still sums its own list in ascending id order.
+template <int CP, int GQ>
 __global__ void __launch_bounds__(Q_THREADS) k_query(QueryArgs a) {
     __shared__ float rows[Q_THREADS * (CP + 1)];
     if (*a.status != SQ_OK) return;
@@ -51,32 +67,53 @@ __global__ void __launch_bounds__(Q_THREADS) k_query(QueryArgs a) {
         float acc[CP];
 #pragma unroll
         for (int c = 0; c < CP; ++c) acc[c] = 0.f;
+        float dens = 0.f, x[3] = {0.f, 0.f, 0.f};
+        int n = 0, f = 0;
         if (v < a.nvox) {
             const int iz = (int)(v % nz);
             const int iy = (int)((v / nz) % ny);
             const int ix = (int)(v / ((long long)ny * nz));
             const int id[3] = {ix, iy, iz};
-            float x[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i)
                 x[i] = __fadd_rn(a.g.lo[i], __fmul_rn(__fadd_rn(__int2float_rn(id[i]), 0.5f), a.g.vs[i]));
-            const int n = __ldg(a.v_n + v), f = __ldg(a.v_f + v);
-            float dens = 0.f;
-            for (int e = 0; e < n; ++e) {
-                const int k = __ldg(a.v_sq + f + e);
-                Prim p = load_prim(a.rec, k);
-                const float po = occupancy(p, x);
-                dens = fmaf(po, p.sigma, dens);
-                const float4* cr = lp4 + (size_t)k * (CP / 4);
+            n = __ldg(a.v_n + v);
+            f = __ldg(a.v_f + v);
+        }
+        int e = 0;
+        int head = n > 0 ? __ldg(a.v_sq + f) : INT_MAX;
+        int head2 = n > 1 ? __ldg(a.v_sq + f + 1) : INT_MAX;
+        int kmin = group_min<GQ>(head);
+        Prim p;
+        if (kmin != INT_MAX) p = load_prim(a.rec, kmin);
+        while (__any_sync(0xffffffffu, kmin != INT_MAX)) {
+            const int knext = group_min<GQ>(head == kmin ? head2 : head);
+            Prim pn;
+            if (knext != INT_MAX) pn = load_prim(a.rec, knext);
+            if (kmin != INT_MAX) {
+                const float4* cr = lp4 + (size_t)kmin * (CP / 4);
+                float4 cv[CP / 4];
 #pragma unroll
-                for (int q = 0; q < CP / 4; ++q) {
-                    float4 cv = __ldg(cr + q);
-                    acc[4 * q + 0] = fmaf(po, cv.x, acc[4 * q + 0]);
-                    acc[4 * q + 1] = fmaf(po, cv.y, acc[4 * q + 1]);
-                    acc[4 * q + 2] = fmaf(po, cv.z, acc[4 * q + 2]);
-                    acc[4 * q + 3] = fmaf(po, cv.w, acc[4 * q + 3]);
+                for (int q = 0; q < CP / 4; ++q) cv[q] = __ldg(cr + q);
+                if (head == kmin) {
+                    const float po = occupancy(p, x);
+                    dens = fmaf(po, p.sigma, dens);
+#pragma unroll
+                    for (int q = 0; q < CP / 4; ++q) {
+                        acc[4 * q + 0] = fmaf(po, cv[q].x, acc[4 * q + 0]);
+                        acc[4 * q + 1] = fmaf(po, cv[q].y, acc[4 * q + 1]);
+                        acc[4 * q + 2] = fmaf(po, cv[q].z, acc[4 * q + 2]);
+                        acc[4 * q + 3] = fmaf(po, cv[q].w, acc[4 * q + 3]);
+                    }
+                    ++e;
+                    head = head2;
+                    head2 = e + 1 < n ? __ldg(a.v_sq + f + e + 1) : INT_MAX;
                 }
             }
+            kmin = knext;
+            p = pn;
+        }
+        if (v < a.nvox) {
             a.density[v] = dens;
             if (a.label) {
                 int best = 0;
@@ -96,9 +133,9 @@ __global__ void __launch_bounds__(Q_THREADS) k_query(QueryArgs a) {
         const long long nrow = (a.nvox - base) < Q_THREADS ? (a.nvox - base) : Q_THREADS;
         const long long total = nrow * a.C;
         float* out = a.sem + base * a.C;
-        for (long long e = threadIdx.x; e < total; e += Q_THREADS) {
-            const int row = (int)(e / a.C), c = (int)(e - (long long)row * a.C);
-            out[e] = rows[row * (CP + 1) + c];
+        for (long long e2 = threadIdx.x; e2 < total; e2 += Q_THREADS) {
+            const int row = (int)(e2 / a.C), c = (int)(e2 - (long long)row * a.C);
+            out[e2] = rows[row * (CP + 1) + c];
         }
         __syncthreads();
     }
@@ -116,10 +153,24 @@ struct QueryBwdArgs {
     GridC g;
     int n, C;
     const float* grad_density;
-    const float* grad_sem;
+    const float4* gsp;  // [nvox, CP/4] grad_sem rows zero-padded to CP classes
     float* gacc;  // [n, GF] raw sums, zeroed
     int* ctr;     // zeroed work counter over (primitive, chunk)
 };
+
+// grad_sem [V, C] copied to rows of CP classes (zero padding), one thread per
+// (voxel, group of four classes), so that a pair reads its voxel's row with CP / 4
+// vector loads.
+__global__ void k_pad_rows(const float* __restrict__ in, long long rows, int C, int cp4, float4* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cp4) return;
+    const long long r = i / cp4;
+    const int q = (int)(i - r * cp4);
+    float v[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = 4 * q + c < C ? __ldg(in + r * C + 4 * q + c) : 0.f;
+    out[i] = make_float4(v[0], v[1], v[2], v[3]);
+}
 
 // One warp per (primitive, chunk of its range), drawn from a counter: over the
 // voxels v of the chunk, dL/dp_o = gd[v] sigma + <gs[v], c>; the row gets the 11
@@ -174,11 +225,17 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_bwd(QueryBwdArgs a) {
                 const float gd = __ldg(a.grad_density + v);
                 float gs[CP];
                 float cd = 0.f;
+                const float4* gr = a.gsp + v * (CP / 4);
 #pragma unroll
-                for (int c = 0; c < CP; ++c) {
-                    gs[c] = c < a.C ? __ldg(a.grad_sem + v * a.C + c) : 0.f;
-                    cd = fmaf(gs[c], cl[c], cd);
+                for (int q = 0; q < CP / 4; ++q) {
+                    const float4 g4 = __ldg(gr + q);
+                    gs[4 * q] = g4.x;
+                    gs[4 * q + 1] = g4.y;
+                    gs[4 * q + 2] = g4.z;
+                    gs[4 * q + 3] = g4.w;
                 }
+#pragma unroll
+                for (int c = 0; c < CP; ++c) cd = fmaf(gs[c], cl[c], cd);
                 float pr[11];
                 const float po = occupancy_partials(P, x, pr);
                 if (po != 0.f) {
@@ -217,12 +274,20 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_bwd(QueryBwdArgs a) {
 
 size_t render_workspace_size(const sq_prims_t* p);
 
+// The grid query's workspace: the render workspace's per-primitive blocks (records,
+// padded logits, accumulator, a counter: the backward's layout stays inside it),
+// then for the backward the cotangent rows of every voxel padded to CP classes.
+size_t query_workspace_size(const sq_prims_t* p, const sq_grid_t* g) {
+    const long long nvox = (long long)g->nx * g->ny * g->nz;
+    return align_up(render_workspace_size(p), 256) + align_up((size_t)nvox * cpad(p->n_classes) * sizeof(float), 256);
+}
+
 template <int CP>
 static sq_status_t launch_query_cp(const QueryArgs& a, cudaStream_t st) {
     long long want = (a.nvox + Q_THREADS - 1) / Q_THREADS;
     int blocks = (int)(want < 152LL * 64 ? want : 152LL * 64);
     if (blocks < 1) blocks = 1;
-    SQ_LAUNCH("k_query", st, k_query<CP><<<blocks, Q_THREADS, 0, st>>>(a));
+    SQ_LAUNCH("k_query", st, k_query<CP, Q_GROUP><<<blocks, Q_THREADS, 0, st>>>(a));
     return SQ_OK;
 }
 
@@ -287,7 +352,7 @@ sq_status_t query_grid_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, 
                                 const float* grad_density, const float* grad_sem, float* g_means, float* g_quats,
                                 float* g_scales, float* g_eps, float* g_opacity, float* g_logits, void* ws,
                                 size_t ws_bytes, cudaStream_t st) {
-    const size_t need = render_workspace_size(prims);
+    const size_t need = query_workspace_size(prims, grid);
     if (ws == nullptr || ws_bytes < need) {
         set_last_error("sq_query_grid_bwd: workspace of %zu bytes given, %zu needed", ws_bytes, need);
         return SQ_ERR_INVALID_ARG;
@@ -305,8 +370,14 @@ sq_status_t query_grid_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, 
     float* gacc = (float*)(base + at);
     at = align_up(at + (size_t)n * GF * sizeof(float), 256);
     int* ctr = (int*)(base + at);
+    at = align_up(at + sizeof(int), 256);
+    float4* gsp = (float4*)(base + at);  // after the render workspace's blocks (query_workspace_size)
+    const long long nvox = (long long)grid->nx * grid->ny * grid->nz;
     sq_status_t s = launch_pack(prims, rec, aux, lpad, cp, st);
     if (s != SQ_OK) return s;
+    SQ_LAUNCH("k_pad_rows", st,
+              k_pad_rows<<<(unsigned)((nvox * (cp / 4) + 255) / 256), 256, 0, st>>>(grad_sem, nvox, prims->n_classes,
+                                                                                     cp / 4, gsp));
     cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "memset counter");
     e = cudaMemsetAsync(gacc, 0, (size_t)n * GF * sizeof(float), st);
@@ -321,7 +392,7 @@ sq_status_t query_grid_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, 
     a.n = n;
     a.C = prims->n_classes;
     a.grad_density = grad_density;
-    a.grad_sem = grad_sem;
+    a.gsp = gsp;
     a.gacc = gacc;
     a.ctr = ctr;
     switch (cp) {
