@@ -46,10 +46,10 @@ def mix_peak(sfu, mix):
 # kernel source is unchanged (sha256 of the file holding it).
 NCU_TRAFFIC = {
     "k_backward": {"src": "sqr_bwd.cu", "src_sha": "34900eef8431e285", "bytes_per_launch": 310181888},
-    "k_forward": {"src": "sqr_fwd.cu", "src_sha": "bbf4eba00091e5d5", "bytes_per_launch": 1718119936},
-    "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "34900eef8431e285", "bytes_per_launch": 1938695008},
-    "k_pm_tiles": {"src": "sqr_bwd_pm.cu", "src_sha": "6befed5cd5f897b3", "bytes_per_launch": 7529036072},
-    "k_query": {"src": "sqr_query.cu", "src_sha": "87960f15eac3b56a", "bytes_per_launch": 176335872},
+    "k_forward": {"src": "sqr_fwd.cu", "src_sha": "a571a00694b870a5", "bytes_per_launch": 1763261696},
+    "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "7575a9aeb7331d3e", "bytes_per_launch": 1920478720},
+    "k_pm_tiles": {"src": "sqr_bwd_pm.cu", "src_sha": "40cf39302124fd54", "bytes_per_launch": 3948897280},
+    "k_query": {"src": "sqr_query.cu", "src_sha": "d753ddfce208ed94", "bytes_per_launch": 176852992},
 }
 
 
