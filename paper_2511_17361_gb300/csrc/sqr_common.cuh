@@ -115,7 +115,7 @@ __device__ __forceinline__ float rcp(float x) {
 //   r3 = (M2.x, M2.y, M2.z, ec)   ea = 2/eps2, eb = eps2/eps1, ec = 2/eps1
 // Backward extras, 3 x float4 = 48 B per primitive:
 //   a0 = (qn.w, qn.x, qn.y, qn.z)   normalised quaternion
-//   a1 = (1/|q|, s.x, s.y, s.z)
+//   a1 = (1/|q|, 1/s.x, 1/s.y, 1/s.z)
 //   a2 = (eps1, eps2, 1/eps1, 1/eps2)
 constexpr int REC4 = 4;
 constexpr int AUX4 = 3;
