@@ -355,7 +355,7 @@ struct PmSmem {
     float red[PM_WARPS][NRAW];
     float4 cacc[PM_WARPS][PM_CSUB][8];  // class gradient partials: per warp and slot lane group, classes 4q..4q+3
     int nz[PM_CHUNK];            // the pass's non-empty slots, in slot order
-    float lp[32];                // class vector of the tile's primitive (lpad row)
+    alignas(16) float lp[32];    // class vector of the tile's primitive (lpad row)
     int wtot[PM_WARPS];
     int ztot[PM_WARPS];
     int tile;
@@ -518,27 +518,14 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
                 tl_sum += len[i];
             }
 #pragma unroll
-            for (int i = 0; i < PM_CPT; ++i) {  // slot data of the non-empty runs, <dL/dS, c_k>
+            for (int i = 0; i < PM_CPT; ++i) {  // slot data of the non-empty runs
                 if (len[i] == 0) continue;
                 const int slot = tid * PM_CPT + i;
-                const float4* gsr = S.pm_gs + (long long)rr[i] * (CP / 4);
-                float4 gv[CP / 4];
-#pragma unroll
-                for (int q = 0; q < CP / 4; ++q) gv[q] = __ldg(gsr + q);
-                float cdv = 0.f;
-#pragma unroll
-                for (int q = 0; q < CP / 4; ++q) {
-                    cdv = fmaf(gv[q].x, sh.lp[4 * q + 0], cdv);
-                    cdv = fmaf(gv[q].y, sh.lp[4 * q + 1], cdv);
-                    cdv = fmaf(gv[q].z, sh.lp[4 * q + 2], cdv);
-                    cdv = fmaf(gv[q].w, sh.lp[4 * q + 3], cdv);
-                }
                 sh.d[0][slot] = dv[i].x;
                 sh.d[1][slot] = dv[i].y;
                 sh.d[2][slot] = dv[i].z;
                 sh.r[slot] = rr[i];
                 sh.jc[slot] = j0s[i] | (cam[i] << 10);
-                sh.cd[slot] = cdv;
             }
             // ---- exclusive scan of the run lengths in slot order; list the non-empty slots
             int npairs, nnz;
@@ -576,6 +563,37 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
                 tpairs += tl2;
                 if (tid == 0) sh.pre[PM_CHUNK] = tl2;
                 sh.head_slot[tid] = -1;
+            }
+            __syncthreads();
+            // ---- <dL/dS of the ray, c_k> of each non-empty run: lane (sub, q) of a warp
+            // reads float4 q of run sub's padded gS row (a row is 8 lanes' contiguous
+            // loads), two runs per lane group in flight; the group sums its lanes'
+            // partial dot products in a fixed tree
+            {
+                const int sub = lane >> 3, q = lane & 7;
+                const unsigned gm = 0xffu << (lane & 24);
+                const float4 l4 = q < CP / 4 ? reinterpret_cast<const float4*>(sh.lp)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                constexpr int STEP = PM_WARPS * PM_CSUB;
+                for (int e = wid * PM_CSUB + sub; e < nnz; e += 2 * STEP) {
+                    const int e2 = e + STEP;
+                    const int s1 = sh.nz[e], s2 = e2 < nnz ? sh.nz[e2] : -1;
+                    float4 g1 = make_float4(0.f, 0.f, 0.f, 0.f), g2 = g1;
+                    if (q < CP / 4) {
+                        g1 = __ldg(S.pm_gs + (long long)sh.r[s1] * (CP / 4) + q);
+                        if (s2 >= 0) g2 = __ldg(S.pm_gs + (long long)sh.r[s2] * (CP / 4) + q);
+                    }
+                    float v1 = fmaf(g1.w, l4.w, fmaf(g1.z, l4.z, fmaf(g1.y, l4.y, g1.x * l4.x)));
+                    float v2 = fmaf(g2.w, l4.w, fmaf(g2.z, l4.z, fmaf(g2.y, l4.y, g2.x * l4.x)));
+#pragma unroll
+                    for (int o = 1; o < 8; o <<= 1) {
+                        v1 += __shfl_xor_sync(gm, v1, o);
+                        v2 += __shfl_xor_sync(gm, v2, o);
+                    }
+                    if (q == 0) {
+                        sh.cd[s1] = v1;
+                        if (s2 >= 0) sh.cd[s2] = v2;
+                    }
+                }
             }
             __syncthreads();
 
