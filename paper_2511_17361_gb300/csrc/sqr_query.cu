@@ -141,6 +141,190 @@ __global__ void __launch_bounds__(Q_THREADS) k_query(QueryArgs a) {
     }
 }
 
+// Tile-major form of the same sums.  A block takes a tile of QT_X x QT_Y x QT_Z
+// voxels, one voxel per thread.  It scans the primitives' packed voxel ranges in
+// rounds of QT_ROUND ids, warp w the w-th window of QT_WIN ids of the round,
+// and keeps those that meet the tile, each with the tile-local bit masks of its
+// x, y and z extent; the warps' lists, in warp order, are the round's list in id
+// order.  Then, QT_STAGE primitives at a time, it stages their records and class
+// rows in shared memory.  Every thread
+// adds the terms of the primitives whose range holds its voxel.  A voxel's
+// list Q(v) is exactly the primitives whose range holds v, so every voxel still
+// sums its own list in ascending id order: the sums are those of k_query.
+// Warp w holds one z layer of half the tile's xy square, so a range that is thin
+// in z is all in or all out for the warp's lanes along z.
+constexpr int QT_X = 8, QT_Y = 8, QT_Z = 4;
+constexpr int QT_THREADS = QT_X * QT_Y * QT_Z;
+constexpr int QT_WIN = 128;                           // ids a warp scans per round
+constexpr int QT_ROUND = QT_WIN * (QT_THREADS / 32);  // ids per round
+constexpr int QT_STAGE = 64;                          // primitives staged in shared memory at a time
+static_assert(QT_THREADS == 256 && QT_WIN % 32 == 0, "tile shape");
+static_assert(QT_X <= 8 && QT_Y <= 8 && QT_Z <= 8, "8-bit extent masks");
+
+template <int CP>
+struct QtSmem {
+    int wid_[QT_THREADS / 32][QT_WIN];       // each warp's hits of the round, in id order
+    unsigned wmsk[QT_THREADS / 32][QT_WIN];  // x extent bits 0-7, y bits 8-15, z bits 16-23 (tile-local)
+    int id[QT_ROUND];                         // the round's hits in id order
+    unsigned msk[QT_ROUND];
+    union {
+        struct {
+            float4 rec[QT_STAGE][REC4];
+            float4 cls[QT_STAGE][CP / 4];
+        } st;
+        float rows[QT_THREADS * (CP + 1)];  // the tile's semantic rows, for coalesced stores
+    } u;
+    int wtot[QT_THREADS / 32];
+};
+
+// Bits lo..hi of a tile-local extent (empty when hi < lo).
+__device__ __forceinline__ unsigned span_bits(int lo, int hi) {
+    return hi < lo ? 0u : (2u << hi) - (1u << lo);
+}
+
+template <int CP>
+__global__ void __launch_bounds__(QT_THREADS) k_query_tiles(QueryArgs a, const int4* __restrict__ boxes, int n,
+                                                            int ntx, int nty, int ntz) {
+    __shared__ QtSmem<CP> sh;
+    if (*a.status != SQ_OK) return;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int lx = t & (QT_X - 1), ly = (t / QT_X) & (QT_Y - 1), lz = t / (QT_X * QT_Y);
+    const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
+    const float4* lp4 = reinterpret_cast<const float4*>(a.lpad);
+    for (int tile = blockIdx.x; tile < ntx * nty * ntz; tile += gridDim.x) {
+        const int tz = tile % ntz, ty = (tile / ntz) % nty, tx = tile / (ntz * nty);
+        const int x0 = tx * QT_X, y0 = ty * QT_Y, z0 = tz * QT_Z;
+        const int x1 = min(x0 + QT_X, nx) - 1, y1 = min(y0 + QT_Y, ny) - 1, z1 = min(z0 + QT_Z, nz) - 1;
+        const int ix = x0 + lx, iy = y0 + ly, iz = z0 + lz;
+        const bool valid = ix <= x1 && iy <= y1 && iz <= z1;
+        float x[3];
+        {
+            const int id3[3] = {ix, iy, iz};
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                x[i] = __fadd_rn(a.g.lo[i], __fmul_rn(__fadd_rn(__int2float_rn(id3[i]), 0.5f), a.g.vs[i]));
+        }
+        float acc[CP];
+#pragma unroll
+        for (int c = 0; c < CP; ++c) acc[c] = 0.f;
+        float dens = 0.f;
+        const unsigned sel = (1u << lx) | (1u << (8 + ly)) | (1u << (16 + lz));  // this voxel's bits
+        for (int r0 = 0; r0 < n; r0 += QT_ROUND) {
+            // ---- warp wid: the primitives of its window that meet the tile, in id order
+            int wc = 0;
+#pragma unroll
+            for (int s2 = 0; s2 < QT_WIN / 32; ++s2) {
+                const int k = r0 + wid * QT_WIN + s2 * 32 + lane;
+                unsigned m = 0u;
+                if (k < n) {
+                    const int4 b = __ldg(boxes + k);
+                    const int bx0 = b.x & 0xffff, bx1 = (int)((unsigned)b.x >> 16);
+                    const int by0 = b.y & 0xffff, by1 = (int)((unsigned)b.y >> 16);
+                    const int bz0 = b.z & 0xffff, bz1 = (int)((unsigned)b.z >> 16);
+                    if (bx0 <= x1 && bx1 >= x0 && by0 <= y1 && by1 >= y0 && bz0 <= z1 && bz1 >= z0 &&
+                        bx0 <= bx1 && by0 <= by1 && bz0 <= bz1)
+                        m = span_bits(max(bx0, x0) - x0, min(bx1, x1) - x0) |
+                            (span_bits(max(by0, y0) - y0, min(by1, y1) - y0) << 8) |
+                            (span_bits(max(bz0, z0) - z0, min(bz1, z1) - z0) << 16);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, m != 0u);
+                if (m != 0u) {
+                    const int pos = wc + __popc(bal & ((1u << lane) - 1u));
+                    sh.wid_[wid][pos] = k;
+                    sh.wmsk[wid][pos] = m;
+                }
+                wc += __popc(bal);
+            }
+            if (lane == 0) sh.wtot[wid] = wc;
+            __syncthreads();
+            // ---- the round's list: the warps' lists in warp order
+            int before = 0, nc = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < QT_THREADS / 32; ++w2) {
+                const int v = sh.wtot[w2];
+                before += w2 < wid ? v : 0;
+                nc += v;
+            }
+            for (int j = lane; j < wc; j += 32) {
+                sh.id[before + j] = sh.wid_[wid][j];
+                sh.msk[before + j] = sh.wmsk[wid][j];
+            }
+            __syncthreads();
+            // ---- the listed primitives' terms, QT_STAGE at a time
+            for (int j0 = 0; j0 < nc; j0 += QT_STAGE) {
+                const int nj = min(QT_STAGE, nc - j0);
+                constexpr int PER = REC4 + CP / 4;
+                for (int i = t; i < nj * PER; i += QT_THREADS) {
+                    const int j = i / PER, q = i - j * PER;
+                    const int kk = sh.id[j0 + j];
+                    if (q < REC4) sh.u.st.rec[j][q] = __ldg(a.rec + (size_t)kk * REC4 + q);
+                    else sh.u.st.cls[j][q - REC4] = __ldg(lp4 + (size_t)kk * (CP / 4) + (q - REC4));
+                }
+                __syncthreads();
+                for (int j = 0; j < nj; ++j) {
+                    // the warp evaluates when any of its voxels is in the range; the
+                    // others add an exact zero (p_o is finite at every point)
+                    const bool mem = (sh.msk[j0 + j] & sel) == sel;
+                    if (__any_sync(0xffffffffu, mem)) {
+                        const float4 r0v = sh.u.st.rec[j][0], r1 = sh.u.st.rec[j][1], r2 = sh.u.st.rec[j][2],
+                                     r3 = sh.u.st.rec[j][3];
+                        Prim p;
+                        p.m[0] = r0v.x; p.m[1] = r0v.y; p.m[2] = r0v.z; p.sigma = r0v.w;
+                        p.M[0][0] = r1.x; p.M[0][1] = r1.y; p.M[0][2] = r1.z; p.ea = r1.w;
+                        p.M[1][0] = r2.x; p.M[1][1] = r2.y; p.M[1][2] = r2.z; p.eb = r2.w;
+                        p.M[2][0] = r3.x; p.M[2][1] = r3.y; p.M[2][2] = r3.z; p.ec = r3.w;
+                        const float pv = occupancy(p, x);
+                        const float po = mem ? pv : 0.f;
+                        dens = fmaf(po, p.sigma, dens);
+#pragma unroll
+                        for (int q = 0; q < CP / 4; ++q) {
+                            const float4 cv = sh.u.st.cls[j][q];
+                            acc[4 * q + 0] = fmaf(po, cv.x, acc[4 * q + 0]);
+                            acc[4 * q + 1] = fmaf(po, cv.y, acc[4 * q + 1]);
+                            acc[4 * q + 2] = fmaf(po, cv.z, acc[4 * q + 2]);
+                            acc[4 * q + 3] = fmaf(po, cv.w, acc[4 * q + 3]);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // ---- outputs: density and label per thread; the semantic rows through shared
+        // memory, one warp per column (x, y) of the tile, whose z voxels' rows are
+        // contiguous in [nvox, C]
+        if (valid) {
+            const long long v = ((long long)ix * ny + iy) * nz + iz;
+            a.density[v] = dens;
+            if (a.label) {
+                int best = 0;
+                float bv = acc[0];
+#pragma unroll
+                for (int c = 1; c < CP; ++c)
+                    if (c < a.C && acc[c] > bv) {
+                        bv = acc[c];
+                        best = c;
+                    }
+                a.label[v] = (unsigned char)(dens >= a.tau ? best : a.C);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CP; ++c) sh.u.rows[t * (CP + 1) + c] = acc[c];
+        __syncthreads();
+        {
+            const int ncy = y1 - y0 + 1, ncol = (x1 - x0 + 1) * ncy, nzt = z1 - z0 + 1;
+            for (int col = wid; col < ncol; col += QT_THREADS / 32) {
+                const int cx = col / ncy, cy = col - cx * ncy;
+                float* out = a.sem + (((long long)(x0 + cx) * ny + (y0 + cy)) * nz + z0) * a.C;
+                for (int vz = 0; vz < nzt; ++vz) {
+                    const float* row = sh.u.rows + (vz * (QT_X * QT_Y) + cy * QT_X + cx) * (CP + 1);
+                    for (int c = lane; c < a.C; c += 32) out[vz * a.C + c] = row[c];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 constexpr int QB_THREADS = 256;
 constexpr int QB_SPLIT = 8;  // chunks per primitive range (ranges differ widely in size)
 
@@ -283,7 +467,15 @@ size_t query_workspace_size(const sq_prims_t* p, const sq_grid_t* g) {
 }
 
 template <int CP>
-static sq_status_t launch_query_cp(const QueryArgs& a, cudaStream_t st) {
+static sq_status_t launch_query_cp(const QueryArgs& a, const int4* boxes, int n, cudaStream_t st) {
+    if (boxes) {  // tile-major
+        const int ntx = (a.g.n[0] + QT_X - 1) / QT_X, nty = (a.g.n[1] + QT_Y - 1) / QT_Y,
+                  ntz = (a.g.n[2] + QT_Z - 1) / QT_Z;
+        const long long ntiles = (long long)ntx * nty * ntz;
+        const int blocks = (int)(ntiles < (1LL << 30) ? ntiles : (1LL << 30));
+        SQ_LAUNCH("k_query_tiles", st, k_query_tiles<CP><<<blocks, QT_THREADS, 0, st>>>(a, boxes, n, ntx, nty, ntz));
+        return SQ_OK;
+    }
     long long want = (a.nvox + Q_THREADS - 1) / Q_THREADS;
     int blocks = (int)(want < 152LL * 64 ? want : 152LL * 64);
     if (blocks < 1) blocks = 1;
@@ -300,10 +492,20 @@ sq_status_t query_grid_impl(const sq_prims_t* prims, const sq_index_t* idx, cons
         return SQ_ERR_INVALID_ARG;
     }
     const int cp = cpad(prims->n_classes);
-    // packed records at the start of the workspace, padded logits after them
+    // packed records at the start of the workspace, padded logits after them, then
+    // the packed voxel ranges (inside the render workspace's per-primitive blocks)
     char* base = (char*)ws;
     float4* rec = (float4*)base;
-    float* lpad = (float*)(base + align_up((size_t)prims->n * REC4 * sizeof(float4), 256));
+    const size_t lp_at = align_up((size_t)prims->n * REC4 * sizeof(float4), 256);
+    float* lpad = (float*)(base + lp_at);
+    const size_t bx_at = lp_at + align_up((size_t)prims->n * cp * sizeof(float), 256);
+    int4* boxes = nullptr;
+    if (grid->nx <= 65535 && grid->ny <= 65535 && grid->nz <= 65535 && prims->n > 0 &&
+        bx_at + (size_t)prims->n * sizeof(int4) <= need) {
+        boxes = (int4*)(base + bx_at);
+        sq_status_t sb = launch_pack_boxes(idx->ranges, prims->n, boxes, st);
+        if (sb != SQ_OK) return sb;
+    }
     sq_status_t s = launch_pack(prims, rec, nullptr, lpad, cp, st);
     if (s != SQ_OK) return s;
     QueryArgs a;
@@ -321,14 +523,14 @@ sq_status_t query_grid_impl(const sq_prims_t* prims, const sq_index_t* idx, cons
     a.sem = sem;
     a.label = label;
     switch (cp) {
-        case 4: return launch_query_cp<4>(a, st);
-        case 8: return launch_query_cp<8>(a, st);
-        case 12: return launch_query_cp<12>(a, st);
-        case 16: return launch_query_cp<16>(a, st);
-        case 20: return launch_query_cp<20>(a, st);
-        case 24: return launch_query_cp<24>(a, st);
-        case 28: return launch_query_cp<28>(a, st);
-        case 32: return launch_query_cp<32>(a, st);
+        case 4: return launch_query_cp<4>(a, boxes, prims->n, st);
+        case 8: return launch_query_cp<8>(a, boxes, prims->n, st);
+        case 12: return launch_query_cp<12>(a, boxes, prims->n, st);
+        case 16: return launch_query_cp<16>(a, boxes, prims->n, st);
+        case 20: return launch_query_cp<20>(a, boxes, prims->n, st);
+        case 24: return launch_query_cp<24>(a, boxes, prims->n, st);
+        case 28: return launch_query_cp<28>(a, boxes, prims->n, st);
+        case 32: return launch_query_cp<32>(a, boxes, prims->n, st);
         default: return SQ_ERR_INVALID_ARG;
     }
 }
