@@ -279,13 +279,12 @@ __global__ void k_pm_dirs(Batch B) {
 
 // grad_sem of every ray of the batch copied to rows of CP classes (zero padding),
 // so that a tile reads a ray's row with CP / 4 aligned vector loads: one thread
-// per (ray, group of four classes).
+// per (ray, group of four classes), threadIdx.x the group, threadIdx.y the ray.
 __global__ void k_pm_gs(Batch B) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int cp4 = B.d[0].cp >> 2;  // the scenes of a batch share n_classes
-    const long long gr = i / cp4;
+    const long long gr = (long long)blockIdx.x * blockDim.y + threadIdx.y;
     if (gr >= B.total) return;
-    const int q = (int)(i - gr * cp4);
+    const int cp4 = B.d[0].cp >> 2;  // the scenes of a batch share n_classes
+    const int q = (int)threadIdx.x;
     const int s = scene_of(B, gr);
     const SceneDesc& S = B.d[s];
     const long long r = gr - __ldg(B.off + s);
@@ -793,8 +792,7 @@ sq_status_t launch_backward_pm(const Batch& B, const PmArgs& A, int cp, cudaStre
     SQ_LAUNCH("k_pm_rects", st, k_pm_rects<<<(unsigned)(((long long)A.ntot * 32 + 127) / 128), 128, 0, st>>>(B, A));
     if (B.total > 0) {
         SQ_LAUNCH("k_pm_dirs", st, k_pm_dirs<<<(unsigned)((B.total + 255) / 256), 256, 0, st>>>(B));
-        const long long ng = B.total * (cp / 4);
-        SQ_LAUNCH("k_pm_gs", st, k_pm_gs<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(B));
+        SQ_LAUNCH("k_pm_gs", st, k_pm_gs<<<(unsigned)((B.total + 63) / 64), dim3(cp / 4, 64), 0, st>>>(B));
     }
     SQ_LAUNCH("k_pm_scan", st, k_pm_scan<<<1, 1024, 0, st>>>(A));
     int per_sm = 0;

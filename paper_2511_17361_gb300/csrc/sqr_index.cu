@@ -305,12 +305,19 @@ __global__ void __launch_bounds__(256) k_scatter(const int* __restrict__ ranges,
         int dx = r[1] - r[0] + 1, dy = r[3] - r[2] + 1, dz = r[5] - r[4] + 1;
         if (dx <= 0 || dy <= 0 || dz <= 0) continue;
         long long vol = (long long)dx * dy * dz;
+        // the thread's voxel of range offset l, advanced by blockDim.x offsets per
+        // step as a mixed-radix sum (z fastest): no division inside the loop
+        int iz = (int)(threadIdx.x % dz), iy = (int)((threadIdx.x / dz) % dy), ix = (int)(threadIdx.x / dz / dy);
+        const int sz = (int)(blockDim.x % dz), syz = (int)(blockDim.x / dz), sy = syz % dy, sx = syz / dy;
         for (long long l = threadIdx.x; l < vol; l += blockDim.x) {
-            int iz = (int)(l % dz);
-            long long q = l / dz;
-            int iy = (int)(q % dy);
-            int ix = (int)(q / dy);
             int v = ((r[0] + ix) * ny + (r[2] + iy)) * nz + (r[4] + iz);
+            iz += sz;
+            const int cy = iz >= dz ? 1 : 0;
+            iz -= cy * dz;
+            iy += sy + cy;
+            const int cx = iy >= dy ? 1 : 0;
+            iy -= cx * dy;
+            ix += sx + cx;
             int pos = atomicAdd(cursor + v, 1);
             long long at = (long long)v_f[v] + pos;
             if (at < capacity) v_sq[at] = k;

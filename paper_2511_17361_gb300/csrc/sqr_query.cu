@@ -343,13 +343,13 @@ struct QueryBwdArgs {
 };
 
 // grad_sem [V, C] copied to rows of CP classes (zero padding), one thread per
-// (voxel, group of four classes), so that a pair reads its voxel's row with CP / 4
-// vector loads.
+// (voxel, group of four classes): threadIdx.x the group, threadIdx.y the voxel,
+// so that a pair reads its voxel's row with CP / 4 vector loads.
 __global__ void k_pad_rows(const float* __restrict__ in, long long rows, int C, int cp4, float4* __restrict__ out) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows * cp4) return;
-    const long long r = i / cp4;
-    const int q = (int)(i - r * cp4);
+    const long long r = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+    if (r >= rows) return;
+    const int q = (int)threadIdx.x;
+    const long long i = r * cp4 + q;
     float v[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) v[c] = 4 * q + c < C ? __ldg(in + r * C + 4 * q + c) : 0.f;
@@ -396,10 +396,22 @@ __global__ void __launch_bounds__(QB_THREADS) k_query_bwd(QueryBwdArgs a) {
                 cl[4 * q + 2] = c4.z;
                 cl[4 * q + 3] = c4.w;
             }
-            for (long long t = t_beg + lane; t < t_end; t += 32) {
-                const int iz = k0 + (int)(t % nzb);
-                const long long rest = t / nzb;
-                const int iy = j0 + (int)(rest % nyb), ix = i0 + (int)(rest / nyb);
+            // the lane's voxel (ix, iy, iz) of range offset t, advanced by 32 offsets per
+            // step as a mixed-radix sum (z fastest): no division inside the loop
+            const long long t_first = t_beg + lane;
+            int oz = (int)(t_first % nzb);
+            const long long rest0 = t_first / nzb;
+            int oy = (int)(rest0 % nyb), ox = (int)(rest0 / nyb);
+            const int dz = 32 % nzb, dyz = 32 / nzb, dy = dyz % nyb, dx = dyz / nyb;
+            for (long long t = t_first; t < t_end; t += 32) {
+                const int iz = k0 + oz, iy = j0 + oy, ix = i0 + ox;
+                oz += dz;
+                const int cy = oz >= nzb ? 1 : 0;
+                oz -= cy * nzb;
+                oy += dy + cy;
+                const int cx = oy >= nyb ? 1 : 0;
+                oy -= cx * nyb;
+                ox += dx + cx;
                 const long long v = ((long long)ix * ny + iy) * nz + iz;
                 const int id[3] = {ix, iy, iz};
                 float x[3];
@@ -578,8 +590,8 @@ sq_status_t query_grid_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, 
     sq_status_t s = launch_pack(prims, rec, aux, lpad, cp, st);
     if (s != SQ_OK) return s;
     SQ_LAUNCH("k_pad_rows", st,
-              k_pad_rows<<<(unsigned)((nvox * (cp / 4) + 255) / 256), 256, 0, st>>>(grad_sem, nvox, prims->n_classes,
-                                                                                     cp / 4, gsp));
+              k_pad_rows<<<(unsigned)((nvox + 63) / 64), dim3(cp / 4, 64), 0, st>>>(grad_sem, nvox, prims->n_classes,
+                                                                                   cp / 4, gsp));
     cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "memset counter");
     e = cudaMemsetAsync(gacc, 0, (size_t)n * GF * sizeof(float), st);
