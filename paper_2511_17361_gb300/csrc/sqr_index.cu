@@ -295,6 +295,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int* __restri
 }
 
 // -------------------------------------------------------------- scatter
+constexpr int SC_UNROLL = 4;
 __global__ void __launch_bounds__(256) k_scatter(const int* __restrict__ ranges, int n, int ny, int nz,
                                                  const int* __restrict__ v_f, int* __restrict__ cursor,
                                                  int* __restrict__ v_sq, long long capacity,
@@ -309,18 +310,30 @@ __global__ void __launch_bounds__(256) k_scatter(const int* __restrict__ ranges,
         // step as a mixed-radix sum (z fastest): no division inside the loop
         int iz = (int)(threadIdx.x % dz), iy = (int)((threadIdx.x / dz) % dy), ix = (int)(threadIdx.x / dz / dy);
         const int sz = (int)(blockDim.x % dz), syz = (int)(blockDim.x / dz), sy = syz % dy, sx = syz / dy;
-        for (long long l = threadIdx.x; l < vol; l += blockDim.x) {
-            int v = ((r[0] + ix) * ny + (r[2] + iy)) * nz + (r[4] + iz);
-            iz += sz;
-            const int cy = iz >= dz ? 1 : 0;
-            iz -= cy * dz;
-            iy += sy + cy;
-            const int cx = iy >= dy ? 1 : 0;
-            iy -= cx * dy;
-            ix += sx + cx;
-            int pos = atomicAdd(cursor + v, 1);
-            long long at = (long long)v_f[v] + pos;
-            if (at < capacity) v_sq[at] = k;
+        // SC_UNROLL entries per thread at a time: their cursor atomics and list offsets
+        // are all in flight before any is used
+        for (long long l = threadIdx.x; l < vol; l += (long long)SC_UNROLL * blockDim.x) {
+            int vv[SC_UNROLL], fv[SC_UNROLL], pos[SC_UNROLL];
+#pragma unroll
+            for (int u = 0; u < SC_UNROLL; ++u) {
+                vv[u] = l + (long long)u * blockDim.x < vol ? ((r[0] + ix) * ny + (r[2] + iy)) * nz + (r[4] + iz) : -1;
+                iz += sz;
+                const int cy = iz >= dz ? 1 : 0;
+                iz -= cy * dz;
+                iy += sy + cy;
+                const int cx = iy >= dy ? 1 : 0;
+                iy -= cx * dy;
+                ix += sx + cx;
+            }
+#pragma unroll
+            for (int u = 0; u < SC_UNROLL; ++u) fv[u] = vv[u] >= 0 ? __ldg(v_f + vv[u]) : 0;
+#pragma unroll
+            for (int u = 0; u < SC_UNROLL; ++u) pos[u] = vv[u] >= 0 ? atomicAdd(cursor + vv[u], 1) : 0;
+#pragma unroll
+            for (int u = 0; u < SC_UNROLL; ++u) {
+                const long long at = (long long)fv[u] + pos[u];
+                if (vv[u] >= 0 && at < capacity) v_sq[at] = k;
+            }
         }
     }
 }
@@ -359,6 +372,50 @@ __device__ void warp_bitonic(int n, int lane, Load ld, Store st) {
     }
 }
 
+// Ascending bitonic sort of 32 * E keys held E per lane, element e of lane l
+// being key e * 32 + l: compare-exchanges of keys 32 or more apart stay in the
+// lane, the others go through shuffles.
+template <int E>
+__device__ __forceinline__ void reg_bitonic(int (&x)[E], int lane) {
+    constexpr int N = 32 * E;
+#pragma unroll
+    for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int es = stride >> 5;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if ((e & es) == 0) {
+                        const bool up = ((e * 32 + lane) & size) == 0;
+                        const int a = x[e], b = x[e | es];
+                        x[e] = up ? min(a, b) : max(a, b);
+                        x[e | es] = up ? max(a, b) : min(a, b);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int y = __shfl_xor_sync(0xffffffffu, x[e], stride);
+                    const bool up = ((e * 32 + lane) & size) == 0, lower = (lane & stride) == 0;
+                    x[e] = (lower == up) ? min(x[e], y) : max(x[e], y);
+                }
+            }
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void sort_list_regs(int* list, int n, int lane) {
+    int x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = e * 32 + lane < n ? list[e * 32 + lane] : 0x7fffffff;
+    reg_bitonic<E>(x, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (e * 32 + lane < n) list[e * 32 + lane] = x[e];
+}
+
 // Range-boundary flags of primitive k listed in voxel (ix, iy, iz): per axis a,
 // bit 4a: lo == v, 4a+1: lo == v - 1, 4a+2: hi == v, 4a+3: hi == v + 1.
 __device__ __forceinline__ unsigned short entry_flags(const int* __restrict__ ranges, int k, int ix, int iy, int iz) {
@@ -394,19 +451,13 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_sort(const int* __restrict_
         if (n == 1) {
             // a single entry is sorted
         } else if (n <= 32) {
-            int x = lane < n ? list[lane] : 0x7fffffff;
-#pragma unroll
-            for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    int y = __shfl_xor_sync(0xffffffffu, x, stride);
-                    bool up = ((lane & size) == 0);
-                    bool lower = ((lane & stride) == 0);
-                    int lo = min(x, y), hi = max(x, y);
-                    x = (lower == up) ? lo : hi;
-                }
-            }
-            if (lane < n) list[lane] = x;
+            sort_list_regs<1>(list, n, lane);
+        } else if (n <= 64) {
+            sort_list_regs<2>(list, n, lane);
+        } else if (n <= 128) {
+            sort_list_regs<4>(list, n, lane);
+        } else if (n <= 256) {
+            sort_list_regs<8>(list, n, lane);
         } else if (n <= SORT_SMEM) {
             int* s = sh[wid];
             for (int i = lane; i < n; i += 32) s[i] = list[i];
