@@ -759,15 +759,18 @@ __global__ void k_pm_final(Batch B, PmArgs A) {
     if (i == PM_VISIT_SLOT) {  // pairs the tiles of the primitive evaluated
         if (S.pair_visits) {
             long long nv = 0;
-            for (int t = __ldg(A.toff + g); t < __ldg(A.toff + g + 1); ++t)
-                nv += __float_as_int(A.part[(size_t)t * GF + i]);
+            const int t0 = __ldg(A.toff + g), t1 = __ldg(A.toff + g + 1);
+#pragma unroll 4
+            for (int t = t0; t < t1; ++t) nv += __float_as_int(__ldg(A.part + (size_t)t * GF + i));
             S.pair_visits[k] = nv;
         }
         return;
     }
     if (i >= NRAW + S.C) return;
-    float v = 0.f;
-    for (int t = __ldg(A.toff + g); t < __ldg(A.toff + g + 1); ++t) v += A.part[(size_t)t * GF + i];
+    float v = 0.f;  // in tile order
+    const int t0 = __ldg(A.toff + g), t1 = __ldg(A.toff + g + 1);
+#pragma unroll 4
+    for (int t = t0; t < t1; ++t) v += __ldg(A.part + (size_t)t * GF + i);
     S.gacc[(size_t)k * GF + i] = v;
 }
 

@@ -482,6 +482,53 @@ def test_query_grid_full(sqr):
     assert np.array_equal(lab[clear], rl[clear])
 
 
+def _query_scene(seed, n, gn, lo, hi, C=7):
+    rng = np.random.default_rng(seed)
+    lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+    means = rng.uniform(lo, hi, (n, 3))
+    pr = prims_from(means, rng.standard_normal((n, 4)), rng.uniform(0.1, 1.2, (n, 3)), rng.uniform(0.2, 1.8, (n, 2)),
+                    rng.uniform(0.05, 0.9, n), rng.standard_normal((n, C)))
+    return pr, synth.grid_spec(*gn, lo=lo, hi=hi)
+
+
+@pytest.mark.parametrize("gn", [(13, 11, 7), (9, 17, 5), (1, 1, 1)])
+def test_query_grid_partial_tiles(sqr, gn):
+    """Grids whose sides are not multiples of the 8 x 8 x 4 voxel tiles, with more
+    primitives than one scan round (1,024 ids): density, semantics and labels
+    against the oracle at every voxel centre."""
+    pr, grid = _query_scene(31, 2500, gn, (-6.0, -6.0, -2.0), (6.0, 6.0, 2.0))
+    prims_d = sqr.to_device(pr)
+    g = dev_grid(grid)
+    ix = sqr.build_index(prims_d, g)
+    dens, sem, lab = sqr.query_grid(prims_d, ix, g, tau=0.05)
+    torch.cuda.synchronize()
+    rd, rs, rl = oracle.query_grid(pr, grid, oracle_index(ix, pr, grid), tau=0.05)
+    dens, sem, lab = dens.cpu().numpy(), sem.cpu().numpy(), lab.cpu().numpy()
+    assert np.max(np.abs(dens - rd) / np.maximum(1.0, rd)) < 5e-5
+    assert np.max(np.abs(sem - rs) / np.maximum(1.0, np.abs(rs))) < 5e-5
+    assert np.array_equal(np.where(dens >= 0.05, np.argmax(sem, 1), 7), lab)
+
+
+def test_query_grid_long_axis(sqr):
+    """A grid with more than 65,535 voxels along x: the query runs without voxel
+    tiles (one lane per voxel, lane groups merging their lists) and still matches
+    the oracle."""
+    pr, grid = _query_scene(32, 300, (66000, 2, 2), (0.0, -1.0, -1.0), (6600.0, 1.0, 1.0))
+    prims_d = sqr.to_device(pr)
+    g = dev_grid(grid)
+    ix = sqr.build_index(prims_d, g)
+    sqr.profile_enable(True)
+    dens, sem, lab = sqr.query_grid(prims_d, ix, g, tau=0.05)
+    torch.cuda.synchronize()
+    sqr.profile_enable(False)
+    assert sqr.profile_query("k_query")[0] == 1 and sqr.profile_query("k_query_tiles")[0] == 0
+    rd, rs, rl = oracle.query_grid(pr, grid, oracle_index(ix, pr, grid), tau=0.05)
+    dens, sem = dens.cpu().numpy(), sem.cpu().numpy()
+    assert rd.max() > 0.05
+    assert np.max(np.abs(dens - rd) / np.maximum(1.0, rd)) < 5e-5
+    assert np.max(np.abs(sem - rs) / np.maximum(1.0, np.abs(rs))) < 5e-5
+
+
 def test_query_backward_full(sqr):
     """Backward of the grid query (dense cotangents on all 20,000 voxels of the
     256-superquadric scene) against the FP64 oracle."""
