@@ -16,6 +16,7 @@
 #include <stdio.h>
 
 #include "sqr_common.cuh"
+#include "sqr_render.cuh"
 
 namespace sqr {
 
@@ -295,7 +296,6 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int* __restri
 }
 
 // -------------------------------------------------------------- scatter
-constexpr int SC_UNROLL = 4;
 __global__ void __launch_bounds__(256) k_scatter(const int* __restrict__ ranges, int n, int ny, int nz,
                                                  const int* __restrict__ v_f, int* __restrict__ cursor,
                                                  int* __restrict__ v_sq, long long capacity,
@@ -310,30 +310,18 @@ __global__ void __launch_bounds__(256) k_scatter(const int* __restrict__ ranges,
         // step as a mixed-radix sum (z fastest): no division inside the loop
         int iz = (int)(threadIdx.x % dz), iy = (int)((threadIdx.x / dz) % dy), ix = (int)(threadIdx.x / dz / dy);
         const int sz = (int)(blockDim.x % dz), syz = (int)(blockDim.x / dz), sy = syz % dy, sx = syz / dy;
-        // SC_UNROLL entries per thread at a time: their cursor atomics and list offsets
-        // are all in flight before any is used
-        for (long long l = threadIdx.x; l < vol; l += (long long)SC_UNROLL * blockDim.x) {
-            int vv[SC_UNROLL], fv[SC_UNROLL], pos[SC_UNROLL];
-#pragma unroll
-            for (int u = 0; u < SC_UNROLL; ++u) {
-                vv[u] = l + (long long)u * blockDim.x < vol ? ((r[0] + ix) * ny + (r[2] + iy)) * nz + (r[4] + iz) : -1;
-                iz += sz;
-                const int cy = iz >= dz ? 1 : 0;
-                iz -= cy * dz;
-                iy += sy + cy;
-                const int cx = iy >= dy ? 1 : 0;
-                iy -= cx * dy;
-                ix += sx + cx;
-            }
-#pragma unroll
-            for (int u = 0; u < SC_UNROLL; ++u) fv[u] = vv[u] >= 0 ? __ldg(v_f + vv[u]) : 0;
-#pragma unroll
-            for (int u = 0; u < SC_UNROLL; ++u) pos[u] = vv[u] >= 0 ? atomicAdd(cursor + vv[u], 1) : 0;
-#pragma unroll
-            for (int u = 0; u < SC_UNROLL; ++u) {
-                const long long at = (long long)fv[u] + pos[u];
-                if (vv[u] >= 0 && at < capacity) v_sq[at] = k;
-            }
+        for (long long l = threadIdx.x; l < vol; l += blockDim.x) {
+            int v = ((r[0] + ix) * ny + (r[2] + iy)) * nz + (r[4] + iz);
+            iz += sz;
+            const int cy = iz >= dz ? 1 : 0;
+            iz -= cy * dz;
+            iy += sy + cy;
+            const int cx = iy >= dy ? 1 : 0;
+            iy -= cx * dy;
+            ix += sx + cx;
+            int pos = atomicAdd(cursor + v, 1);
+            long long at = (long long)v_f[v] + pos;
+            if (at < capacity) v_sq[at] = k;
         }
     }
 }
@@ -478,6 +466,101 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_sort(const int* __restrict_
     }
 }
 
+// -------------------------------------------------------------- lists by voxel tiles
+// V_sq without atomics or a sort: a block takes a tile of LT_X x LT_Y x LT_Z voxels,
+// one voxel per thread, and scans the packed voxel ranges in id order (rounds of
+// LT_ROUND ids, warp w the w-th window of LT_WIN ids, the warps' hits in warp
+// order being the round's hits in id order), each hit with the tile-local bit
+// masks of its x, y and z extent.  Every thread then walks the round's hits and
+// appends those whose range holds its voxel to the voxel's list: the list is
+// written in ascending id, exactly the sorted list of the primitives whose range
+// contains the voxel.  Each warp holds a 4 x 4 x 2 block of the tile.
+constexpr int LT_X = 8, LT_Y = 8, LT_Z = 4, LT_THREADS = LT_X * LT_Y * LT_Z;
+constexpr int LT_WIN = 128, LT_ROUND = LT_WIN * (LT_THREADS / 32);
+static_assert(LT_THREADS == 256, "warps of 4 x 4 x 2 voxels");
+
+__device__ __forceinline__ unsigned lt_span(int lo, int hi) { return hi < lo ? 0u : (2u << hi) - (1u << lo); }
+
+__global__ void __launch_bounds__(LT_THREADS) k_lists_tiles(const int4* __restrict__ boxes, int n,
+                                                           const int* __restrict__ v_f, int* __restrict__ v_sq,
+                                                           long long capacity, const int* __restrict__ status,
+                                                           const int* __restrict__ ranges,
+                                                           unsigned short* __restrict__ v_flags, int nx, int ny,
+                                                           int nz, int ntx, int nty, int ntz) {
+    __shared__ int wid_[LT_THREADS / 32][LT_WIN];
+    __shared__ unsigned wmsk[LT_THREADS / 32][LT_WIN];
+    __shared__ int lid[LT_ROUND];
+    __shared__ unsigned lmsk[LT_ROUND];
+    __shared__ int wtot[LT_THREADS / 32];
+    if (*status != SQ_OK) return;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int lx = (wid & 1) * 4 + (lane & 3), ly = ((wid >> 1) & 1) * 4 + ((lane >> 2) & 3),
+              lz = (wid >> 2) * 2 + (lane >> 4);
+    const unsigned sel = (1u << lx) | (1u << (8 + ly)) | (1u << (16 + lz));
+    for (int tile = blockIdx.x; tile < ntx * nty * ntz; tile += gridDim.x) {
+        const int tz = tile % ntz, ty = (tile / ntz) % nty, tx = tile / (ntz * nty);
+        const int x0 = tx * LT_X, y0 = ty * LT_Y, z0 = tz * LT_Z;
+        const int x1 = min(x0 + LT_X, nx) - 1, y1 = min(y0 + LT_Y, ny) - 1, z1 = min(z0 + LT_Z, nz) - 1;
+        const int ix = x0 + lx, iy = y0 + ly, iz = z0 + lz;
+        const bool valid = ix <= x1 && iy <= y1 && iz <= z1;
+        const long long v = valid ? ((long long)ix * ny + iy) * nz + iz : 0;
+        const long long vf = valid ? (long long)__ldg(v_f + v) : 0;
+        int cnt = 0;
+        for (int r0 = 0; r0 < n; r0 += LT_ROUND) {
+            int wc = 0;
+#pragma unroll
+            for (int s2 = 0; s2 < LT_WIN / 32; ++s2) {
+                const int k = r0 + wid * LT_WIN + s2 * 32 + lane;
+                unsigned m = 0u;
+                if (k < n) {
+                    const int4 b = __ldg(boxes + k);
+                    const int bx0 = b.x & 0xffff, bx1 = (int)((unsigned)b.x >> 16);
+                    const int by0 = b.y & 0xffff, by1 = (int)((unsigned)b.y >> 16);
+                    const int bz0 = b.z & 0xffff, bz1 = (int)((unsigned)b.z >> 16);
+                    if (bx0 <= x1 && bx1 >= x0 && by0 <= y1 && by1 >= y0 && bz0 <= z1 && bz1 >= z0 &&
+                        bx0 <= bx1 && by0 <= by1 && bz0 <= bz1)
+                        m = lt_span(max(bx0, x0) - x0, min(bx1, x1) - x0) |
+                            (lt_span(max(by0, y0) - y0, min(by1, y1) - y0) << 8) |
+                            (lt_span(max(bz0, z0) - z0, min(bz1, z1) - z0) << 16);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, m != 0u);
+                if (m != 0u) {
+                    const int pos = wc + __popc(bal & ((1u << lane) - 1u));
+                    wid_[wid][pos] = k;
+                    wmsk[wid][pos] = m;
+                }
+                wc += __popc(bal);
+            }
+            if (lane == 0) wtot[wid] = wc;
+            __syncthreads();
+            int before = 0, nc = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < LT_THREADS / 32; ++w2) {
+                const int c = wtot[w2];
+                before += w2 < wid ? c : 0;
+                nc += c;
+            }
+            for (int j = lane; j < wc; j += 32) {
+                lid[before + j] = wid_[wid][j];
+                lmsk[before + j] = wmsk[wid][j];
+            }
+            __syncthreads();
+            for (int j = 0; j < nc; ++j) {
+                if ((lmsk[j] & sel) == sel) {  // only valid voxels have their bits set
+                    const long long at = vf + cnt;
+                    const int k = lid[j];
+                    if (at < capacity) {
+                        v_sq[at] = k;
+                        if (v_flags) v_flags[at] = entry_flags(ranges, k, ix, iy, iz);
+                    }
+                    ++cnt;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- workspace
@@ -515,11 +598,18 @@ sq_status_t build_index_impl(const sq_prims_t* prims, const sq_grid_t* grid, con
     const size_t ndiff = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
     const int n_tiles = (int)((nvox + SCAN_TILE - 1) / SCAN_TILE);
 
+    // The lists are built by voxel tiles when the ranges pack into 16 bits per end
+    // and the packed ranges fit in the cursor block (which that build does not use);
+    // otherwise by the scatter and the per-voxel sort.
+    const bool by_tiles = nx <= 65535 && ny <= 65535 && nz <= 65535 && prims->n > 0 &&
+                          (size_t)prims->n * sizeof(int4) <= (size_t)nvox * sizeof(int);
     cudaError_t e;
     e = cudaMemsetAsync(diff, 0, ndiff * sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "memset diff");
-    e = cudaMemsetAsync(cursor, 0, (size_t)nvox * sizeof(int), st);
-    if (e != cudaSuccess) return cuda_status(e, "memset cursor");
+    if (!by_tiles) {
+        e = cudaMemsetAsync(cursor, 0, (size_t)nvox * sizeof(int), st);
+        if (e != cudaSuccess) return cuda_status(e, "memset cursor");
+    }
     e = cudaMemsetAsync(idx->status, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "memset status");
 
@@ -546,7 +636,18 @@ sq_status_t build_index_impl(const sq_prims_t* prims, const sq_grid_t* grid, con
     SQ_LAUNCH("k_scan_reduce", st, k_scan_reduce<<<n_tiles, SCAN_THREADS, 0, st>>>(idx->v_n, nvox, tiles));
     SQ_LAUNCH("k_scan_tiles", st, k_scan_tiles<<<1, SCAN_THREADS, 0, st>>>(tiles, n_tiles, idx->capacity, idx->p_total, idx->status));
     SQ_LAUNCH("k_scan_apply", st, k_scan_apply<<<n_tiles, SCAN_THREADS, 0, st>>>(idx->v_n, nvox, tiles, idx->v_f));
-    if (prims->n > 0) {
+    if (by_tiles) {
+        int4* boxes = reinterpret_cast<int4*>(cursor);  // 16-byte aligned (a 256-byte aligned block)
+        sq_status_t sb = launch_pack_boxes(idx->ranges, prims->n, boxes, st);
+        if (sb != SQ_OK) return sb;
+        const int ntx = (nx + LT_X - 1) / LT_X, nty = (ny + LT_Y - 1) / LT_Y, ntz = (nz + LT_Z - 1) / LT_Z;
+        const long long ntl = (long long)ntx * nty * ntz;
+        const int lblocks = (int)(ntl < (1LL << 30) ? ntl : (1LL << 30));
+        SQ_LAUNCH("k_lists_tiles", st,
+                  k_lists_tiles<<<lblocks, LT_THREADS, 0, st>>>(boxes, prims->n, idx->v_f, idx->v_sq, idx->capacity,
+                                                                idx->status, idx->ranges, idx->v_flags, nx, ny, nz,
+                                                                ntx, nty, ntz));
+    } else if (prims->n > 0) {
         int blocks = prims->n < 65535 ? prims->n : 65535;
         SQ_LAUNCH("k_scatter", st, k_scatter<<<blocks, 256, 0, st>>>(idx->ranges, prims->n, ny, nz, idx->v_f, cursor, idx->v_sq, idx->capacity,
                                           idx->status));
