@@ -415,6 +415,21 @@ sq_status_t sq_profile_query(const char* name, long long* launches, double* tota
  * two CUDA events; allocates no device memory. */
 sq_status_t sq_measure_sfu(int op, double* ops_per_s, void* stream);
 
+/* Bounds checks of the debug build, no counterpart in the paper (the stand-in for a
+ * memory checker).  The library built with -DSQR_CHECK (libsqr_check.so) checks the
+ * indices its kernels take from caller-owned data before using them: a voxel list
+ * (V_f, V_n) lying outside V_sq's capacity (site 1), a listed id that is not a
+ * primitive (site 2), a saved-state page outside the saved buffer (site 3).  A failed
+ * check skips the access and records its site in a device word; the kernel goes on
+ * (no trap, no assert) and its outputs are then not meaningful.  Covered: the
+ * forward render, the backward sweep, the ray-major backward's listed ids, and the
+ * untiled grid query; the index build, the primitive-major backward and the tiled
+ * query read only data the library derives itself.
+ * sq_check_query writes 1 to *compiled when the loaded library has the checks (0
+ * otherwise, and then *site = 0), and to *site the first failing site since the
+ * last query (0: none), clearing it.  Host-synchronous (device-to-host copies). */
+sq_status_t sq_check_query(int* compiled, int* site);
+
 #ifdef __cplusplus
 }
 #endif

@@ -3,7 +3,9 @@
 Each translation unit under csrc/ is compiled in parallel to an object, then
 linked into ``paper_2511_17361_gb300/_lib/libsqr.so`` (static CUDA runtime, so
 the library only needs the driver).  Objects are rebuilt when a source or a
-header is newer.
+header is newer.  ``build(check=True)`` builds the same sources with -DSQR_CHECK
+into ``_lib/libsqr_check.so``: the debug library whose kernels check the indices
+they take from caller-owned data (sq_check_query).
 """
 from __future__ import annotations
 
@@ -19,6 +21,8 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libsqr.so")
+LIB_CHECK = os.path.join(OUT_DIR, "libsqr_check.so")
+OBJ_DIR_CHECK = os.path.join(PKG, "_build_check")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-I" + os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
@@ -39,12 +43,12 @@ def _headers():
     return sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
-def _compile(src: str, extra=()) -> str:
-    obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
+def _compile(src: str, extra=(), obj_dir: str = OBJ_DIR, defs=()) -> str:
+    obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not extra:
         return obj
-    cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(defs) + list(extra) + ["-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stderr}")
@@ -52,24 +56,27 @@ def _compile(src: str, extra=()) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    """Compile every csrc/*.cu for sm_103a and link libsqr.so; returns its path."""
+def build(verbose: bool = False, extra=(), check: bool = False) -> str:
+    """Compile every csrc/*.cu for sm_103a and link libsqr.so (libsqr_check.so with
+    check=True); returns its path."""
+    lib, obj_dir = (LIB_CHECK, OBJ_DIR_CHECK) if check else (LIB, OBJ_DIR)
+    defs = ["-DSQR_CHECK"] if check else []
     os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(OBJ_DIR, exist_ok=True)
+    os.makedirs(obj_dir, exist_ok=True)
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs) and not extra:
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, extra, obj_dir, defs), srcs))
+    if os.path.exists(lib) and os.path.getmtime(lib) >= max(os.path.getmtime(o) for o in objs) and not extra:
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"link of libsqr.so failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+        raise RuntimeError(f"link of {os.path.basename(lib)} failed:\n{r.stderr}")
+    os.replace(tmp, lib)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", lib)
+    return lib
 
 
 if __name__ == "__main__":

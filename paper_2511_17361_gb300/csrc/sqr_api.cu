@@ -262,6 +262,14 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_vloss(const float* __restrict_
 
 using namespace sqr;
 
+#ifdef SQR_CHECK
+namespace sqr {
+unsigned check_take_fwd();
+unsigned check_take_bwd();
+unsigned check_take_query();
+}  // namespace sqr
+#endif
+
 extern "C" {
 
 const char* sq_status_string(sq_status_t s) {
@@ -483,6 +491,24 @@ sq_status_t sq_autotune(const sq_scene_t* scenes, int n_scenes, void* workspace,
     }
     return autotune_impl(scenes, n_scenes, workspace, workspace_bytes, (cudaStream_t)stream, best, fwd_ms, bwd_ms,
                          reps);
+}
+
+sq_status_t sq_check_query(int* compiled, int* site) {
+    if (compiled == nullptr || site == nullptr) {
+        sqr::set_last_error("sq_check_query: compiled and site must be non-NULL");
+        return SQ_ERR_INVALID_ARG;
+    }
+#ifdef SQR_CHECK
+    unsigned first = 0;
+    for (unsigned v : {sqr::check_take_fwd(), sqr::check_take_bwd(), sqr::check_take_query()})
+        if (first == 0) first = v;
+    *compiled = 1;
+    *site = (int)first;
+#else
+    *compiled = 0;
+    *site = 0;
+#endif
+    return SQ_OK;
 }
 
 }  // extern "C"

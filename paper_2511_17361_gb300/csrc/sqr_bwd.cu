@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(256) k_bwd_sweep(Batch B) {
             const int pidx = j / SAVE_PS;
             int pg = __shfl_sync(0xffffffffu, pent, pidx & 31);
             if (!reg_table) pg = valid ? __ldg(prow + pidx) : -1;
+            if (valid && pg >= 0 && !SQ_BOUND(pg < S.save_cap, 3)) pg = -1;
             float sa = 0.f, T = 0.f, tj = 0.f;
             float4 sc[CP / 4];
 #pragma unroll
@@ -377,7 +378,8 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
                         st[u] = ml[u] == MK_ALL || (fv[u] & (unsigned)(ml[u] & MK_FLAGS)) != 0u;
                         if (ml[u] == MK_BOX) {
                             const int2 pl = tb.pv[eq * lmax + jl[u] - 1];
-                            st[u] = !box_has(__ldg(S.boxes + __ldg(S.v_sq + ent[u])), pl);
+                            const int kk = __ldg(S.v_sq + ent[u]);
+                            st[u] = SQ_BOUND((unsigned)kk < (unsigned)S.n, 2) ? !box_has(__ldg(S.boxes + kk), pl) : false;
                         }
                     }
 #pragma unroll
@@ -416,6 +418,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_backward(Batch B) {
                         q[u] = tk.y >> 16;
                         j0[u] = tk.y & 0xffff;
                         k[u] = __ldg(S.v_sq + tk.x);
+                        if (!SQ_BOUND((unsigned)k[u] < (unsigned)S.n, 2)) k[u] = 0;
                     }
                 }
                 int4 box[RU];
@@ -683,5 +686,9 @@ sq_status_t launch_pack_boxes(const int* ranges, int n, int4* boxes, cudaStream_
     SQ_LAUNCH("k_pack_boxes", st, k_pack_boxes<<<(n + 127) / 128, 128, 0, st>>>(ranges, n, boxes));
     return SQ_OK;
 }
+
+#ifdef SQR_CHECK
+unsigned check_take_bwd() { return check_take(); }
+#endif
 
 }  // namespace sqr

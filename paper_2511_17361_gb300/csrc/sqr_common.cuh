@@ -37,6 +37,30 @@ void prof_end(cudaStream_t st);
         SQ_CHECK_LAUNCH(name);         \
     } while (0)
 
+// ---------------------------------------------------------------- bounds checks
+// Debug build (-DSQR_CHECK, libsqr_check.so): SQ_BOUND(cond, site) records the first
+// failing check of the translation unit in a device word and returns false, and the
+// caller skips the access it guards.  No trap, no assert: the kernel goes on, and the
+// host reads and clears the words with sq_check_query.  In the normal build it is
+// `true` and compiles away.  Sites: 1 a voxel list (V_f, V_n) outside V_sq, 2 a
+// listed id that is not a primitive, 3 a saved-state page outside the buffer.
+#ifdef SQR_CHECK
+static __device__ unsigned int g_check_site;
+__device__ __forceinline__ bool check_ok(bool c, unsigned site) {
+    if (!c) atomicCAS(&g_check_site, 0u, site);
+    return c;
+}
+static inline unsigned check_take() {
+    unsigned v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_check_site, sizeof v) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_check_site, &z, sizeof z);
+    return v;
+}
+#define SQ_BOUND(cond, site) ::sqr::check_ok((cond), (site))
+#else
+#define SQ_BOUND(cond, site) true
+#endif
+
 // ---------------------------------------------------------------- grid
 struct GridC {
     int n[3];

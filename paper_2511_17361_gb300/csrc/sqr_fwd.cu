@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
         if (vox >= 0) {
             n = __ldg(S.v_n + vox);
             f = __ldg(S.v_f + vox);
+            if (n > 0 && !SQ_BOUND(f >= 0 && (long long)f + n <= S.v_cap, 1)) n = 0;
         }
         float asum = 0.f;
         float sacc[CP];
@@ -143,28 +144,32 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
 #pragma unroll
         for (int o2 = GS / 2; o2 > 0; o2 >>= 1) kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o2, GS));
         Prim p;  // the group's record, loaded one step ahead
-        if (kmin != INT_MAX) p = load_prim(rec, kmin);
+        if (kmin != INT_MAX && SQ_BOUND((unsigned)kmin < (unsigned)S.n, 2)) p = load_prim(rec, kmin);
         while (__any_sync(0xffffffffu, kmin != INT_MAX)) {
             // the group's next id is known before this step's work: its record loads overlap the math
             int knext = head == kmin ? head2 : head;
 #pragma unroll
             for (int o2 = GS / 2; o2 > 0; o2 >>= 1) knext = min(knext, __shfl_xor_sync(0xffffffffu, knext, o2, GS));
             Prim pn;
-            if (knext != INT_MAX) pn = load_prim(rec, knext);
+            if (knext != INT_MAX && SQ_BOUND((unsigned)knext < (unsigned)S.n, 2)) pn = load_prim(rec, knext);
             if (kmin != INT_MAX) {
-                const float4* cr = lp4 + (size_t)kmin * (CP / 4);
+                // (a listed id that is not a primitive is skipped, its list still advances)
+                const bool idok = SQ_BOUND((unsigned)kmin < (unsigned)S.n, 2);
+                const float4* cr = lp4 + (size_t)(idok ? kmin : 0) * (CP / 4);
                 float4 cv[CP / 4];
 #pragma unroll
-                for (int q = 0; q < CP / 4; ++q) cv[q] = __ldg(cr + q);
+                for (int q = 0; q < CP / 4; ++q) cv[q] = idok ? __ldg(cr + q) : make_float4(0.f, 0.f, 0.f, 0.f);
                 if (head == kmin) {
-                    const float po = occupancy(p, x);
-                    asum = fmaf(po, p.sigma, asum);
+                    if (idok) {
+                        const float po = occupancy(p, x);
+                        asum = fmaf(po, p.sigma, asum);
 #pragma unroll
-                    for (int q = 0; q < CP / 4; ++q) {
-                        sacc[4 * q + 0] = fmaf(po, cv[q].x, sacc[4 * q + 0]);
-                        sacc[4 * q + 1] = fmaf(po, cv[q].y, sacc[4 * q + 1]);
-                        sacc[4 * q + 2] = fmaf(po, cv[q].z, sacc[4 * q + 2]);
-                        sacc[4 * q + 3] = fmaf(po, cv[q].w, sacc[4 * q + 3]);
+                        for (int q = 0; q < CP / 4; ++q) {
+                            sacc[4 * q + 0] = fmaf(po, cv[q].x, sacc[4 * q + 0]);
+                            sacc[4 * q + 1] = fmaf(po, cv[q].y, sacc[4 * q + 1]);
+                            sacc[4 * q + 2] = fmaf(po, cv[q].z, sacc[4 * q + 2]);
+                            sacc[4 * q + 3] = fmaf(po, cv[q].w, sacc[4 * q + 3]);
+                        }
                     }
                     ++e;
                     head = head2;
@@ -306,5 +311,9 @@ sq_status_t launch_forward(const Batch& B, int cp, const Tuning& tn, cudaStream_
     set_last_error("n_classes padding %d not supported", cp);
     return SQ_ERR_INVALID_ARG;
 }
+
+#ifdef SQR_CHECK
+unsigned check_take_fwd() { return check_take(); }
+#endif
 
 }  // namespace sqr

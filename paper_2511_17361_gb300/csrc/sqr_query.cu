@@ -36,6 +36,8 @@ struct QueryArgs {
     const int* status;
     GridC g;
     long long nvox;
+    long long v_cap;  // entries V_sq holds
+    int n;            // primitives
     int C;
     float tau;
     float* density;
@@ -79,24 +81,27 @@ __global__ void __launch_bounds__(Q_THREADS) k_query(QueryArgs a) {
                 x[i] = __fadd_rn(a.g.lo[i], __fmul_rn(__fadd_rn(__int2float_rn(id[i]), 0.5f), a.g.vs[i]));
             n = __ldg(a.v_n + v);
             f = __ldg(a.v_f + v);
+            if (n > 0 && !SQ_BOUND(f >= 0 && (long long)f + n <= a.v_cap, 1)) n = 0;
         }
         int e = 0;
         int head = n > 0 ? __ldg(a.v_sq + f) : INT_MAX;
         int head2 = n > 1 ? __ldg(a.v_sq + f + 1) : INT_MAX;
         int kmin = group_min<GQ>(head);
         Prim p;
-        if (kmin != INT_MAX) p = load_prim(a.rec, kmin);
+        if (kmin != INT_MAX && SQ_BOUND((unsigned)kmin < (unsigned)a.n, 2)) p = load_prim(a.rec, kmin);
         while (__any_sync(0xffffffffu, kmin != INT_MAX)) {
             const int knext = group_min<GQ>(head == kmin ? head2 : head);
             Prim pn;
-            if (knext != INT_MAX) pn = load_prim(a.rec, knext);
+            if (knext != INT_MAX && SQ_BOUND((unsigned)knext < (unsigned)a.n, 2)) pn = load_prim(a.rec, knext);
             if (kmin != INT_MAX) {
-                const float4* cr = lp4 + (size_t)kmin * (CP / 4);
+                // (a listed id that is not a primitive is skipped, its list still advances)
+                const bool idok = SQ_BOUND((unsigned)kmin < (unsigned)a.n, 2);
+                const float4* cr = lp4 + (size_t)(idok ? kmin : 0) * (CP / 4);
                 float4 cv[CP / 4];
 #pragma unroll
-                for (int q = 0; q < CP / 4; ++q) cv[q] = __ldg(cr + q);
+                for (int q = 0; q < CP / 4; ++q) cv[q] = idok ? __ldg(cr + q) : make_float4(0.f, 0.f, 0.f, 0.f);
                 if (head == kmin) {
-                    const float po = occupancy(p, x);
+                    const float po = idok ? occupancy(p, x) : 0.f;
                     dens = fmaf(po, p.sigma, dens);
 #pragma unroll
                     for (int q = 0; q < CP / 4; ++q) {
@@ -529,6 +534,8 @@ sq_status_t query_grid_impl(const sq_prims_t* prims, const sq_index_t* idx, cons
     a.v_n = idx->v_n;
     a.v_f = idx->v_f;
     a.v_sq = idx->v_sq;
+    a.v_cap = idx->capacity;
+    a.n = prims->n;
     a.status = idx->status;
     a.g = make_grid(grid);
     a.nvox = (long long)grid->nx * grid->ny * grid->nz;
@@ -636,5 +643,9 @@ sq_status_t query_grid_bwd_impl(const sq_prims_t* prims, const sq_index_t* idx, 
     S.status = idx->status;
     return launch_grad_out(S, g_means, g_quats, g_scales, g_eps, g_opacity, g_logits, st);
 }
+
+#ifdef SQR_CHECK
+unsigned check_take_query() { return check_take(); }
+#endif
 
 }  // namespace sqr

@@ -356,6 +356,7 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
         D.v_n = s.index.v_n;
         D.v_f = s.index.v_f;
         D.v_sq = s.index.v_sq;
+        D.v_cap = s.index.capacity;
         D.v_flags = s.index.v_flags;
         D.status = s.index.status;
         D.g = make_grid(&s.grid);

@@ -25,6 +25,7 @@ struct SceneDesc {
     const int* v_n;
     const int* v_f;
     const int* v_sq;
+    long long v_cap;     // entries V_sq holds (the bounds checks of the debug build)
     const unsigned short* v_flags;  // nullable: per-entry range-boundary flags
     const int* status;
     GridC g;

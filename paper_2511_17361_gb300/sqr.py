@@ -18,7 +18,9 @@ from dataclasses import dataclass
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "libsqr.so")
+# SQR_CHECK=1 in the environment loads the debug build with bounds checks
+# (libsqr_check.so, sq_check_query) instead of the library.
+LIB_PATH = os.path.join(_PKG, "_lib", "libsqr_check.so" if os.environ.get("SQR_CHECK") == "1" else "libsqr.so")
 
 SQ_OK, SQ_ERR_INVALID_ARG, SQ_ERR_CAPACITY, SQ_ERR_CUDA, SQ_ERR_TIMEOUT, SQ_ERR_NUMERIC = range(6)
 SQ_INDEX_OBB, SQ_INDEX_CUBE, SQ_INDEX_OBB_OPACITY = 0, 1, 2
@@ -71,7 +73,7 @@ class SqrError(RuntimeError):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libsqr.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+        raise ImportError(f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH}); run __graft_entry__.build() or "
                           "python -m paper_2511_17361_gb300._build")
     lib = ctypes.CDLL(LIB_PATH)
     P = ctypes.POINTER
@@ -109,6 +111,8 @@ def _load():
                                       _vp, ctypes.c_size_t, _vp]
     lib.sq_measure_sfu.restype = ctypes.c_int
     lib.sq_measure_sfu.argtypes = [ctypes.c_int, P(ctypes.c_double), _vp]
+    lib.sq_check_query.restype = ctypes.c_int
+    lib.sq_check_query.argtypes = [P(ctypes.c_int), P(ctypes.c_int)]
     lib.sq_profile_enable.restype = ctypes.c_int
     lib.sq_profile_enable.argtypes = [ctypes.c_int]
     lib.sq_profile_query.restype = ctypes.c_int
@@ -461,6 +465,15 @@ def measure_sfu(op: str) -> float:
     v = ctypes.c_double()
     _check(lib.sq_measure_sfu({"ex2": 0, "lg2": 1, "rcp": 2}[op], ctypes.byref(v), _stream()), "sq_measure_sfu")
     return float(v.value)
+
+
+def check_query():
+    """(compiled, site) of the debug build's bounds checks (sq_check_query): whether
+    the loaded library has them, and the site of a failed check since the last
+    query (0: none), which it clears.  Host-synchronous."""
+    c, site = ctypes.c_int(), ctypes.c_int()
+    _check(lib.sq_check_query(ctypes.byref(c), ctypes.byref(site)), "sq_check_query")
+    return bool(c.value), int(site.value)
 
 
 def profile_enable(on: bool = True):

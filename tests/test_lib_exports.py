@@ -33,6 +33,21 @@ def test_library_exports_every_declared_symbol():
         assert re.search(rf"\bT {n}$", nm, re.M), n
 
 
+def test_checked_build_exports_the_same_symbols():
+    """The debug build with bounds checks (-DSQR_CHECK, libsqr_check.so) has the same
+    boundary; the normal library answers sq_check_query with "not compiled" and
+    makes no CUDA call doing so (it works without a GPU)."""
+    from paper_2511_17361_gb300 import _build
+    path = _build.build(check=True)
+    assert os.path.basename(path) == "libsqr_check.so"
+    nm = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    for n in _declared():
+        assert re.search(rf"\bT {n}$", nm, re.M), n
+    from paper_2511_17361_gb300 import sqr
+    assert os.path.basename(sqr.LIB_PATH) == "libsqr.so"
+    assert sqr.check_query() == (False, 0)
+
+
 def test_library_is_sm103a_only():
     from paper_2511_17361_gb300 import _build
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
