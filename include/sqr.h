@@ -298,17 +298,19 @@ typedef struct {
  *     on the six-camera frame; sq_autotune measures both on a given batch). */
 enum { SQ_BWD_DEFAULT = 0, SQ_BWD_RAY_MAJOR = 1, SQ_BWD_PRIMITIVE_MAJOR = 2 };
 
-/* Launch configuration: lanes (= samples marched together) per ray in the
- * forward (4, 8 or 16), warps per CTA in the forward (1..8) and in the
- * ray-major backward (1..8, or 0: the count that keeps the most warps resident
- * for the batch's largest L, whose sample tables set the backward's shared
- * memory), and the backward order (SQ_BWD_*).  The defaults are {4, 8, 0,
- * SQ_BWD_DEFAULT}. */
+/* Launch configuration: lanes (= samples marched together, the sample chunk)
+ * per ray in the forward (4, 8 or 16), warps per CTA in the forward (1..8) and
+ * in the ray-major backward (1..8, or 0: the count that keeps the most warps
+ * resident for the batch's largest L, whose sample tables set the backward's
+ * shared memory), the backward order (SQ_BWD_*), and the forward's ray tile: the
+ * consecutive rays a lane group takes from the batch's work queue at a time
+ * (1..64; 0 = 1).  The defaults are {4, 8, 0, SQ_BWD_DEFAULT, 1}. */
 typedef struct {
     int fwd_lanes_per_ray;
     int fwd_warps_per_cta;
     int bwd_warps_per_cta;
     int bwd_order;
+    int fwd_ray_tile;
 } sq_tuning_t;
 
 /* Workspace bytes for sq_render_batched / sq_autotune on these scenes; when
@@ -321,13 +323,13 @@ size_t sq_batched_workspace_size(const sq_scene_t* scenes, int n_scenes);
 sq_status_t sq_render_batched(int op, const sq_scene_t* scenes, int n_scenes, const sq_tuning_t* tuning,
                               void* workspace, size_t workspace_bytes, void* stream);
 
-/* Autotuner: times every forward configuration (lanes per ray x warps per CTA)
- * and, when every scene has saved state and cotangents, every backward one on
- * these scenes (reps timed launches each, CUDA events on the stream) and writes
- * the fastest to *best.  fwd_ms[4] / bwd_ms[4] (nullable) receive the mean
- * times of the candidates in the order {4,4},{4,8},{8,4},{8,8} (lanes, warps)
- * and ray-major with {0},{4},{8} warps per CTA (0 = automatic), then
- * primitive-major.
+/* Autotuner: times every forward configuration (lanes per ray x warps per CTA x
+ * ray tile) and, when every scene has saved state and cotangents, every backward
+ * one on these scenes (reps timed launches each, CUDA events on the stream) and
+ * writes the fastest to *best.  fwd_ms[8] / bwd_ms[4] (nullable) receive the
+ * mean times of the candidates in the order {4,4,1},{4,8,1},{8,4,1},{8,8,1},
+ * {4,4,16},{4,8,16},{8,4,16},{8,8,16} (lanes, warps, ray tile) and ray-major
+ * with {0},{4},{8} warps per CTA (0 = automatic), then primitive-major.
  * Host-synchronous and overwrites the scenes' outputs; call it outside any
  * stream capture. */
 sq_status_t sq_autotune(const sq_scene_t* scenes, int n_scenes, void* workspace, size_t workspace_bytes, void* stream,

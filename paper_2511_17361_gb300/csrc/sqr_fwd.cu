@@ -58,17 +58,20 @@ __device__ __forceinline__ float group_composite(float alpha, int s, int gbase, 
     return w;
 }
 
-template <int CP, int GS>
+template <int CP, int GS, bool TILED>
 __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
     static_assert(GS % SAVE_PS == 0 || SAVE_PS % GS == 0, "chunks and pages of the saved state nest");
     const int lane = threadIdx.x & 31;
     const int s = lane & (GS - 1), gbase = lane & ~(GS - 1);
     const unsigned gmask = (GS == 32) ? 0xffffffffu : ((1u << GS) - 1u);
 
-    // draw the group's first ray
+    // draw the group's first ray: the group takes B.ray_tile consecutive rays from
+    // the work counter at a time (a tile of neighbouring pixels) and marches them in turn
+    const int rt = TILED ? B.ray_tile : 1;
     int gn = 0;
-    if (s == 0) gn = atomicAdd(B.ctr, 1);
+    if (s == 0) gn = atomicAdd(B.ctr, rt);
     long long gr = __shfl_sync(0xffffffffu, gn, gbase);
+    long long tend = gr + rt;  // end of the group's tile
     int si = 0;
     long long r = 0;
     bool live = gr < B.total;
@@ -245,10 +248,12 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
                 if (S.save_n) S.save_n[r] = used_total;
             }
             int nr = 0;
-            if (fin && s == 0) nr = atomicAdd(B.ctr, 1);
+            const bool refill = fin && (!TILED || gr + 1 >= tend);
+            if (refill && s == 0) nr = atomicAdd(B.ctr, rt);
             nr = __shfl_sync(0xffffffffu, nr, gbase);
             if (fin) {
-                gr = nr;
+                gr = refill ? (long long)nr : gr + 1;
+                if (TILED && refill) tend = gr + rt;
                 live = gr < B.total;
                 if (live) {
                     si = scene_of(B, gr);
@@ -269,18 +274,25 @@ __global__ void __launch_bounds__(MAX_WARPS * 32) k_forward(Batch B) {
     }
 }
 
-template <int CP, int GS>
-sq_status_t launch_cp_gs(const Batch& B, int warps, cudaStream_t st) {
+template <int CP, int GS, bool TILED>
+sq_status_t launch_cp_gs_t(const Batch& B, int warps, cudaStream_t st) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward<CP, GS>, warps * 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward<CP, GS, TILED>, warps * 32, 0);
     if (e != cudaSuccess) return cuda_status(e, "k_forward occupancy");
     const long long per_block = (long long)warps * (32 / GS);
     const long long need = (B.total + per_block - 1) / per_block;
     long long blocks = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    SQ_LAUNCH("k_forward", st, k_forward<CP, GS><<<(int)blocks, warps * 32, 0, st>>>(B));
+    SQ_LAUNCH("k_forward", st, k_forward<CP, GS, TILED><<<(int)blocks, warps * 32, 0, st>>>(B));
     return SQ_OK;
+}
+
+// Ray tiles of more than one ray take a separate instance, so that the default
+// (one ray per fetch) is compiled without the tile bookkeeping.
+template <int CP, int GS>
+sq_status_t launch_cp_gs(const Batch& B, int warps, cudaStream_t st) {
+    return B.ray_tile > 1 ? launch_cp_gs_t<CP, GS, true>(B, warps, st) : launch_cp_gs_t<CP, GS, false>(B, warps, st);
 }
 
 template <int CP>

@@ -244,7 +244,7 @@ void saved_ptrs(const sq_rays_t* r, int C, void* saved, size_t bytes, SceneDesc&
     D.save_np = (int)np;
 }
 
-Tuning default_tuning() { return Tuning{4, 8, 0, SQ_BWD_PRIMITIVE_MAJOR}; }
+Tuning default_tuning() { return Tuning{4, 8, 0, SQ_BWD_PRIMITIVE_MAJOR, 1}; }
 
 }  // namespace
 
@@ -450,7 +450,7 @@ sq_status_t batched_impl(int op, const sq_scene_t* sc, int n, const Tuning& tn, 
     SQ_LAUNCH("k_write_desc", st, k_write_desc<<<1, 32, 0, st>>>(P, d, off, boff, gboff, poff));
     cudaError_t e = cudaMemsetAsync(ctr, 0, 256, st);
     if (e != cudaSuccess) return cuda_status(e, "memset counter");
-    Batch B{d, off, boff, n, total, ctr, lmax};
+    Batch B{d, off, boff, n, total, ctr, lmax, tn.fwd_tile};
     sq_status_t ls = (op == SQ_OP_FWD) ? launch_forward(B, cp, tn, st) : launch_sweep(B, cp, st);
     if (ls != SQ_OK) return ls;
     if (op == SQ_OP_BWD) {
@@ -533,6 +533,11 @@ sq_status_t batched_api_impl(int op, const sq_scene_t* sc, int n, const sq_tunin
         t.fwd_warps = tuning->fwd_warps_per_cta;
         t.bwd_warps = tuning->bwd_warps_per_cta;
         if (tuning->bwd_order != SQ_BWD_DEFAULT) t.bwd_order = tuning->bwd_order;
+        t.fwd_tile = tuning->fwd_ray_tile > 0 ? tuning->fwd_ray_tile : 1;
+    }
+    if (t.fwd_tile < 1 || t.fwd_tile > 64) {
+        set_last_error("forward ray tile %d not supported (1..64)", t.fwd_tile);
+        return SQ_ERR_INVALID_ARG;
     }
     if (t.bwd_order != SQ_BWD_RAY_MAJOR && t.bwd_order != SQ_BWD_PRIMITIVE_MAJOR) {
         set_last_error("backward order %d not supported", t.bwd_order);
@@ -546,7 +551,8 @@ sq_status_t batched_api_impl(int op, const sq_scene_t* sc, int n, const sq_tunin
 // stream and keeps the fastest of each.  Host-synchronous.
 sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes, cudaStream_t st, sq_tuning_t* best,
                           float* fwd_ms, float* bwd_ms, int reps) {
-    const Tuning fcand[4] = {{4, 4, 8}, {4, 8, 8}, {8, 4, 8}, {8, 8, 8}};
+    const Tuning fcand[8] = {{4, 4, 8, 0, 1},  {4, 8, 8, 0, 1},  {8, 4, 8, 0, 1},  {8, 8, 8, 0, 1},
+                             {4, 4, 8, 0, 16}, {4, 8, 8, 0, 16}, {8, 4, 8, 0, 16}, {8, 8, 8, 0, 16}};
     // ray-major with 0 (the most resident warps for the batch's L), 4 or 8 warps per
     // CTA, then primitive-major
     const int bcand[4] = {0, 4, 8, 0};
@@ -563,11 +569,13 @@ sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes
     sq_status_t s = SQ_OK;
     float bestf = 1e30f, bestb = 1e30f;
     Tuning tb = default_tuning();
-    for (int c = 0; c < 4 && s == SQ_OK; ++c) {
-        s = batched_impl(SQ_OP_FWD, sc, n, fcand[c], ws, ws_bytes, st);  // warm-up
+    for (int c = 0; c < 8 && s == SQ_OK; ++c) {
+        Tuning fc = fcand[c];
+        fc.bwd_order = tb.bwd_order;
+        s = batched_impl(SQ_OP_FWD, sc, n, fc, ws, ws_bytes, st);  // warm-up
         if (s != SQ_OK) break;
         cudaEventRecord(e0, st);
-        for (int r = 0; r < reps && s == SQ_OK; ++r) s = batched_impl(SQ_OP_FWD, sc, n, fcand[c], ws, ws_bytes, st);
+        for (int r = 0; r < reps && s == SQ_OK; ++r) s = batched_impl(SQ_OP_FWD, sc, n, fc, ws, ws_bytes, st);
         cudaEventRecord(e1, st);
         if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
             s = cuda_status(e, "autotune sync");
@@ -579,8 +587,9 @@ sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes
         if (fwd_ms) fwd_ms[c] = ms;
         if (ms < bestf) {
             bestf = ms;
-            tb.fwd_lanes = fcand[c].fwd_lanes;
-            tb.fwd_warps = fcand[c].fwd_warps;
+            tb.fwd_lanes = fc.fwd_lanes;
+            tb.fwd_warps = fc.fwd_warps;
+            tb.fwd_tile = fc.fwd_tile;
         }
     }
     if (s == SQ_OK) s = batched_impl(SQ_OP_FWD, sc, n, tb, ws, ws_bytes, st);  // saved state for the backward
@@ -616,6 +625,7 @@ sq_status_t autotune_impl(const sq_scene_t* sc, int n, void* ws, size_t ws_bytes
     best->fwd_warps_per_cta = tb.fwd_warps;
     best->bwd_warps_per_cta = tb.bwd_warps;
     best->bwd_order = tb.bwd_order;
+    best->fwd_ray_tile = tb.fwd_tile;
     return SQ_OK;
 }
 

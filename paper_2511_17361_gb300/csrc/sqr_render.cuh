@@ -80,6 +80,7 @@ struct Batch {
     long long total;
     int* ctr;
     int lmax;  // largest L of the batch
+    int ray_tile = 1;  // forward: consecutive rays a lane group takes from the work counter at a time
 };
 
 __device__ __forceinline__ int scene_of(const Batch& B, long long g) {
@@ -106,6 +107,7 @@ struct Tuning {
     int fwd_warps;  // warps per CTA, forward: 4 or 8
     int bwd_warps;  // warps per CTA, ray-major backward: 1..8, or 0 for the count that keeps the most warps resident
     int bwd_order;  // SQ_BWD_RAY_MAJOR or SQ_BWD_PRIMITIVE_MAJOR
+    int fwd_tile;   // consecutive rays a forward lane group takes from the work queue at a time
 };
 
 // Primitive-major backward (Sec. 3.3.3, Processes 2-3): the primitives of all

@@ -64,7 +64,7 @@ class SqScene(ctypes.Structure):
 
 class SqTuning(ctypes.Structure):
     _fields_ = [("fwd_lanes_per_ray", ctypes.c_int), ("fwd_warps_per_cta", ctypes.c_int),
-                ("bwd_warps_per_cta", ctypes.c_int), ("bwd_order", ctypes.c_int)]
+                ("bwd_warps_per_cta", ctypes.c_int), ("bwd_order", ctypes.c_int), ("fwd_ray_tile", ctypes.c_int)]
 
 
 class SqrError(RuntimeError):
@@ -375,7 +375,7 @@ def render_bwd(prims: dict, index: Index, grid: dict, rays: Rays, grad_depth, gr
             sc.pair_visits = _ptr(pair_visits)
         arr = (SqScene * 1)(sc)
         ws = _ws.get("bwd", lib.sq_batched_workspace_size(arr, 1), device)
-        tn = SqTuning(4, 8, 0, order)
+        tn = SqTuning(4, 8, 0, order, 1)
         _check(lib.sq_render_batched(SQ_OP_BWD, arr, 1, ctypes.byref(tn), _ptr(ws), ws.numel(), _stream()),
                "sq_render_batched")
         return out
@@ -598,7 +598,8 @@ def render_batched(op: int, scenes, tuning: dict | None = None):
     device = scenes[0].prims["means"].device
     ws = _ws.get("batched", lib.sq_batched_workspace_size(arr, len(scenes)), device)
     tn = None if tuning is None else SqTuning(tuning["fwd_lanes_per_ray"], tuning["fwd_warps_per_cta"],
-                                              tuning["bwd_warps_per_cta"], tuning.get("bwd_order", SQ_BWD_DEFAULT))
+                                              tuning["bwd_warps_per_cta"], tuning.get("bwd_order", SQ_BWD_DEFAULT),
+                                              tuning.get("fwd_ray_tile", 1))
     _check(lib.sq_render_batched(op, arr, len(scenes), ctypes.byref(tn) if tn else None, _ptr(ws), ws.numel(),
                                  _stream()), "sq_render_batched")
 
@@ -629,12 +630,13 @@ def autotune(scenes, reps: int = 3, use_cache: bool = True) -> dict:
     device = scenes[0].prims["means"].device
     ws = _ws.get("batched", lib.sq_batched_workspace_size(arr, len(scenes)), device)
     best = SqTuning()
-    fms = (ctypes.c_float * 4)()
+    fms = (ctypes.c_float * 8)()
     bms = (ctypes.c_float * 4)()
     _check(lib.sq_autotune(arr, len(scenes), _ptr(ws), ws.numel(), _stream(), reps, ctypes.byref(best), fms, bms),
            "sq_autotune")
     out = {"fwd_lanes_per_ray": best.fwd_lanes_per_ray, "fwd_warps_per_cta": best.fwd_warps_per_cta,
-           "bwd_warps_per_cta": best.bwd_warps_per_cta, "bwd_order": best.bwd_order, "fwd_ms": list(fms),
+           "bwd_warps_per_cta": best.bwd_warps_per_cta, "bwd_order": best.bwd_order,
+           "fwd_ray_tile": best.fwd_ray_tile, "fwd_ms": list(fms),
            "bwd_ms": list(bms)}
     if use_cache:
         cache[key] = out

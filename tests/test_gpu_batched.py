@@ -88,13 +88,13 @@ def test_batched_scene_against_oracle(sqr):
             check_grad(sc.grads[k].cpu().numpy(), ref[k], k)
 
 
-@pytest.mark.parametrize("lanes,fw,bw", [(4, 4, 4), (8, 8, 8), (16, 4, 2), (4, 8, 0)])
-def test_every_tuning_gives_the_same_render(sqr, lanes, fw, bw):
+@pytest.mark.parametrize("lanes,fw,bw,tile", [(4, 4, 4, 1), (8, 8, 8, 16), (16, 4, 2, 3), (4, 8, 0, 64)])
+def test_every_tuning_gives_the_same_render(sqr, lanes, fw, bw, tile):
     scenes, _ = _scenes(sqr, seed=2)
     sqr.render_batched(sqr.SQ_OP_FWD, scenes)
     sqr.render_batched(sqr.SQ_OP_BWD, scenes)
     base = [(sc.depth.clone(), sc.sem.clone(), {k: v.clone() for k, v in sc.grads.items()}) for sc in scenes]
-    tn = {"fwd_lanes_per_ray": lanes, "fwd_warps_per_cta": fw, "bwd_warps_per_cta": bw}
+    tn = {"fwd_lanes_per_ray": lanes, "fwd_warps_per_cta": fw, "bwd_warps_per_cta": bw, "fwd_ray_tile": tile}
     sqr.render_batched(sqr.SQ_OP_FWD, scenes, tn)
     sqr.render_batched(sqr.SQ_OP_BWD, scenes, tn)
     torch.cuda.synchronize()
@@ -111,14 +111,22 @@ def test_autotuner_picks_a_measured_candidate(sqr):
     assert best["fwd_lanes_per_ray"] in (4, 8) and best["fwd_warps_per_cta"] in (4, 8)
     assert best["bwd_warps_per_cta"] in (0, 4, 8)
     assert all(ms > 0 for ms in best["fwd_ms"]) and all(ms > 0 for ms in best["bwd_ms"])
-    cands = [(4, 4), (4, 8), (8, 4), (8, 8)]
-    i = cands.index((best["fwd_lanes_per_ray"], best["fwd_warps_per_cta"]))
+    cands = [(lanes, warps, tile) for tile in (1, 16) for lanes, warps in ((4, 4), (4, 8), (8, 4), (8, 8))]
+    assert len(best["fwd_ms"]) == 8
+    i = cands.index((best["fwd_lanes_per_ray"], best["fwd_warps_per_cta"], best["fwd_ray_tile"]))
     assert best["fwd_ms"][i] == min(best["fwd_ms"])
     assert len(best["bwd_ms"]) == 4 and best["bwd_order"] in (sqr.SQ_BWD_RAY_MAJOR, sqr.SQ_BWD_PRIMITIVE_MAJOR)
     bc = [(sqr.SQ_BWD_RAY_MAJOR, 0), (sqr.SQ_BWD_RAY_MAJOR, 4), (sqr.SQ_BWD_RAY_MAJOR, 8),
           (sqr.SQ_BWD_PRIMITIVE_MAJOR, 0)]
     j = bc.index((best["bwd_order"], best["bwd_warps_per_cta"]))
     assert best["bwd_ms"][j] == min(best["bwd_ms"])
+
+
+def test_ray_tile_outside_range_is_refused(sqr):
+    scenes, _ = _scenes(sqr, seed=2)
+    with pytest.raises(sqr.SqrError, match="ray tile"):
+        sqr.render_batched(sqr.SQ_OP_FWD, scenes, {"fwd_lanes_per_ray": 4, "fwd_warps_per_cta": 8,
+                                                   "bwd_warps_per_cta": 0, "fwd_ray_tile": 65})
 
 
 def test_cuda_graph_replay_matches_eager(sqr):
