@@ -46,10 +46,10 @@ def mix_peak(sfu, mix):
 # kernel source is unchanged (sha256 of the file holding it).
 NCU_TRAFFIC = {
     "k_backward": {"src": "sqr_bwd.cu", "src_sha": "34900eef8431e285", "bytes_per_launch": 310181888},
-    "k_forward": {"src": "sqr_fwd.cu", "src_sha": "a571a00694b870a5", "bytes_per_launch": 1760619520},
-    "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "7575a9aeb7331d3e", "bytes_per_launch": 1920553984},
-    "k_pm_tiles": {"src": "sqr_bwd_pm.cu", "src_sha": "85067280abf0773c", "bytes_per_launch": 3741314816},
-    "k_query_tiles": {"src": "sqr_query.cu", "src_sha": "36445990efc1317c", "bytes_per_launch": 1766400},
+    "k_forward": {"src": "sqr_fwd.cu", "src_sha": "2c7c5b9d99e1072e", "bytes_per_launch": 1759382784},
+    "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "1613935cf015e3f4", "bytes_per_launch": 1920811520},
+    "k_pm_tiles": {"src": "sqr_bwd_pm.cu", "src_sha": "85067280abf0773c", "bytes_per_launch": 3744836608},
+    "k_query_tiles": {"src": "sqr_query.cu", "src_sha": "9af6b77fa1963cdb", "bytes_per_launch": 1784576},
 }
 
 
