@@ -162,9 +162,10 @@ typedef struct {
 size_t sq_workspace_size(int op, const sq_prims_t* prims, const sq_grid_t* grid, const sq_rays_t* rays);
 
 /* Sec. 3.3.1 "Preliminary Construction": per-primitive voxel ranges, V_n by a
- * count pass, V_f by an exclusive scan, V_sq by a scatter and a per-voxel sort
- * by id.  Writes ranges, v_n, v_f, p_total, status and (when P <= capacity)
- * v_sq.  On P > capacity, status = SQ_ERR_CAPACITY, v_sq is left partial and
+ * count pass, V_f by an exclusive scan, V_sq sorted by id: written by voxel
+ * tiles, each voxel appending in id order the primitives whose range holds it
+ * (grids up to 65,535 voxels per axis), else by a scatter and a per-voxel sort.
+ * Writes ranges, v_n, v_f, p_total, status and (when P <= capacity) v_sq.  On P > capacity, status = SQ_ERR_CAPACITY, v_sq is left partial and
  * p_total holds the needed capacity. */
 sq_status_t sq_build_index(const sq_prims_t* prims, const sq_grid_t* grid, const sq_index_opts_t* opts,
                            sq_index_t* index, void* workspace, size_t workspace_bytes, void* stream);
@@ -338,7 +339,11 @@ sq_status_t sq_autotune(const sq_scene_t* scenes, int n_scenes, void* workspace,
 /* Supp. A.4 voxelisation at every voxel centre p = lo + (i + 0.5) vs (FP32):
  *   density[v] = sum_{k in Q(v)} p_o(p, S_k) sigma_k, sem[v, :] = sum p_o c_k,
  *   label[v] = argmax_c sem[v, c] (lowest c on ties) if density >= tau, else
- *   n_classes ("free").  label is nullable (uint8, so n_classes <= 255). */
+ *   n_classes ("free").  label is nullable (uint8, so n_classes <= 255).  Every
+ *   voxel sums its list Q(v) in ascending id order; the sums are evaluated by
+ *   voxel tiles (the primitives whose voxel range meets the tile, staged in
+ *   shared memory) on grids up to 65,535 voxels per axis, else by lane groups
+ *   merging neighbouring voxels' lists.  The index's ranges and lists are read. */
 sq_status_t sq_query_grid(const sq_prims_t* prims, const sq_index_t* index, const sq_grid_t* grid, float tau,
                           float* density, float* sem, unsigned char* label, void* workspace, size_t workspace_bytes,
                           void* stream);
