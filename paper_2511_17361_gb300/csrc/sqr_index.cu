@@ -471,12 +471,14 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_sort(const int* __restrict_
 // one voxel per thread, and scans the packed voxel ranges in id order (rounds of
 // LT_ROUND ids, warp w the w-th window of LT_WIN ids, the warps' hits in warp
 // order being the round's hits in id order), each hit with the tile-local bit
-// masks of its x, y and z extent.  Every thread then walks the round's hits and
-// appends those whose range holds its voxel to the voxel's list: the list is
-// written in ascending id, exactly the sorted list of the primitives whose range
-// contains the voxel.  Each warp holds a 4 x 4 x 2 block of the tile.
+// masks of its x, y and z extent.  Every thread then walks the held hits (up to
+// LT_CAP, several rounds') and appends those whose range holds its voxel to the
+// voxel's list: the list is written in ascending id, exactly the sorted list of
+// the primitives whose range contains the voxel.  Each warp holds a 4 x 4 x 2
+// block of the tile.
 constexpr int LT_X = 8, LT_Y = 8, LT_Z = 4, LT_THREADS = LT_X * LT_Y * LT_Z;
 constexpr int LT_WIN = 128, LT_ROUND = LT_WIN * (LT_THREADS / 32);
+constexpr int LT_CAP = 2 * LT_ROUND;  // hits held before the voxels append them (a round adds at most LT_ROUND)
 static_assert(LT_THREADS == 256, "warps of 4 x 4 x 2 voxels");
 
 __device__ __forceinline__ unsigned lt_span(int lo, int hi) { return hi < lo ? 0u : (2u << hi) - (1u << lo); }
@@ -489,8 +491,8 @@ __global__ void __launch_bounds__(LT_THREADS) k_lists_tiles(const int4* __restri
                                                            int nz, int ntx, int nty, int ntz) {
     __shared__ int wid_[LT_THREADS / 32][LT_WIN];
     __shared__ unsigned wmsk[LT_THREADS / 32][LT_WIN];
-    __shared__ int lid[LT_ROUND];
-    __shared__ unsigned lmsk[LT_ROUND];
+    __shared__ int lid[LT_CAP];
+    __shared__ unsigned lmsk[LT_CAP];
     __shared__ int wtot[LT_THREADS / 32];
     if (*status != SQ_OK) return;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -506,6 +508,7 @@ __global__ void __launch_bounds__(LT_THREADS) k_lists_tiles(const int4* __restri
         const long long v = valid ? ((long long)ix * ny + iy) * nz + iz : 0;
         const long long vf = valid ? (long long)__ldg(v_f + v) : 0;
         int cnt = 0;
+        int base = 0;  // hits held in lid / lmsk (the same in every thread)
         for (int r0 = 0; r0 < n; r0 += LT_ROUND) {
             int wc = 0;
 #pragma unroll
@@ -541,22 +544,27 @@ __global__ void __launch_bounds__(LT_THREADS) k_lists_tiles(const int4* __restri
                 nc += c;
             }
             for (int j = lane; j < wc; j += 32) {
-                lid[before + j] = wid_[wid][j];
-                lmsk[before + j] = wmsk[wid][j];
+                lid[base + before + j] = wid_[wid][j];
+                lmsk[base + before + j] = wmsk[wid][j];
             }
+            base += nc;
             __syncthreads();
-            for (int j = 0; j < nc; ++j) {
-                if ((lmsk[j] & sel) == sel) {  // only valid voxels have their bits set
-                    const long long at = vf + cnt;
-                    const int k = lid[j];
-                    if (at < capacity) {
-                        v_sq[at] = k;
-                        if (v_flags) v_flags[at] = entry_flags(ranges, k, ix, iy, iz);
+            // the held hits, in id order, once the buffer could not take another round
+            if (base > LT_CAP - LT_ROUND || r0 + LT_ROUND >= n) {
+                for (int j = 0; j < base; ++j) {
+                    if ((lmsk[j] & sel) == sel) {  // only valid voxels have their bits set
+                        const long long at = vf + cnt;
+                        const int k = lid[j];
+                        if (at < capacity) {
+                            v_sq[at] = k;
+                            if (v_flags) v_flags[at] = entry_flags(ranges, k, ix, iy, iz);
+                        }
+                        ++cnt;
                     }
-                    ++cnt;
                 }
+                base = 0;
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
 }
