@@ -36,6 +36,19 @@ BWD_ORDER = 0  # SQ_BWD_DEFAULT; --bwd-order
 # and 5 ex2, the backward's partial derivatives add 4 rcp
 MUFU_MIX = {"fwd": {"ex2": 5, "lg2": 4, "rcp": 0}, "bwd": {"ex2": 5, "lg2": 4, "rcp": 4}}
 MUFU_PER_PAIR = {k: sum(v.values()) for k, v in MUFU_MIX.items()}
+# Nominal FP32 operations per pair for the FP32-pipe bound: the forward's transform,
+# f and class sums (about 45), the backward about twice that.
+FP32_PER_PAIR = {"fwd": 45, "bwd": 90}
+
+
+def _fp32_pipe(dev, pairs, per_pair, ms):
+    """The FP32-pipe bound of a pair kernel: pairs x per_pair FP32 operations in ms
+    against 128 FP32 lanes per clock per SM at the top clock (2070 MHz)."""
+    import torch
+    peak = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2070e6 / 1e9
+    achieved = pairs * per_pair / (ms / 1e3) / 1e9
+    return {"ops_per_pair": per_pair, "pairs": pairs, "peak": peak, "unit": "GFP32op/s", "achieved": achieved,
+            "frac": achieved / peak}
 
 
 def mix_peak(sfu, mix):
@@ -381,6 +394,9 @@ def run_mine(args):
     sm_count = props.multi_processor_count
     peak_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     nominal = sm_count * 16 * peak_mhz * 1e6 / 1e9  # G MUFU ops / s
+    # the FP32-pipe bound beside it: FP32_PER_PAIR over 128 FP32 lanes per clock per
+    # SM at the top clock
+    fp32_peak = sm_count * 128 * peak_mhz * 1e6 / 1e9  # G FP32 ops / s
     sfu = {op: sqr.measure_sfu(op) / 1e9 for op in ("ex2", "lg2", "rcp")}
     pair_kernels = {}
     for kname in ("k_forward", "k_backward", "k_pm_tiles"):
@@ -395,7 +411,11 @@ def run_mine(args):
                                "unit": "GMUFUop/s", "frac": achieved / peak, "frac_evaluated": achieved / peak,
                                "frac_survey": Q * 9 / (k_mean_ms / 1e3) / 1e9 / nominal,
                                "mufu_per_pair": mufu, "pairs_evaluated": q_eval, "pairs_Q": Q,
-                               "traffic": _traffic(kname), "kernel_ms_per_launch": k_mean_ms}
+                               "traffic": _traffic(kname), "kernel_ms_per_launch": k_mean_ms,
+                               "fp32_pipe": {"ops_per_pair": FP32_PER_PAIR[kind], "pairs": Q, "peak": fp32_peak,
+                                             "unit": "GFP32op/s",
+                                             "achieved": Q * FP32_PER_PAIR[kind] / (k_mean_ms / 1e3) / 1e9,
+                                             "frac": Q * FP32_PER_PAIR[kind] / (k_mean_ms / 1e3) / 1e9 / fp32_peak}}
     # the dominant kernel: the longer of the pair-evaluating kernels
     kdom = max(pair_kernels, key=lambda k: pair_kernels[k]["kernel_ms_per_launch"]) if pair_kernels else None
     roof = dict(pair_kernels[kdom]) if kdom else None
@@ -553,9 +573,11 @@ def query_result(sqr, dev, steps, warmup, sfu=None):
             "backward": {"what": "voxel CE + BCE losses (sq_loss_voxel) and the query backward of their gradients",
                          "ms_per_step": ms_bwd, "value": nvox / (ms_bwd / 1e3), "unit": "voxels/s",
                          "roofline": {"bound": "alu", "kernel": "k_query_bwd", "achieved": achieved_b,
-                                      "peak": peak_b, "unit": "GMUFUop/s", "frac": achieved_b / peak_b}},
+                                      "peak": peak_b, "unit": "GMUFUop/s", "frac": achieved_b / peak_b,
+                                      "fp32_pipe": _fp32_pipe(dev, P, FP32_PER_PAIR["bwd"], kb_ms)}},
             "roofline": {"bound": "alu", "kernel": qk, "achieved": achieved, "peak": peak_f,
-                         "unit": "GMUFUop/s", "frac": achieved / peak_f, "traffic": _traffic(qk)},
+                         "unit": "GMUFUop/s", "frac": achieved / peak_f, "traffic": _traffic(qk),
+                         "fp32_pipe": _fp32_pipe(dev, P, FP32_PER_PAIR["fwd"], k_ms)},
             "sfu_measured_Gops": sfu,
             "hbm": {"kernel": qk, "bound": "hbm", "algorithmic_bytes": hbm_bytes,
                     "achieved_GBps": hbm_bytes / (k_ms / 1e3) / 1e9,
