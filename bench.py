@@ -58,7 +58,7 @@ def mix_peak(sfu, mix):
 # DRAM traffic per launch from the committed ncu summaries, valid only while the
 # kernel source is unchanged (sha256 of the file holding it).
 NCU_TRAFFIC = {
-    "k_backward": {"src": "sqr_bwd.cu", "src_sha": "34900eef8431e285", "bytes_per_launch": 310181888},
+    "k_backward": {"src": "sqr_bwd.cu", "src_sha": "1613935cf015e3f4", "bytes_per_launch": 309359616},
     "k_forward": {"src": "sqr_fwd.cu", "src_sha": "2c7c5b9d99e1072e", "bytes_per_launch": 1759382784},
     "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "1613935cf015e3f4", "bytes_per_launch": 1920811520},
     "k_pm_tiles": {"src": "sqr_bwd_pm.cu", "src_sha": "85067280abf0773c", "bytes_per_launch": 3744836608},
