@@ -412,10 +412,11 @@ def run_mine(args):
                                "frac_survey": Q * 9 / (k_mean_ms / 1e3) / 1e9 / nominal,
                                "mufu_per_pair": mufu, "pairs_evaluated": q_eval, "pairs_Q": Q,
                                "traffic": _traffic(kname), "kernel_ms_per_launch": k_mean_ms,
-                               "fp32_pipe": {"ops_per_pair": FP32_PER_PAIR[kind], "pairs": Q, "peak": fp32_peak,
+                               "fp32_pipe": {"ops_per_pair": FP32_PER_PAIR[kind], "pairs": q_eval, "peak": fp32_peak,
                                              "unit": "GFP32op/s",
-                                             "achieved": Q * FP32_PER_PAIR[kind] / (k_mean_ms / 1e3) / 1e9,
-                                             "frac": Q * FP32_PER_PAIR[kind] / (k_mean_ms / 1e3) / 1e9 / fp32_peak}}
+                                             "achieved": q_eval * FP32_PER_PAIR[kind] / (k_mean_ms / 1e3) / 1e9,
+                                             "frac": q_eval * FP32_PER_PAIR[kind] / (k_mean_ms / 1e3) / 1e9 /
+                                             fp32_peak}}
     # the dominant kernel: the longer of the pair-evaluating kernels
     kdom = max(pair_kernels, key=lambda k: pair_kernels[k]["kernel_ms_per_launch"]) if pair_kernels else None
     roof = dict(pair_kernels[kdom]) if kdom else None
