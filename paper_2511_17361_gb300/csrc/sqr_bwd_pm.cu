@@ -15,9 +15,11 @@
 //   k_pm_tiles  (Process 3) persistent blocks (4 per SM) take tiles from a counter:
 //               for each candidate pixel a conservative slab test, then the exact
 //               sample interval of its ray inside the box (the same FP32
-//               sample/voxel rule the forward used, an estimate moved onto the
-//               exact boundary, a binary search as the fallback), then the pass's
-//               pairs split evenly over the threads, each accumulating the partial
+//               sample/voxel rule the forward used: the interval the six plane
+//               crossings estimate, accepted when the rule puts its end samples
+//               inside the box and their outer neighbours outside, else per-axis
+//               searches from the estimates, a binary search as their fallback),
+//               then the pass's pairs split evenly over the threads, each accumulating the partial
 //               derivatives of its pairs; a block reduction writes the tile's sums;
 //   k_pm_final  sums each primitive's tiles in tile order into its accumulator.
 // Every sum is taken in a fixed order, so the gradients are bitwise reproducible
@@ -315,19 +317,25 @@ __device__ __noinline__ int lead_search(const float* ts, int Le, float o, float 
     return n;
 }
 
-// The same prefix length, starting from an estimate: the ray meets the plane
-// u = thr at t* = (lo + thr vs - o) / d (id: an approximate 1 / d), and with
-// evenly spaced samples about (t* - t_0) / dt samples lie before it.  The
-// estimate is moved to the exact boundary by testing the predicate itself (at
-// most a few steps each way, then the binary search), so the result never
-// depends on the estimate's rounding.
+// Estimated prefix length: the ray meets the plane u = thr at t* = (lo + thr vs -
+// o) / d (id: an approximate 1 / d), and with evenly spaced samples about
+// (t* - t_0) / dt samples lie before it.
+__device__ __forceinline__ int lead_est(float o, float id, float glo, float vs, float thr, float t0, float inv_dt,
+                                        int Le) {
+    const float tstar = (fmaf(thr, vs, glo) - o) * id;
+    const float fe = ceilf((tstar - t0) * inv_dt);
+    return (int)fminf(fmaxf(fe, 0.f), (float)Le);
+}
+
+// The same prefix length, starting from the estimate, which is moved to the
+// exact boundary by testing the predicate itself (at most a few steps each way,
+// then the binary search), so the result never depends on the estimate's
+// rounding.
 __device__ __forceinline__ int lead(const float* ts, int Le, float o, float d, float id, float glo, float inv,
                                     float vs, float thr, bool neg, float t0, float inv_dt) {
     if (Le <= 0) return 0;
     if (d == 0.f) return below(ts, 0, o, d, glo, inv, thr, neg) ? Le : 0;  // u_j constant
-    const float tstar = (fmaf(thr, vs, glo) - o) * id;
-    const float fe = ceilf((tstar - t0) * inv_dt);
-    int n = (int)fminf(fmaxf(fe, 0.f), (float)Le);
+    int n = lead_est(o, id, glo, vs, thr, t0, inv_dt, Le);
     for (int k = 0; n > 0 && !below(ts, n - 1, o, d, glo, inv, thr, neg); ++k) {
         if (k == 4) return lead_search(ts, Le, o, d, glo, inv, thr, neg);
         --n;
@@ -339,12 +347,26 @@ __device__ __forceinline__ int lead(const float* ts, int Le, float o, float d, f
     return n;
 }
 
+// Sample j's voxel (the forward's FP32 rule) inside the box [blo, bhi) on every axis.
+__device__ __forceinline__ bool in_box(const float* ts, int j, const float o[3], const float d[3], const GridC& g,
+                                       const float blo[3], const float bhi[3]) {
+    const float tj = ts[j];
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float u = __fmul_rn(__fsub_rn(__fadd_rn(o[a], __fmul_rn(tj, d[a])), g.lo[a]), g.inv_vs[a]);
+        in = in && u >= blo[a] && u < bhi[a];
+    }
+    return in;
+}
+
 struct PmSmem {
-    float d[3][PM_CHUNK];        // ray direction of each candidate slot
+    // the pass's non-empty runs in candidate order, run e at index e
+    float d[3][PM_CHUNK];        // ray direction
     float cd[PM_CHUNK];          // <dL/dS of the ray, c_k>
     int r[PM_CHUNK];             // ray index in its scene
     int jc[PM_CHUNK];            // first sample of the run | camera << 10
-    int pre[PM_CHUNK + 1];       // exclusive prefix of the run lengths (pairs)
+    int pre[PM_CHUNK + 1];       // exclusive prefix of the run lengths (pairs); the pass's pairs from nnz on
     float wsum[PM_CHUNK];        // sum over the run of w_j p_o
     float ts[SQ_MAX_SAMPLES];    // sample distances of the tile's scene
     int4 rc[PM_SMCAM];           // the primitive's rectangles (n_cam <= PM_SMCAM)
@@ -352,8 +374,7 @@ struct PmSmem {
     int head_slot[PM_THREADS];   // run a thread's slice starts inside (-1: none)
     float head_val[PM_THREADS];  // that thread's part of the run's w p_o sum
     float red[PM_WARPS][NRAW];
-    float4 cacc[PM_WARPS][PM_CSUB][8];  // class gradient partials: per warp and slot lane group, classes 4q..4q+3
-    int nz[PM_CHUNK];            // the pass's non-empty slots, in slot order
+    float4 cacc[PM_WARPS][PM_CSUB][8];  // class gradient partials: per warp and run lane group, classes 4q..4q+3
     alignas(16) float lp[32];    // class vector of the tile's primitive (lpad row)
     int wtot[PM_WARPS];
     int ztot[PM_WARPS];
@@ -424,9 +445,9 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
         __syncthreads();
 
         for (int cb = cbeg; cb < cend; cb += PM_CHUNK) {
-            // ---- candidates -> runs: thread tid holds slots tid * PM_CPT + i, slot q
-            // being candidate cb + q.  Three stages over the thread's candidates, so
-            // that the loads of all of them are in flight together.
+            // ---- candidates -> runs: thread tid holds candidates cb + tid * PM_CPT + i.
+            // Three stages over the thread's candidates, so that the loads of all of
+            // them are in flight together.
             int rr[PM_CPT], cam[PM_CPT], Le[PM_CPT], j0s[PM_CPT], len[PM_CPT];
             float4 dv[PM_CPT];
 #pragma unroll
@@ -497,36 +518,56 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
                     }
                 }
                 if (!(te <= tx)) continue;
+                // The samples inside the box form one interval (u_j is monotone in j on
+                // every axis), so an interval whose end samples pass the voxel rule and
+                // whose outer neighbours fail it is the exact one: the plane-crossing
+                // estimates almost always give it, and the per-axis searches run only
+                // when the check fails (a sample within rounding of a plane, a ray
+                // parallel to an axis, an empty estimate).
                 int j0 = 0, j1 = Le[i];
+                bool fast = false;
+                if (id[0] != 0.f && id[1] != 0.f && id[2] != 0.f) {
+                    int j0e = 0, j1e = Le[i];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const bool neg = d[a] < 0.f;
-                    j0 = max(j0, lead(sh.ts, Le[i], o[a], d[a], id[a], S.g.lo[a], S.g.inv_vs[a], S.g.vs[a],
-                                      neg ? bhi[a] : blo[a], neg, t0, inv_dt));
+                    for (int a = 0; a < 3; ++a) {
+                        const bool neg = d[a] < 0.f;
+                        j0e = max(j0e, lead_est(o[a], id[a], S.g.lo[a], S.g.vs[a], neg ? bhi[a] : blo[a], t0, inv_dt,
+                                                Le[i]));
+                        j1e = min(j1e, lead_est(o[a], id[a], S.g.lo[a], S.g.vs[a], neg ? blo[a] : bhi[a], t0, inv_dt,
+                                                Le[i]));
+                    }
+                    if (j0e < j1e && in_box(sh.ts, j0e, o, d, S.g, blo, bhi) &&
+                        in_box(sh.ts, j1e - 1, o, d, S.g, blo, bhi) &&
+                        (j0e == 0 || !in_box(sh.ts, j0e - 1, o, d, S.g, blo, bhi)) &&
+                        (j1e == Le[i] || !in_box(sh.ts, j1e, o, d, S.g, blo, bhi))) {
+                        j0 = j0e;
+                        j1 = j1e;
+                        fast = true;
+                    }
                 }
-                if (j0 >= j1) continue;
+                if (!fast) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const bool neg = d[a] < 0.f;
-                    j1 = min(j1, lead(sh.ts, Le[i], o[a], d[a], id[a], S.g.lo[a], S.g.inv_vs[a], S.g.vs[a],
-                                      neg ? blo[a] : bhi[a], neg, t0, inv_dt));
+                    for (int a = 0; a < 3; ++a) {
+                        const bool neg = d[a] < 0.f;
+                        j0 = max(j0, lead(sh.ts, Le[i], o[a], d[a], id[a], S.g.lo[a], S.g.inv_vs[a], S.g.vs[a],
+                                          neg ? bhi[a] : blo[a], neg, t0, inv_dt));
+                    }
+                    if (j0 >= j1) continue;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const bool neg = d[a] < 0.f;
+                        j1 = min(j1, lead(sh.ts, Le[i], o[a], d[a], id[a], S.g.lo[a], S.g.inv_vs[a], S.g.vs[a],
+                                          neg ? blo[a] : bhi[a], neg, t0, inv_dt));
+                    }
+                    if (j1 <= j0) continue;
                 }
-                if (j1 <= j0) continue;
                 len[i] = j1 - j0;
                 j0s[i] = j0;
                 tl_sum += len[i];
             }
-#pragma unroll
-            for (int i = 0; i < PM_CPT; ++i) {  // slot data of the non-empty runs
-                if (len[i] == 0) continue;
-                const int slot = tid * PM_CPT + i;
-                sh.d[0][slot] = dv[i].x;
-                sh.d[1][slot] = dv[i].y;
-                sh.d[2][slot] = dv[i].z;
-                sh.r[slot] = rr[i];
-                sh.jc[slot] = j0s[i] | (cam[i] << 10);
-            }
-            // ---- exclusive scan of the run lengths in slot order; list the non-empty slots
+            // ---- exclusive scans, in candidate order, of the run lengths and of the
+            // non-empty runs: the runs' data go to shared memory at their index, so the
+            // walk and the class stages take runs e = 0 .. nnz - 1 with no empty slots
             int npairs, nnz;
             {
                 int nzt = 0;
@@ -553,14 +594,20 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
                 }
                 int pl = wl + il - tl_sum, zp = zw + zl - nzt;
 #pragma unroll
-                for (int i = 0; i < PM_CPT; ++i) {
-                    sh.pre[tid * PM_CPT + i] = pl;
+                for (int i = 0; i < PM_CPT; ++i) {  // the non-empty runs' data at their index
+                    if (len[i] == 0) continue;
+                    sh.d[0][zp] = dv[i].x;
+                    sh.d[1][zp] = dv[i].y;
+                    sh.d[2][zp] = dv[i].z;
+                    sh.r[zp] = rr[i];
+                    sh.jc[zp] = j0s[i] | (cam[i] << 10);
+                    sh.pre[zp] = pl;
                     pl += len[i];
-                    if (len[i] > 0) sh.nz[zp++] = tid * PM_CPT + i;
+                    ++zp;
                 }
                 npairs = tl2;
                 tpairs += tl2;
-                if (tid == 0) sh.pre[PM_CHUNK] = tl2;
+                for (int e = nnz + tid; e <= PM_CHUNK; e += PM_THREADS) sh.pre[e] = tl2;  // bounds the run search
                 sh.head_slot[tid] = -1;
             }
             __syncthreads();
@@ -575,7 +622,7 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
                 constexpr int STEP = PM_WARPS * PM_CSUB;
                 for (int e = wid * PM_CSUB + sub; e < nnz; e += 2 * STEP) {
                     const int e2 = e + STEP;
-                    const int s1 = sh.nz[e], s2 = e2 < nnz ? sh.nz[e2] : -1;
+                    const int s1 = e, s2 = e2 < nnz ? e2 : -1;
                     float4 g1 = make_float4(0.f, 0.f, 0.f, 0.f), g2 = g1;
                     if (q < CP / 4) {
                         g1 = __ldg(S.pm_gs + (long long)sh.r[s1] * (CP / 4) + q);
@@ -626,16 +673,14 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
                     for (int i = 0; i < PM_NS; ++i) gq[i] = i < m ? gwr[jj + i] : make_float2(0.f, 0.f);
                     for (;;) {
                         const int pn = p + m;
-                        // the next step: same run, or the next non-empty slot; its loads
+                        // the next step: same run, or the next run; its loads
                         // are issued before this step's arithmetic
                         const bool more = pn < p1;
                         const bool sw = more && pn == rend;
                         int slot_n = slot, jj_n = jj + m, rend_n = rend;
                         const float2* gwr_n = gwr;
                         if (sw) {
-                            do {
-                                ++slot_n;
-                            } while (sh.pre[slot_n + 1] == sh.pre[slot_n]);
+                            ++slot_n;
                             jj_n = sh.jc[slot_n] & 1023;
                             rend_n = sh.pre[slot_n + 1];
                             gwr_n = S.gw + (long long)sh.r[slot_n] * L;
@@ -708,9 +753,8 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
                 if (q < CP / 4) {
                     float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
                     for (int e = wid * PM_CSUB + sub; e < nnz; e += PM_WARPS * PM_CSUB) {
-                        const int slot = sh.nz[e];
-                        const float wv = sh.wsum[slot];
-                        const float4 g4 = __ldg(S.pm_gs + (long long)sh.r[slot] * (CP / 4) + q);
+                        const float wv = sh.wsum[e];
+                        const float4 g4 = __ldg(S.pm_gs + (long long)sh.r[e] * (CP / 4) + q);
                         a.x = fmaf(wv, g4.x, a.x);
                         a.y = fmaf(wv, g4.y, a.y);
                         a.z = fmaf(wv, g4.z, a.z);
