@@ -327,15 +327,12 @@ __device__ __forceinline__ int lead_est(float o, float id, float glo, float vs, 
     return (int)fminf(fmaxf(fe, 0.f), (float)Le);
 }
 
-// The same prefix length, starting from the estimate, which is moved to the
-// exact boundary by testing the predicate itself (at most a few steps each way,
-// then the binary search), so the result never depends on the estimate's
-// rounding.
-__device__ __forceinline__ int lead(const float* ts, int Le, float o, float d, float id, float glo, float inv,
-                                    float vs, float thr, bool neg, float t0, float inv_dt) {
-    if (Le <= 0) return 0;
-    if (d == 0.f) return below(ts, 0, o, d, glo, inv, thr, neg) ? Le : 0;  // u_j constant
-    int n = lead_est(o, id, glo, vs, thr, t0, inv_dt, Le);
+// The same prefix length, starting from an estimate n (lead_est), which is moved
+// to the exact boundary by testing the predicate itself (at most a few steps each
+// way, then the binary search), so the result never depends on the estimate's
+// rounding; exact for any n in [0, Le], a ray parallel to the axis included.
+__device__ __forceinline__ int lead_at(const float* ts, int Le, float o, float d, float glo, float inv, float thr,
+                                       bool neg, int n) {
     for (int k = 0; n > 0 && !below(ts, n - 1, o, d, glo, inv, thr, neg); ++k) {
         if (k == 4) return lead_search(ts, Le, o, d, glo, inv, thr, neg);
         --n;
@@ -521,21 +518,23 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
                 // The samples inside the box form one interval (u_j is monotone in j on
                 // every axis), so an interval whose end samples pass the voxel rule and
                 // whose outer neighbours fail it is the exact one: the plane-crossing
-                // estimates almost always give it, and the per-axis searches run only
-                // when the check fails (a sample within rounding of a plane, a ray
-                // parallel to an axis, an empty estimate).
+                // estimates almost always give it, and the per-axis searches, started
+                // from the same estimates, run only when the check fails (a sample
+                // within rounding of a plane, a ray parallel to an axis, an empty
+                // estimate).
                 int j0 = 0, j1 = Le[i];
                 bool fast = false;
-                if (id[0] != 0.f && id[1] != 0.f && id[2] != 0.f) {
-                    int j0e = 0, j1e = Le[i];
+                int ne[3], nx[3];  // estimated leads of the entry and exit planes
+                int j0e = 0, j1e = Le[i];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const bool neg = d[a] < 0.f;
-                        j0e = max(j0e, lead_est(o[a], id[a], S.g.lo[a], S.g.vs[a], neg ? bhi[a] : blo[a], t0, inv_dt,
-                                                Le[i]));
-                        j1e = min(j1e, lead_est(o[a], id[a], S.g.lo[a], S.g.vs[a], neg ? blo[a] : bhi[a], t0, inv_dt,
-                                                Le[i]));
-                    }
+                for (int a = 0; a < 3; ++a) {
+                    const bool neg = d[a] < 0.f;
+                    ne[a] = lead_est(o[a], id[a], S.g.lo[a], S.g.vs[a], neg ? bhi[a] : blo[a], t0, inv_dt, Le[i]);
+                    nx[a] = lead_est(o[a], id[a], S.g.lo[a], S.g.vs[a], neg ? blo[a] : bhi[a], t0, inv_dt, Le[i]);
+                    j0e = max(j0e, ne[a]);
+                    j1e = min(j1e, nx[a]);
+                }
+                if (id[0] != 0.f && id[1] != 0.f && id[2] != 0.f) {
                     if (j0e < j1e && in_box(sh.ts, j0e, o, d, S.g, blo, bhi) &&
                         in_box(sh.ts, j1e - 1, o, d, S.g, blo, bhi) &&
                         (j0e == 0 || !in_box(sh.ts, j0e - 1, o, d, S.g, blo, bhi)) &&
@@ -549,15 +548,15 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const bool neg = d[a] < 0.f;
-                        j0 = max(j0, lead(sh.ts, Le[i], o[a], d[a], id[a], S.g.lo[a], S.g.inv_vs[a], S.g.vs[a],
-                                          neg ? bhi[a] : blo[a], neg, t0, inv_dt));
+                        j0 = max(j0, lead_at(sh.ts, Le[i], o[a], d[a], S.g.lo[a], S.g.inv_vs[a], neg ? bhi[a] : blo[a],
+                                             neg, ne[a]));
                     }
                     if (j0 >= j1) continue;
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const bool neg = d[a] < 0.f;
-                        j1 = min(j1, lead(sh.ts, Le[i], o[a], d[a], id[a], S.g.lo[a], S.g.inv_vs[a], S.g.vs[a],
-                                          neg ? blo[a] : bhi[a], neg, t0, inv_dt));
+                        j1 = min(j1, lead_at(sh.ts, Le[i], o[a], d[a], S.g.lo[a], S.g.inv_vs[a], neg ? blo[a] : bhi[a],
+                                             neg, nx[a]));
                     }
                     if (j1 <= j0) continue;
                 }
@@ -673,18 +672,15 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
                     for (int i = 0; i < PM_NS; ++i) gq[i] = i < m ? gwr[jj + i] : make_float2(0.f, 0.f);
                     for (;;) {
                         const int pn = p + m;
-                        // the next step: same run, or the next run; its loads
-                        // are issued before this step's arithmetic
+                        // the next step: same run, or the next run (its data read every
+                        // step, selected without a branch); its loads are issued before
+                        // this step's arithmetic
                         const bool more = pn < p1;
                         const bool sw = more && pn == rend;
-                        int slot_n = slot, jj_n = jj + m, rend_n = rend;
-                        const float2* gwr_n = gwr;
-                        if (sw) {
-                            ++slot_n;
-                            jj_n = sh.jc[slot_n] & 1023;
-                            rend_n = sh.pre[slot_n + 1];
-                            gwr_n = S.gw + (long long)sh.r[slot_n] * L;
-                        }
+                        const int slot_n = slot + (sw ? 1 : 0);
+                        const int jcn = sh.jc[slot_n], rn = sh.r[slot_n], pren = sh.pre[slot_n + 1];
+                        const int jj_n = sw ? (jcn & 1023) : jj + m, rend_n = sw ? pren : rend;
+                        const float2* gwr_n = sw ? S.gw + (long long)rn * L : gwr;
                         const int se_n = min(rend_n, p1);
                         const int m_n = more ? min(PM_NS, se_n - pn) : 0;
                         float2 gq_n[PM_NS];
@@ -714,13 +710,11 @@ __global__ void __launch_bounds__(PM_THREADS, 4) k_pm_tiles(Batch B, PmArgs A) {
                             acc[12] = 0.f;
                         }
                         if (!more) break;
-                        if (sw) {
-                            jcs = sh.jc[slot_n];
-                            camera_origin(S, jcs >> 10, o);
+                        jcs = sh.jc[slot_n];
+                        camera_origin(S, jcs >> 10, o);
 #pragma unroll
-                            for (int a = 0; a < 3; ++a) d[a] = sh.d[a][slot_n];
-                            cd = sh.cd[slot_n];
-                        }
+                        for (int a = 0; a < 3; ++a) d[a] = sh.d[a][slot_n];
+                        cd = sh.cd[slot_n];
                         slot = slot_n;
                         jj = jj_n;
                         rend = rend_n;
