@@ -165,6 +165,78 @@ def test_full_frame_primitives_never_miss_a_run():
     assert _check(cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], kmax=12) > 10000
 
 
+def _runs_from_estimates(pr, grid, rig, t, kmax=None):
+    """For every (ray, primitive) of the scene: the samples whose FP32 voxel lies in
+    the primitive's box form one interval, and whenever k_pm_tiles' four voxel-rule
+    tests accept the interval the six plane-crossing estimates give (its end samples
+    inside the box, the samples just outside it outside), that interval is the exact
+    one.  Returns (runs, runs accepted by the tests)."""
+    ix = oracle.build_index(pr, grid)
+    ranges = ix["ranges"]
+    d_all, o_all = _rays(rig)
+    t = t.astype(f32)
+    L = len(t)
+    lo = np.asarray(grid["lo"], f32)
+    vs = np.asarray(grid["vs"], f32)
+    inv = (f32(1.0) / vs).astype(f32)
+    nf = np.asarray(grid["n"]).astype(f32)
+    inv_dt = f32((L - 1) / (t[-1] - t[0])) if L > 1 and t[-1] > t[0] else f32(0)
+    H, W = rig["H"], rig["W"]
+    prims = [k for k in range(len(pr["means"]) if kmax is None else kmax)
+             if ranges[k][1] >= ranges[k][0] and ranges[k][3] >= ranges[k][2] and ranges[k][5] >= ranges[k][4]]
+    runs = accepted = 0
+    for c in range(rig["n_cam"]):
+        d, o = d_all[c * H * W:(c + 1) * H * W], o_all[c * H * W:(c + 1) * H * W]
+        x = (o[:, None, :] + (t[None, :, None] * d[:, None, :]).astype(f32)).astype(f32)
+        u = ((x - lo).astype(f32) * inv).astype(f32)
+        inside = np.all((u >= 0) & (u < nf), -1)
+        idx = np.floor(np.where(inside[..., None], u, 0)).astype(np.int32)
+        rows = np.arange(H * W)
+        for k in prims:
+            r6 = ranges[k]
+            hit = inside & np.all((idx >= r6[[0, 2, 4]]) & (idx <= r6[[1, 3, 5]]), -1)
+            n_in = hit.sum(1)
+            has = n_in > 0
+            first = np.argmax(hit, 1)
+            last = L - 1 - np.argmax(hit[:, ::-1], 1)
+            assert np.all(n_in[has] == last[has] - first[has] + 1), f"primitive {k}: a run is not one interval"
+            runs += int(has.sum())
+            # the estimates, as k_pm_tiles forms them (an exact quotient stands in for the approximate 1 / d)
+            blo = np.asarray(r6[[0, 2, 4]], f32)
+            bhi = (np.asarray(r6[[1, 3, 5]]) + 1).astype(f32)
+            neg = d < 0
+            ok = np.all(d != 0, 1)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                def est(thr):
+                    ts = ((thr * vs + lo - o) / np.where(d != 0, d, f32(1))).astype(f32)
+                    return np.clip(np.ceil((ts - t[0]) * inv_dt), 0, L).astype(np.int64)
+                j0e = est(np.where(neg, bhi, blo)).max(1)
+                j1e = est(np.where(neg, blo, bhi)).min(1)
+            cand = ok & (j0e < j1e)
+            j0c, j1c = np.clip(j0e, 0, L - 1), np.clip(j1e - 1, 0, L - 1)
+            before = np.where(j0e > 0, hit[rows, np.clip(j0e - 1, 0, L - 1)], False)
+            after = np.where(j1e < L, hit[rows, np.clip(j1e, 0, L - 1)], False)
+            acc = cand & hit[rows, j0c] & hit[rows, j1c] & ~before & ~after
+            assert np.all(first[acc] == j0e[acc]) and np.all(last[acc] + 1 == j1e[acc]), \
+                f"primitive {k}, camera {c}: an accepted interval is not the run"
+            accepted += int(acc.sum())
+    return runs, accepted
+
+
+def test_confirmed_estimates_give_the_exact_run():
+    """The run ends k_pm_tiles takes without a search: on the ring scene and on the
+    six-camera frame's first 12 primitives (every ray, every sample), each run is one
+    interval, every interval the four tests accept is the run, and they accept nearly
+    all runs (the rest go to the per-axis searches)."""
+    pr, grid = synth.prims_driving(300, 24), synth.grid_spec(50, 50, 8)
+    rig, t = synth.rig_ring(n_cam=6, H=12, W=20, f=9.0), synth.sample_depths(40)
+    runs, accepted = _runs_from_estimates(pr, grid, rig, t)
+    assert runs > 500 and accepted >= 0.95 * runs
+    cfg = synth.make_config(1)
+    runs, accepted = _runs_from_estimates(cfg["prims"], cfg["grid"], cfg["rig"], cfg["t"], kmax=12)
+    assert runs > 10000 and accepted >= 0.95 * runs
+
+
 def test_box_sums_equal_brute_force():
     """The summed-volume box sums used by the pair-visit check equal direct sums
     over every inclusive range, empty ranges giving 0."""
