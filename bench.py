@@ -61,7 +61,7 @@ NCU_TRAFFIC = {
     "k_backward": {"src": "sqr_bwd.cu", "src_sha": "1613935cf015e3f4", "bytes_per_launch": 309359616},
     "k_forward": {"src": "sqr_fwd.cu", "src_sha": "2c7c5b9d99e1072e", "bytes_per_launch": 1759382784},
     "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "1613935cf015e3f4", "bytes_per_launch": 1920811520},
-    "k_pm_tiles": {"src": "sqr_bwd_pm.cu", "src_sha": "07fe0df84d7afc87", "bytes_per_launch": 3719922944},
+    "k_pm_tiles": {"src": "sqr_bwd_pm.cu", "src_sha": "7fc2f5f99959880c", "bytes_per_launch": 3747588864},
     "k_query_tiles": {"src": "sqr_query.cu", "src_sha": "9af6b77fa1963cdb", "bytes_per_launch": 1784576},
 }
 

@@ -19,8 +19,9 @@
 //               crossings estimate, accepted when the rule puts its end samples
 //               inside the box and their outer neighbours outside, else per-axis
 //               searches from the estimates, a binary search as their fallback),
-//               then the pass's pairs split evenly over the threads, each accumulating the partial
-//               derivatives of its pairs; a block reduction writes the tile's sums;
+//               then the pass's non-empty runs at their index and its pairs split
+//               evenly over the threads, each accumulating the partial derivatives
+//               of its pairs; a block reduction writes the tile's sums;
 //   k_pm_final  sums each primitive's tiles in tile order into its accumulator.
 // Every sum is taken in a fixed order, so the gradients are bitwise reproducible
 // (the ray-major path flushes with atomic adds).
