@@ -63,6 +63,7 @@ NCU_TRAFFIC = {
     "k_bwd_sweep": {"src": "sqr_bwd.cu", "src_sha": "1613935cf015e3f4", "bytes_per_launch": 1920811520},
     "k_pm_tiles": {"src": "sqr_bwd_pm.cu", "src_sha": "7fc2f5f99959880c", "bytes_per_launch": 3747588864},
     "k_query_tiles": {"src": "sqr_query.cu", "src_sha": "9af6b77fa1963cdb", "bytes_per_launch": 1784576},
+    "k_query_bwd": {"src": "sqr_query.cu", "src_sha": "9af6b77fa1963cdb", "bytes_per_launch": 56938752},
 }
 
 
@@ -575,6 +576,7 @@ def query_result(sqr, dev, steps, warmup, sfu=None):
                          "ms_per_step": ms_bwd, "value": nvox / (ms_bwd / 1e3), "unit": "voxels/s",
                          "roofline": {"bound": "alu", "kernel": "k_query_bwd", "achieved": achieved_b,
                                       "peak": peak_b, "unit": "GMUFUop/s", "frac": achieved_b / peak_b,
+                                      "traffic": _traffic("k_query_bwd"),
                                       "fp32_pipe": _fp32_pipe(dev, P, FP32_PER_PAIR["bwd"], kb_ms)}},
             "roofline": {"bound": "alu", "kernel": qk, "achieved": achieved, "peak": peak_f,
                          "unit": "GMUFUop/s", "frac": achieved / peak_f, "traffic": _traffic(qk),
