@@ -364,7 +364,9 @@ sq_status_t sq_query_grid_bwd(const sq_prims_t* prims, const sq_index_t* index, 
 /* Training loss of Supp. A.5 (Eq. 8) and its gradient w.r.t. the rendered maps:
  *   L = lambda_s * mean_r CE(softmax(sem[r]), label[r]) + lambda_d * mean_r (depth[r] - target[r])^2.
  * Writes loss (device scalar, overwritten), grad_depth [R], grad_sem [R, C].
- * labels are int32 in [0, C). */
+ * labels are int32 in [0, C); a label outside it makes the loss NaN (that ray's
+ * gradient row then has no one-hot term).  n_classes in [1, SQ_MAX_CLASSES],
+ * else SQ_ERR_INVALID_ARG. */
 sq_status_t sq_loss_ce_mse(const float* depth, const float* sem, const float* target_depth, const int* target_label,
                            long long n_rays, int n_classes, float lambda_s, float lambda_d, float* loss,
                            float* grad_depth, float* grad_sem, void* stream);

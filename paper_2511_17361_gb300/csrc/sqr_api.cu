@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include "sqr_common.cuh"
+#include "sqr_render.cuh"
 
 namespace sqr {
 
@@ -151,31 +152,83 @@ static sq_status_t check_scenes(const sq_scene_t* sc, int n) {
 namespace {
 constexpr int LOSS_THREADS = 256;
 
+constexpr int LOSS_WARPS = LOSS_THREADS / 32;
+
+// A warp takes 32 consecutive rays at a time: their semantic rows are read into
+// shared memory with coalesced loads (flat index i = lane + 32 k of the chunk, row
+// i / C, column i % C, stepped without division), each lane computes its ray's
+// softmax cross-entropy and gradient row there (row stride C | 1 words, so the
+// lanes' rows fall in distinct banks), and the gradient rows leave with coalesced
+// stores.  Per class one expf, as the gradient reuses the softmax numerators.  A
+// label outside [0, C) makes that ray's loss NaN and adds no one-hot term.
 __global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float* __restrict__ depth, const float* __restrict__ sem,
                                                        const float* __restrict__ td, const int* __restrict__ lab,
                                                        long long R, int C, float ws, float wd, float* __restrict__ loss,
                                                        float* __restrict__ gd, float* __restrict__ gs) {
-    __shared__ float red[LOSS_THREADS / 32];
+    extern __shared__ float lrows[];  // [LOSS_WARPS][32][C | 1]
+    __shared__ float red[LOSS_WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int sp = C | 1;
+    float* buf = lrows + (size_t)wid * 32 * sp;
+    const int row0 = lane / C, col0 = lane % C, drow = 32 / C, dcol = 32 % C;  // C <= 32
     float part = 0.f;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (long long)gridDim.x * blockDim.x) {
-        const float* s = sem + r * C;
-        float mx = s[0];
-        for (int c = 1; c < C; ++c) mx = fmaxf(mx, s[c]);
-        float z = 0.f;
-        for (int c = 0; c < C; ++c) z += expf(s[c] - mx);
-        const int y = lab[r];
-        const float ce = mx + logf(z) - s[y];
-        const float iz = 1.f / z;
-        for (int c = 0; c < C; ++c) gs[r * C + c] = ws * (expf(s[c] - mx) * iz - (c == y ? 1.f : 0.f));
-        const float diff = depth[r] - td[r];
-        gd[r] = wd * 2.f * diff;
-        part += ws * ce + wd * diff * diff;
+    const long long nchunk = (R + 31) / 32;
+    for (long long ch = (long long)blockIdx.x * LOSS_WARPS + wid; ch < nchunk; ch += (long long)gridDim.x * LOSS_WARPS) {
+        const long long r0 = ch * 32;
+        const int n = (int)min(32LL, R - r0) * C;
+        const float* src = sem + r0 * C;
+        int row = row0, col = col0;
+        for (int i = lane; i < n; i += 32) {
+            buf[row * sp + col] = __ldg(src + i);
+            row += drow;
+            col += dcol;
+            if (col >= C) {
+                col -= C;
+                ++row;
+            }
+        }
+        __syncwarp();
+        const long long r = r0 + lane;
+        if (r < R) {
+            float* sr = buf + lane * sp;
+            float mx = sr[0];
+            for (int c = 1; c < C; ++c) mx = fmaxf(mx, sr[c]);
+            const int y = lab[r];
+            const bool yok = y >= 0 && y < C;
+            const float sy = yok ? sr[y] : __int_as_float(0x7fc00000);
+            float z = 0.f;
+            for (int c = 0; c < C; ++c) {
+                const float e = expf(sr[c] - mx);
+                sr[c] = e;
+                z += e;
+            }
+            const float ce = mx + logf(z) - sy;
+            const float iz = 1.f / z;
+            for (int c = 0; c < C; ++c) sr[c] = ws * (sr[c] * iz - (c == y ? 1.f : 0.f));
+            const float diff = depth[r] - td[r];
+            gd[r] = wd * 2.f * diff;
+            part += ws * ce + wd * diff * diff;
+        }
+        __syncwarp();
+        float* dst = gs + r0 * C;
+        row = row0;
+        col = col0;
+        for (int i = lane; i < n; i += 32) {
+            dst[i] = buf[row * sp + col];
+            row += drow;
+            col += dcol;
+            if (col >= C) {
+                col -= C;
+                ++row;
+            }
+        }
+        __syncwarp();
     }
     part = warp_sum(part);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    if (lane == 0) red[wid] = part;
     __syncthreads();
     if (threadIdx.x < 32) {
-        float v = threadIdx.x < (LOSS_THREADS / 32) ? red[threadIdx.x] : 0.f;
+        float v = threadIdx.x < LOSS_WARPS ? red[threadIdx.x] : 0.f;
         v = warp_sum(v);
         if (threadIdx.x == 0) atomicAdd(loss, v);
     }
@@ -426,10 +479,15 @@ sq_status_t sq_loss_ce_mse(const float* depth, const float* sem, const float* ta
     if (e != cudaSuccess) return cuda_status(e, "memset loss");
     if (n_rays == 0) return SQ_OK;
     const float ws = lambda_s / (float)n_rays, wd = lambda_d / (float)n_rays;
-    long long want = (n_rays + LOSS_THREADS - 1) / LOSS_THREADS;
-    int blocks = (int)(want < 152LL * 16 ? want : 152LL * 16);
-    SQ_LAUNCH("k_loss", st, k_loss<<<blocks, LOSS_THREADS, 0, st>>>(depth, sem, target_depth, target_label, n_rays, n_classes, ws, wd, loss,
-                                            grad_depth, grad_sem));
+    if (n_classes > SQ_MAX_CLASSES) {
+        set_last_error("sq_loss_ce_mse: %d classes, at most %d", n_classes, SQ_MAX_CLASSES);
+        return SQ_ERR_INVALID_ARG;
+    }
+    const long long chunks = (n_rays + 31) / 32, want = (chunks + LOSS_WARPS - 1) / LOSS_WARPS;
+    const int blocks = (int)(want < (long long)device_sm_count() * 8 ? want : (long long)device_sm_count() * 8);
+    const size_t smem = (size_t)LOSS_WARPS * 32 * (n_classes | 1) * sizeof(float);
+    SQ_LAUNCH("k_loss", st, k_loss<<<blocks, LOSS_THREADS, smem, st>>>(depth, sem, target_depth, target_label, n_rays,
+                                                                      n_classes, ws, wd, loss, grad_depth, grad_sem));
     return SQ_OK;
 }
 

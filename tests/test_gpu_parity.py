@@ -631,9 +631,11 @@ def test_kernel_timing_records_every_launch(sqr):
 
 
 # ----------------------------------------------------------------------- loss
-def test_loss_kernel_matches_torch(sqr):
-    rng = np.random.default_rng(0)
-    R, C = 1000, 18
+@pytest.mark.parametrize("R,C", [(1000, 18), (77, 5), (4097, 32), (64, 1)])
+def test_loss_kernel_matches_torch(sqr, R, C):
+    """Ray counts that leave a partial 32-ray chunk, odd and even class counts up to
+    the maximum, a single class."""
+    rng = np.random.default_rng(R + C)
     d = torch.from_numpy(rng.uniform(0, 40, R).astype(np.float32)).cuda()
     s = torch.from_numpy(rng.standard_normal((R, C)).astype(np.float32)).cuda()
     td = torch.from_numpy(rng.uniform(0.5, 45, R).astype(np.float32)).cuda()
@@ -645,6 +647,29 @@ def test_loss_kernel_matches_torch(sqr):
     assert abs(loss.item() - ref.item()) < 1e-4 * abs(ref.item())
     torch.testing.assert_close(gd.cpu().double(), dc.grad, rtol=1e-5, atol=1e-9)
     torch.testing.assert_close(gs.cpu().double(), sc.grad, rtol=1e-4, atol=1e-9)
+
+
+def test_loss_label_outside_classes_gives_nan(sqr):
+    """A label outside [0, C) makes the loss NaN; the other rays' gradient rows are
+    those of a valid batch, and that ray's row is its softmax without a one-hot term."""
+    rng = np.random.default_rng(5)
+    R, C = 100, 18
+    d = torch.from_numpy(rng.uniform(0, 40, R).astype(np.float32)).cuda()
+    s = torch.from_numpy(rng.standard_normal((R, C)).astype(np.float32)).cuda()
+    td = torch.from_numpy(rng.uniform(0.5, 45, R).astype(np.float32)).cuda()
+    good = rng.integers(0, C, R).astype(np.int32)
+    bad = good.copy()
+    bad[37] = C + 3
+    loss_b, _, gs_b = sqr.loss_ce_mse(d, s, td, torch.from_numpy(bad).cuda())
+    _, _, gs_g = sqr.loss_ce_mse(d, s, td, torch.from_numpy(good).cuda())
+    assert np.isnan(loss_b.item())
+    keep = np.arange(R) != 37
+    assert torch.equal(gs_b[keep], gs_g[keep])
+    row = gs_g[37].clone()
+    row[int(good[37])] += 2.0 / R  # lambda_s / R times the one-hot term
+    torch.testing.assert_close(gs_b[37], row, rtol=1e-6, atol=1e-8)
+    with pytest.raises(sqr.SqrError):
+        sqr.loss_ce_mse(d, torch.zeros((R, 33), device="cuda"), td, torch.from_numpy(good).cuda())
 
 
 def test_voxel_loss_kernel_matches_oracle(sqr):
