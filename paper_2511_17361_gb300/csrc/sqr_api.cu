@@ -154,12 +154,43 @@ constexpr int LOSS_THREADS = 256;
 
 constexpr int LOSS_WARPS = LOSS_THREADS / 32;
 
+// The n = rows * C floats of `rows` consecutive rows of a row-major [*, C] array
+// (C <= 32) to and from a warp's shared-memory block of 32 rows of stride sp, with
+// coalesced global accesses: lane l takes flat indices i = l + 32 k, row i / C,
+// column i % C, stepped as a mixed-radix sum (no division in the loop).
+__device__ __forceinline__ void rows_in(float* buf, const float* __restrict__ src, int n, int C, int sp, int lane) {
+    int row = lane / C, col = lane % C;
+    const int drow = 32 / C, dcol = 32 % C;
+    for (int i = lane; i < n; i += 32) {
+        buf[row * sp + col] = __ldg(src + i);
+        row += drow;
+        col += dcol;
+        if (col >= C) {
+            col -= C;
+            ++row;
+        }
+    }
+}
+
+__device__ __forceinline__ void rows_out(float* __restrict__ dst, const float* buf, int n, int C, int sp, int lane) {
+    int row = lane / C, col = lane % C;
+    const int drow = 32 / C, dcol = 32 % C;
+    for (int i = lane; i < n; i += 32) {
+        dst[i] = buf[row * sp + col];
+        row += drow;
+        col += dcol;
+        if (col >= C) {
+            col -= C;
+            ++row;
+        }
+    }
+}
+
 // A warp takes 32 consecutive rays at a time: their semantic rows are read into
-// shared memory with coalesced loads (flat index i = lane + 32 k of the chunk, row
-// i / C, column i % C, stepped without division), each lane computes its ray's
+// shared memory with coalesced loads (rows_in), each lane computes its ray's
 // softmax cross-entropy and gradient row there (row stride C | 1 words, so the
 // lanes' rows fall in distinct banks), and the gradient rows leave with coalesced
-// stores.  Per class one expf, as the gradient reuses the softmax numerators.  A
+// stores (rows_out).  Per class one expf, as the gradient reuses the softmax numerators.  A
 // label outside [0, C) makes that ray's loss NaN and adds no one-hot term.
 __global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float* __restrict__ depth, const float* __restrict__ sem,
                                                        const float* __restrict__ td, const int* __restrict__ lab,
@@ -170,23 +201,12 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float* __restrict__
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int sp = C | 1;
     float* buf = lrows + (size_t)wid * 32 * sp;
-    const int row0 = lane / C, col0 = lane % C, drow = 32 / C, dcol = 32 % C;  // C <= 32
     float part = 0.f;
     const long long nchunk = (R + 31) / 32;
     for (long long ch = (long long)blockIdx.x * LOSS_WARPS + wid; ch < nchunk; ch += (long long)gridDim.x * LOSS_WARPS) {
         const long long r0 = ch * 32;
         const int n = (int)min(32LL, R - r0) * C;
-        const float* src = sem + r0 * C;
-        int row = row0, col = col0;
-        for (int i = lane; i < n; i += 32) {
-            buf[row * sp + col] = __ldg(src + i);
-            row += drow;
-            col += dcol;
-            if (col >= C) {
-                col -= C;
-                ++row;
-            }
-        }
+        rows_in(buf, sem + r0 * C, n, C, sp, lane);
         __syncwarp();
         const long long r = r0 + lane;
         if (r < R) {
@@ -210,18 +230,7 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float* __restrict__
             part += ws * ce + wd * diff * diff;
         }
         __syncwarp();
-        float* dst = gs + r0 * C;
-        row = row0;
-        col = col0;
-        for (int i = lane; i < n; i += 32) {
-            dst[i] = buf[row * sp + col];
-            row += drow;
-            col += dcol;
-            if (col >= C) {
-                col -= C;
-                ++row;
-            }
-        }
+        rows_out(gs + r0 * C, buf, n, C, sp, lane);
         __syncwarp();
     }
     part = warp_sum(part);
@@ -254,52 +263,72 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_vloss_count(const int* __restr
     }
 }
 
+// Rows of 32 voxels at a time through shared memory, as k_loss does.
 __global__ void __launch_bounds__(LOSS_THREADS) k_vloss(const float* __restrict__ dens, const float* __restrict__ sem,
                                                         const int* __restrict__ lab, long long V, int C, float ls,
                                                         float lo, const int* __restrict__ counts,
                                                         float* __restrict__ loss, float* __restrict__ gd,
                                                         float* __restrict__ gs) {
-    __shared__ float red[2][LOSS_THREADS / 32];
+    extern __shared__ float lrows[];  // [LOSS_WARPS][32][C | 1]
+    __shared__ float red[2][LOSS_WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int sp = C | 1;
+    float* buf = lrows + (size_t)wid * 32 * sp;
     const int no = counts[0], nl = counts[1];
     const float ws = no > 0 ? ls / (float)no : 0.f, wo = nl > 0 ? lo / (float)nl : 0.f;
     float pce = 0.f, pbce = 0.f;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-        const int y = lab[v];
-        const float* s = sem + v * C;
-        float* g = gs + v * C;
-        if (y >= 0 && y < C) {  // cross-entropy of the class probabilities
-            float mx = s[0];
-            for (int c = 1; c < C; ++c) mx = fmaxf(mx, s[c]);
-            float z = 0.f;
-            for (int c = 0; c < C; ++c) z += expf(s[c] - mx);
-            pce += mx + logf(z) - s[y];
-            const float iz = 1.f / z;
-            for (int c = 0; c < C; ++c) g[c] = ws * (expf(s[c] - mx) * iz - (c == y ? 1.f : 0.f));
-        } else {
-            for (int c = 0; c < C; ++c) g[c] = 0.f;
+    const long long nchunk = (V + 31) / 32;
+    for (long long ch = (long long)blockIdx.x * LOSS_WARPS + wid; ch < nchunk; ch += (long long)gridDim.x * LOSS_WARPS) {
+        const long long v0 = ch * 32;
+        const int n = (int)min(32LL, V - v0) * C;
+        rows_in(buf, sem + v0 * C, n, C, sp, lane);
+        __syncwarp();
+        const long long v = v0 + lane;
+        if (v < V) {
+            const int y = lab[v];
+            float* sr = buf + lane * sp;
+            if (y >= 0 && y < C) {  // cross-entropy of the class probabilities
+                float mx = sr[0];
+                for (int c = 1; c < C; ++c) mx = fmaxf(mx, sr[c]);
+                const float sy = sr[y];
+                float z = 0.f;
+                for (int c = 0; c < C; ++c) {
+                    const float e = expf(sr[c] - mx);
+                    sr[c] = e;
+                    z += e;
+                }
+                pce += mx + logf(z) - sy;
+                const float iz = 1.f / z;
+                for (int c = 0; c < C; ++c) sr[c] = ws * (sr[c] * iz - (c == y ? 1.f : 0.f));
+            } else {
+                for (int c = 0; c < C; ++c) sr[c] = 0.f;
+            }
+            const float d = fmaxf(dens[v], 0.f);
+            float gdv = 0.f;
+            if (y == C) {  // free: -log(1 - p) = d
+                pbce += d;
+                gdv = dens[v] > 0.f ? wo : 0.f;
+            } else if (y >= 0 && y < C) {  // occupied: -log p
+                const float dc = fmaxf(d, 1e-6f);
+                pbce += -logf(-expm1f(-dc));
+                gdv = d > 1e-6f ? -wo / expm1f(dc) : 0.f;
+            }
+            gd[v] = gdv;
         }
-        const float d = fmaxf(dens[v], 0.f);
-        float gdv = 0.f;
-        if (y == C) {  // free: -log(1 - p) = d
-            pbce += d;
-            gdv = dens[v] > 0.f ? wo : 0.f;
-        } else if (y >= 0 && y < C) {  // occupied: -log p
-            const float dc = fmaxf(d, 1e-6f);
-            pbce += -logf(-expm1f(-dc));
-            gdv = d > 1e-6f ? -wo / expm1f(dc) : 0.f;
-        }
-        gd[v] = gdv;
+        __syncwarp();
+        rows_out(gs + v0 * C, buf, n, C, sp, lane);
+        __syncwarp();
     }
     pce = warp_sum(pce);
     pbce = warp_sum(pbce);
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = pce;
-        red[1][threadIdx.x >> 5] = pbce;
+    if (lane == 0) {
+        red[0][wid] = pce;
+        red[1][wid] = pbce;
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        float a = threadIdx.x < (LOSS_THREADS / 32) ? red[0][threadIdx.x] : 0.f;
-        float b = threadIdx.x < (LOSS_THREADS / 32) ? red[1][threadIdx.x] : 0.f;
+        float a = threadIdx.x < LOSS_WARPS ? red[0][threadIdx.x] : 0.f;
+        float b = threadIdx.x < LOSS_WARPS ? red[1][threadIdx.x] : 0.f;
         a = warp_sum(a) * ws;
         b = warp_sum(b) * wo;
         if (threadIdx.x == 0) {
@@ -505,11 +534,19 @@ sq_status_t sq_loss_voxel(const float* density, const float* sem, const int* lab
     e = cudaMemsetAsync(counts, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "memset counts");
     if (n_voxels == 0) return SQ_OK;
+    if (n_classes > SQ_MAX_CLASSES) {
+        set_last_error("sq_loss_voxel: %d classes, at most %d", n_classes, SQ_MAX_CLASSES);
+        return SQ_ERR_INVALID_ARG;
+    }
     const long long want = (n_voxels + LOSS_THREADS - 1) / LOSS_THREADS;
     const int blocks = (int)(want < 152LL * 16 ? want : 152LL * 16);
     SQ_LAUNCH("k_vloss_count", st, k_vloss_count<<<blocks, LOSS_THREADS, 0, st>>>(label, n_voxels, n_classes, counts));
-    SQ_LAUNCH("k_vloss", st, k_vloss<<<blocks, LOSS_THREADS, 0, st>>>(density, sem, label, n_voxels, n_classes, lambda_s,
-                                                                     lambda_o, counts, loss, grad_density, grad_sem));
+    const long long chunks = (n_voxels + 31) / 32, vwant = (chunks + LOSS_WARPS - 1) / LOSS_WARPS;
+    const int vblocks = (int)(vwant < (long long)device_sm_count() * 8 ? vwant : (long long)device_sm_count() * 8);
+    const size_t smem = (size_t)LOSS_WARPS * 32 * (n_classes | 1) * sizeof(float);
+    SQ_LAUNCH("k_vloss", st, k_vloss<<<vblocks, LOSS_THREADS, smem, st>>>(density, sem, label, n_voxels, n_classes,
+                                                                        lambda_s, lambda_o, counts, loss,
+                                                                        grad_density, grad_sem));
     return SQ_OK;
 }
 

@@ -672,12 +672,13 @@ def test_loss_label_outside_classes_gives_nan(sqr):
         sqr.loss_ce_mse(d, torch.zeros((R, 33), device="cuda"), td, torch.from_numpy(good).cuda())
 
 
-def test_voxel_loss_kernel_matches_oracle(sqr):
+@pytest.mark.parametrize("V,C", [(20000, 18), (1001, 7), (77, 32)])
+def test_voxel_loss_kernel_matches_oracle(sqr, V, C):
     """sq_loss_voxel (CE on semantic voxels, BCE on 1 - exp(-density)) against the
     FP64 oracle: counts exact, loss terms 1e-5 relative, gradients 1e-5 of each
-    tensor's largest entry (FP32 exp/log/expm1 of single terms)."""
-    rng = np.random.default_rng(7)
-    V, C = 20000, 18
+    tensor's largest entry (FP32 exp/log/expm1 of single terms); voxel counts with a
+    partial 32-voxel chunk, odd and maximal class counts."""
+    rng = np.random.default_rng(7 + V + C)
     dens = rng.uniform(-0.2, 4.0, V).astype(np.float32)
     dens[::17] = 0.0
     sem = (rng.standard_normal((V, C)) * 3).astype(np.float32)
