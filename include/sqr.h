@@ -382,7 +382,8 @@ sq_status_t sq_loss_ce_mse(const float* depth, const float* sem, const float* ta
  * below the clamp).  Negative densities count as 0.  A mean over an empty set is
  * 0.  Writes loss[0..2] = (L, semantic term, occupancy term), counts[0..1] =
  * (occupied, labelled) voxels, grad_density [V], grad_sem [V, C] (all device,
- * overwritten; counts also serves the normalisation). */
+ * overwritten; counts also serves the normalisation).  n_classes in
+ * [1, SQ_MAX_CLASSES], else SQ_ERR_INVALID_ARG. */
 sq_status_t sq_loss_voxel(const float* density, const float* sem, const int* label, long long n_voxels,
                           int n_classes, float lambda_s, float lambda_o, float* loss, int* counts,
                           float* grad_density, float* grad_sem, void* stream);
