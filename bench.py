@@ -387,8 +387,8 @@ def run_mine(args):
     assert save_status == sqr.SQ_OK and pages_after == pages_needed, "saved-state pages changed between steps"
 
     # ---- roofline of the pair kernels (SFU-bound: MUFU ops per pair) against the
-    # measured SFU rate; frac_survey is the survey's count (every in-grid sample's
-    # pairs Q, 9 MUFU each) against the nominal 16 MUFU/clk/SM at the top clock
+    # measured SFU rate; frac_survey is the coarser count of every in-grid sample's
+    # pairs Q, 9 MUFU each, against the nominal 16 MUFU/clk/SM at the top clock
     mean_phase = phase.mean(0)
     names = ["index", "fwd", "loss", "bwd"]
     props = torch.cuda.get_device_properties(dev)
